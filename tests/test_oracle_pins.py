@@ -1,0 +1,416 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (``oracle/``) against something other than
+itself: closed forms derived by hand, exact polynomial reproduction of a
+consistent Galerkin method, invariants of the RT_k x Q_k pair, brute-force
+dense constructions, and library solvers.  References are to Kanschat,
+Lazarov & Mao, arXiv:1602.04858.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import basis, fem, krylov
+from oracle import multigrid as mg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def bordered_solve(S, A, b):
+    """Direct solve of A x = b on the free dofs with zero pressure mean (dense)."""
+    cm = S.constrained()
+    fr = ~cm
+    w = S.pressure_weights()
+    Af = A[fr][:, fr].toarray()
+    n = Af.shape[0]
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = Af
+    M[:n, n] = w[fr]
+    M[n, :n] = w[fr]
+    y = np.linalg.solve(M, np.concatenate([b[fr], [0.0]]))
+    x = b.copy()
+    x[fr] = y[:n]
+    return x
+
+
+# --- 1-D basis ------------------------------------------------------------
+
+def test_nodes_closed_forms():
+    assert np.allclose(basis.gauss_lobatto(2), [0, 1], atol=0, rtol=0)
+    assert np.allclose(basis.gauss_lobatto(3), [0, 0.5, 1], atol=1e-15)
+    s5 = 1 / np.sqrt(5)
+    assert np.allclose(basis.gauss_lobatto(4), [0, (1 - s5) / 2, (1 + s5) / 2, 1], atol=1e-15)
+    t, w = basis.gauss(2)
+    assert np.allclose(t, [0.5 - 0.5 / np.sqrt(3), 0.5 + 0.5 / np.sqrt(3)], atol=1e-15)
+    assert np.allclose(w, [0.5, 0.5], atol=1e-15)
+
+
+@pytest.mark.parametrize("nodes", [basis.gauss_lobatto(3), basis.gauss(2)[0], basis.gauss_lobatto(4)])
+def test_lagrange_partition_of_unity(nodes):
+    x = np.linspace(-0.3, 1.3, 17)
+    assert np.allclose(sum(basis.lagrange(nodes, a, x) for a in range(len(nodes))), 1.0, atol=1e-13)
+    assert np.allclose(sum(basis.lagrange_deriv(nodes, a, x) for a in range(len(nodes))), 0.0, atol=1e-12)
+    # derivative against central differences of the value
+    e = 1e-6
+    for a in range(len(nodes)):
+        fd = (basis.lagrange(nodes, a, x + e) - basis.lagrange(nodes, a, x - e)) / (2 * e)
+        assert np.allclose(basis.lagrange_deriv(nodes, a, x), fd, atol=1e-7)
+
+
+# --- operator: closed forms, exactness, symmetry ---------------------------
+
+def _golden_energy_vectors(S, name):
+    x = np.zeros(S.ndof)
+    g = basis.dg_nodes(1)
+    if name == "rt0_interior_face_hat":
+        x[S.index_u(0, np.array([2, 1]))] = 1.0
+    elif name == "rt1_interior_cell_bubble_times_eta":
+        for b in range(2):
+            x[S.index_u(0, np.array([3, 2 + b]))] = g[b]
+    elif name == "rt1_boundary_cell_bubble_times_one_minus_eta":
+        for b in range(2):
+            x[S.index_u(0, np.array([3, b]))] = 1.0 - g[b]
+    return x
+
+
+@pytest.mark.parametrize("mu,c0", [(1.0, 0.0), (0.0, 1.0), (0.37, 2.5)])
+def test_energy_closed_forms(mu, c0):
+    """a_h(u,u) for hand-derived cases pins sigma, the factor 2 and the signs of eq. (ipbrinkman)."""
+    data = json.load(open(os.path.join(GOLDEN, "closed_forms.json")))
+    n = 4
+    h = 1.0 / n
+    for case in data["cases"]:
+        S = fem.Space(2, n, case["degree"])
+        A = fem.operator(S, mu, np.full((n, n), c0))
+        x = _golden_energy_vectors(S, case["name"])
+        expect = case["mu_coef"] * mu + case["c_h2_coef"] * c0 * h * h
+        assert abs(x @ (A @ x) - expect) <= 1e-13 * max(1.0, abs(expect)), case["name"]
+
+
+def _manufactured(d, k, mu):
+    if d == 2 and k == 0:
+        u = lambda X: np.stack([X[:, 0], -X[:, 1]], 1)
+        p = lambda X: 0.0 * X[:, 0]
+        f = lambda X, c: c * u(X)
+    elif d == 2 and k == 1:
+        u = lambda X: np.stack([2 * X[:, 0] ** 2 * X[:, 1], -2 * X[:, 0] * X[:, 1] ** 2], 1)
+        p = lambda X: X[:, 0] * X[:, 1] - 0.25
+        f = lambda X, c: np.stack([-4 * mu * X[:, 1] + 2 * c * X[:, 0] ** 2 * X[:, 1] + X[:, 1],
+                                   4 * mu * X[:, 0] - 2 * c * X[:, 0] * X[:, 1] ** 2 + X[:, 0]], 1)
+    else:
+        u = lambda X: np.stack([X[:, 0], X[:, 1], -2 * X[:, 2]], 1)
+        p = lambda X: 0.0 * X[:, 0]
+        f = lambda X, c: c * u(X)
+    return u, p, f
+
+
+@pytest.mark.parametrize("d,k,n", [(2, 0, 4), (2, 1, 4), (3, 0, 2)])
+@pytest.mark.parametrize("mu", [0.0, 0.01, 1.0])
+def test_polynomial_reproduction(d, k, n, mu):
+    """A consistent method reproduces a solution lying in RT_k x Q_k exactly (eq. Brinkman-weak, BCh)."""
+    rng = np.random.default_rng(11)
+    S = fem.Space(d, n, k)
+    c = np.exp(rng.standard_normal((n,) * d))
+    A = fem.operator(S, mu, c)
+    u, p, f = _manufactured(d, k, mu)
+    b = fem.load_vector(S, mu, c, f=f, g=u)
+    x = bordered_solve(S, A, b)
+    xe = fem.interpolate(S, u, p)
+    assert np.max(np.abs(x - xe)) <= 1e-11 * max(1.0, np.max(np.abs(xe)))
+
+
+@pytest.mark.parametrize("d,k,n", [(2, 0, 5), (2, 1, 4), (3, 0, 3)])
+def test_symmetry_and_velocity_spd(d, k, n):
+    rng = np.random.default_rng(2)
+    S = fem.Space(d, n, k)
+    c = np.exp(2 * rng.standard_normal((n,) * d))
+    A = fem.operator(S, 0.3, c)
+    assert abs(A - A.T).max() <= 1e-14 * abs(A).max()
+    fr = ~S.constrained()
+    vel = np.arange(S.ndof) < S.n_u
+    Auu = A[fr & vel][:, fr & vel].toarray()
+    assert np.linalg.eigvalsh(Auu).min() > 0.0
+
+
+def test_pressure_constant_is_the_kernel():
+    S = fem.Space(2, 4, 1)
+    A = fem.operator(S, 0.1, np.ones((4, 4)))
+    one_p = np.zeros(S.ndof)
+    one_p[S.n_u:] = 1.0
+    assert np.max(np.abs(A @ one_p)) < 1e-13
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_literal_channel_rhs_closed_form(k):
+    """f = (1,0) = grad x, g = 0, no-slip: u_h = 0 and p_h = Pi_Q x - 1/2 for any c and mu."""
+    from paper_1602_04858_gb300 import inputs
+    n = 8
+    S = fem.Space(2, n, k)
+    c = inputs.channel_c(n, 3, 7)
+    mu = 0.01
+    A = fem.operator(S, mu, c)
+    b = fem.load_vector(S, mu, c, f=lambda X, cc: np.stack([np.ones(len(X)), np.zeros(len(X))], 1))
+    x = bordered_solve(S, A, b)
+    X, kind = S.node_coords()
+    assert np.max(np.abs(x[:S.n_u])) < 1e-9
+    assert np.max(np.abs(x[S.n_u:] - (X[S.n_u:, 0] - 0.5))) < 1e-9
+
+
+@pytest.mark.parametrize("d,k,n", [(2, 0, 4), (2, 1, 3), (3, 0, 2)])
+def test_divergence_is_exact_pointwise(d, k, n):
+    """div V_h = Q_h: with a source g_h in Q_h, div u_h = g_h at every point (Sec. 2.3)."""
+    rng = np.random.default_rng(5)
+    S = fem.Space(d, n, k)
+    c = np.exp(rng.standard_normal((n,) * d))
+    A = fem.operator(S, 0.2, c)
+    w = S.pressure_weights()
+    gq = rng.standard_normal(S.n_p)
+    gq -= np.dot(w[S.n_u:], gq) / np.sum(w[S.n_u:])
+    b = np.zeros(S.ndof)
+    b[S.n_u:] = -w[S.n_u:] * gq            # -(q_i, g_h) with the diagonal Gauss mass
+    x = bordered_solve(S, A, b)
+    pts = rng.uniform(0.0, 1.0, size=(40, d))
+    _, _, div = fem.evaluate(S, x, pts)
+    gvec = np.zeros(S.ndof)
+    gvec[S.n_u:] = gq
+    _, gval, _ = fem.evaluate(S, gvec, pts)
+    assert np.max(np.abs(div - gval)) < 1e-10 * max(1.0, np.max(np.abs(gval)))
+
+
+# --- transfers ----------------------------------------------------------------
+
+@pytest.mark.parametrize("d,k,nc", [(2, 0, 2), (2, 1, 2), (3, 0, 2)])
+def test_prolongation_reproduces_coarse_functions(d, k, nc):
+    rng = np.random.default_rng(8)
+    Sc, Sf = fem.Space(d, nc, k), fem.Space(d, 2 * nc, k)
+    P = mg.prolongation(Sc, Sf)
+    xc = rng.standard_normal(Sc.ndof)
+    xc[Sc.constrained()] = rng.standard_normal(np.count_nonzero(Sc.constrained()))
+    xf = P @ xc
+    pts = rng.uniform(0.0, 1.0, size=(30, d))
+    uc, pc, dc = fem.evaluate(Sc, xc, pts)
+    uf, pf, df = fem.evaluate(Sf, xf, pts)
+    assert np.max(np.abs(uc - uf)) < 1e-12
+    assert np.max(np.abs(pc - pf)) < 1e-12
+    assert np.max(np.abs(dc - df)) < 1e-10      # div(P u) = P_p div u (cochain property)
+
+
+@pytest.mark.parametrize("d,k,nc", [(2, 0, 2), (2, 1, 2), (3, 0, 2)])
+@pytest.mark.parametrize("mu", [0.0, 0.05])
+def test_galerkin_identity(d, k, nc, mu):
+    """P^T A_j P is the level-(j-1) form with the fine penalty (k+1)(k+2)/h_j on the coarse faces.
+
+    Coarse functions have no jumps across fine faces inside a coarse cell and
+    the same gradients, so only the penalty coefficient differs; with c
+    constant on every coarse cell the mass terms agree exactly.
+    """
+    rng = np.random.default_rng(9)
+    Sc, Sf = fem.Space(d, nc, k), fem.Space(d, 2 * nc, k)
+    cc = np.exp(rng.standard_normal((nc,) * d))
+    cf = cc
+    for ax in range(d):
+        cf = np.repeat(cf, 2, axis=ax)
+    P = mg.prolongation(Sc, Sf)
+    Af = fem.assemble_full(Sf, mu, cf)
+    Ac = fem.assemble_full(Sc, mu, cc, sigma=fem.penalty(k, Sf.h))
+    G = (P.T @ Af @ P).toarray()
+    assert np.max(np.abs(G - Ac.toarray())) < 1e-12 * max(1.0, np.max(np.abs(G)))
+
+
+def test_coarsen_is_arithmetic_mean_of_permeability():
+    c = np.array([[1.0, 1.0], [1.0, 1e6]])
+    assert np.isclose(mg.coarsen_c(c, 2)[0, 0], 4.0 / (3.0 + 1e-6), rtol=1e-15)
+    assert np.isclose(mg.coarsen_c(c, 2, "arithmetic")[0, 0], (3 + 1e6) / 4, rtol=1e-15)
+
+
+# --- smoother and V-cycle ---------------------------------------------------------
+
+def _hier(d, k, n0, L, mu, seed=3, sigma_c=1.0):
+    rng = np.random.default_rng(seed)
+    nf = n0 * 2 ** (L - 1)
+    c = np.exp(sigma_c * rng.standard_normal((nf,) * d))
+    return mg.Hierarchy(d, n0, L, k, mu, c)
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_patch_count_and_colours(d, k):
+    S = fem.Space(d, 6, k)
+    cols = mg.patches(S)
+    total = sum(v.shape[0] for v, _ in cols)
+    assert total == 5 ** d
+    nv = {2: {0: 8, 1: 40}, 3: {0: 20}}[d][k]
+    for v, dofs in cols:
+        if dofs.shape[0]:
+            assert dofs.shape[1] == nv
+    # patches of one colour have disjoint dof sets and do not couple through A
+    A = fem.operator(S, 0.5, np.ones((6,) * d))
+    for v, dofs in cols:
+        for p in range(dofs.shape[0]):
+            for q in range(p + 1, dofs.shape[0]):
+                assert not set(dofs[p]) & set(dofs[q])
+                assert abs(A[dofs[p]][:, dofs[q]]).max() == 0.0
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_one_step_on_single_patch_mesh_is_exact(d, k):
+    """On a 2^d mesh the single vertex patch holds every free dof: one step solves A x = b."""
+    rng = np.random.default_rng(4)
+    S = fem.Space(d, 2, k)
+    L = mg.Level(S, 0.7, np.exp(rng.standard_normal((2,) * d)))
+    b = rng.standard_normal(S.ndof)
+    b[L.cm] = 0.0
+    b[S.n_u:] -= b[S.n_u:].mean()
+    x = mg.smooth_step(L, np.zeros(S.ndof), b)
+    r = b - L.A @ x
+    assert np.max(np.abs(r[L.free])) < 1e-10 * np.max(np.abs(b))
+
+
+def test_patch_projection_idempotent():
+    H = _hier(2, 1, 2, 3, 0.1)
+    L = H.levels[-1]
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(L.S.ndof)
+    x = rng.standard_normal(L.S.ndof)
+    dofs, Sv, _ = L.colours[4]
+    p = 1
+    x1 = x.copy()
+    x1[dofs[p]] += Sv[p] @ (b - L.A @ x1)[dofs[p]]
+    x2 = x1.copy()
+    x2[dofs[p]] += Sv[p] @ (b - L.A @ x2)[dofs[p]]
+    assert np.max(np.abs(x2 - x1)) < 1e-12 * np.max(np.abs(x1))
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_colour_pass_equals_patch_by_patch(d, k):
+    H = _hier(d, k, 2, 3 if d == 2 else 2, 0.2)
+    L = H.levels[-1]
+    rng = np.random.default_rng(7)
+    b = rng.standard_normal(L.S.ndof)
+    x0 = rng.standard_normal(L.S.ndof)
+    x1 = mg.smooth_step(L, x0, b)
+    x2 = mg.smooth_step_sequential(L, x0, b)
+    assert np.max(np.abs(x1 - x2)) < 1e-12 * np.max(np.abs(x1))
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 0, 3), (2, 1, 3), (3, 0, 2)])
+@pytest.mark.parametrize("variable", [False, True])
+def test_vcycle_is_symmetric(d, k, L, variable):
+    H = _hier(d, k, 2, L, 0.05)
+    LJ = H.levels[-1]
+    N = LJ.S.ndof
+    B = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        B[:, i] = mg.vcycle(H, e, 1, variable)
+    fr = LJ.free
+    Bf = B[np.ix_(fr, fr)]
+    assert np.max(np.abs(Bf - Bf.T)) < 1e-12 * np.max(np.abs(Bf))
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1)])
+def test_two_grid_against_dense_ritz_construction(d, k):
+    """V-cycle on 4x4 (levels 2x2 -> 4x4) against a dense brute-force two-grid.
+
+    The brute force uses the Ritz projections of Sec. 3.3 written with an
+    explicit basis Z of the patch space (velocity dofs and mean-zero patch
+    pressures, Z = null(w_v^T)) instead of the bordered inverse, one patch at a
+    time in the colour order, and the coarse solve through an explicit basis
+    of the mean-zero coarse space.
+    """
+    from scipy.linalg import null_space
+    rng = np.random.default_rng(12)
+    H = _hier(d, k, 2, 2, 0.3, seed=12, sigma_c=1.5)
+    LJ, L0 = H.levels[1], H.levels[0]
+    A = LJ.A.toarray()
+    b = rng.standard_normal(LJ.S.ndof)
+    b[LJ.cm] = 0.0
+    C = len(LJ.colours)
+    order = list(range(C)) + list(range(C - 2, -1, -1))
+    plist = []
+    for col in order:
+        entry = LJ.colours[col]
+        if entry is None:
+            continue
+        for dofs in entry[0]:
+            wv = LJ.w[dofs]
+            Z = null_space(wv[None, :])
+            plist.append((dofs, Z))
+
+    def smooth(x):
+        for dofs, Z in plist:
+            r = (b - A @ x)[dofs]
+            Azz = Z.T @ A[np.ix_(dofs, dofs)] @ Z
+            x = x.copy()
+            x[dofs] += Z @ np.linalg.solve(Azz, Z.T @ r)
+        return x
+
+    x = smooth(np.zeros_like(b))
+    r = b - A @ x
+    r[LJ.cm] = 0.0
+    Pm = H.P[1].toarray()
+    bc = Pm.T @ r
+    bc[L0.cm] = 0.0
+    fr = L0.free
+    Z0 = null_space(L0.w[fr][None, :])
+    Ac = L0.A.toarray()[np.ix_(fr, fr)]
+    xc = np.zeros(L0.S.ndof)
+    xc[fr] = Z0 @ np.linalg.solve(Z0.T @ Ac @ Z0, Z0.T @ bc[fr])
+    x = x + Pm @ xc
+    x = smooth(x)
+    z = mg.vcycle(H, b, m_fine=1, variable=False)
+    assert np.max(np.abs(z - x)) < 1e-11 * np.max(np.abs(x))
+
+
+# --- Krylov solver and convergence -------------------------------------------
+
+def test_fgmres_matches_dense_solve():
+    rng = np.random.default_rng(1)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.3
+    b = rng.standard_normal(n)
+    M = np.diag(1.0 / np.diag(A))
+    x, its, hist = krylov.fgmres(lambda v: A @ v, lambda v: M @ v, b, tol=1e-13, maxit=200, restart=25)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+    assert hist[-1] <= 1e-13
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_solution_equals_direct_solve(k):
+    H = _hier(2, k, 2, 3, 0.01, seed=21, sigma_c=2.0)
+    LJ = H.levels[-1]
+    S = LJ.S
+    rng = np.random.default_rng(22)
+    b = rng.standard_normal(S.ndof)
+    b[LJ.cm] = 0.0
+    b[S.n_u:] -= b[S.n_u:].mean()
+    x, its, hist = krylov.fgmres(lambda v: LJ.A @ v, lambda v: mg.vcycle(H, v), b, tol=1e-12)
+    xd = bordered_solve(S, LJ.A, b)
+    w = S.pressure_weights()
+    x[S.n_u:] -= np.dot(w[S.n_u:], x[S.n_u:]) / np.sum(w[S.n_u:])
+    cond = np.linalg.cond(LJ.A[LJ.free][:, LJ.free].toarray()[:S.n_u - np.count_nonzero(LJ.cm), :S.n_u - np.count_nonzero(LJ.cm)])
+    assert np.max(np.abs(x - xd)) <= max(1e-9, cond * 1e-12) * np.max(np.abs(xd))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,mu", [(0, 0.0), (1, 0.01)])
+def test_h_independent_iterations(k, mu):
+    """Sec. 4: iteration counts do not grow under refinement (field fixed at 8x8 resolution)."""
+    rng = np.random.default_rng(3)
+    c8 = np.exp(1.5 * rng.standard_normal((8, 8)))
+    its = []
+    for L in (2, 3, 4, 5):
+        nf = 4 * 2 ** (L - 1)
+        c = np.kron(c8, np.ones((nf // 8, nf // 8)))
+        H = mg.Hierarchy(2, 4, L, k, mu, c)
+        LJ = H.levels[-1]
+        b = np.random.default_rng(5).standard_normal(LJ.S.ndof)
+        b[LJ.cm] = 0.0
+        b[LJ.S.n_u:] -= b[LJ.S.n_u:].mean()
+        _, it, _ = krylov.fgmres(lambda v: LJ.A @ v, lambda v: mg.vcycle(H, v), b, tol=1e-8)
+        its.append(it)
+    assert max(its) - min(its) <= 3, its
+    assert its[-1] <= its[0] + 2, its
