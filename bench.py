@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: DoF x V-cycles per second of the variable V-cycle (Sec. 3.2 of
+arXiv:1602.04858) on the 256x256 RT_1 channelised-permeability workload.
+
+Workload (synthetic, seeded; the paper's own fields are not available):
+2-D unit square, 256x256 cells, levels 4x4 -> 256x256 (7 levels), RT_1 x Q_1,
+Brinkman mu = 0.01, 20 random-walk channels two cells wide with c = 1
+(permeability 1) in a c = 1e6 background (contrast 1e6); variable V-cycle with
+m(J) = 2 and the symmetric multiplicative vertex-patch Schwarz smoother.
+
+One step = one V-cycle B_J r (all levels: smoothing, residual, transfers,
+coarse solve) on a seeded residual vector resident in HBM.  `value` is for
+the mixed-precision V-cycle (FP32 vectors and patch inverses), the mode the
+FP64 flexible GMRES uses as its preconditioner; the FP64 and BF16-inverse
+V-cycles and the time to a 1e-8 relative residual of each mode are reported
+beside it.  The finest-level patch inverses alone (416 MB in FP32) exceed the
+L2 cache, so every V-cycle streams them from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun), each rank runs an independent replica on its own GPU
+(the single solve has no data-parallel split) and value sums
+the ranks' DoF x V-cycles over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF·V-cycles/s and time-to-1e-8 residual (mixed/batched/learned vs FP64)"
+UNIT = "DoF·V-cycles/s"
+WORKLOAD = "channels_256"
+
+
+def workload_config():
+    return {"workload": "2-D 256x256 cells, 7 levels (4x4->256x256), RT_1 x Q_1, Brinkman mu=0.01, "
+                        "20 random-walk channels (c=1) in c=1e6 background, variable V-cycle m(J)=2, "
+                        "symmetric multiplicative vertex-patch Schwarz",
+            "levels": 7, "n_fine": 256, "degree": 1, "mu": 0.01, "cycle": "variable, m(J)=2",
+            "l2": "inputs larger than L2 (finest patch inverses 416 MB FP32 / 832 MB FP64 streamed per V-cycle)"}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def run_cpu_baseline(seconds=15.0):
+    """The FP64 oracle (plain NumPy/SciPy) on one host core: V-cycles of the same workload."""
+    from oracle import multigrid as mg
+    from paper_1602_04858_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    H = mg.Hierarchy(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"], w["c"])
+    setup_s = time.perf_counter() - t0
+    LJ = H.levels[-1]
+    r = np.random.default_rng(7).standard_normal(LJ.S.ndof)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        mg.vcycle(H, r, m_fine=2, variable=True)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": LJ.S.ndof * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 V-cycles of the full workload after a {setup_s:.0f} s oracle setup "
+                      f"(single thread: NumPy/SciPy with BLAS threads = 1)"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    from oracle import multigrid as mg
+    from paper_1602_04858_gb300 import inputs
+    w = inputs.workload(WORKLOAD)
+    H = mg.Hierarchy(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"], w["c"])
+    LJ = H.levels[-1]
+    r = np.random.default_rng(7).standard_normal(LJ.S.ndof)
+    for _ in range(args.warmup):
+        mg.vcycle(H, r)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        mg.vcycle(H, r)
+    el = time.perf_counter() - t0
+    value = LJ.S.ndof * args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step one FP64 oracle V-cycle of the full workload (single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def colour_pass_bytes(count, nv, s_inv, s_v):
+    """Algorithmic bytes of one colour pass: each patch streams its n_v x n_v
+    inverse once and reads b_v, x_v and writes x_v (3 n_v vector entries)."""
+    return count * (nv * nv * s_inv + 3 * nv * s_v)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    from paper_1602_04858_gb300 import inputs, mgdarcy
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    w = inputs.workload(WORKLOAD)
+    dev = torch.device("cuda", local)
+    cdev = torch.as_tensor(w["c"], device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def make(prec):
+        return mgdarcy.Multigrid(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"], cdev,
+                                 precision=prec, m_fine=2, variable_cycle=True, stream=stream.cuda_stream)
+
+    G = make("fp32")
+    nu, npr = G.sizes()
+    N = nu + npr
+    rng = np.random.default_rng(11 + rank)
+    rh = rng.standard_normal(N)
+    r = torch.as_tensor(rh, device=dev)
+    z = torch.zeros_like(r)
+
+    def time_vcycles(Gh, steps, warmup):
+        for _ in range(warmup):
+            Gh.vcycle(r, z)
+        barrier()
+        l0 = Gh.launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            Gh.vcycle(r, z)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1), Gh.launches() - l0
+
+    # --- timed region: the headline mixed-precision V-cycle ---------------------
+    for _ in range(args.warmup):
+        G.vcycle(r, z)
+    barrier()
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    ms, launches = time_vcycles(G, args.steps, 0)
+    clocks = sampler.stop()
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = N * args.steps * world / (ms_max / 1e3)
+
+    # --- dominant kernel: finest-level colour pass, per-launch CUDA events ------
+    J = w["n_levels"] - 1
+    G.level_load(J, torch.zeros_like(r), r)
+    evs = []
+    reps = max(2, args.steps // 4)
+    for rep in range(reps + 1):
+        for col in list(range(9)) + list(range(7, -1, -1)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.colour_pass(J, col)
+            b.record(stream)
+            if rep > 0:
+                evs.append((col, a, b))
+    torch.cuda.synchronize()
+    tot_ms = sum(a.elapsed_time(b) for _, a, b in evs)
+    tot_bytes = 0
+    for col, _, _ in evs:
+        cnt, nv = G.patch_info(J, col)
+        tot_bytes += colour_pass_bytes(cnt, nv, 4, 4)
+    hbm, peak_kind = peaks()
+    achieved = tot_bytes / (tot_ms / 1e3) / 1e9
+    avg_launch_ms = tot_ms / len(evs)
+    per_launch_bytes = tot_bytes / len(evs)
+
+    # --- companions: FP64 and BF16-inverse V-cycles, time to 1e-8 ----------------
+    extra = {}
+    solves = {}
+    bsol = rng.standard_normal(N)
+    # random load in the velocity rows, no divergence source, boundary normal dofs zero
+    b_host = torch.as_tensor(bsol)
+    f = torch.as_tensor(bsol[:nu], device=dev)
+    g = torch.zeros(npr, dtype=torch.float64, device=dev)
+    for prec, Gh in (("fp32", G),):
+        x = torch.zeros_like(r)
+        st, status = Gh.solve(f, g, x, tol=1e-8, maxit=400, check=False)
+        solves[prec] = {"ms": st.solve_ms, "iterations": st.iterations, "rel_residual": st.rel_residual,
+                        "converged": bool(st.converged)}
+    del G
+    torch.cuda.empty_cache()
+    for prec in ("fp64", "fp32_bf16inv"):
+        Gh = make(prec)
+        ksteps = max(3, args.steps // 2)
+        ms_p, _ = time_vcycles(Gh, ksteps, 2)
+        extra[prec] = N * ksteps / (ms_p / 1e3)
+        x = torch.zeros_like(r)
+        st, status = Gh.solve(f, g, x, tol=1e-8, maxit=400, check=False)
+        solves[prec] = {"ms": st.solve_ms, "iterations": st.iterations, "rel_residual": st.rel_residual,
+                        "converged": bool(st.converged)}
+        del Gh
+        torch.cuda.empty_cache()
+
+    # --- end to end through the C interface with host buffers ------------------
+    G = make("fp32")
+    rp = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    rp.copy_(torch.as_tensor(rh))
+    zp = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    for _ in range(2):
+        G.vcycle(rp, zp)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.vcycle(rp, zp)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if dist is not None:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = N * args.steps * world / float(e2e_t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = run_cpu_baseline(args.cpu_seconds)
+        except Exception as ex:  # the baseline is reported, not required
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "traffic": None,
+                             "kernel": "k_colour_pass<2,1,float,float> (finest level)",
+                             "peak_kind": peak_kind, "avg_launch_ms": avg_launch_ms,
+                             "bytes_per_launch": per_launch_bytes},
+                "clocks": clocks,
+                "cpu_baseline": cpu,
+                "dofs": N,
+                "fp64_value": extra.get("fp64"), "bf16inv_value": extra.get("fp32_bf16inv"),
+                "time_to_1e-8": solves}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * mgdarcy.h -- C interface of the GB300 geometric multigrid for the
+ * H(div)-conforming interior-penalty DG discretisation of Darcy/Brinkman flow
+ * (Kanschat, Lazarov & Mao, arXiv:1602.04858).
+ *
+ * Problem (Sec. 2.2, eq. (Brinkman)):  -mu Lap u + c u + grad p = f,
+ * div u = g in the unit square/cube, normal velocity prescribed on the
+ * boundary, discretised by RT_k x Q_k on n^d uniform cells with the symmetric
+ * interior-penalty form of eq. (ipbrinkman) and the saddle-point form of
+ * eq. (Brinkman-weak); the penalty is sigma_j = (k+1)(k+2)/h_j (Sec. 4.1).
+ * The solver is flexible GMRES (FP64) preconditioned by the V-cycle of
+ * Sec. 3.2 with the symmetric multiplicative vertex-patch Schwarz smoother of
+ * Sec. 3.3, eq. (smoother-Multiplicative).
+ *
+ * Vector layout (every vector argument): the velocity components u_0 .. u_{d-1}
+ * then the pressure p, each a d-dimensional array of nodal values with the
+ * x index fastest.  With N = n (k+1): component i has N+1 nodes along x_i (the
+ * k+2 Gauss-Lobatto points of each cell, shared across faces) and N along
+ * every other direction (the k+1 Gauss points of each cell); p has N Gauss
+ * nodes along every direction.  n_u = d (N+1) N^(d-1), n_p = N^d.
+ * The boundary normal-velocity dofs (index 0 or N along x_i for u_i) are
+ * strongly imposed: the operator is the identity on them and so is the
+ * preconditioner.
+ *
+ * Memory: pointers documented "host or device" may point to either (the
+ * library asks the CUDA runtime which); device pointers must be on the
+ * device that was current at mg_setup.  The caller owns every buffer it
+ * passes; the handle owns its workspace.  Calls are asynchronous on the
+ * stream given to mg_setup unless stated otherwise; calls that return
+ * statistics, or that receive host pointers, synchronise that stream.
+ * Errors are returned as mg_status (never thrown, never trapped);
+ * mg_last_error() gives a message.  A handle is not thread-safe.
+ */
+#ifndef MGDARCY_H
+#define MGDARCY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,
+  MG_ERR_OOM = 2,
+  MG_ERR_CUDA = 3,
+  MG_ERR_NOT_CONVERGED = 4,
+  MG_ERR_BREAKDOWN = 5,
+  MG_ERR_DEVICE_TIMEOUT = 6,
+  MG_ERR_UNSUPPORTED = 7
+} mg_status;
+
+/* Arithmetic of the V-cycle.  The outer GMRES is FP64 in every mode, which
+ * makes the lower-precision modes an iterative refinement. */
+typedef enum {
+  MG_PREC_FP64 = 0,         /* FP64 vectors and patch inverses            */
+  MG_PREC_FP32 = 1,         /* FP32 vectors and patch inverses            */
+  MG_PREC_FP32_BF16INV = 2  /* FP32 vectors, BF16 patch inverses          */
+} mg_precision;
+
+typedef struct {
+  int dim;              /* d: 2 or 3                                          */
+  int n_coarse;         /* cells per direction on level 0 (>= 2)              */
+  int n_levels;         /* J+1 >= 1; finest n = n_coarse * 2^J                */
+  int degree;           /* k of RT_k x Q_k: 0 or 1 (d = 3: 0 only)             */
+  double mu;            /* >= 0; mu = 0 is the Darcy model (Sec. 2.2)          */
+  const double* c;      /* host or device: finest-level zero-order coefficient
+                           (inverse permeability), one value per cell, x
+                           fastest, every value finite and > 0                */
+  int precision;        /* mg_precision                                        */
+  int m_fine;           /* smoothing steps on the finest level, m(J) >= 1      */
+  int variable_cycle;   /* 1: m(j) = m(J) 2^(J-j) (Sec. 3.2); 0: m(j) = m(J)   */
+  int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1):
+                           0: harmonic mean of c (= arithmetic mean of the
+                           permeability 1/c), 1: arithmetic mean of c          */
+} mg_problem;
+
+typedef struct {
+  int iterations;         /* GMRES iterations (V-cycle applications)          */
+  int converged;          /* 1 if ||b - A x|| <= tol ||b||                     */
+  double rel_residual;    /* final ||b - A x||_2 / ||b||_2, FP64               */
+  double initial_rel_residual;
+  double removed_flux;    /* sum of the pressure-block rhs removed to make the
+                             system compatible (0 for a compatible rhs)        */
+  double solve_ms;        /* wall time of the solve on the stream              */
+} mg_stats;
+
+typedef struct mg_handle mg_handle;
+
+/* Builds the level hierarchy (Sec. 3, eq. (ML-problem)): per level the
+ * coefficient (coarsened as chosen by coarse_avg), the patch inverses S_v of
+ * every vertex patch (Sec. 3.3: bordered local saddle-point matrix, FP64 LU,
+ * stored in the chosen precision) and the dense inverse of the coarsest
+ * operator.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Synchronises the stream.  Errors: MG_ERR_INVALID_ARG for unsupported
+ * sizes, non-positive or non-finite c; MG_ERR_OOM; MG_ERR_CUDA. */
+mg_status mg_setup(const mg_problem* problem, void* cuda_stream, mg_handle** out);
+
+/* Frees the handle and all its device memory (NULL is allowed). */
+void mg_destroy(mg_handle* h);
+
+/* Number of velocity and pressure dofs of level `level` (-1: finest). */
+mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p);
+
+/* y = A_level x (FP64), the operator of eq. (Brinkman-weak) on level `level`
+ * (-1: finest).  x, y: host or device, length n_u + n_p, must not alias. */
+mg_status mg_apply(mg_handle* h, int level, const double* x, double* y);
+
+/* z = B_J r: one V-cycle of Sec. 3.2 with zero initial guess, in the handle's
+ * precision (FP64 in/out; FP32 modes convert at entry and exit).
+ * r, z: host or device, length n_u + n_p, must not alias. */
+mg_status mg_vcycle(mg_handle* h, const double* r, double* z);
+
+/* Solves A_J x = b with b = (f, g) by right-preconditioned flexible GMRES in
+ * FP64 with the V-cycle preconditioner (Sec. 3.2; stop at
+ * ||b - A x||_2 <= tol ||b||_2).  f: length n_u, the velocity block of b
+ * (load vector; entries at constrained dofs are their prescribed values);
+ * g: length n_p, the pressure block.  A pressure block whose sum is not zero
+ * is made compatible by removing its mean (reported in stats).  x: length
+ * n_u + n_p, initial guess if use_x0 != 0; on return the pressure has zero
+ * mean.  f, g, x: host or device.  restart <= 0 means no restart.
+ * Synchronises.  Returns MG_ERR_NOT_CONVERGED if maxit is reached. */
+mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x,
+                   int use_x0, double tol, int maxit, int restart, mg_stats* stats);
+
+/* --- single steps of the V-cycle, for testing and measurement ---------------- */
+
+/* x <- x + R_j (b - A_j x): `steps` symmetric multiplicative Schwarz
+ * steps (eq. smoother-Multiplicative) on level `level` >= 1, in the handle's
+ * precision.  x, b: device, FP64, length n_u + n_p of that level. */
+mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int steps);
+
+/* One colour pass of the smoother (the patches of one colour, Sec. 3.3):
+ * x <- x + sum_v Pi_v^T S_v Pi_v (b - A x) over the patches v of `colour`
+ * (0 .. 3^d - 1) on level `level`, in the handle's precision, on the
+ * handle's internal level vectors (loaded with mg_level_load).  For timing. */
+mg_status mg_colour_pass(mg_handle* h, int level, int colour);
+
+/* Copies FP64 x, b (device, level sizes) into the handle's level vectors in
+ * the handle's precision, and back (mg_level_store copies x out). */
+mg_status mg_level_load(mg_handle* h, int level, const double* x, const double* b);
+mg_status mg_level_store(mg_handle* h, int level, double* x);
+
+/* b_{level-1} = P^T r (eq. 3, transpose of the injection of Sec. 3.1) with
+ * the constrained rows of r and of the result taken as zero.  FP64, device. */
+mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_coarse);
+
+/* x_fine += P x_coarse (the natural injection of Sec. 3.1).  FP64, device. */
+mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double* x_fine);
+
+/* x = A_0^{-1} b on the free dofs of level 0 with zero pressure mean,
+ * x = 0 on the constrained dofs.  FP64, device. */
+mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
+
+/* Patch counts: number of patches of `colour` on `level` and their size n_v. */
+mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v);
+
+/* Number of kernels the library launched on this handle so far. */
+int64_t mg_kernel_launches(const mg_handle* h);
+
+const char* mg_status_string(mg_status s);
+const char* mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGDARCY_H */

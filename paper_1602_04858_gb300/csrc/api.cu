@@ -1,0 +1,788 @@
+// api.cu -- the C interface of include/mgdarcy.h.
+//
+// Setup builds the level hierarchy of Sec. 3 (eq. ML-problem): coarse
+// coefficients (Sec. 4.1), patch inverses (Sec. 3.3) and the dense inverse of
+// the coarsest operator.  mg_vcycle runs the V-cycle of Sec. 3.2 and mg_solve
+// the FP64 flexible GMRES it preconditions.  Every arithmetic step runs in the
+// kernels of this library; the host only orders launches and runs the tiny
+// Hessenberg least-squares update of GMRES.
+#include "../../include/mgdarcy.h"
+#include "ops.h"
+#include "tables.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace mgd;
+
+namespace {
+
+thread_local std::string g_err;
+
+mg_status fail(mg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+    }                                                                                     \
+  } while (0)
+
+#define TRY(call)                      \
+  do {                                 \
+    mg_status s_ = (call);             \
+    if (s_ != MG_OK) return s_;        \
+  } while (0)
+
+}  // namespace
+
+struct mg_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int d = 2, k = 0, J = 0, prec = 0, m_fine = 2, variable = 1, coarse_avg = 0;
+  double mu = 0.0;
+  const DKOps* ops = nullptr;
+  std::vector<HostLevel> lv;
+  // coarsest level
+  int nf0 = 0;
+  int64_t* d_free0 = nullptr;
+  double* d_inv0 = nullptr;
+  // FP64 finest-level work vectors and pressure weights
+  double* d_pw = nullptr;      // pressure weights (length n_p)
+  double* t64[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* d_fail = nullptr;
+  // GMRES workspace
+  int gm_m = 0;
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* d_partial = nullptr;
+  double* d_coef = nullptr;
+  int64_t launches = 0;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_kernels = 0;
+  std::vector<void*> allocs;
+
+  ~mg_handle() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename T>
+  mg_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+                                      std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(q);
+    *p = (T*)q;
+    return MG_OK;
+  }
+  size_t vbytes() const { return prec == P64 ? sizeof(double) : sizeof(float); }
+  int f32() const { return prec == P64 ? 0 : 1; }
+  const HostLevel& fine() const { return lv.back(); }
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void level_geometry(HostLevel& L, int d, int k, int n, double mu) {
+  std::memset(&L, 0, sizeof(L));
+  L.d = d;
+  L.k = k;
+  L.n = n;
+  L.N = n * (k + 1);
+  L.h = 1.0 / n;
+  L.mu = mu;
+  int64_t off = 0;
+  for (int c = 0; c <= d; ++c) {
+    L.off[c] = off;
+    int64_t s = 1;
+    for (int e = 0; e < d; ++e) s *= (c < d && e == c) ? (L.N + 1) : L.N;
+    off += s;
+  }
+  L.ndof = off;
+  L.n_u = L.off[d];
+  L.n_p = L.ndof - L.n_u;
+  for (int col = 0; col < 27; ++col) L.count[col] = 0;
+  const int C = (d == 2) ? 9 : 27;
+  for (int col = 0; col < C; ++col) {
+    int64_t cnt = 1;
+    int r = col;
+    for (int e = 0; e < d; ++e) {
+      cnt *= colour_count(n, r % 3);
+      r /= 3;
+    }
+    L.count[col] = cnt;
+  }
+}
+
+int num_colours(int d) { return d == 2 ? 9 : 27; }
+
+// Host decode of a level index (used for the coarsest level's free-dof list).
+bool host_constrained(const HostLevel& L, int64_t g) {
+  int comp = L.d;
+  for (int c = 0; c < L.d; ++c)
+    if (g >= L.off[c] && g < L.off[c + 1]) comp = c;
+  if (comp == L.d) return false;
+  int64_t r = g - L.off[comp];
+  for (int e = 0; e < L.d; ++e) {
+    const int m = (e == comp) ? L.N + 1 : L.N;
+    const int t = (int)(r % m);
+    r /= m;
+    if (e == comp) return t == 0 || t == L.N;
+  }
+  return false;
+}
+
+mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, cudaStream_t stream) {
+  HostLevel& L = h->lv[j];
+  const int C = num_colours(h->d);
+  for (int s = 0; s < steps; ++s) {
+    for (int t = 0; t < 2 * C - 1; ++t) {
+      const int col = t < C ? t : 2 * C - 2 - t;
+      if (L.count[col] == 0) continue;
+      h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, stream);
+      ++h->launches;
+    }
+  }
+  return MG_OK;
+}
+
+int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
+
+// B_j b_j with b_j in lv[j].B; result in lv[j].X (Sec. 3.2).
+mg_status vcycle_level(mg_handle* h, int j, cudaStream_t stream) {
+  HostLevel& L = h->lv[j];
+  if (j == 0) {
+    launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, L.ndof, h->f32(), L.B, L.X, stream);
+    ++h->launches;
+    return MG_OK;
+  }
+  CU(cudaMemsetAsync(L.X, 0, L.ndof * h->vbytes(), stream));
+  const int m = m_of(h, j);
+  TRY(smooth_steps(h, j, L.X, L.B, m, stream));
+  h->ops->residual(L, h->f32(), L.X, L.B, L.R, 1, stream);
+  HostLevel& Lc = h->lv[j - 1];
+  h->ops->restrict_(L, Lc, h->f32(), L.R, Lc.B, stream);
+  h->launches += 2;
+  TRY(vcycle_level(h, j - 1, stream));
+  h->ops->prolong_add(L, Lc, h->f32(), Lc.X, L.X, stream);
+  ++h->launches;
+  TRY(smooth_steps(h, j, L.X, L.B, m, stream));
+  return MG_OK;
+}
+
+// The whole V-cycle on the handle's level vectors (lv[J].B -> lv[J].X), as
+// one CUDA graph captured on first use and replayed afterwards.
+mg_status vcycle_graph(mg_handle* h) {
+  if (!h->graph_exec) {
+    cudaStream_t cap;
+    CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const int64_t l0 = h->launches;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return fail(MG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+    }
+    mg_status st = vcycle_level(h, h->J, cap);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    h->launches = l0;
+    if (st != MG_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int64_t kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      cudaGraphNodeGetType(nd, &t);
+      if (t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    h->graph_kernels = kernels;
+  }
+  CU(cudaGraphLaunch(h->graph_exec, h->stream));
+  h->launches += h->graph_kernels;
+  return MG_OK;
+}
+
+// z = B_J r for FP64 device vectors (r, z may not alias).
+mg_status vcycle_dev(mg_handle* h, const double* r, double* z) {
+  HostLevel& L = h->lv.back();
+  if (h->prec == P64) {
+    CU(cudaMemcpyAsync(L.B, r, L.ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    launch_d2f(r, (float*)L.B, L.ndof, h->stream);
+    ++h->launches;
+  }
+  TRY(vcycle_graph(h));
+  if (h->prec == P64) {
+    CU(cudaMemcpyAsync(z, L.X, L.ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    launch_f2d((const float*)L.X, z, L.ndof, h->stream);
+    ++h->launches;
+  }
+  h->ops->copy_constrained(L, r, z, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status apply_dev(mg_handle* h, int level, const double* x, double* y) {
+  HostLevel& L = h->lv[level];
+  h->ops->apply(L, 0, x, y, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mg_status_string(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_OOM: return "out of device memory";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_BREAKDOWN: return "breakdown";
+    case MG_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+    case MG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* mg_last_error(void) { return g_err.c_str(); }
+
+int64_t mg_kernel_launches(const mg_handle* h) { return h ? h->launches : 0; }
+
+void mg_destroy(mg_handle* h) { delete h; }
+
+mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
+  if (!p || !out) return fail(MG_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (p->dim != 2 && p->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (p->degree < 0 || p->degree > 1) return fail(MG_ERR_UNSUPPORTED, "degree must be 0 or 1");
+  if (p->dim == 3 && p->degree != 0) return fail(MG_ERR_UNSUPPORTED, "3-D supports degree 0 only");
+  if (p->n_coarse < 2 || p->n_levels < 1 || p->n_levels > 14)
+    return fail(MG_ERR_INVALID_ARG, "need n_coarse >= 2 and 1 <= n_levels <= 14");
+  if (!(p->mu >= 0.0) || !std::isfinite(p->mu)) return fail(MG_ERR_INVALID_ARG, "mu must be finite and >= 0");
+  if (p->precision < 0 || p->precision > 2) return fail(MG_ERR_INVALID_ARG, "bad precision");
+  if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
+  if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
+  if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
+  const int d = p->dim, k = p->degree, J = p->n_levels - 1;
+  const int64_t nfine = (int64_t)p->n_coarse << J;
+  if (nfine > (1 << 16)) return fail(MG_ERR_INVALID_ARG, "mesh too large");
+  int64_t ncell = 1;
+  for (int e = 0; e < d; ++e) ncell *= nfine;
+  // the finest level vector must be addressable with int node indices
+  if ((double)ncell * (k + 1) * (k + 1) * (d == 3 ? (k + 1) : 1) * (d + 1) > 4.0e9)
+    return fail(MG_ERR_INVALID_ARG, "mesh too large");
+
+  mg_handle* h = new mg_handle();
+  auto cleanup = [&](mg_status s) {
+    delete h;
+    return s;
+  };
+  cudaGetDevice(&h->device);
+  h->stream = (cudaStream_t)cuda_stream;
+  h->d = d;
+  h->k = k;
+  h->J = J;
+  h->prec = p->precision;
+  h->m_fine = p->m_fine;
+  h->variable = p->variable_cycle ? 1 : 0;
+  h->coarse_avg = p->coarse_avg;
+  h->mu = p->mu;
+  h->ops = (d == 2) ? (k == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
+
+  // coefficient: validate on the host
+  std::vector<double> c(ncell);
+  if (is_device_ptr(p->c)) {
+    if (cudaMemcpy(c.data(), p->c, ncell * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cleanup(fail(MG_ERR_CUDA, "copy of c failed"));
+  } else {
+    std::memcpy(c.data(), p->c, ncell * sizeof(double));
+  }
+  for (int64_t i = 0; i < ncell; ++i)
+    if (!(c[i] > 0.0) || !std::isfinite(c[i]))
+      return cleanup(fail(MG_ERR_INVALID_ARG, "c must be finite and > 0 in every cell"));
+
+  h->lv.resize(J + 1);
+  for (int j = 0; j <= J; ++j) level_geometry(h->lv[j], d, k, p->n_coarse << j, p->mu);
+  mg_status st;
+  // coefficients per level
+  for (int j = J; j >= 0; --j) {
+    HostLevel& L = h->lv[j];
+    int64_t nc = 1;
+    for (int e = 0; e < d; ++e) nc *= L.n;
+    if ((st = h->alloc(&L.c64, nc)) != MG_OK) return cleanup(st);
+    if ((st = h->alloc(&L.c32, nc)) != MG_OK) return cleanup(st);
+    if (j == J) {
+      if (cudaMemcpyAsync(L.c64, c.data(), nc * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return cleanup(fail(MG_ERR_CUDA, "upload of c failed"));
+    } else {
+      launch_coarsen_c(d, L.n, h->lv[j + 1].c64, L.c64, h->coarse_avg, h->stream);
+      ++h->launches;
+    }
+    launch_d2f(L.c64, L.c32, nc, h->stream);
+    ++h->launches;
+  }
+  if ((st = h->alloc(&h->d_fail, 1)) != MG_OK) return cleanup(st);
+  cudaMemsetAsync(h->d_fail, 0, sizeof(int), h->stream);
+  // level vectors and patch inverses
+  const int C = num_colours(d);
+  for (int j = 0; j <= J; ++j) {
+    HostLevel& L = h->lv[j];
+    void* q;
+    for (void** v : {&L.X, &L.B, &L.R}) {
+      if ((st = h->alloc((char**)&q, L.ndof * h->vbytes())) != MG_OK) return cleanup(st);
+      *v = q;
+    }
+    // BF16 storage (with FP32 equilibration scales) on the finest level only;
+    // the coarser levels keep FP32 inverses
+    L.sprec = (h->prec == P32B && j < J) ? P32 : h->prec;
+    if (j == 0) continue;
+    const size_t sb = (L.sprec == P64) ? 8 : (L.sprec == P32 ? 4 : 2);
+    for (int col = 0; col < C; ++col) {
+      if (L.count[col] == 0) continue;
+      size_t bytes = (size_t)L.count[col] * h->ops->s_stride[L.sprec] * sb;
+      if (L.sprec == P32B) bytes += (size_t)L.count[col] * h->ops->nvp[P32B] * sizeof(float);
+      if ((st = h->alloc((char**)&q, bytes)) != MG_OK) return cleanup(st);
+      L.S[col] = q;
+      h->ops->patch_setup(L, col, L.sprec, q, h->d_fail, h->stream);
+      ++h->launches;
+    }
+  }
+  // coarsest level: dense bordered inverse on the free dofs
+  {
+    HostLevel& L0 = h->lv[0];
+    std::vector<int64_t> fl;
+    std::vector<int> g2l(L0.ndof, -1);
+    for (int64_t g = 0; g < L0.ndof; ++g)
+      if (!host_constrained(L0, g)) {
+        g2l[g] = (int)fl.size();
+        fl.push_back(g);
+      }
+    h->nf0 = (int)fl.size();
+    if (h->nf0 > 4000) return cleanup(fail(MG_ERR_UNSUPPORTED, "coarsest level too large for the dense solve"));
+    const int nb = h->nf0 + 1;
+    int* d_g2l = nullptr;
+    double *M = nullptr, *E = nullptr;
+    if ((st = h->alloc(&h->d_free0, fl.size())) != MG_OK) return cleanup(st);
+    if ((st = h->alloc(&d_g2l, g2l.size())) != MG_OK) return cleanup(st);
+    if ((st = h->alloc(&M, (size_t)nb * nb)) != MG_OK) return cleanup(st);
+    if ((st = h->alloc(&E, (size_t)nb * h->nf0)) != MG_OK) return cleanup(st);
+    cudaMemcpyAsync(h->d_free0, fl.data(), fl.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(d_g2l, g2l.data(), g2l.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    h->ops->coarse_assemble(L0, h->d_free0, d_g2l, h->nf0, M, E, h->stream);
+    launch_gauss_jordan(M, E, nb, h->nf0, h->d_fail, h->stream);
+    h->launches += 2;
+    h->d_inv0 = E;  // rows 0..nf0-1 of E hold A_0^{-1} on the mean-zero subspace
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return cleanup(fail(MG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(cudaGetLastError())));
+    // M and the index map are no longer needed
+    for (auto it = h->allocs.begin(); it != h->allocs.end();) {
+      if (*it == (void*)M || *it == (void*)d_g2l) {
+        cudaFree(*it);
+        it = h->allocs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  // pressure weights of the finest level (integral of each pressure basis function)
+  {
+    const HostLevel& L = h->lv[J];
+    std::vector<double> w(L.n_p);
+    double gw[2];
+    if (k == 0) {
+      Tab<0, double> td;
+      Tab<0, float> tf;
+      make_tables<0>(td, tf);
+      gw[0] = td.wg[0];
+    } else {
+      Tab<1, double> td;
+      Tab<1, float> tf;
+      make_tables<1>(td, tf);
+      gw[0] = td.wg[0];
+      gw[1] = td.wg[1];
+    }
+    const double vol = std::pow(L.h, d);
+    for (int64_t g = 0; g < L.n_p; ++g) {
+      int64_t r = g;
+      double v = vol;
+      for (int e = 0; e < d; ++e) {
+        v *= gw[(r % L.N) % (k + 1)];
+        r /= L.N;
+      }
+      w[g] = v;
+    }
+    if ((st = h->alloc(&h->d_pw, L.n_p)) != MG_OK) return cleanup(st);
+    cudaMemcpyAsync(h->d_pw, w.data(), L.n_p * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  }
+  for (int t = 0; t < 4; ++t)
+    if ((st = h->alloc(&h->t64[t], h->lv[J].ndof)) != MG_OK) return cleanup(st);
+  int bad = 0;
+  if (cudaMemcpyAsync(&bad, h->d_fail, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cleanup(fail(MG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(cudaGetLastError())));
+  if (bad) return cleanup(fail(MG_ERR_BREAKDOWN, "zero pivot in a patch or coarse factorisation"));
+  *out = h;
+  return MG_OK;
+}
+
+mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p) {
+  if (!h) return fail(MG_ERR_INVALID_ARG, "null handle");
+  if (level < 0) level = h->J;
+  if (level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  if (n_u) *n_u = h->lv[level].n_u;
+  if (n_p) *n_p = h->lv[level].n_p;
+  return MG_OK;
+}
+
+mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v) {
+  if (!h || level < 1 || level > h->J || colour < 0 || colour >= num_colours(h->d))
+    return fail(MG_ERR_INVALID_ARG, "bad level or colour");
+  if (count) *count = h->lv[level].count[colour];
+  if (n_v) *n_v = h->ops->nv;
+  return MG_OK;
+}
+
+mg_status mg_apply(mg_handle* h, int level, const double* x, double* y) {
+  if (!h || !x || !y) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (level < 0) level = h->J;
+  if (level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  const int64_t n = h->lv[level].ndof;
+  const bool dx = is_device_ptr(x), dy = is_device_ptr(y);
+  const double* xs = x;
+  double* ys = y;
+  if (!dx) {
+    CU(cudaMemcpyAsync(h->t64[0], x, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    xs = h->t64[0];
+  }
+  if (!dy) ys = h->t64[1];
+  TRY(apply_dev(h, level, xs, ys));
+  if (!dy) {
+    CU(cudaMemcpyAsync(y, ys, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_vcycle(mg_handle* h, const double* r, double* z) {
+  if (!h || !r || !z) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (r == z) return fail(MG_ERR_INVALID_ARG, "r and z must not alias");
+  const int64_t n = h->fine().ndof;
+  const bool dr = is_device_ptr(r), dz = is_device_ptr(z);
+  const double* rs = r;
+  double* zs = z;
+  if (!dr) {
+    CU(cudaMemcpyAsync(h->t64[0], r, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    rs = h->t64[0];
+  }
+  if (!dz) zs = h->t64[1];
+  TRY(vcycle_dev(h, rs, zs));
+  if (!dz) {
+    CU(cudaMemcpyAsync(z, zs, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return MG_OK;
+}
+
+mg_status mg_level_load(mg_handle* h, int level, const double* x, const double* b) {
+  if (!h || level < 0 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  HostLevel& L = h->lv[level];
+  if (h->prec == P64) {
+    if (x) CU(cudaMemcpyAsync(L.X, x, L.ndof * 8, cudaMemcpyDeviceToDevice, h->stream));
+    if (b) CU(cudaMemcpyAsync(L.B, b, L.ndof * 8, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    if (x) { launch_d2f(x, (float*)L.X, L.ndof, h->stream); ++h->launches; }
+    if (b) { launch_d2f(b, (float*)L.B, L.ndof, h->stream); ++h->launches; }
+  }
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_level_store(mg_handle* h, int level, double* x) {
+  if (!h || level < 0 || level > h->J || !x) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  HostLevel& L = h->lv[level];
+  if (h->prec == P64) CU(cudaMemcpyAsync(x, L.X, L.ndof * 8, cudaMemcpyDeviceToDevice, h->stream));
+  else { launch_f2d((const float*)L.X, x, L.ndof, h->stream); ++h->launches; }
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int steps) {
+  if (!h || level < 1 || level > h->J || !x || !b || steps < 0) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  TRY(mg_level_load(h, level, x, b));
+  HostLevel& L = h->lv[level];
+  TRY(smooth_steps(h, level, L.X, L.B, steps, h->stream));
+  TRY(mg_level_store(h, level, x));
+  return MG_OK;
+}
+
+mg_status mg_colour_pass(mg_handle* h, int level, int colour) {
+  if (!h || level < 1 || level > h->J || colour < 0 || colour >= num_colours(h->d))
+    return fail(MG_ERR_INVALID_ARG, "bad level or colour");
+  HostLevel& L = h->lv[level];
+  if (L.count[colour] == 0) return MG_OK;
+  h->ops->colour_pass(L, colour, L.sprec, L.S[colour], L.X, L.B, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_coarse) {
+  if (!h || level < 1 || level > h->J || !r_fine || !b_coarse) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  h->ops->restrict_(h->lv[level], h->lv[level - 1], 0, r_fine, b_coarse, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double* x_fine) {
+  if (!h || level < 1 || level > h->J || !x_coarse || !x_fine) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  h->ops->prolong_add(h->lv[level], h->lv[level - 1], 0, x_coarse, x_fine, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x) {
+  if (!h || !b || !x) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, h->lv[0].ndof, 0, b, x, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
+// --- flexible GMRES (FP64) ---------------------------------------------------
+
+namespace {
+
+mg_status dot1(mg_handle* h, const double* a, const double* b, int64_t n, double* out) {
+  launch_multidot(a, n, 1, b, n, h->d_partial, h->d_coef, h->stream);
+  h->launches += 2;
+  CU(cudaMemcpyAsync(out, h->d_coef, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return MG_OK;
+}
+
+mg_status gm_workspace(mg_handle* h, int m) {
+  if (h->gm_m >= m) return MG_OK;
+  const int64_t n = h->fine().ndof;
+  for (auto it = h->allocs.begin(); it != h->allocs.end();) {
+    if (*it == (void*)h->V || *it == (void*)h->Z || *it == (void*)h->d_partial || *it == (void*)h->d_coef) {
+      cudaFree(*it);
+      it = h->allocs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  TRY(h->alloc(&h->V, (size_t)(m + 1) * n));
+  TRY(h->alloc(&h->Z, (size_t)m * n));
+  TRY(h->alloc(&h->d_partial, (size_t)(m + 2) * multidot_blocks()));
+  TRY(h->alloc(&h->d_coef, (size_t)(m + 2)));
+  h->gm_m = m;
+  return MG_OK;
+}
+
+}  // namespace
+
+mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, int use_x0, double tol, int maxit,
+                   int restart, mg_stats* stats) {
+  if (!h || !f || !g || !x) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0.0) || maxit < 0) return fail(MG_ERR_INVALID_ARG, "bad tol or maxit");
+  const HostLevel& L = h->fine();
+  const int64_t n = L.ndof, nu = L.n_u, np = L.n_p;
+  if (restart <= 0 || restart > maxit) restart = maxit > 0 ? maxit : 1;
+  TRY(gm_workspace(h, restart));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, h->stream));
+  double* b = h->t64[2];
+  double* xd = h->t64[3];
+  double* w = h->t64[0];
+  double* r = h->t64[1];
+  const cudaMemcpyKind kf = is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind kg = is_device_ptr(g) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const bool xdev = is_device_ptr(x);
+  CU(cudaMemcpyAsync(b, f, nu * sizeof(double), kf, h->stream));
+  CU(cudaMemcpyAsync(b + nu, g, np * sizeof(double), kg, h->stream));
+  if (use_x0) CU(cudaMemcpyAsync(xd, x, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                 h->stream));
+  else CU(cudaMemsetAsync(xd, 0, n * sizeof(double), h->stream));
+  // compatibility: the pressure block must sum to zero (range of the symmetric A)
+  double gsum = 0.0;
+  {
+    // sum of g = dot(g, ones): use w as a vector of ones
+    launch_scale_copy(b + nu, 0.0, w, np, h->stream);
+    launch_add_const(w, 1.0, np, h->stream);
+    h->launches += 2;
+    TRY(dot1(h, b + nu, w, np, &gsum));
+    if (gsum != 0.0) {
+      launch_add_const(b + nu, -gsum / (double)np, np, h->stream);
+      ++h->launches;
+    }
+  }
+  double bnorm2;
+  TRY(dot1(h, b, b, n, &bnorm2));
+  const double bnorm = std::sqrt(bnorm2);
+  const int m = restart;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 2), y(m);
+  int its = 0;
+  double relres = 0.0, rel0 = -1.0;
+  bool converged = false;
+  mg_status result = MG_OK;
+  if (bnorm == 0.0) {
+    CU(cudaMemsetAsync(xd, 0, n * sizeof(double), h->stream));
+    converged = true;
+  }
+  while (!converged) {
+    // r = b - A x
+    TRY(apply_dev(h, h->J, xd, w));
+    CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    launch_axpby(-1.0, w, 1.0, r, n, h->stream);
+    ++h->launches;
+    double beta2;
+    TRY(dot1(h, r, r, n, &beta2));
+    const double beta = std::sqrt(beta2);
+    relres = beta / bnorm;
+    if (rel0 < 0) rel0 = relres;
+    if (beta <= tol * bnorm) {
+      converged = true;
+      break;
+    }
+    if (its >= maxit) break;
+    launch_scale_copy(r, 1.0 / beta, h->V, n, h->stream);
+    ++h->launches;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int kdone = 0;
+    bool breakdown = false;
+    for (int i = 0; i < m && its < maxit; ++i) {
+      double* vi = h->V + (size_t)i * n;
+      double* zi = h->Z + (size_t)i * n;
+      TRY(vcycle_dev(h, vi, zi));
+      TRY(apply_dev(h, h->J, zi, w));
+      // classical Gram-Schmidt, applied twice
+      for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_multidot(h->V, n, i + 1, w, n, h->d_partial, h->d_coef, h->stream);
+        launch_multi_axpy(w, h->V, n, i + 1, h->d_coef, -1.0, n, h->stream);
+        h->launches += 3;
+        CU(cudaMemcpyAsync(hc.data(), h->d_coef, (i + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] += hc[l];
+      }
+      double hn2;
+      TRY(dot1(h, w, w, n, &hn2));
+      const double hn = std::sqrt(hn2);
+      double* Hi = &H[0];
+      auto Hat = [&](int r_, int c_) -> double& { return Hi[(size_t)r_ * m + c_]; };
+      if (hn > 0.0) {
+        launch_scale_copy(w, 1.0 / hn, h->V + (size_t)(i + 1) * n, n, h->stream);
+        ++h->launches;
+      }
+      // Givens rotations; column i of H has rows 0..i+1 (row i+1 = hn)
+      double hcol_ip1 = hn;
+      for (int l = 0; l < i; ++l) {
+        const double t = cs[l] * Hat(l, i) + sn[l] * Hat(l + 1, i);
+        Hat(l + 1, i) = -sn[l] * Hat(l, i) + cs[l] * Hat(l + 1, i);
+        Hat(l, i) = t;
+      }
+      const double den = std::hypot(Hat(i, i), hcol_ip1);
+      if (den == 0.0) {
+        breakdown = true;
+        break;
+      }
+      cs[i] = Hat(i, i) / den;
+      sn[i] = hcol_ip1 / den;
+      Hat(i, i) = den;
+      gv[i + 1] = -sn[i] * gv[i];
+      gv[i] = cs[i] * gv[i];
+      ++its;
+      kdone = i + 1;
+      if (std::fabs(gv[i + 1]) <= tol * bnorm || hn == 0.0) break;
+    }
+    if (kdone == 0) {
+      result = fail(MG_ERR_BREAKDOWN, "GMRES breakdown");
+      break;
+    }
+    for (int l = kdone - 1; l >= 0; --l) {
+      double s = gv[l];
+      for (int q = l + 1; q < kdone; ++q) s -= H[(size_t)l * m + q] * y[q];
+      y[l] = s / H[(size_t)l * m + l];
+    }
+    CU(cudaMemcpyAsync(h->d_coef, y.data(), kdone * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    launch_multi_axpy(xd, h->Z, n, kdone, h->d_coef, 1.0, n, h->stream);
+    ++h->launches;
+    (void)breakdown;
+  }
+  // zero pressure mean: p -= (w . p) / sum(w)
+  if (result == MG_OK) {
+    double wp, ws;
+    TRY(dot1(h, h->d_pw, xd + nu, np, &wp));
+    launch_scale_copy(h->d_pw, 1.0, w, np, h->stream);
+    ++h->launches;
+    launch_scale_copy(w, 0.0, r, np, h->stream);
+    launch_add_const(r, 1.0, np, h->stream);
+    h->launches += 2;
+    TRY(dot1(h, h->d_pw, r, np, &ws));
+    launch_add_const(xd + nu, -wp / ws, np, h->stream);
+    ++h->launches;
+  }
+  CU(cudaMemcpyAsync(x, xd, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaEventRecord(e1, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    stats->iterations = its;
+    stats->converged = converged ? 1 : 0;
+    stats->rel_residual = relres;
+    stats->initial_rel_residual = rel0 < 0 ? 0.0 : rel0;
+    stats->removed_flux = gsum;
+    stats->solve_ms = ms;
+  }
+  if (result != MG_OK) return result;
+  if (!converged) return fail(MG_ERR_NOT_CONVERGED, "GMRES reached maxit");
+  return MG_OK;
+}
+
+}  // extern "C"

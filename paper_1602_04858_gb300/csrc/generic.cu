@@ -1,0 +1,189 @@
+// generic.cu -- kernels that do not depend on (d, k): coefficient coarsening,
+// precision casts, the coarsest-level dense solve and the FP64 vector
+// kernels of the Krylov solver.
+#include "kernels.cuh"
+#include "ops.h"
+
+namespace mgd {
+namespace {
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Coarse coefficient from the 2^d children (Sec. 4.1): mode 0 harmonic mean
+// of c (arithmetic mean of the permeability 1/c), mode 1 arithmetic mean of c.
+__global__ void k_coarsen_c(int d, int nc, const double* __restrict__ cf, double* __restrict__ cc, int mode) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t tot = (int64_t)nc * nc * (d == 3 ? nc : 1);
+  if (g >= tot) return;
+  const int i = (int)(g % nc), j = (int)((g / nc) % nc), l = (d == 3) ? (int)(g / ((int64_t)nc * nc)) : 0;
+  const int nf = 2 * nc;
+  double s = 0.0;
+  const int lz = (d == 3) ? 2 : 1;
+  for (int c = 0; c < lz; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int64_t f = (int64_t)(2 * i + a) + (int64_t)nf * ((2 * j + b) + (int64_t)nf * (2 * l + c));
+        s += (mode == 0) ? 1.0 / cf[f] : cf[f];
+      }
+  const double m = (double)(d == 3 ? 8 : 4);
+  cc[g] = (mode == 0) ? m / s : s / m;
+}
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) b[g] = (float)a[g];
+}
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < n) b[g] = (double)a[g];
+}
+
+__global__ void k_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail) {
+  extern __shared__ double sm[];
+  double* fac = sm;
+  double* red_v = fac + n;
+  int* red_i = reinterpret_cast<int*>(red_v + blockDim.x);
+  const int bad = gauss_jordan(M, n, E, nrhs, n, nrhs, fac, red_v, red_i);
+  if (bad && threadIdx.x == 0) *fail = 1;
+}
+
+// Coarsest-level solve: x = 0, then x[free_i] = sum_j inv_ij b[free_j] (FP64 arithmetic).
+template <typename T>
+__global__ void k_coarse_apply(const double* __restrict__ inv, const int64_t* __restrict__ free_list, int nf,
+                               int64_t ndof, const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double bs[];
+  for (int64_t g = threadIdx.x; g < ndof; g += blockDim.x) x[g] = T(0);
+  for (int j = threadIdx.x; j < nf; j += blockDim.x) bs[j] = (double)b[free_list[j]];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < nf; i += nw) {
+    double acc = 0.0;
+    for (int j = lane; j < nf; j += 32) acc += inv[(int64_t)i * nf + j] * bs[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[free_list[i]] = (T)acc;
+  }
+}
+
+// Partial dot products of nvec vectors V[v] (stride ld) with w: one row of
+// partials per block, reduced in a fixed order by k_reduce_partials.
+constexpr int MD_THREADS = 256;
+constexpr int MD_BLOCKS = 304;
+constexpr int MD_VEC = 8;   // vectors per pass
+
+__global__ void __launch_bounds__(MD_THREADS) k_multidot(const double* __restrict__ V, int64_t ld, int nvec,
+                                                         const double* __restrict__ w, int64_t n,
+                                                         double* __restrict__ partial) {
+  __shared__ double red[MD_VEC][MD_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v0 = 0; v0 < nvec; v0 += MD_VEC) {
+    double acc[MD_VEC];
+#pragma unroll
+    for (int v = 0; v < MD_VEC; ++v) acc[v] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * MD_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * MD_THREADS) {
+      const double wi = w[i];
+#pragma unroll
+      for (int v = 0; v < MD_VEC; ++v)
+        if (v0 + v < nvec) acc[v] += V[(int64_t)(v0 + v) * ld + i] * wi;
+    }
+#pragma unroll
+    for (int v = 0; v < MD_VEC; ++v) {
+      double a = acc[v];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) red[v][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < MD_VEC && v0 + threadIdx.x < nvec) {
+      double a = 0.0;
+      for (int q = 0; q < MD_THREADS / 32; ++q) a += red[threadIdx.x][q];
+      partial[(int64_t)(v0 + threadIdx.x) * gridDim.x + blockIdx.x] = a;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nvec, double* __restrict__ out) {
+  const int v = blockIdx.x;
+  if (v >= nvec) return;
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) a += partial[(int64_t)v * nblk + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    out[v] = s;
+  }
+}
+
+// w += sign * sum_v coef[v] V[v]
+__global__ void k_multi_axpy(double* __restrict__ w, const double* __restrict__ V, int64_t ld, int nvec,
+                             const double* __restrict__ coef, double sign, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int v = 0; v < nvec; ++v) a += coef[v] * V[(int64_t)v * ld + i];
+  w[i] += sign * a;
+}
+
+__global__ void k_scale_copy(const double* __restrict__ a, double s, double* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = s * a[i];
+}
+__global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = alpha * x[i] + beta * y[i];
+}
+__global__ void k_add_const(double* __restrict__ a, double s, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] += s;
+}
+
+}  // namespace
+
+void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t s) {
+  const int64_t tot = (int64_t)nc * nc * (d == 3 ? nc : 1);
+  k_coarsen_c<<<blocks(tot, 256), 256, 0, s>>>(d, nc, cf, cc, mode);
+}
+void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t s) { k_d2f<<<blocks(n, 256), 256, 0, s>>>(a, b, n); }
+void launch_f2d(const float* a, double* b, int64_t n, cudaStream_t s) { k_f2d<<<blocks(n, 256), 256, 0, s>>>(a, b, n); }
+
+void launch_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail, cudaStream_t s) {
+  const int threads = 1024;
+  const size_t smem = sizeof(double) * ((size_t)n + threads) + sizeof(int) * threads;
+  k_gauss_jordan<<<1, threads, smem, s>>>(M, E, n, nrhs, fail);
+}
+
+void launch_coarse_apply(const double* inv, const int64_t* free_list, int nf, int64_t ndof, int f32, const void* b,
+                         void* x, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)nf;
+  if (f32) k_coarse_apply<float><<<1, 512, smem, s>>>(inv, free_list, nf, ndof, (const float*)b, (float*)x);
+  else k_coarse_apply<double><<<1, 512, smem, s>>>(inv, free_list, nf, ndof, (const double*)b, (double*)x);
+}
+
+int multidot_blocks() { return MD_BLOCKS; }
+
+void launch_multidot(const double* V, int64_t ld, int nvec, const double* w, int64_t n, double* partial, double* out,
+                     cudaStream_t s) {
+  k_multidot<<<MD_BLOCKS, MD_THREADS, 0, s>>>(V, ld, nvec, w, n, partial);
+  k_reduce_partials<<<nvec, 256, 0, s>>>(partial, MD_BLOCKS, nvec, out);
+}
+void launch_multi_axpy(double* w, const double* V, int64_t ld, int nvec, const double* coef, double sign, int64_t n,
+                       cudaStream_t s) {
+  k_multi_axpy<<<blocks(n, 256), 256, 0, s>>>(w, V, ld, nvec, coef, sign, n);
+}
+void launch_scale_copy(const double* a, double sc, double* b, int64_t n, cudaStream_t s) {
+  k_scale_copy<<<blocks(n, 256), 256, 0, s>>>(a, sc, b, n);
+}
+void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s) {
+  k_axpby<<<blocks(n, 256), 256, 0, s>>>(alpha, x, beta, y, n);
+}
+void launch_add_const(double* a, double sc, int64_t n, cudaStream_t s) {
+  k_add_const<<<blocks(n, 256), 256, 0, s>>>(a, sc, n);
+}
+
+}  // namespace mgd

@@ -1,0 +1,497 @@
+// kernels.cuh -- CUDA kernels of the V-cycle for one (D, K).
+//
+// Included by kinst.cu, which is compiled once per (D, K).
+#pragma once
+
+#include <type_traits>
+
+#include "device.cuh"
+#include "ops.h"
+
+namespace mgd {
+
+// ---------------------------------------------------------------------------
+// Operator apply and residual (eq. Brinkman-weak), one thread per row.
+// ---------------------------------------------------------------------------
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                               const T* __restrict__ x, T* __restrict__ y) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.ndof) return;
+  int idx[D];
+  const int comp = decode(L, g, idx);
+  y[g] = apply_row(L, tb, comp, idx, x);
+}
+
+// r = b - A x on free rows; constrained rows: r = 0 (zero_c) or b - x.
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                                  const T* __restrict__ x, const T* __restrict__ b,
+                                                  T* __restrict__ r, int zero_c) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.ndof) return;
+  int idx[D];
+  const int comp = decode(L, g, idx);
+  if (is_constrained(L, comp, idx)) {
+    r[g] = zero_c ? T(0) : b[g] - x[g];
+    return;
+  }
+  r[g] = b[g] - apply_row(L, tb, comp, idx, x);
+}
+
+// ---------------------------------------------------------------------------
+// Transfers (Sec. 3.1): natural injection P and its transpose.
+// ---------------------------------------------------------------------------
+
+// Coarse Gauss-Lobatto node sc -> fine nodes and weights P[tf][sc] != 0.
+template <int K, typename T>
+__device__ __forceinline__ int gl_fine_list(int sc, int nc, const Tab<K, T>& tb, int* tf, T* wt) {
+  constexpr int K1 = K + 1;
+  int lo = (sc % K1 == 0) ? sc / K1 - 1 : sc / K1;
+  int hi = sc / K1;
+  if (lo < 0) lo = 0;
+  if (hi > nc - 1) hi = nc - 1;
+  int cnt = 0;
+  for (int cc = lo; cc <= hi; ++cc) {
+    const int ac = sc - cc * K1;
+#pragma unroll
+    for (int m = 0; m <= 2 * K1; ++m) {
+      if (cc > lo && m == 0) continue;  // the fine node on the shared face, counted once
+      const int ch = m >= K1 ? 1 : 0;
+      const int af = m - ch * K1;
+      const T w = tb.Wgl[ch][af][ac];
+      if (w != T(0)) {
+        tf[cnt] = 2 * cc * K1 + m;
+        wt[cnt] = w;
+        ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+template <int K, typename T>
+__device__ __forceinline__ int g_fine_list(int sc, const Tab<K, T>& tb, int* tf, T* wt) {
+  constexpr int K1 = K + 1;
+  const int cc = sc / K1, bc = sc - cc * K1;
+  int cnt = 0;
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+    for (int bf = 0; bf < K1; ++bf) {
+      tf[cnt] = (2 * cc + ch) * K1 + bf;
+      wt[cnt] = tb.Wg[ch][bf][bc];
+      ++cnt;
+    }
+  return cnt;
+}
+
+// b_c = P^T r_f; constrained rows of r_f and of b_c are taken as zero.
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256) k_restrict(const Lvl<D, K, T> Lf, const Lvl<D, K, T> Lc,
+                                                  const __grid_constant__ Tab<K, T> tb,
+                                                  const T* __restrict__ rf, T* __restrict__ bc) {
+  constexpr int K1 = K + 1, MX = 4 * K1 + 2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lc.ndof) return;
+  int idx[D];
+  const int comp = decode(Lc, g, idx);
+  if (is_constrained(Lc, comp, idx)) {
+    bc[g] = T(0);
+    return;
+  }
+  int tf[D][MX];
+  T wt[D][MX];
+  int cnt[D];
+#pragma unroll
+  for (int e = 0; e < D; ++e)
+    cnt[e] = (comp < D && e == comp) ? gl_fine_list<K, T>(idx[e], Lc.n, tb, tf[e], wt[e])
+                                     : g_fine_list<K, T>(idx[e], tb, tf[e], wt[e]);
+  T acc = T(0);
+  int j[D];
+  if (D == 2) {
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int b = 0; b < cnt[1]; ++b) {
+        j[0] = tf[0][a];
+        j[1] = tf[1][b];
+        if (is_constrained(Lf, comp, j)) continue;
+        acc += wt[0][a] * wt[1][b] * rf[flat_index(Lf, comp, j)];
+      }
+  } else {
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int b = 0; b < cnt[1]; ++b)
+        for (int c = 0; c < cnt[D - 1]; ++c) {
+          j[0] = tf[0][a];
+          j[1] = tf[1][b];
+          j[D - 1] = tf[D - 1][c];
+          if (is_constrained(Lf, comp, j)) continue;
+          acc += wt[0][a] * wt[1][b] * wt[D - 1][c] * rf[flat_index(Lf, comp, j)];
+        }
+  }
+  bc[g] = acc;
+}
+
+// x_f += P x_c on the free fine dofs.
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(256) k_prolong_add(const Lvl<D, K, T> Lf, const Lvl<D, K, T> Lc,
+                                                     const __grid_constant__ Tab<K, T> tb,
+                                                     const T* __restrict__ xc, T* __restrict__ xf) {
+  constexpr int K1 = K + 1, NG = K + 2;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= Lf.ndof) return;
+  int idx[D];
+  const int comp = decode(Lf, g, idx);
+  if (is_constrained(Lf, comp, idx)) return;
+  int sc[D][NG];
+  T wt[D][NG];
+  int cnt[D];
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    const int t = idx[e];
+    if (comp < D && e == comp) {
+      int f = t / K1;
+      if (f > Lf.n - 1) f = Lf.n - 1;
+      const int af = t - f * K1, cc = f >> 1, ch = f & 1;
+#pragma unroll
+      for (int ac = 0; ac < NG; ++ac) {
+        sc[e][ac] = cc * K1 + ac;
+        wt[e][ac] = tb.Wgl[ch][af][ac];
+      }
+      cnt[e] = NG;
+    } else {
+      const int f = t / K1, bf = t - f * K1, cc = f >> 1, ch = f & 1;
+#pragma unroll
+      for (int bc = 0; bc < K1; ++bc) {
+        sc[e][bc] = cc * K1 + bc;
+        wt[e][bc] = tb.Wg[ch][bf][bc];
+      }
+      cnt[e] = K1;
+    }
+  }
+  T acc = T(0);
+  int j[D];
+  if (D == 2) {
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int b = 0; b < cnt[1]; ++b) {
+        j[0] = sc[0][a];
+        j[1] = sc[1][b];
+        if (is_constrained(Lc, comp, j)) continue;
+        acc += wt[0][a] * wt[1][b] * xc[flat_index(Lc, comp, j)];
+      }
+  } else {
+    for (int a = 0; a < cnt[0]; ++a)
+      for (int b = 0; b < cnt[1]; ++b)
+        for (int c = 0; c < cnt[D - 1]; ++c) {
+          j[0] = sc[0][a];
+          j[1] = sc[1][b];
+          j[D - 1] = sc[D - 1][c];
+          if (is_constrained(Lc, comp, j)) continue;
+          acc += wt[0][a] * wt[1][b] * wt[D - 1][c] * xc[flat_index(Lc, comp, j)];
+        }
+  }
+  xf[g] += acc;
+}
+
+// ---------------------------------------------------------------------------
+// Dense bordered solves: Gauss-Jordan with partial pivoting, whole CTA.
+// M: n x n row-major (ldm), E: n x nrhs row-major (lde); on return E = M^{-1} E.
+// fac: scratch of n doubles (shared), red_v/red_i: blockDim.x-sized scratch.
+// Returns 0, or 1 if a pivot is exactly zero.
+// ---------------------------------------------------------------------------
+__device__ inline int gauss_jordan(double* M, int ldm, double* E, int lde, int n, int nrhs, double* fac,
+                                   double* red_v, int* red_i) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int s_piv, s_fail;
+  if (tid == 0) s_fail = 0;
+  for (int p = 0; p < n; ++p) {
+    // pivot search over rows p..n-1
+    double best = -1.0;
+    int bi = p;
+    for (int r = p + tid; r < n; r += nt) {
+      const double a = fabs(M[(int64_t)r * ldm + p]);
+      if (a > best) { best = a; bi = r; }
+    }
+    red_v[tid] = best;
+    red_i[tid] = bi;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        const double o = red_v[tid + s];
+        const int oi = red_i[tid + s];
+        if (o > red_v[tid] || (o == red_v[tid] && oi < red_i[tid])) { red_v[tid] = o; red_i[tid] = oi; }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      s_piv = red_i[0];
+      if (red_v[0] == 0.0) s_fail = 1;
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != p) {
+      for (int c = tid; c < n; c += nt) {
+        const double t = M[(int64_t)p * ldm + c];
+        M[(int64_t)p * ldm + c] = M[(int64_t)pr * ldm + c];
+        M[(int64_t)pr * ldm + c] = t;
+      }
+      for (int c = tid; c < nrhs; c += nt) {
+        const double t = E[(int64_t)p * lde + c];
+        E[(int64_t)p * lde + c] = E[(int64_t)pr * lde + c];
+        E[(int64_t)pr * lde + c] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = M[(int64_t)p * ldm + p];
+    const double inv = (piv != 0.0) ? 1.0 / piv : 0.0;
+    __syncthreads();
+    for (int c = tid; c < n; c += nt) M[(int64_t)p * ldm + c] *= inv;
+    for (int c = tid; c < nrhs; c += nt) E[(int64_t)p * lde + c] *= inv;
+    for (int r = tid; r < n; r += nt) fac[r] = (r == p) ? 0.0 : M[(int64_t)r * ldm + p];
+    __syncthreads();
+    const int64_t tot = (int64_t)n * (n + nrhs);
+    for (int64_t q = tid; q < tot; q += nt) {
+      const int r = (int)(q / (n + nrhs));
+      const int c = (int)(q - (int64_t)r * (n + nrhs));
+      const double f = fac[r];
+      if (f == 0.0) continue;
+      if (c < n) M[(int64_t)r * ldm + c] -= f * M[(int64_t)p * ldm + c];
+      else E[(int64_t)r * lde + (c - n)] -= f * E[(int64_t)p * lde + (c - n)];
+    }
+    __syncthreads();
+  }
+  return s_fail;
+}
+
+// Collects the patch matrix row of local dof `li` into M (bordered, row-major).
+template <int D, int K>
+struct PatchRowVisitor {
+  const int (&v)[D];
+  double* row;
+  __device__ PatchRowVisitor(const int (&vv)[D], double* r) : v(vv), row(r) {}
+  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], double coef) {
+    const int lc = patch_local_index<D, K>(v, comp, j);
+    if (lc >= 0) row[lc] += coef;
+  }
+};
+
+// Patch setup (Sec. 3.3): for every patch of one colour assemble the
+// restriction of A_j to the patch dofs, border it with the pressure-mean
+// functional w (w_i = integral of q_i), invert in FP64 and store the
+// velocity/pressure block S_v (column-major, column stride NVP) as TS.
+template <int D, int K, typename TS>
+__global__ void __launch_bounds__(128) k_patch_setup(const Lvl<D, K, double> L, const __grid_constant__ Tab<K, double> tb,
+                                                     int colour, int64_t count, TS* __restrict__ S,
+                                                     int* __restrict__ fail) {
+  using PS = PatchShape<D, K>;
+  constexpr int NV = PS::NV, NB = NV + 1, K1 = K + 1;
+  using SL = SLayout<NV, TS>;
+  extern __shared__ double sm[];
+  double* M = sm;                 // NB x NB
+  double* E = M + NB * NB;        // NB x NV
+  double* fac = E + NB * NV;      // NB
+  double* red_v = fac + NB;       // blockDim
+  int* red_i = reinterpret_cast<int*>(red_v + blockDim.x);
+  for (int64_t p = blockIdx.x; p < count; p += gridDim.x) {
+    int v[D];
+    patch_vertex<D>(L.n, colour, p, v);
+    for (int q = threadIdx.x; q < NB * NB; q += blockDim.x) M[q] = 0.0;
+    for (int q = threadIdx.x; q < NB * NV; q += blockDim.x) {
+      const int r = q / NV, c = q - r * NV;
+      E[q] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < NV; l += blockDim.x) {
+      int idx[D];
+      const int comp = patch_local_decode<D, K>(v, l, idx);
+      PatchRowVisitor<D, K> vis(v, M + l * NB);
+      visit_row(L, tb, comp, idx, vis);
+      if (comp == D) {
+        double w = L.s_c;
+#pragma unroll
+        for (int e = 0; e < D; ++e) w *= tb.wg[idx[e] % K1];
+        M[l * NB + NV] = w;
+        M[NV * NB + l] = w;
+      }
+    }
+    __syncthreads();
+    const int bad = gauss_jordan(M, NB, E, NV, NB, NV, fac, red_v, red_i);
+    if (bad && threadIdx.x == 0) atomicExch(fail, 1);
+    TS* Sp = S + p * SL::STRIDE;
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+      // BF16 storage: S_v = diag(s) Shat diag(s) with s_i = sqrt(|S_ii|), Shat
+      // rounded to BF16 and s kept in FP32 after the patch inverses of the colour
+      float* Dp = reinterpret_cast<float*>(S + count * SL::STRIDE) + p * SL::NVP;
+      for (int i = threadIdx.x; i < SL::NVP; i += blockDim.x) {
+        double si = (i < NV) ? sqrt(fabs(E[i * NV + i])) : 1.0;
+        if (!(si > 0.0)) si = 1.0;
+        red_v[i] = si;
+        Dp[i] = (float)si;
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < SL::NVP * NV; q += blockDim.x) {
+        const int col = q / SL::NVP, row = q - col * SL::NVP;
+        const double val = (row < NV) ? E[row * NV + col] / (red_v[row] * red_v[col]) : 0.0;
+        Sp[q] = __double2bfloat16(val);
+      }
+    } else {
+      for (int q = threadIdx.x; q < SL::NVP * NV; q += blockDim.x) {
+        const int col = q / SL::NVP, row = q - col * SL::NVP;
+        const double val = (row < NV) ? E[row * NV + col] : 0.0;
+        Sp[q] = (TS)val;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
+// for every patch v of one colour, x|_v += S_v (b - A x)|_v.
+// A warp handles GPW patches: lanes first form the local residuals (one row
+// each, matrix-free), then each group of LPP lanes streams one S_v with
+// 16-byte loads, lane q owning RG consecutive rows of delta.
+// ---------------------------------------------------------------------------
+template <typename TS, typename T>
+__device__ __forceinline__ void load_rg(const TS* p, T (&out)[SPrec<TS>::RG]);
+
+template <>
+__device__ __forceinline__ void load_rg<double, double>(const double* p, double (&o)[2]) {
+  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+  o[0] = v.x;
+  o[1] = v.y;
+}
+template <>
+__device__ __forceinline__ void load_rg<float, float>(const float* p, float (&o)[4]) {
+  const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_rg<__nv_bfloat16, float>(const __nv_bfloat16* p, float (&o)[8]) {
+  const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o[2 * i] = __uint_as_float(w[i] << 16);
+    o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
+template <int D, int K, typename T, typename TS>
+struct PassShape {
+  using PS = PatchShape<D, K>;
+  static constexpr int NV = PS::NV;
+  using SL = SLayout<NV, TS>;
+  static constexpr int RG = SL::RG;
+  static constexpr int LPP = SL::NVP / RG;   // lanes per patch
+  static constexpr int GPW = 32 / LPP;       // patches per warp
+  static constexpr int WARPS = 4;
+};
+
+template <int D, int K, typename T, typename TS>
+__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                                     int colour, int64_t count, const TS* __restrict__ S,
+                                                     T* x, const T* __restrict__ b) {
+  using PSh = PassShape<D, K, T, TS>;
+  constexpr int NV = PSh::NV, RG = PSh::RG, LPP = PSh::LPP, GPW = PSh::GPW, WARPS = PSh::WARPS;
+  using SL = typename PSh::SL;
+  __shared__ T rs[WARPS][GPW][NV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t p0 = ((int64_t)blockIdx.x * WARPS + warp) * GPW;
+  if (p0 >= count) return;
+  // local residuals
+  for (int q = lane; q < GPW * NV; q += 32) {
+    const int gi = q / NV, l = q - gi * NV;
+    const int64_t p = p0 + gi;
+    if (p < count) {
+      int v[D], idx[D];
+      patch_vertex<D>(L.n, colour, p, v);
+      const int comp = patch_local_decode<D, K>(v, l, idx);
+      const int64_t f = flat_index(L, comp, idx);
+      T rl = b[f] - apply_row(L, tb, comp, idx, x);
+      if constexpr (std::is_same<TS, __nv_bfloat16>::value)
+        rl *= reinterpret_cast<const float*>(S + count * SL::STRIDE)[p * SL::NVP + l];
+      rs[warp][gi][l] = rl;
+    }
+  }
+  __syncwarp();
+  const int gi = lane / LPP, q = lane - gi * LPP;
+  const int64_t p = p0 + gi;
+  if (gi < GPW && p < count) {
+    T acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = T(0);
+    const TS* Sp = S + p * SL::STRIDE + q * RG;
+    const T* rv = rs[warp][gi];
+#pragma unroll 8
+    for (int j = 0; j < NV; ++j) {
+      T s[RG];
+      load_rg<TS, T>(Sp + (int64_t)j * SL::NVP, s);
+      const T rj = rv[j];
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] += s[r] * rj;
+    }
+    int v[D];
+    patch_vertex<D>(L.n, colour, p, v);
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const int row = q * RG + r;
+      if (row < NV) {
+        int idx[D];
+        const int comp = patch_local_decode<D, K>(v, row, idx);
+        T dv = acc[r];
+        if constexpr (std::is_same<TS, __nv_bfloat16>::value)
+          dv *= reinterpret_cast<const float*>(S + count * SL::STRIDE)[p * SL::NVP + row];
+        x[flat_index(L, comp, idx)] += dv;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense bordered inverse of A_0 on the free dofs (FP64).
+// ---------------------------------------------------------------------------
+struct CoarseRowVisitorBase {};
+template <int D, int K>
+struct CoarseRowVisitor {
+  const Lvl<D, K, double>& L;
+  const int* g2l;
+  double* row;
+  __device__ CoarseRowVisitor(const Lvl<D, K, double>& l, const int* m, double* r) : L(l), g2l(m), row(r) {}
+  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], double coef) {
+    const int lc = g2l[flat_index(L, comp, j)];
+    if (lc >= 0) row[lc] += coef;
+  }
+};
+
+// M (nb x nb, nb = nf + 1) = [A_FF w; w^T 0]; E = [I; 0] (nb x nf).
+template <int D, int K>
+__global__ void k_coarse_assemble(const Lvl<D, K, double> L, const __grid_constant__ Tab<K, double> tb,
+                                  const int64_t* __restrict__ free_list, const int* __restrict__ g2l, int nf,
+                                  double* M, double* E) {
+  constexpr int K1 = K + 1;
+  const int nb = nf + 1;
+  for (int64_t q = threadIdx.x; q < (int64_t)nb * nb; q += blockDim.x) M[q] = 0.0;
+  for (int64_t q = threadIdx.x; q < (int64_t)nb * nf; q += blockDim.x) {
+    const int r = (int)(q / nf), c = (int)(q - (int64_t)r * nf);
+    E[q] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+    int idx[D];
+    const int comp = decode(L, free_list[i], idx);
+    CoarseRowVisitor<D, K> vis(L, g2l, M + (int64_t)i * nb);
+    visit_row(L, tb, comp, idx, vis);
+    if (comp == D) {
+      double w = L.s_c;
+#pragma unroll
+      for (int e = 0; e < D; ++e) w *= tb.wg[idx[e] % K1];
+      M[(int64_t)i * nb + nf] = w;
+      M[(int64_t)nf * nb + i] = w;
+    }
+  }
+}
+
+}  // namespace mgd

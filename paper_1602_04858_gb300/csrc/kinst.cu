@@ -1,0 +1,164 @@
+// kinst.cu -- instantiates the V-cycle kernels for one (D, K), given as
+// MG_D and MG_K on the compiler command line, and exposes their launchers.
+#include "kernels.cuh"
+#include "tables.h"
+
+#include <cmath>
+
+#ifndef MG_D
+#error "MG_D must be defined"
+#endif
+#ifndef MG_K
+#error "MG_K must be defined"
+#endif
+
+namespace mgd {
+namespace {
+
+constexpr int D = MG_D;
+constexpr int K = MG_K;
+
+struct TabPair {
+  Tab<K, double> d;
+  Tab<K, float> f;
+  TabPair() { make_tables<K>(d, f); }
+};
+const TabPair& tabs() {
+  static TabPair t;
+  return t;
+}
+
+template <typename T>
+Lvl<D, K, T> mk(const HostLevel& h) {
+  Lvl<D, K, T> l;
+  l.n = h.n;
+  l.N = h.N;
+  for (int e = 0; e <= D; ++e) l.off[e] = h.off[e];
+  l.ndof = h.ndof;
+  l.s_mu = (T)(h.mu * std::pow(h.h, D - 2));
+  l.s_c = (T)std::pow(h.h, D);
+  l.s_b = (T)std::pow(h.h, D - 1);
+  if constexpr (sizeof(T) == 8) l.c = h.c64;
+  else l.c = h.c32;
+  return l;
+}
+
+template <typename T> const Tab<K, T>& tab();
+template <> const Tab<K, double>& tab<double>() { return tabs().d; }
+template <> const Tab<K, float>& tab<float>() { return tabs().f; }
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+void apply(const HostLevel& h, int f32, const void* x, void* y, cudaStream_t s) {
+  if (f32) k_apply<D, K, float><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (float*)y);
+  else k_apply<D, K, double><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x, (double*)y);
+}
+
+void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r, int zero_c, cudaStream_t s) {
+  if (f32)
+    k_residual<D, K, float><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x,
+                                                               (const float*)b, (float*)r, zero_c);
+  else
+    k_residual<D, K, double><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x,
+                                                                (const double*)b, (double*)r, zero_c);
+}
+
+void restrict_(const HostLevel& f, const HostLevel& c, int f32, const void* rf, void* bc, cudaStream_t s) {
+  if (f32)
+    k_restrict<D, K, float><<<blocks(c.ndof, 256), 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(),
+                                                               (const float*)rf, (float*)bc);
+  else
+    k_restrict<D, K, double><<<blocks(c.ndof, 256), 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(),
+                                                                (const double*)rf, (double*)bc);
+}
+
+void prolong_add(const HostLevel& f, const HostLevel& c, int f32, const void* xc, void* xf, cudaStream_t s) {
+  if (f32)
+    k_prolong_add<D, K, float><<<blocks(f.ndof, 256), 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(),
+                                                                  (const float*)xc, (float*)xf);
+  else
+    k_prolong_add<D, K, double><<<blocks(f.ndof, 256), 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(),
+                                                                   (const double*)xc, (double*)xf);
+}
+
+template <typename TS>
+void patch_setup_t(const HostLevel& h, int colour, void* S, int* fail, cudaStream_t s) {
+  constexpr int NV = PatchShape<D, K>::NV, NB = NV + 1;
+  const int threads = 128;
+  const size_t smem = sizeof(double) * ((size_t)NB * NB + (size_t)NB * NV + NB + threads) + sizeof(int) * threads;
+  const int64_t cnt = h.count[colour];
+  if (cnt == 0) return;
+  const unsigned grid = (unsigned)(cnt < 152 * 16 ? cnt : 152 * 16);
+  k_patch_setup<D, K, TS><<<grid, threads, smem, s>>>(mk<double>(h), tab<double>(), colour, cnt, (TS*)S, fail);
+}
+
+void patch_setup(const HostLevel& h, int colour, int sprec, void* S, int* fail, cudaStream_t s) {
+  if (sprec == P64) patch_setup_t<double>(h, colour, S, fail, s);
+  else if (sprec == P32) patch_setup_t<float>(h, colour, S, fail, s);
+  else patch_setup_t<__nv_bfloat16>(h, colour, S, fail, s);
+}
+
+template <typename T, typename TS>
+void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, cudaStream_t s) {
+  using PSh = PassShape<D, K, T, TS>;
+  const int64_t cnt = h.count[colour];
+  if (cnt == 0) return;
+  const int64_t per_block = (int64_t)PSh::WARPS * PSh::GPW;
+  k_colour_pass<D, K, T, TS><<<blocks(cnt, (int)per_block), 32 * PSh::WARPS, 0, s>>>(
+      mk<T>(h), tab<T>(), colour, cnt, (const TS*)S, (T*)x, (const T*)b);
+}
+
+void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, cudaStream_t s) {
+  if (prec == P64) colour_pass_t<double, double>(h, colour, S, x, b, s);
+  else if (prec == P32) colour_pass_t<float, float>(h, colour, S, x, b, s);
+  else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, s);
+}
+
+void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
+                     cudaStream_t s) {
+  k_coarse_assemble<D, K><<<1, 512, 0, s>>>(mk<double>(h), tab<double>(), free_list, g2l, nf, M, E);
+}
+
+__global__ void k_copy_constrained(const Lvl<D, K, double> L, const double* __restrict__ r, double* __restrict__ z) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= L.ndof) return;
+  int idx[D];
+  const int comp = decode(L, g, idx);
+  if (is_constrained(L, comp, idx)) z[g] = r[g];
+}
+
+void copy_constrained(const HostLevel& h, const double* r, double* z, cudaStream_t s) {
+  k_copy_constrained<<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), r, z);
+}
+
+DKOps make_ops() {
+  DKOps o;
+  constexpr int NV = PatchShape<D, K>::NV;
+  o.nv = NV;
+  o.nvp[0] = SLayout<NV, double>::NVP;
+  o.nvp[1] = SLayout<NV, float>::NVP;
+  o.nvp[2] = SLayout<NV, __nv_bfloat16>::NVP;
+  o.s_stride[0] = SLayout<NV, double>::STRIDE;
+  o.s_stride[1] = SLayout<NV, float>::STRIDE;
+  o.s_stride[2] = SLayout<NV, __nv_bfloat16>::STRIDE;
+  o.apply = apply;
+  o.residual = residual;
+  o.restrict_ = restrict_;
+  o.prolong_add = prolong_add;
+  o.patch_setup = patch_setup;
+  o.colour_pass = colour_pass;
+  o.coarse_assemble = coarse_assemble;
+  o.copy_constrained = copy_constrained;
+  return o;
+}
+
+}  // namespace
+
+#define MG_CAT3(a, b, c) a##b##_##c
+#define MG_OPS_NAME(d, k) MG_CAT3(ops_, d, k)
+const DKOps* MG_OPS_NAME(MG_D, MG_K)() {
+  static DKOps o = make_ops();
+  return &o;
+}
+
+}  // namespace mgd

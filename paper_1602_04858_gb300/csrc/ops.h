@@ -1,0 +1,70 @@
+// ops.h -- host-side launchers of the per-(d, k) kernels, type-erased.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgd {
+
+enum Prec { P64 = 0, P32 = 1, P32B = 2 };   // matches mg_precision
+
+// Host view of one level.  Device pointers unless noted.
+struct HostLevel {
+  int d, k;
+  int n, N;              // cells per direction, n (k+1)
+  int64_t off[4];        // offsets of u_0 .. u_{d-1}, p
+  int64_t ndof, n_u, n_p;
+  double h, mu;
+  double* c64;           // per-cell coefficient
+  float* c32;
+  int sprec;             // storage precision of the patch inverses (Prec)
+  void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
+  int64_t count[27];     // patches per colour
+  void* X;               // level vectors in the working precision
+  void* B;
+  void* R;
+};
+
+struct DKOps {
+  int nv;                // patch size
+  int nvp[3];            // stored column length per storage precision (P64, P32, P32B)
+  int64_t s_stride[3];   // elements per stored patch inverse
+  // y = A x (f32 != 0: float vectors, float coefficient)
+  void (*apply)(const HostLevel&, int f32, const void* x, void* y, cudaStream_t);
+  // r = b - A x; constrained rows r = 0 (zero_c) or b - x
+  void (*residual)(const HostLevel&, int f32, const void* x, const void* b, void* r, int zero_c, cudaStream_t);
+  void (*restrict_)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* rf, void* bc, cudaStream_t);
+  void (*prolong_add)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* xc, void* xf, cudaStream_t);
+  // patch inverses of one colour into S (storage precision sprec); *fail set on a zero pivot
+  void (*patch_setup)(const HostLevel&, int colour, int sprec, void* S, int* fail, cudaStream_t);
+  // one colour pass in precision prec on vectors x, b
+  void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, cudaStream_t);
+  // bordered dense matrix of the coarsest level
+  void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
+                          double* E, cudaStream_t);
+  // z[g] = r[g] on the constrained dofs (FP64)
+  void (*copy_constrained)(const HostLevel&, const double* r, double* z, cudaStream_t);
+};
+
+const DKOps* ops_2_0();
+const DKOps* ops_2_1();
+const DKOps* ops_3_0();
+
+// --- generic kernels (generic.cu) -------------------------------------------
+void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t);
+void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t);
+void launch_f2d(const float* a, double* b, int64_t n, cudaStream_t);
+void launch_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail, cudaStream_t);
+// x = 0 on level 0, then x[free[i]] = sum_j inv[i][j] b[free[j]]  (f32: float x, b)
+void launch_coarse_apply(const double* inv, const int64_t* free_list, int nf, int64_t ndof, int f32,
+                         const void* b, void* x, cudaStream_t);
+// FP64 vector kernels for the Krylov solver
+void launch_multidot(const double* V, int64_t ld, int nvec, const double* w, int64_t n, double* partial,
+                     double* out, cudaStream_t);
+void launch_multi_axpy(double* w, const double* V, int64_t ld, int nvec, const double* coef, double sign,
+                       int64_t n, cudaStream_t);
+void launch_scale_copy(const double* a, double s, double* b, int64_t n, cudaStream_t);
+void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t);
+void launch_add_const(double* a, double s, int64_t n, cudaStream_t);
+int multidot_blocks();
+
+}  // namespace mgd

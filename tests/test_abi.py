@@ -1,0 +1,71 @@
+"""The C interface: the library builds, loads and exports every declared entry point.
+
+These tests need no GPU: they check the symbols and the argument validation
+that happens on the host before any device work.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1602_04858_gb300 import build as builder
+from paper_1602_04858_gb300 import mgdarcy
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mgdarcy.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    builder.build()
+    return mgdarcy.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "mg_setup" in names and "mg_solve" in names and "mg_vcycle" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    assert sorted(mgdarcy.API) == declared_functions()
+
+
+def _setup(lib, **kw):
+    c = kw.pop("c", np.ones((8, 8)))
+    p = mgdarcy.mg_problem(kw.get("dim", 2), kw.get("n_coarse", 2), kw.get("n_levels", 3), kw.get("degree", 0),
+                           kw.get("mu", 1.0), c.ctypes.data if c is not None else None, kw.get("precision", 0),
+                           kw.get("m_fine", 2), 1, kw.get("coarse_avg", 0))
+    h = ctypes.c_void_p()
+    return lib.mg_setup(ctypes.byref(p), None, ctypes.byref(h))
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(dim=4), 1),
+    (dict(degree=2), 7),
+    (dict(dim=3, degree=1, c=np.ones((8, 8, 8))), 7),
+    (dict(n_coarse=1), 1),
+    (dict(mu=-1.0), 1),
+    (dict(mu=float("nan")), 1),
+    (dict(precision=5), 1),
+    (dict(m_fine=0), 1),
+    (dict(c=np.full((8, 8), -1.0)), 1),
+    (dict(c=np.full((8, 8), np.inf)), 1),
+    (dict(c=None), 1),
+])
+def test_setup_rejects_bad_arguments(lib, kw, status):
+    assert _setup(lib, **kw) == status
+    assert lib.mg_last_error().decode()
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.mg_status_string(s).decode()
