@@ -169,10 +169,44 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
+    """Whole-job DoF x V-cycles/s over N independent replicas: the DoF-cycles of
+    all ranks divided by the slowest rank's time (max over ranks)."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms_max = float(t.item())
+    return dofs * steps * world / (ms_max / 1e3), ms_max
+
+
 def colour_pass_bytes(count, nv, s_inv, s_v):
     """Algorithmic bytes of one colour pass: each patch streams its n_v x n_v
     inverse once and reads b_v, x_v and writes x_v (3 n_v vector entries)."""
     return count * (nv * nv * s_inv + 3 * nv * s_v)
+
+
+def end_to_end(args, make, rh, N, barrier, dist, dev, world):
+    """The same metric through the C interface with host (pinned) buffers:
+    every step copies r host->device and z device->host inside mg_vcycle."""
+    import torch
+    G = make("fp32")
+    rp = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    rp.copy_(torch.as_tensor(rh))
+    zp = torch.empty(N, dtype=torch.float64, pin_memory=True)
+    for _ in range(2):
+        G.vcycle(rp, zp)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        G.vcycle(rp, zp)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value, _ = aggregate_throughput(N, args.steps, 1e3 * e2e_s, dist, dev)
+
+    return e2e_value
 
 
 def main():
@@ -183,6 +217,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-companions", action="store_true",
+                    help="skip the FP64/BF16 V-cycles, the solves and the end-to-end pass (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -244,11 +280,7 @@ def main():
     sampler = ClockSampler(gpu_uuid(torch, dev))
     ms, launches = time_vcycles(G, args.steps, 0)
     clocks = sampler.stop()
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = N * args.steps * world / (ms_max / 1e3)
+    value, ms_max = aggregate_throughput(N, args.steps, ms, dist, dev)
 
     # --- dominant kernel: finest-level colour pass, per-launch CUDA events ------
     J = w["n_levels"] - 1
@@ -278,19 +310,20 @@ def main():
     # --- companions: FP64 and BF16-inverse V-cycles, time to 1e-8 ----------------
     extra = {}
     solves = {}
+    e2e_value = None
     bsol = rng.standard_normal(N)
     # random load in the velocity rows, no divergence source, boundary normal dofs zero
     b_host = torch.as_tensor(bsol)
     f = torch.as_tensor(bsol[:nu], device=dev)
     g = torch.zeros(npr, dtype=torch.float64, device=dev)
-    for prec, Gh in (("fp32", G),):
+    for prec, Gh in (() if args.no_companions else (("fp32", G),)):
         x = torch.zeros_like(r)
         st, status = Gh.solve(f, g, x, tol=1e-8, maxit=400, check=False)
         solves[prec] = {"ms": st.solve_ms, "iterations": st.iterations, "rel_residual": st.rel_residual,
                         "converged": bool(st.converged)}
     del G
     torch.cuda.empty_cache()
-    for prec in ("fp64", "fp32_bf16inv"):
+    for prec in (() if args.no_companions else ("fp64", "fp32_bf16inv")):
         Gh = make(prec)
         ksteps = max(3, args.steps // 2)
         ms_p, _ = time_vcycles(Gh, ksteps, 2)
@@ -303,23 +336,10 @@ def main():
         torch.cuda.empty_cache()
 
     # --- end to end through the C interface with host buffers ------------------
-    G = make("fp32")
-    rp = torch.empty(N, dtype=torch.float64, pin_memory=True)
-    rp.copy_(torch.as_tensor(rh))
-    zp = torch.empty(N, dtype=torch.float64, pin_memory=True)
-    for _ in range(2):
-        G.vcycle(rp, zp)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        G.vcycle(rp, zp)
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if dist is not None:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = N * args.steps * world / float(e2e_t.item())
+    if not args.no_companions:
+        e2e_value = end_to_end(args, make, rh, N, barrier, dist, dev, world)
 
+    cpu = None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -332,7 +352,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(),
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N},
+                "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
+                        if e2e_value is not None else None),
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm, "traffic": None,

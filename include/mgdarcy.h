@@ -124,6 +124,14 @@ mg_status mg_vcycle(mg_handle* h, const double* r, double* z);
 mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x,
                    int use_x0, double tol, int maxit, int restart, mg_stats* stats);
 
+/* ||b - A_level x||_2 in FP64 (eq. Brinkman-weak; constrained rows give b - x),
+ * the residual that GMRES monitors (Sec. 4.1), in one pass over the level.
+ * x, b: device, length n_u + n_p of the level (-1: finest).  r: device or NULL;
+ * if not NULL it receives b - A x.  norm: host or device pointer to one double
+ * (host: the call synchronises the stream).  Uses the handle's partial-sum
+ * workspace; calls on one handle must not overlap. */
+mg_status mg_residual_norm(mg_handle* h, int level, const double* x, const double* b, double* r, double* norm);
+
 /* --- single steps of the V-cycle, for testing and measurement ---------------- */
 
 /* x <- x + R_j (b - A_j x): `steps` symmetric multiplicative Schwarz

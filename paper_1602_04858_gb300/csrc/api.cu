@@ -65,6 +65,9 @@ struct mg_handle {
   double* Z = nullptr;
   double* d_partial = nullptr;
   double* d_coef = nullptr;
+  // residual-norm partial sums (one per block of the finest level) and result
+  double* d_rnp = nullptr;
+  double* d_rn = nullptr;
   int64_t launches = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;
@@ -453,6 +456,8 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
   }
   for (int t = 0; t < 4; ++t)
     if ((st = h->alloc(&h->t64[t], h->lv[J].ndof)) != MG_OK) return cleanup(st);
+  if ((st = h->alloc(&h->d_rnp, residual_norm_blocks(h->lv[J].ndof))) != MG_OK) return cleanup(st);
+  if ((st = h->alloc(&h->d_rn, 1)) != MG_OK) return cleanup(st);
   int bad = 0;
   if (cudaMemcpyAsync(&bad, h->d_fail, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -587,6 +592,24 @@ mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x) {
   return MG_OK;
 }
 
+mg_status mg_residual_norm(mg_handle* h, int level, const double* x, const double* b, double* r, double* norm) {
+  if (!h || !x || !b || !norm) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (level < 0) level = h->J;
+  if (level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  if (!is_device_ptr(x) || !is_device_ptr(b) || (r && !is_device_ptr(r)))
+    return fail(MG_ERR_INVALID_ARG, "x, b and r must be device pointers");
+  const int64_t nb = h->ops->residual_norm(h->lv[level], x, b, r, h->d_rnp, h->stream);
+  const bool ndev = is_device_ptr(norm);
+  launch_sqrt_sum(h->d_rnp, nb, ndev ? norm : h->d_rn, h->stream);
+  h->launches += 2;
+  CU(cudaGetLastError());
+  if (!ndev) {
+    CU(cudaMemcpyAsync(norm, h->d_rn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return MG_OK;
+}
+
 // --- flexible GMRES (FP64) ---------------------------------------------------
 
 namespace {
@@ -671,14 +694,13 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     converged = true;
   }
   while (!converged) {
-    // r = b - A x
-    TRY(apply_dev(h, h->J, xd, w));
-    CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    launch_axpby(-1.0, w, 1.0, r, n, h->stream);
-    ++h->launches;
-    double beta2;
-    TRY(dot1(h, r, r, n, &beta2));
-    const double beta = std::sqrt(beta2);
+    // r = b - A x and ||r|| in one pass
+    const int64_t nb = h->ops->residual_norm(L, xd, b, r, h->d_rnp, h->stream);
+    launch_sqrt_sum(h->d_rnp, nb, h->d_rn, h->stream);
+    h->launches += 2;
+    double beta;
+    CU(cudaMemcpyAsync(&beta, h->d_rn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     relres = beta / bnorm;
     if (rel0 < 0) rel0 = relres;
     if (beta <= tol * bnorm) {

@@ -130,6 +130,21 @@ __global__ void k_multi_axpy(double* __restrict__ w, const double* __restrict__ 
   w[i] += sign * a;
 }
 
+__global__ void k_sqrt_sum(const double* __restrict__ partial, int64_t n, double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) a += partial[q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+    out[0] = sqrt(s);
+  }
+}
+
 __global__ void k_scale_copy(const double* __restrict__ a, double s, double* __restrict__ b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = s * a[i];
@@ -166,6 +181,10 @@ void launch_coarse_apply(const double* inv, const int64_t* free_list, int nf, in
 }
 
 int multidot_blocks() { return MD_BLOCKS; }
+
+void launch_sqrt_sum(const double* partial, int64_t n, double* out, cudaStream_t s) {
+  k_sqrt_sum<<<1, 1024, 0, s>>>(partial, n, out);
+}
 
 void launch_multidot(const double* V, int64_t ld, int nvec, const double* w, int64_t n, double* partial, double* out,
                      cudaStream_t s) {

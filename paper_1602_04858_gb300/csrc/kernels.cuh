@@ -39,6 +39,35 @@ __global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L, const __
   r[g] = b[g] - apply_row(L, tb, comp, idx, x);
 }
 
+// r = b - A x (stored if r != nullptr; constrained rows: b - x) and one
+// partial sum of |r|^2 per block, reduced in a fixed order afterwards.
+constexpr int RN_THREADS = 256;
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(RN_THREADS) k_residual_norm(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                                              const T* __restrict__ x, const T* __restrict__ b,
+                                                              T* __restrict__ r, double* __restrict__ partial) {
+  __shared__ double red[RN_THREADS / 32];
+  const int64_t g = (int64_t)blockIdx.x * RN_THREADS + threadIdx.x;
+  double sq = 0.0;
+  if (g < L.ndof) {
+    int idx[D];
+    const int comp = decode(L, g, idx);
+    const T rv = is_constrained(L, comp, idx) ? b[g] - x[g] : b[g] - apply_row(L, tb, comp, idx, x);
+    if (r) r[g] = rv;
+    sq = (double)rv * (double)rv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < RN_THREADS / 32; ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Transfers (Sec. 3.1): natural injection P and its transpose.
 // ---------------------------------------------------------------------------

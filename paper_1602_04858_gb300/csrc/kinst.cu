@@ -119,6 +119,13 @@ void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2
   k_coarse_assemble<D, K><<<1, 512, 0, s>>>(mk<double>(h), tab<double>(), free_list, g2l, nf, M, E);
 }
 
+int64_t residual_norm(const HostLevel& h, const double* x, const double* b, double* r, double* partial,
+                      cudaStream_t s) {
+  const int64_t nb = residual_norm_blocks(h.ndof);
+  k_residual_norm<D, K, double><<<(unsigned)nb, RN_THREADS, 0, s>>>(mk<double>(h), tab<double>(), x, b, r, partial);
+  return nb;
+}
+
 __global__ void k_copy_constrained(const Lvl<D, K, double> L, const double* __restrict__ r, double* __restrict__ z) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.ndof) return;
@@ -149,6 +156,7 @@ DKOps make_ops() {
   o.colour_pass = colour_pass;
   o.coarse_assemble = coarse_assemble;
   o.copy_constrained = copy_constrained;
+  o.residual_norm = residual_norm;
   return o;
 }
 

@@ -41,6 +41,10 @@ struct DKOps {
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);
+  // FP64 r = b - A x (r may be null) and per-block partial sums of |r|^2;
+  // returns the number of partials (blocks) written
+  int64_t (*residual_norm)(const HostLevel&, const double* x, const double* b, double* r, double* partial,
+                           cudaStream_t);
   // z[g] = r[g] on the constrained dofs (FP64)
   void (*copy_constrained)(const HostLevel&, const double* r, double* z, cudaStream_t);
 };
@@ -65,6 +69,10 @@ void launch_multi_axpy(double* w, const double* V, int64_t ld, int nvec, const d
 void launch_scale_copy(const double* a, double s, double* b, int64_t n, cudaStream_t);
 void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t);
 void launch_add_const(double* a, double s, int64_t n, cudaStream_t);
+// out[0] = sqrt(sum of partial[0..n)), fixed summation order, one block
+void launch_sqrt_sum(const double* partial, int64_t n, double* out, cudaStream_t);
+// number of partial sums k_residual_norm writes for a level of ndof dofs
+inline int64_t residual_norm_blocks(int64_t ndof) { return (ndof + 255) / 256; }
 int multidot_blocks();
 
 }  // namespace mgd

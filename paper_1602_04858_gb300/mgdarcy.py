@@ -23,7 +23,7 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_kernel_launches", "mg_status_string", "mg_last_error",
+    "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm",
 ]
 
 
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_prolong_add.argtypes = [vp, i, vp, vp]
     lib.mg_coarse_solve.argtypes = [vp, vp, vp]
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
+    lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -188,6 +189,12 @@ class Multigrid:
         cnt, nv = ctypes.c_int64(), ctypes.c_int()
         _check(load().mg_patch_info(self.h, level, colour, ctypes.byref(cnt), ctypes.byref(nv)))
         return cnt.value, nv.value
+
+    def residual_norm(self, x, b, r=None, level=-1):
+        """||b - A x||_2 (FP64) of device tensors; also stores r = b - A x if given."""
+        out = ctypes.c_double()
+        _check(load().mg_residual_norm(self.h, level, _ptr(x), _ptr(b), _ptr(r), ctypes.addressof(out)))
+        return out.value
 
     def launches(self):
         return load().mg_kernel_launches(self.h)

@@ -271,3 +271,18 @@ def test_setup_rejects_bad_coefficient_on_device():
     with pytest.raises(mgdarcy.MGError) as e:
         mgdarcy.Multigrid(2, 2, 3, 0, 1.0, dev(c))
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_residual_norm_parity(case):
+    H, G = build(case)
+    LJ = H.levels[-1]
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal(LJ.S.ndof)
+    b = rng.standard_normal(LJ.S.ndof)
+    r = torch.zeros_like(dev(x))
+    nrm = G.residual_norm(dev(x), dev(b), r)
+    ro = b - LJ.A @ x
+    bound = 1e-13 * (abs(LJ.A) @ np.abs(x) + np.abs(b))
+    assert np.all(np.abs(host(r) - ro) <= bound)
+    assert abs(nrm - np.linalg.norm(ro)) <= 1e-12 * np.linalg.norm(ro)
