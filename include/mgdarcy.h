@@ -132,6 +132,28 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x,
  * workspace; calls on one handle must not overlap. */
 mg_status mg_residual_norm(mg_handle* h, int level, const double* x, const double* b, double* r, double* norm);
 
+/* ||b - A x||_2 (FP64) of one level given by plain arguments, without any
+ * device allocation.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- an application whose own
+ * allocator owns the device (a pool that must not be bypassed), code running
+ * where cudaMalloc is not allowed or would synchronise, or a caller that has
+ * no mg_handle because mg_setup allocates.  It computes the same value as
+ * mg_residual_norm, with the per-block partial sums in a file-scope static
+ * device array of 65,536 doubles (512 KiB, held by every device that loads
+ * the library until the process exits), so the level may have at most
+ * 16,777,216 dofs; larger levels return MG_ERR_INVALID_ARG.
+ * dim, degree, n, mu: the level (n cells per direction, as in mg_problem);
+ * c: device, the level's coefficient per cell (x fastest); x, b: device,
+ * length n_u + n_p; norm: device pointer receiving one double.  Asynchronous
+ * on cuda_stream.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it: make that first call before
+ * any stream capture.  Every call shares the one array and leaves its
+ * partial sums there; each call writes every partial it reads, so nothing
+ * needs clearing, but calls that overlap on the GPU (other streams, other
+ * threads) race on the array. */
+mg_status mg_residual_norm_noalloc(int dim, int degree, int n, double mu, const double* c, const double* x,
+                                   const double* b, double* norm, void* cuda_stream);
+
 /* --- single steps of the V-cycle, for testing and measurement ---------------- */
 
 /* x <- x + R_j (b - A_j x): `steps` symmetric multiplicative Schwarz

@@ -29,6 +29,7 @@ UNITS = [
     ("kinst.cu", "k30.o", ["-DMG_D=3", "-DMG_K=0"]),
     ("generic.cu", "generic.o", []),
     ("api.cu", "api.o", []),
+    ("noalloc.cu", "noalloc.o", []),
     ("tables.cpp", "tables.o", ["-x", "cu"]),
 ]
 

@@ -44,6 +44,8 @@ mg_status fail(mg_status s, const std::string& msg) {
 
 }  // namespace
 
+mg_status mgd::set_last_error(mg_status s, const std::string& msg) { return fail(s, msg); }
+
 struct mg_handle {
   int device = 0;
   cudaStream_t stream = nullptr;

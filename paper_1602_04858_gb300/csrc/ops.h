@@ -2,6 +2,9 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <string>
+
+#include "../../include/mgdarcy.h"
 
 namespace mgd {
 
@@ -48,6 +51,9 @@ struct DKOps {
   // z[g] = r[g] on the constrained dofs (FP64)
   void (*copy_constrained)(const HostLevel&, const double* r, double* z, cudaStream_t);
 };
+
+// Records msg as the text of mg_last_error() and returns s.
+mg_status set_last_error(mg_status s, const std::string& msg);
 
 const DKOps* ops_2_0();
 const DKOps* ops_2_1();

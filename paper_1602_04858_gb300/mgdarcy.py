@@ -23,7 +23,7 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm",
+    "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
 ]
 
 
@@ -75,6 +75,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_coarse_solve.argtypes = [vp, vp, vp]
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
+    lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -111,6 +112,13 @@ def _stream_ptr(stream):
         return stream
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def residual_norm_noalloc(dim, degree, n, mu, c, x, b, norm, stream=None):
+    """mg_residual_norm_noalloc: ||b - A x||_2 into the device scalar `norm`,
+    for callers that cannot allocate device memory (no handle needed)."""
+    _check(load().mg_residual_norm_noalloc(int(dim), int(degree), int(n), float(mu), _ptr(c), _ptr(x), _ptr(b),
+                                           _ptr(norm), ctypes.c_void_p(_stream_ptr(stream))))
 
 
 class Multigrid:
