@@ -74,6 +74,14 @@ typedef struct {
   int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1):
                            0: harmonic mean of c (= arithmetic mean of the
                            permeability 1/c), 1: arithmetic mean of c          */
+  int dense_level;      /* the V-cycle B_j of levels 0..j (Sec. 3.2) is a fixed
+                           linear map; setup may store it as a dense matrix,
+                           computed by running that sub-cycle on the unit
+                           vectors, and apply it in one product instead of its
+                           sequential smoothing passes (same operator up to
+                           rounding).  -1: automatic (the largest j < J whose
+                           matrix fits 1 GiB in FP32 / 256 MiB in FP64 modes),
+                           0: never, j >= 1: level j.                          */
 } mg_problem;
 
 typedef struct {

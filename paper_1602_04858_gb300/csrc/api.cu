@@ -10,6 +10,7 @@
 #include "ops.h"
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +43,12 @@ mg_status fail(mg_status s, const std::string& msg) {
     if (s_ != MG_OK) return s_;        \
   } while (0)
 
+// Vectors a V-cycle runs on: per level, nrhs vectors stored one after another.
+struct VecSet {
+  int nrhs = 1;
+  std::vector<void*> X, B, R;
+};
+
 }  // namespace
 
 mg_status mgd::set_last_error(mg_status s, const std::string& msg) { return fail(s, msg); }
@@ -70,6 +77,12 @@ struct mg_handle {
   // residual-norm partial sums (one per block of the finest level) and result
   double* d_rnp = nullptr;
   double* d_rn = nullptr;
+  // dense operator of the sub-cycle at level Ls (Ls < 1: none):
+  // Bd[r][i] = (B_Ls e_r)_i in the working precision
+  int Ls = -1;
+  void* Bd = nullptr;
+  void* Bd_partial = nullptr;
+  VecSet main;    // the level vectors X, B, R of the single right-hand side
   int64_t launches = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;
@@ -155,14 +168,14 @@ bool host_constrained(const HostLevel& L, int64_t g) {
   return false;
 }
 
-mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, cudaStream_t stream) {
+mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, int nrhs, cudaStream_t stream) {
   HostLevel& L = h->lv[j];
   const int C = num_colours(h->d);
   for (int s = 0; s < steps; ++s) {
     for (int t = 0; t < 2 * C - 1; ++t) {
       const int col = t < C ? t : 2 * C - 2 - t;
       if (L.count[col] == 0) continue;
-      h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, stream);
+      h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, h->d_fail, nrhs, stream);
       ++h->launches;
     }
   }
@@ -171,25 +184,32 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, c
 
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
-// B_j b_j with b_j in lv[j].B; result in lv[j].X (Sec. 3.2).
-mg_status vcycle_level(mg_handle* h, int j, cudaStream_t stream) {
+// B_j b_j for the nrhs vectors of vs.B[j]; result in vs.X[j] (Sec. 3.2).  With
+// use_dense, the sub-cycle at level Ls is the precomputed dense operator.
+mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cudaStream_t stream) {
   HostLevel& L = h->lv[j];
+  const int nr = vs.nrhs;
+  if (use_dense && j == h->Ls) {
+    launch_dense_apply(h->f32(), h->Bd, L.ndof, vs.B[j], vs.X[j], h->Bd_partial, stream);
+    h->launches += 2;
+    return MG_OK;
+  }
   if (j == 0) {
-    launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, L.ndof, h->f32(), L.B, L.X, stream);
+    launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, L.ndof, h->f32(), vs.B[0], vs.X[0], nr, stream);
     ++h->launches;
     return MG_OK;
   }
-  CU(cudaMemsetAsync(L.X, 0, L.ndof * h->vbytes(), stream));
+  CU(cudaMemsetAsync(vs.X[j], 0, L.ndof * nr * h->vbytes(), stream));
   const int m = m_of(h, j);
-  TRY(smooth_steps(h, j, L.X, L.B, m, stream));
-  h->ops->residual(L, h->f32(), L.X, L.B, L.R, 1, stream);
+  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], m, nr, stream));
+  h->ops->residual(L, h->f32(), vs.X[j], vs.B[j], vs.R[j], 1, nr, stream);
   HostLevel& Lc = h->lv[j - 1];
-  h->ops->restrict_(L, Lc, h->f32(), L.R, Lc.B, stream);
+  h->ops->restrict_(L, Lc, h->f32(), vs.R[j], vs.B[j - 1], nr, stream);
   h->launches += 2;
-  TRY(vcycle_level(h, j - 1, stream));
-  h->ops->prolong_add(L, Lc, h->f32(), Lc.X, L.X, stream);
+  TRY(vcycle_level(h, j - 1, vs, use_dense, stream));
+  h->ops->prolong_add(L, Lc, h->f32(), vs.X[j - 1], vs.X[j], nr, stream);
   ++h->launches;
-  TRY(smooth_steps(h, j, L.X, L.B, m, stream));
+  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], m, nr, stream));
   return MG_OK;
 }
 
@@ -205,7 +225,7 @@ mg_status vcycle_graph(mg_handle* h) {
       cudaStreamDestroy(cap);
       return fail(MG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
     }
-    mg_status st = vcycle_level(h, h->J, cap);
+    mg_status st = vcycle_level(h, h->J, h->main, true, cap);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
@@ -304,6 +324,7 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
   if (p->precision < 0 || p->precision > 2) return fail(MG_ERR_INVALID_ARG, "bad precision");
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
+  if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -379,6 +400,12 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
     L.sprec = (h->prec == P32B && j < J) ? P32 : h->prec;
     if (j == 0) continue;
     const size_t sb = (L.sprec == P64) ? 8 : (L.sprec == P32 ? 4 : 2);
+    {
+      int64_t np = 0;
+      for (int col = 0; col < C; ++col) np += L.count[col];
+      // levels whose inverses would crowd the L2 cache stream them evict-first
+      L.s_evict_first = (double)np * h->ops->s_stride[L.sprec] * sb > 48.0e6 ? 1 : 0;
+    }
     for (int col = 0; col < C; ++col) {
       if (L.count[col] == 0) continue;
       size_t bytes = (size_t)L.count[col] * h->ops->s_stride[L.sprec] * sb;
@@ -388,6 +415,12 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
       h->ops->patch_setup(L, col, L.sprec, q, h->d_fail, h->stream);
       ++h->launches;
     }
+  }
+  h->main.nrhs = 1;
+  for (int j = 0; j <= J; ++j) {
+    h->main.X.push_back(h->lv[j].X);
+    h->main.B.push_back(h->lv[j].B);
+    h->main.R.push_back(h->lv[j].R);
   }
   // coarsest level: dense bordered inverse on the free dofs
   {
@@ -455,6 +488,60 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
     }
     if ((st = h->alloc(&h->d_pw, L.n_p)) != MG_OK) return cleanup(st);
     cudaMemcpyAsync(h->d_pw, w.data(), L.n_p * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  }
+  // dense operator of the sub-cycle at level Ls
+  {
+    int Ls = p->dense_level;
+    if (Ls < 0) {
+      const double budget = (h->prec == P64) ? 256.0 * (1 << 20) : 1024.0 * (1 << 20);
+      Ls = 0;
+      for (int j = 1; j < J; ++j)
+        if ((double)h->lv[j].ndof * h->lv[j].ndof * h->vbytes() <= budget) Ls = j;
+    }
+    if (Ls >= 1) {
+      h->Ls = Ls;
+      const int64_t n = h->lv[Ls].ndof;
+      if ((st = h->alloc((char**)&h->Bd, (size_t)n * n * h->vbytes())) != MG_OK) return cleanup(st);
+      if ((st = h->alloc((char**)&h->Bd_partial, (size_t)DENSE_CHUNKS * n * h->vbytes())) != MG_OK)
+        return cleanup(st);
+      // columns in chunks: every level <= Ls holds chunk vectors X, B, R
+      int64_t per_rhs = 0;
+      for (int j = 0; j <= Ls; ++j) per_rhs += 3 * h->lv[j].ndof * (int64_t)h->vbytes();
+      const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)(2.0e9 / per_rhs)));
+      VecSet bs;
+      std::vector<void*> tmp;
+      for (int j = 0; j <= Ls; ++j) {
+        void *a, *b2, *c2;
+        const size_t bytes = (size_t)h->lv[j].ndof * chunk * h->vbytes();
+        if ((st = h->alloc((char**)&a, bytes)) != MG_OK) return cleanup(st);
+        if ((st = h->alloc((char**)&b2, bytes)) != MG_OK) return cleanup(st);
+        if ((st = h->alloc((char**)&c2, bytes)) != MG_OK) return cleanup(st);
+        bs.X.push_back(a);
+        bs.B.push_back(b2);
+        bs.R.push_back(c2);
+        tmp.insert(tmp.end(), {a, b2, c2});
+      }
+      for (int64_t c0 = 0; c0 < n; c0 += chunk) {
+        const int nc = (int)std::min<int64_t>(chunk, n - c0);
+        bs.nrhs = nc;
+        launch_set_units(h->f32(), bs.B[Ls], n, c0, nc, h->stream);
+        ++h->launches;
+        if ((st = vcycle_level(h, Ls, bs, false, h->stream)) != MG_OK) return cleanup(st);
+        if (cudaMemcpyAsync((char*)h->Bd + (size_t)c0 * n * h->vbytes(), bs.X[Ls], (size_t)nc * n * h->vbytes(),
+                            cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+          return cleanup(fail(MG_ERR_CUDA, "copy of the dense sub-cycle failed"));
+      }
+      if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return cleanup(fail(MG_ERR_CUDA, std::string("dense sub-cycle: ") + cudaGetErrorString(cudaGetLastError())));
+      for (auto it = h->allocs.begin(); it != h->allocs.end();) {
+        if (std::find(tmp.begin(), tmp.end(), *it) != tmp.end()) {
+          cudaFree(*it);
+          it = h->allocs.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
   }
   for (int t = 0; t < 4; ++t)
     if ((st = h->alloc(&h->t64[t], h->lv[J].ndof)) != MG_OK) return cleanup(st);
@@ -554,7 +641,7 @@ mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int ste
   if (!h || level < 1 || level > h->J || !x || !b || steps < 0) return fail(MG_ERR_INVALID_ARG, "bad argument");
   TRY(mg_level_load(h, level, x, b));
   HostLevel& L = h->lv[level];
-  TRY(smooth_steps(h, level, L.X, L.B, steps, h->stream));
+  TRY(smooth_steps(h, level, L.X, L.B, steps, 1, h->stream));
   TRY(mg_level_store(h, level, x));
   return MG_OK;
 }
@@ -564,7 +651,7 @@ mg_status mg_colour_pass(mg_handle* h, int level, int colour) {
     return fail(MG_ERR_INVALID_ARG, "bad level or colour");
   HostLevel& L = h->lv[level];
   if (L.count[colour] == 0) return MG_OK;
-  h->ops->colour_pass(L, colour, L.sprec, L.S[colour], L.X, L.B, h->stream);
+  h->ops->colour_pass(L, colour, L.sprec, L.S[colour], L.X, L.B, h->d_fail, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -572,7 +659,7 @@ mg_status mg_colour_pass(mg_handle* h, int level, int colour) {
 
 mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_coarse) {
   if (!h || level < 1 || level > h->J || !r_fine || !b_coarse) return fail(MG_ERR_INVALID_ARG, "bad argument");
-  h->ops->restrict_(h->lv[level], h->lv[level - 1], 0, r_fine, b_coarse, h->stream);
+  h->ops->restrict_(h->lv[level], h->lv[level - 1], 0, r_fine, b_coarse, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -580,7 +667,7 @@ mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_c
 
 mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double* x_fine) {
   if (!h || level < 1 || level > h->J || !x_coarse || !x_fine) return fail(MG_ERR_INVALID_ARG, "bad argument");
-  h->ops->prolong_add(h->lv[level], h->lv[level - 1], 0, x_coarse, x_fine, h->stream);
+  h->ops->prolong_add(h->lv[level], h->lv[level - 1], 0, x_coarse, x_fine, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -588,7 +675,7 @@ mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double
 
 mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x) {
   if (!h || !b || !x) return fail(MG_ERR_INVALID_ARG, "bad argument");
-  launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, h->lv[0].ndof, 0, b, x, h->stream);
+  launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, h->lv[0].ndof, 0, b, x, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -804,6 +891,9 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     stats->removed_flux = gsum;
     stats->solve_ms = ms;
   }
+  int flag = 0;
+  CU(cudaMemcpy(&flag, h->d_fail, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag == 2) return fail(MG_ERR_DEVICE_TIMEOUT, "a patch-inverse copy did not complete in time");
   if (result != MG_OK) return result;
   if (!converged) return fail(MG_ERR_NOT_CONVERGED, "GMRES reached maxit");
   return MG_OK;

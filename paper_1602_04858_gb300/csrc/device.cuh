@@ -146,7 +146,7 @@ __device__ __forceinline__ void visit_u_row(const Lvl<D, K, T>& L, const Tab<K, 
   for (int cx = lo; cx <= hi; ++cx) {
     const int a = t - cx * K1;
     cell[i] = cx;
-    const T cK = L.c[cell_linear(L, cell)];
+    const T cK = vis.cell_c(cell);
 #pragma unroll
     for (int ap = 0; ap < NG; ++ap) {
       const int tp = cx * K1 + ap;
@@ -224,6 +224,9 @@ __device__ __forceinline__ void visit_row(const Lvl<D, K, T>& L, const Tab<K, T>
   else visit_p_row(L, tb, idx, vis);
 }
 
+// Visitors receive every (column, coefficient) of a row through operator()
+// and supply the cell coefficient of the mass term through cell_c().
+
 // Accumulates coef * x[column].
 template <int D, int K, typename T>
 struct DotVisitor {
@@ -234,6 +237,7 @@ struct DotVisitor {
   __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
     acc += coef * x[flat_index(L, comp, j)];
   }
+  __device__ __forceinline__ T cell_c(const int (&cell)[D]) const { return L.c[cell_linear(L, cell)]; }
 };
 
 // (A x) of one row; the identity on constrained rows.

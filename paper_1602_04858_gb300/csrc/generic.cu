@@ -50,8 +50,10 @@ __global__ void k_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail)
 // Coarsest-level solve: x = 0, then x[free_i] = sum_j inv_ij b[free_j] (FP64 arithmetic).
 template <typename T>
 __global__ void k_coarse_apply(const double* __restrict__ inv, const int64_t* __restrict__ free_list, int nf,
-                               int64_t ndof, const T* __restrict__ b, T* __restrict__ x) {
+                               int64_t ndof, const T* __restrict__ b, T* __restrict__ x, int64_t vs) {
   extern __shared__ double bs[];
+  b += blockIdx.x * vs;   // one block per right-hand side
+  x += blockIdx.x * vs;
   for (int64_t g = threadIdx.x; g < ndof; g += blockDim.x) x[g] = T(0);
   for (int j = threadIdx.x; j < nf; j += blockDim.x) bs[j] = (double)b[free_list[j]];
   __syncthreads();
@@ -158,7 +160,56 @@ __global__ void k_add_const(double* __restrict__ a, double s, int64_t n) {
   if (i < n) a[i] += s;
 }
 
+template <typename T>
+__global__ void k_set_units(T* __restrict__ B, int64_t ndof, int64_t c0, int nc) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ndof * nc) return;
+  const int64_t r = g / ndof, i = g - r * ndof;
+  B[g] = (i == c0 + r) ? T(1) : T(0);
+}
+
+// Column-blocked z = Bd^T b: block (x, y) sums rows r of chunk y for DENSE_THREADS entries i.
+constexpr int DENSE_THREADS = 256;
+template <typename T>
+__global__ void __launch_bounds__(DENSE_THREADS) k_dense_partial(const T* __restrict__ Bd, int64_t n,
+                                                                 const T* __restrict__ b, T* __restrict__ partial) {
+  const int64_t i = (int64_t)blockIdx.x * DENSE_THREADS + threadIdx.x;
+  const int64_t per = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = blockIdx.y * per, r1 = (r0 + per < n) ? r0 + per : n;
+  T acc = T(0);
+  if (i < n)
+    for (int64_t r = r0; r < r1; ++r) acc += Bd[r * n + i] * b[r];
+  if (i < n) partial[blockIdx.y * n + i] = acc;
+}
+
+template <typename T>
+__global__ void k_dense_reduce(const T* __restrict__ partial, int chunks, int64_t n, T* __restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc = T(0);
+  for (int y = 0; y < chunks; ++y) acc += partial[y * n + i];
+  z[i] = acc;
+}
+
 }  // namespace
+
+void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaStream_t s) {
+  const unsigned g = blocks(ndof * nc, 256);
+  if (f32) k_set_units<float><<<g, 256, 0, s>>>((float*)B, ndof, c0, nc);
+  else k_set_units<double><<<g, 256, 0, s>>>((double*)B, ndof, c0, nc);
+}
+
+void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, cudaStream_t s) {
+  const dim3 grid(blocks(n, DENSE_THREADS), DENSE_CHUNKS);
+  if (f32) {
+    k_dense_partial<float><<<grid, DENSE_THREADS, 0, s>>>((const float*)Bd, n, (const float*)b, (float*)partial);
+    k_dense_reduce<float><<<blocks(n, 256), 256, 0, s>>>((const float*)partial, DENSE_CHUNKS, n, (float*)z);
+  } else {
+    k_dense_partial<double><<<grid, DENSE_THREADS, 0, s>>>((const double*)Bd, n, (const double*)b,
+                                                           (double*)partial);
+    k_dense_reduce<double><<<blocks(n, 256), 256, 0, s>>>((const double*)partial, DENSE_CHUNKS, n, (double*)z);
+  }
+}
 
 void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t s) {
   const int64_t tot = (int64_t)nc * nc * (d == 3 ? nc : 1);
@@ -174,10 +225,10 @@ void launch_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail, cudaS
 }
 
 void launch_coarse_apply(const double* inv, const int64_t* free_list, int nf, int64_t ndof, int f32, const void* b,
-                         void* x, cudaStream_t s) {
+                         void* x, int nrhs, cudaStream_t s) {
   const size_t smem = sizeof(double) * (size_t)nf;
-  if (f32) k_coarse_apply<float><<<1, 512, smem, s>>>(inv, free_list, nf, ndof, (const float*)b, (float*)x);
-  else k_coarse_apply<double><<<1, 512, smem, s>>>(inv, free_list, nf, ndof, (const double*)b, (double*)x);
+  if (f32) k_coarse_apply<float><<<nrhs, 512, smem, s>>>(inv, free_list, nf, ndof, (const float*)b, (float*)x, ndof);
+  else k_coarse_apply<double><<<nrhs, 512, smem, s>>>(inv, free_list, nf, ndof, (const double*)b, (double*)x, ndof);
 }
 
 int multidot_blocks() { return MD_BLOCKS; }

@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include "async.cuh"
 #include "device.cuh"
 #include "ops.h"
 
@@ -24,12 +25,16 @@ __global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const __gri
 }
 
 // r = b - A x on free rows; constrained rows: r = 0 (zero_c) or b - x.
+// Batched over right-hand sides: blockIdx.y selects the vector, stride vs.
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
                                                   const T* __restrict__ x, const T* __restrict__ b,
-                                                  T* __restrict__ r, int zero_c) {
+                                                  T* __restrict__ r, int zero_c, int64_t vs) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.ndof) return;
+  x += blockIdx.y * vs;
+  b += blockIdx.y * vs;
+  r += blockIdx.y * vs;
   int idx[D];
   const int comp = decode(L, g, idx);
   if (is_constrained(L, comp, idx)) {
@@ -119,10 +124,13 @@ __device__ __forceinline__ int g_fine_list(int sc, const Tab<K, T>& tb, int* tf,
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(256) k_restrict(const Lvl<D, K, T> Lf, const Lvl<D, K, T> Lc,
                                                   const __grid_constant__ Tab<K, T> tb,
-                                                  const T* __restrict__ rf, T* __restrict__ bc) {
+                                                  const T* __restrict__ rf, T* __restrict__ bc, int64_t vsf,
+                                                  int64_t vsc) {
   constexpr int K1 = K + 1, MX = 4 * K1 + 2;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Lc.ndof) return;
+  rf += blockIdx.y * vsf;
+  bc += blockIdx.y * vsc;
   int idx[D];
   const int comp = decode(Lc, g, idx);
   if (is_constrained(Lc, comp, idx)) {
@@ -164,10 +172,13 @@ __global__ void __launch_bounds__(256) k_restrict(const Lvl<D, K, T> Lf, const L
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(256) k_prolong_add(const Lvl<D, K, T> Lf, const Lvl<D, K, T> Lc,
                                                      const __grid_constant__ Tab<K, T> tb,
-                                                     const T* __restrict__ xc, T* __restrict__ xf) {
+                                                     const T* __restrict__ xc, T* __restrict__ xf, int64_t vsc,
+                                                     int64_t vsf) {
   constexpr int K1 = K + 1, NG = K + 2;
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= Lf.ndof) return;
+  xc += blockIdx.y * vsc;
+  xf += blockIdx.y * vsf;
   int idx[D];
   const int comp = decode(Lf, g, idx);
   if (is_constrained(Lf, comp, idx)) return;
@@ -294,13 +305,15 @@ __device__ inline int gauss_jordan(double* M, int ldm, double* E, int lde, int n
 // Collects the patch matrix row of local dof `li` into M (bordered, row-major).
 template <int D, int K>
 struct PatchRowVisitor {
+  const Lvl<D, K, double>& L;
   const int (&v)[D];
   double* row;
-  __device__ PatchRowVisitor(const int (&vv)[D], double* r) : v(vv), row(r) {}
+  __device__ PatchRowVisitor(const Lvl<D, K, double>& l, const int (&vv)[D], double* r) : L(l), v(vv), row(r) {}
   __device__ __forceinline__ void operator()(int comp, const int (&j)[D], double coef) {
     const int lc = patch_local_index<D, K>(v, comp, j);
     if (lc >= 0) row[lc] += coef;
   }
+  __device__ __forceinline__ double cell_c(const int (&cell)[D]) const { return L.c[cell_linear(L, cell)]; }
 };
 
 // Patch setup (Sec. 3.3): for every patch of one colour assemble the
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(128) k_patch_setup(const Lvl<D, K, double> L, 
     for (int l = threadIdx.x; l < NV; l += blockDim.x) {
       int idx[D];
       const int comp = patch_local_decode<D, K>(v, l, idx);
-      PatchRowVisitor<D, K> vis(v, M + l * NB);
+      PatchRowVisitor<D, K> vis(L, v, M + l * NB);
       visit_row(L, tb, comp, idx, vis);
       if (comp == D) {
         double w = L.s_c;
@@ -373,33 +386,27 @@ __global__ void __launch_bounds__(128) k_patch_setup(const Lvl<D, K, double> L, 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
-// for every patch v of one colour, x|_v += S_v (b - A x)|_v.
-// A warp handles GPW patches: lanes first form the local residuals (one row
-// each, matrix-free), then each group of LPP lanes streams one S_v with
-// 16-byte loads, lane q owning RG consecutive rows of delta.
-// ---------------------------------------------------------------------------
+// 16-byte shared-memory load of RG consecutive stored entries, widened to T.
 template <typename TS, typename T>
-__device__ __forceinline__ void load_rg(const TS* p, T (&out)[SPrec<TS>::RG]);
+__device__ __forceinline__ void load_rg_smem(const TS* p, T (&out)[SPrec<TS>::RG]);
 
 template <>
-__device__ __forceinline__ void load_rg<double, double>(const double* p, double (&o)[2]) {
-  const double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+__device__ __forceinline__ void load_rg_smem<double, double>(const double* p, double (&o)[2]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
   o[0] = v.x;
   o[1] = v.y;
 }
 template <>
-__device__ __forceinline__ void load_rg<float, float>(const float* p, float (&o)[4]) {
-  const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+__device__ __forceinline__ void load_rg_smem<float, float>(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
   o[0] = v.x;
   o[1] = v.y;
   o[2] = v.z;
   o[3] = v.w;
 }
 template <>
-__device__ __forceinline__ void load_rg<__nv_bfloat16, float>(const __nv_bfloat16* p, float (&o)[8]) {
-  const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+__device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bfloat16* p, float (&o)[8]) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
   const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -408,62 +415,206 @@ __device__ __forceinline__ void load_rg<__nv_bfloat16, float>(const __nv_bfloat1
   }
 }
 
+// ---------------------------------------------------------------------------
+// Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
+// for every patch v of one colour, x|_v += S_v (b - A x)|_v.
+//
+// A warp owns GPW patches.  Lane 0 first issues one bulk asynchronous copy
+// per patch of its stored inverse S_v into shared memory (S_v does not depend
+// on earlier passes, so this happens before the programmatic-dependent-launch
+// wait and overlaps the previous pass).  The lanes then gather each patch's
+// window of x (every column its rows touch), its b rows and its 2^D cell
+// coefficients into shared memory, form the local residual rows from the
+// matrix-free stencil, wait for S_v, and apply it: a group of LPP lanes per
+// patch, lane q owning RG consecutive rows of delta.
+// ---------------------------------------------------------------------------
 template <int D, int K, typename T, typename TS>
 struct PassShape {
   using PS = PatchShape<D, K>;
+  static constexpr int K1 = K + 1;
   static constexpr int NV = PS::NV;
   using SL = SLayout<NV, TS>;
   static constexpr int RG = SL::RG;
-  static constexpr int LPP = SL::NVP / RG;   // lanes per patch
-  static constexpr int GPW = 32 / LPP;       // patches per warp
+  static constexpr int NVP = SL::NVP;
+  static constexpr int LPP = NVP / RG;      // lanes per patch in the product
+  static constexpr int GPW = 32 / LPP;      // patches per warp
   static constexpr int WARPS = 4;
+  static constexpr int PPB = WARPS * GPW;   // patches per block
+  static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
+  // window of x: velocity component i spans WA nodes along x_i and WB across,
+  // the pressure WP per direction
+  static constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
+  static constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
+  static constexpr int WIN = D * WU + ((D == 2) ? WP * WP : WP * WP * WP);
+  static constexpr int NC = 1 << D;
+  static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
+  static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
+  static constexpr int T_PER_PATCH = WIN + 2 * NV + NC;   // window, b rows, residual, c
+  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + (size_t)PPB * T_PER_PATCH * sizeof(T) +
+                                 (size_t)WARPS * sizeof(uint64_t) + 16;
+};
+
+// Window position of (comp, idx) for the patch at vertex v.
+template <int D, int K>
+__device__ __forceinline__ int win_index(const int (&v)[D], int comp, const int (&idx)[D]) {
+  constexpr int K1 = K + 1;
+  constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
+  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
+  int l = 0, stride = 1;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    const bool own = comp < D && e == comp;
+    const int o = (comp < D && !own) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
+    const int m = (comp == D) ? WP : (own ? WA : WB);
+    l += (idx[e] - o) * stride;
+    stride *= m;
+  }
+  return comp * WU + l;
+}
+
+// Inverse of win_index: window position -> (comp, node); inside = in the domain.
+template <int D, int K>
+__device__ __forceinline__ int win_decode(const int (&v)[D], int N, int w, int (&idx)[D], bool& inside) {
+  constexpr int K1 = K + 1;
+  constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
+  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
+  const int comp = (w / WU < D) ? w / WU : D;
+  int r = w - comp * WU;
+  inside = true;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    const bool own = comp < D && e == comp;
+    const int o = (comp < D && !own) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
+    const int m = (comp == D) ? WP : (own ? WA : WB);
+    idx[e] = o + r % m;
+    r /= m;
+    const int hi = own ? N : N - 1;
+    if (idx[e] < 0 || idx[e] > hi) inside = false;
+  }
+  return comp;
+}
+
+template <int D, int K, typename T>
+struct WinVisitor {
+  const int (&v)[D];
+  const T* win;
+  const T* cw;
+  T acc;
+  __device__ WinVisitor(const int (&vv)[D], const T* w, const T* c) : v(vv), win(w), cw(c), acc(T(0)) {}
+  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
+    acc += coef * win[win_index<D, K>(v, comp, j)];
+  }
+  __device__ __forceinline__ T cell_c(const int (&cell)[D]) const {
+    int l = 0;
+#pragma unroll
+    for (int e = 0; e < D; ++e) l |= (cell[e] - (v[e] - 1)) << e;
+    return cw[l];
+  }
 };
 
 template <int D, int K, typename T, typename TS>
 __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
                                                      int colour, int64_t count, const TS* __restrict__ S,
-                                                     T* x, const T* __restrict__ b) {
-  using PSh = PassShape<D, K, T, TS>;
-  constexpr int NV = PSh::NV, RG = PSh::RG, LPP = PSh::LPP, GPW = PSh::GPW, WARPS = PSh::WARPS;
-  using SL = typename PSh::SL;
-  __shared__ T rs[WARPS][GPW][NV];
+                                                     T* x, const T* __restrict__ b, int evict_first,
+                                                     int* __restrict__ err, int64_t vs) {
+  using P = PassShape<D, K, T, TS>;
+  x += blockIdx.y * vs;
+  b += blockIdx.y * vs;
+  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* s_inv = smem;                                                   // PPB x S_BYTES
+  float* s_scale = reinterpret_cast<float*>(smem + (size_t)PPB * P::S_BYTES);    // PPB x NVP (BF16 only)
+  T* s_t = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(
+      (reinterpret_cast<uintptr_t>(s_t + (size_t)PPB * P::T_PER_PATCH) + 15) & ~uintptr_t(15));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t p0 = ((int64_t)blockIdx.x * WARPS + warp) * GPW;
-  if (p0 >= count) return;
-  // local residuals
-  for (int q = lane; q < GPW * NV; q += 32) {
-    const int gi = q / NV, l = q - gi * NV;
-    const int64_t p = p0 + gi;
-    if (p < count) {
-      int v[D], idx[D];
-      patch_vertex<D>(L.n, colour, p, v);
+  const int64_t pw = ((int64_t)blockIdx.x * P::WARPS + warp) * GPW;   // first patch of this warp
+  const int nmine = (pw >= count) ? 0 : (int)((count - pw) < GPW ? (count - pw) : GPW);
+  uint64_t* bar = s_bar + warp;
+  // 1. stream the inverses of this warp's patches into shared memory
+  if (lane == 0 && nmine > 0) {
+    mbar_init(bar, 1);
+    const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
+    mbar_arrive_expect_tx(bar, (uint32_t)(nmine * (P::S_BYTES + P::SC_BYTES)));
+    for (int g = 0; g < nmine; ++g) {
+      const int slot = warp * GPW + g;
+      bulk_load(s_inv + (size_t)slot * P::S_BYTES, S + (pw + g) * P::SL::STRIDE, P::S_BYTES, bar, pol);
+      if constexpr (P::BF)
+        bulk_load(s_scale + (size_t)slot * NVP,
+                  reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + (pw + g) * NVP, P::SC_BYTES, bar, pol);
+    }
+  }
+  pdl_launch_dependents();
+  pdl_wait();   // x and b come from the preceding kernels
+  __syncwarp();
+  if (nmine == 0) return;
+  // 2. gather windows, b rows and cell coefficients
+  T* tw = s_t + (size_t)(warp * GPW) * P::T_PER_PATCH;
+  for (int q = lane; q < nmine * P::WIN; q += 32) {
+    const int g = q / P::WIN, w = q - g * P::WIN;
+    int v[D], idx[D];
+    patch_vertex<D>(L.n, colour, pw + g, v);
+    bool inside;
+    const int comp = win_decode<D, K>(v, L.N, w, idx, inside);
+    tw[g * P::T_PER_PATCH + w] = inside ? x[flat_index(L, comp, idx)] : T(0);
+  }
+  for (int q = lane; q < nmine * (NV + P::NC); q += 32) {
+    const int g = q / (NV + P::NC), l = q - g * (NV + P::NC);
+    int v[D];
+    patch_vertex<D>(L.n, colour, pw + g, v);
+    T* base = tw + g * P::T_PER_PATCH + P::WIN;
+    if (l < NV) {
+      int idx[D];
       const int comp = patch_local_decode<D, K>(v, l, idx);
-      const int64_t f = flat_index(L, comp, idx);
-      T rl = b[f] - apply_row(L, tb, comp, idx, x);
-      if constexpr (std::is_same<TS, __nv_bfloat16>::value)
-        rl *= reinterpret_cast<const float*>(S + count * SL::STRIDE)[p * SL::NVP + l];
-      rs[warp][gi][l] = rl;
+      base[l] = b[flat_index(L, comp, idx)];
+    } else {
+      const int cl = l - NV;
+      int cell[D];
+#pragma unroll
+      for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cl >> e) & 1);
+      base[2 * NV + cl] = L.c[cell_linear(L, cell)];
     }
   }
   __syncwarp();
-  const int gi = lane / LPP, q = lane - gi * LPP;
-  const int64_t p = p0 + gi;
-  if (gi < GPW && p < count) {
+  // 3. local residual rows (b - A x)|_v from the window
+  for (int q = lane; q < nmine * NV; q += 32) {
+    const int g = q / NV, l = q - g * NV;
+    int v[D], idx[D];
+    patch_vertex<D>(L.n, colour, pw + g, v);
+    const int comp = patch_local_decode<D, K>(v, l, idx);
+    T* base = tw + g * P::T_PER_PATCH;
+    WinVisitor<D, K, T> vis(v, base, base + P::WIN + 2 * NV);
+    visit_row(L, tb, comp, idx, vis);
+    base[P::WIN + NV + l] = base[P::WIN + l] - vis.acc;
+  }
+  __syncwarp();
+  // 4. wait for the inverses (bounded), then delta = S_v r
+  const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
+  if (!ok) {
+    if (lane == 0) atomicExch(err, 2);
+    mbar_wait_bounded(bar, 0, 2000000000ull);   // let copies in flight land before the block exits
+    return;
+  }
+  const int g = lane / LPP, q = lane - g * LPP;
+  if (g < nmine) {
+    const int slot = warp * GPW + g;
+    const TS* Sg = reinterpret_cast<const TS*>(s_inv + (size_t)slot * P::S_BYTES) + q * RG;
+    const T* rv = tw + g * P::T_PER_PATCH + P::WIN + NV;
+    const float* sc = s_scale + (size_t)slot * NVP;
     T acc[RG];
 #pragma unroll
     for (int r = 0; r < RG; ++r) acc[r] = T(0);
-    const TS* Sp = S + p * SL::STRIDE + q * RG;
-    const T* rv = rs[warp][gi];
-#pragma unroll 8
+#pragma unroll 4
     for (int j = 0; j < NV; ++j) {
-      T s[RG];
-      load_rg<TS, T>(Sp + (int64_t)j * SL::NVP, s);
-      const T rj = rv[j];
+      T sv[RG];
+      load_rg_smem<TS, T>(Sg + j * NVP, sv);
+      T rj = rv[j];
+      if constexpr (P::BF) rj *= sc[j];
 #pragma unroll
-      for (int r = 0; r < RG; ++r) acc[r] += s[r] * rj;
+      for (int r = 0; r < RG; ++r) acc[r] += sv[r] * rj;
     }
     int v[D];
-    patch_vertex<D>(L.n, colour, p, v);
+    patch_vertex<D>(L.n, colour, pw + g, v);
 #pragma unroll
     for (int r = 0; r < RG; ++r) {
       const int row = q * RG + r;
@@ -471,8 +622,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
         int idx[D];
         const int comp = patch_local_decode<D, K>(v, row, idx);
         T dv = acc[r];
-        if constexpr (std::is_same<TS, __nv_bfloat16>::value)
-          dv *= reinterpret_cast<const float*>(S + count * SL::STRIDE)[p * SL::NVP + row];
+        if constexpr (P::BF) dv *= sc[row];
         x[flat_index(L, comp, idx)] += dv;
       }
     }
@@ -493,6 +643,7 @@ struct CoarseRowVisitor {
     const int lc = g2l[flat_index(L, comp, j)];
     if (lc >= 0) row[lc] += coef;
   }
+  __device__ __forceinline__ double cell_c(const int (&cell)[D]) const { return L.c[cell_linear(L, cell)]; }
 };
 
 // M (nb x nb, nb = nf + 1) = [A_FF w; w^T 0]; E = [I; 0] (nb x nf).

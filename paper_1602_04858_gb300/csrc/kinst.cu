@@ -54,31 +54,36 @@ void apply(const HostLevel& h, int f32, const void* x, void* y, cudaStream_t s) 
   else k_apply<D, K, double><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x, (double*)y);
 }
 
-void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r, int zero_c, cudaStream_t s) {
+void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r, int zero_c, int nrhs,
+              cudaStream_t s) {
+  const dim3 grid(blocks(h.ndof, 256), nrhs);
   if (f32)
-    k_residual<D, K, float><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x,
-                                                               (const float*)b, (float*)r, zero_c);
+    k_residual<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (const float*)b,
+                                                 (float*)r, zero_c, h.ndof);
   else
-    k_residual<D, K, double><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x,
-                                                                (const double*)b, (double*)r, zero_c);
+    k_residual<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x,
+                                                  (const double*)b, (double*)r, zero_c, h.ndof);
 }
 
-void restrict_(const HostLevel& f, const HostLevel& c, int f32, const void* rf, void* bc, cudaStream_t s) {
+void restrict_(const HostLevel& f, const HostLevel& c, int f32, const void* rf, void* bc, int nrhs, cudaStream_t s) {
+  const dim3 grid(blocks(c.ndof, 256), nrhs);
   if (f32)
-    k_restrict<D, K, float><<<blocks(c.ndof, 256), 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(),
-                                                               (const float*)rf, (float*)bc);
+    k_restrict<D, K, float><<<grid, 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(), (const float*)rf,
+                                                 (float*)bc, f.ndof, c.ndof);
   else
-    k_restrict<D, K, double><<<blocks(c.ndof, 256), 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(),
-                                                                (const double*)rf, (double*)bc);
+    k_restrict<D, K, double><<<grid, 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(), (const double*)rf,
+                                                  (double*)bc, f.ndof, c.ndof);
 }
 
-void prolong_add(const HostLevel& f, const HostLevel& c, int f32, const void* xc, void* xf, cudaStream_t s) {
+void prolong_add(const HostLevel& f, const HostLevel& c, int f32, const void* xc, void* xf, int nrhs,
+                 cudaStream_t s) {
+  const dim3 grid(blocks(f.ndof, 256), nrhs);
   if (f32)
-    k_prolong_add<D, K, float><<<blocks(f.ndof, 256), 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(),
-                                                                  (const float*)xc, (float*)xf);
+    k_prolong_add<D, K, float><<<grid, 256, 0, s>>>(mk<float>(f), mk<float>(c), tab<float>(), (const float*)xc,
+                                                    (float*)xf, c.ndof, f.ndof);
   else
-    k_prolong_add<D, K, double><<<blocks(f.ndof, 256), 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(),
-                                                                   (const double*)xc, (double*)xf);
+    k_prolong_add<D, K, double><<<grid, 256, 0, s>>>(mk<double>(f), mk<double>(c), tab<double>(),
+                                                     (const double*)xc, (double*)xf, c.ndof, f.ndof);
 }
 
 template <typename TS>
@@ -99,19 +104,35 @@ void patch_setup(const HostLevel& h, int colour, int sprec, void* S, int* fail, 
 }
 
 template <typename T, typename TS>
-void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, cudaStream_t s) {
-  using PSh = PassShape<D, K, T, TS>;
+void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
+                   cudaStream_t s) {
+  using P = PassShape<D, K, T, TS>;
   const int64_t cnt = h.count[colour];
   if (cnt == 0) return;
-  const int64_t per_block = (int64_t)PSh::WARPS * PSh::GPW;
-  k_colour_pass<D, K, T, TS><<<blocks(cnt, (int)per_block), 32 * PSh::WARPS, 0, s>>>(
-      mk<T>(h), tab<T>(), colour, cnt, (const TS*)S, (T*)x, (const T*)b);
+  static bool attr = [] {
+    cudaFuncSetAttribute(k_colour_pass<D, K, T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+    return true;
+  }();
+  (void)attr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks(cnt, P::PPB), nrhs);
+  cfg.blockDim = dim3(32 * P::WARPS);
+  cfg.dynamicSmemBytes = P::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S, (T*)x,
+                     (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
-void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, cudaStream_t s) {
-  if (prec == P64) colour_pass_t<double, double>(h, colour, S, x, b, s);
-  else if (prec == P32) colour_pass_t<float, float>(h, colour, S, x, b, s);
-  else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, s);
+void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
+                 cudaStream_t s) {
+  if (prec == P64) colour_pass_t<double, double>(h, colour, S, x, b, err, nrhs, s);
+  else if (prec == P32) colour_pass_t<float, float>(h, colour, S, x, b, err, nrhs, s);
+  else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, err, nrhs, s);
 }
 
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,

@@ -20,6 +20,7 @@ struct HostLevel {
   double* c64;           // per-cell coefficient
   float* c32;
   int sprec;             // storage precision of the patch inverses (Prec)
+  int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision
@@ -33,14 +34,21 @@ struct DKOps {
   int64_t s_stride[3];   // elements per stored patch inverse
   // y = A x (f32 != 0: float vectors, float coefficient)
   void (*apply)(const HostLevel&, int f32, const void* x, void* y, cudaStream_t);
+  // The V-cycle kernels act on nrhs vectors stored one after another (each
+  // of its level's ndof entries).
   // r = b - A x; constrained rows r = 0 (zero_c) or b - x
-  void (*residual)(const HostLevel&, int f32, const void* x, const void* b, void* r, int zero_c, cudaStream_t);
-  void (*restrict_)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* rf, void* bc, cudaStream_t);
-  void (*prolong_add)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* xc, void* xf, cudaStream_t);
+  void (*residual)(const HostLevel&, int f32, const void* x, const void* b, void* r, int zero_c, int nrhs,
+                   cudaStream_t);
+  void (*restrict_)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* rf, void* bc, int nrhs,
+                    cudaStream_t);
+  void (*prolong_add)(const HostLevel& Lf, const HostLevel& Lc, int f32, const void* xc, void* xf, int nrhs,
+                      cudaStream_t);
   // patch inverses of one colour into S (storage precision sprec); *fail set on a zero pivot
   void (*patch_setup)(const HostLevel&, int colour, int sprec, void* S, int* fail, cudaStream_t);
-  // one colour pass in precision prec on vectors x, b
-  void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, cudaStream_t);
+  // one colour pass in precision prec on vectors x, b; a timed-out wait for
+  // the patch inverses sets *err = 2
+  void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, int* err,
+                      int nrhs, cudaStream_t);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);
@@ -66,7 +74,7 @@ void launch_f2d(const float* a, double* b, int64_t n, cudaStream_t);
 void launch_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail, cudaStream_t);
 // x = 0 on level 0, then x[free[i]] = sum_j inv[i][j] b[free[j]]  (f32: float x, b)
 void launch_coarse_apply(const double* inv, const int64_t* free_list, int nf, int64_t ndof, int f32,
-                         const void* b, void* x, cudaStream_t);
+                         const void* b, void* x, int nrhs, cudaStream_t);
 // FP64 vector kernels for the Krylov solver
 void launch_multidot(const double* V, int64_t ld, int nvec, const double* w, int64_t n, double* partial,
                      double* out, cudaStream_t);
@@ -80,5 +88,10 @@ void launch_sqrt_sum(const double* partial, int64_t n, double* out, cudaStream_t
 // number of partial sums k_residual_norm writes for a level of ndof dofs
 inline int64_t residual_norm_blocks(int64_t ndof) { return (ndof + 255) / 256; }
 int multidot_blocks();
+// vectors r = 0..nc-1 of B (each ndof long) become the unit vectors e_{c0+r}
+void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaStream_t);
+// z = Bd^T b with Bd (n x n, row r = B e_r); partial holds DENSE_CHUNKS x n
+constexpr int DENSE_CHUNKS = 64;
+void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, cudaStream_t);
 
 }  // namespace mgd

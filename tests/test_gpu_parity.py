@@ -55,7 +55,7 @@ def physical_rhs(L, seed):
 _cache = {}
 
 
-def build(case, precision="fp64", variable=True, m_fine=2):
+def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1):
     name, d, k, n0, L, mu, cf = case
     nf = n0 * 2 ** (L - 1)
     c = cf(nf)
@@ -63,7 +63,8 @@ def build(case, precision="fp64", variable=True, m_fine=2):
     if key not in _cache:
         _cache[key] = mg.Hierarchy(d, n0, L, k, mu, c)
     H = _cache[key]
-    G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, m_fine=m_fine, variable_cycle=variable)
+    G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, m_fine=m_fine, variable_cycle=variable,
+                          dense_level=dense_level)
     return H, G
 
 
@@ -141,8 +142,11 @@ def test_smoothing_step_parity_fp64(case):
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("variable", [True, False])
-def test_vcycle_parity_fp64(case, variable):
-    H, G = build(case, variable=variable, m_fine=2 if variable else 1)
+@pytest.mark.parametrize("dense_level", [0, -1, 1], ids=["passes", "dense_auto", "dense_1"])
+def test_vcycle_parity_fp64(case, variable, dense_level):
+    """One V-cycle, all levels as colour passes or with the sub-cycle of the
+    coarsest levels applied as its precomputed dense matrix."""
+    H, G = build(case, variable=variable, m_fine=2 if variable else 1, dense_level=dense_level)
     LJ = H.levels[-1]
     rng = np.random.default_rng(5)
     r = rng.standard_normal(LJ.S.ndof)
