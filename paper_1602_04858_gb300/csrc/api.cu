@@ -406,6 +406,13 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
       // levels whose inverses would crowd the L2 cache stream them evict-first
       L.s_evict_first = (double)np * h->ops->s_stride[L.sprec] * sb > 48.0e6 ? 1 : 0;
     }
+    if (L.n >= 4) {   // a level with patches away from the boundary
+      const int64_t te = h->ops->template_elems(L.sprec);
+      if ((st = h->alloc((char**)&q, (size_t)te * h->vbytes())) != MG_OK) return cleanup(st);
+      L.R0 = q;
+      h->ops->build_template(L, L.sprec, q, h->stream);
+      ++h->launches;
+    }
     for (int col = 0; col < C; ++col) {
       if (L.count[col] == 0) continue;
       size_t bytes = (size_t)L.count[col] * h->ops->s_stride[L.sprec] * sb;

@@ -283,13 +283,24 @@ __device__ __forceinline__ int patch_local_decode(const int (&v)[D], int l, int 
   constexpr int K1 = K + 1;
   int comp = l / PS::NU1;
   if (comp > D) comp = D;
-  int r = (comp < D) ? l - comp * PS::NU1 : l - D * PS::NU1;
+  int r = l - comp * PS::NU1;
+  if (comp == D) {
 #pragma unroll
-  for (int e = 0; e < D; ++e) {
-    const int m = (comp < D && e == comp) ? PS::UA : PS::UB;
-    const int le = r % m;
-    r /= m;
-    idx[e] = (v[e] - 1) * K1 + ((comp < D && e == comp) ? 1 : 0) + le;
+    for (int e = 0; e < D; ++e) {
+      idx[e] = (v[e] - 1) * K1 + r % PS::UB;
+      r /= PS::UB;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      if (e == comp) {
+        idx[e] = (v[e] - 1) * K1 + 1 + r % PS::UA;
+        r /= PS::UA;
+      } else {
+        idx[e] = (v[e] - 1) * K1 + r % PS::UB;
+        r /= PS::UB;
+      }
+    }
   }
   return comp;
 }

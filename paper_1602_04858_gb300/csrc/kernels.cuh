@@ -422,11 +422,15 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 // A warp owns GPW patches.  Lane 0 first issues one bulk asynchronous copy
 // per patch of its stored inverse S_v into shared memory (S_v does not depend
 // on earlier passes, so this happens before the programmatic-dependent-launch
-// wait and overlaps the previous pass).  The lanes then gather each patch's
-// window of x (every column its rows touch), its b rows and its 2^D cell
-// coefficients into shared memory, form the local residual rows from the
-// matrix-free stencil, wait for S_v, and apply it: a group of LPP lanes per
-// patch, lane q owning RG consecutive rows of delta.
+// wait and overlaps the previous pass).  The lanes gather each patch's window
+// of x (every column its rows touch), its b rows and its 2^D cell
+// coefficients, and form the local residual.  For a patch away from the
+// boundary the coefficient-free part of its rows (the mu terms and the
+// divergence blocks) is the same dense template R0 for every patch of the
+// level; it is applied from shared memory, RR rows per lane, and the cellwise
+// mass term is added from the 1-D tables.  Patches next to the boundary use
+// the stencil visitor.  Finally S_v is applied: LPP lanes per patch, lane q
+// owning RG consecutive rows of delta.
 // ---------------------------------------------------------------------------
 template <int D, int K, typename T, typename TS>
 struct PassShape {
@@ -445,14 +449,28 @@ struct PassShape {
   // the pressure WP per direction
   static constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
   static constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
-  static constexpr int WIN = D * WU + ((D == 2) ? WP * WP : WP * WP * WP);
+  static constexpr int WPP = (D == 2) ? WP * WP : WP * WP * WP;
+  static constexpr int WIN = D * WU + WPP;
   static constexpr int NC = 1 << D;
+  // residual rows per lane in the template product (16-byte vectors of T)
+  static constexpr int RR = 16 / (int)sizeof(T);
+  static constexpr int NVT = ((NV + RR - 1) / RR) * RR;   // template column length
+  static constexpr int NRG = NVT / RR;
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  static constexpr int T_PER_PATCH = WIN + 2 * NV + NC;   // window, b rows, residual, c
-  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + (size_t)PPB * T_PER_PATCH * sizeof(T) +
-                                 (size_t)WARPS * sizeof(uint64_t) + 16;
+  static constexpr int T_PER_PATCH = WIN + NV + NVT + NC;   // window, b rows, residual, c
+  static constexpr int TPL = WIN * NVT;                     // template entries
+  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + (size_t)TPL * sizeof(T) +
+                                 (size_t)PPB * T_PER_PATCH * sizeof(T) + (size_t)PPB * D * sizeof(int) +
+                                 (size_t)WARPS * sizeof(uint64_t) + 32;
 };
+
+// Window origin along direction e for component comp (D = pressure).
+template <int D, int K>
+__device__ __forceinline__ int win_origin(const int (&v)[D], int comp, int e) {
+  constexpr int K1 = K + 1;
+  return (comp < D && e != comp) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
+}
 
 // Window position of (comp, idx) for the patch at vertex v.
 template <int D, int K>
@@ -464,34 +482,31 @@ __device__ __forceinline__ int win_index(const int (&v)[D], int comp, const int 
 #pragma unroll
   for (int e = 0; e < D; ++e) {
     const bool own = comp < D && e == comp;
-    const int o = (comp < D && !own) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
     const int m = (comp == D) ? WP : (own ? WA : WB);
-    l += (idx[e] - o) * stride;
+    l += (idx[e] - win_origin<D, K>(v, comp, e)) * stride;
     stride *= m;
   }
   return comp * WU + l;
 }
 
-// Inverse of win_index: window position -> (comp, node); inside = in the domain.
-template <int D, int K>
-__device__ __forceinline__ int win_decode(const int (&v)[D], int N, int w, int (&idx)[D], bool& inside) {
+// Local multi-index of window entry r of component C (compile-time shape).
+template <int D, int K, int C>
+__device__ __forceinline__ void win_local(int r, int (&le)[D]) {
   constexpr int K1 = K + 1;
   constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
-  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
-  const int comp = (w / WU < D) ? w / WU : D;
-  int r = w - comp * WU;
-  inside = true;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
-    const bool own = comp < D && e == comp;
-    const int o = (comp < D && !own) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
-    const int m = (comp == D) ? WP : (own ? WA : WB);
-    idx[e] = o + r % m;
-    r /= m;
-    const int hi = own ? N : N - 1;
-    if (idx[e] < 0 || idx[e] > hi) inside = false;
+    if (C == D) {
+      le[e] = r % WP;
+      r /= WP;
+    } else if (e == C) {
+      le[e] = r % WA;
+      r /= WA;
+    } else {
+      le[e] = r % WB;
+      r /= WB;
+    }
   }
-  return comp;
 }
 
 template <int D, int K, typename T>
@@ -512,21 +527,89 @@ struct WinVisitor {
   }
 };
 
+// Builds the coefficient-free interior template: R0[w][l] = coefficient of
+// window column w in patch row l (c = 0), for a patch away from the boundary.
+template <int D, int K, typename T>
+struct TemplateVisitor {
+  const int (&v)[D];
+  T* col;   // R0 + l; column w at col[w * NVT]
+  int nvt;
+  __device__ TemplateVisitor(const int (&vv)[D], T* c, int n) : v(vv), col(c), nvt(n) {}
+  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
+    col[(size_t)win_index<D, K>(v, comp, j) * nvt] += coef;
+  }
+  __device__ __forceinline__ T cell_c(const int (&)[D]) const { return T(0); }
+};
+
+template <int D, int K, typename T, typename TS>
+__global__ void k_build_template(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb, T* __restrict__ R0) {
+  using P = PassShape<D, K, T, TS>;
+  for (int q = threadIdx.x; q < P::TPL; q += blockDim.x) R0[q] = T(0);
+  __syncthreads();
+  int v[D];
+#pragma unroll
+  for (int e = 0; e < D; ++e) v[e] = 2;
+  for (int l = threadIdx.x; l < P::NV; l += blockDim.x) {
+    int idx[D];
+    const int comp = patch_local_decode<D, K>(v, l, idx);
+    TemplateVisitor<D, K, T> vis(v, R0 + l, P::NVT);
+    visit_row(L, tb, comp, idx, vis);
+  }
+}
+
+// Mass term (c u, v) of a velocity row from the window.
+template <int D, int K, typename T>
+__device__ __forceinline__ T mass_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, const int (&v)[D], int i,
+                                      const int (&idx)[D], const T* win, const T* cw) {
+  constexpr int K1 = K + 1, NG = K + 2;
+  const int t = idx[i];
+  T wperp = T(1);
+  int cbits = 0;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == i) continue;
+    wperp *= tb.wg[idx[e] % K1];
+    cbits |= (idx[e] / K1 - (v[e] - 1)) << e;
+  }
+  const int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
+  T acc = T(0);
+  for (int cx = lo; cx <= hi; ++cx) {
+    const int a = t - cx * K1;
+    const T cK = cw[cbits | ((cx - (v[i] - 1)) << i)];
+    int j[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) j[e] = idx[e];
+    T s = T(0);
+#pragma unroll
+    for (int ap = 0; ap < NG; ++ap) {
+      j[i] = cx * K1 + ap;
+      s += tb.Mcg[a][ap] * win[win_index<D, K>(v, i, j)];
+    }
+    acc += cK * s;
+  }
+  return L.s_c * wperp * acc;
+}
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
 template <int D, int K, typename T, typename TS>
 __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
                                                      int colour, int64_t count, const TS* __restrict__ S,
-                                                     T* x, const T* __restrict__ b, int evict_first,
-                                                     int* __restrict__ err, int64_t vs) {
+                                                     const T* __restrict__ R0g, T* x, const T* __restrict__ b,
+                                                     int evict_first, int* __restrict__ err, int64_t vs) {
   using P = PassShape<D, K, T, TS>;
+  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB, RR = P::RR;
   x += blockIdx.y * vs;
   b += blockIdx.y * vs;
-  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* s_inv = smem;                                                   // PPB x S_BYTES
   float* s_scale = reinterpret_cast<float*>(smem + (size_t)PPB * P::S_BYTES);    // PPB x NVP (BF16 only)
-  T* s_t = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(
-      (reinterpret_cast<uintptr_t>(s_t + (size_t)PPB * P::T_PER_PATCH) + 15) & ~uintptr_t(15));
+  T* s_R0 = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
+  T* s_t = s_R0 + P::TPL;
+  int* s_v = reinterpret_cast<int*>(s_t + (size_t)PPB * P::T_PER_PATCH);
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(s_v + PPB * D) + 15) & ~uintptr_t(15));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t pw = ((int64_t)blockIdx.x * P::WARPS + warp) * GPW;   // first patch of this warp
   const int nmine = (pw >= count) ? 0 : (int)((count - pw) < GPW ? (count - pw) : GPW);
@@ -544,24 +627,55 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
                   reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + (pw + g) * NVP, P::SC_BYTES, bar, pol);
     }
   }
+  // the interior template (independent of earlier passes)
+  if (R0g) {
+    using V = typename Vec16<T>::type;
+    const V* src = reinterpret_cast<const V*>(R0g);
+    V* dst = reinterpret_cast<V*>(s_R0);
+    for (int q = threadIdx.x; q < P::TPL / RR; q += blockDim.x) dst[q] = src[q];
+  }
+  if (lane < nmine) {
+    int v[D];
+    patch_vertex<D>(L.n, colour, pw + lane, v);
+#pragma unroll
+    for (int e = 0; e < D; ++e) s_v[(warp * GPW + lane) * D + e] = v[e];
+  }
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
-  __syncwarp();
+  __syncthreads();
   if (nmine == 0) return;
-  // 2. gather windows, b rows and cell coefficients
+  const int* wv = s_v + warp * GPW * D;
   T* tw = s_t + (size_t)(warp * GPW) * P::T_PER_PATCH;
-  for (int q = lane; q < nmine * P::WIN; q += 32) {
-    const int g = q / P::WIN, w = q - g * P::WIN;
-    int v[D], idx[D];
-    patch_vertex<D>(L.n, colour, pw + g, v);
-    bool inside;
-    const int comp = win_decode<D, K>(v, L.N, w, idx, inside);
-    tw[g * P::T_PER_PATCH + w] = inside ? x[flat_index(L, comp, idx)] : T(0);
-  }
+  // 2. gather windows (component by component, compile-time shapes), b rows, c
+  auto gather = [&](auto Cc) {
+    constexpr int C = decltype(Cc)::value;
+    constexpr int WSZ = (C == D) ? P::WPP : P::WU;
+    constexpr int BASE = C * P::WU;
+    for (int q = lane; q < nmine * WSZ; q += 32) {
+      const int g = q / WSZ, w = q - g * WSZ;
+      int v[D], le[D], idx[D];
+#pragma unroll
+      for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
+      win_local<D, K, C>(w, le);
+      bool inside = true;
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        idx[e] = win_origin<D, K>(v, C, e) + le[e];
+        const int hi = (C < D && e == C) ? L.N : L.N - 1;
+        inside = inside && idx[e] >= 0 && idx[e] <= hi;
+      }
+      tw[g * P::T_PER_PATCH + BASE + w] = inside ? x[flat_index(L, C, idx)] : T(0);
+    }
+  };
+  gather(std::integral_constant<int, 0>{});
+  gather(std::integral_constant<int, 1>{});
+  if constexpr (D == 3) gather(std::integral_constant<int, 2>{});
+  gather(std::integral_constant<int, D>{});
   for (int q = lane; q < nmine * (NV + P::NC); q += 32) {
     const int g = q / (NV + P::NC), l = q - g * (NV + P::NC);
     int v[D];
-    patch_vertex<D>(L.n, colour, pw + g, v);
+#pragma unroll
+    for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
     T* base = tw + g * P::T_PER_PATCH + P::WIN;
     if (l < NV) {
       int idx[D];
@@ -572,20 +686,60 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       int cell[D];
 #pragma unroll
       for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cl >> e) & 1);
-      base[2 * NV + cl] = L.c[cell_linear(L, cell)];
+      base[NV + P::NVT + cl] = L.c[cell_linear(L, cell)];
     }
   }
   __syncwarp();
-  // 3. local residual rows (b - A x)|_v from the window
-  for (int q = lane; q < nmine * NV; q += 32) {
-    const int g = q / NV, l = q - g * NV;
-    int v[D], idx[D];
-    patch_vertex<D>(L.n, colour, pw + g, v);
-    const int comp = patch_local_decode<D, K>(v, l, idx);
+  // 3. local residual rows (b - A x)|_v
+  for (int q = lane; q < nmine * P::NRG; q += 32) {
+    const int g = q / P::NRG, rg = q - g * P::NRG;
+    int v[D];
+    bool interior = R0g != nullptr;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      v[e] = wv[g * D + e];
+      interior = interior && v[e] >= 2 && v[e] <= L.n - 2;
+    }
     T* base = tw + g * P::T_PER_PATCH;
-    WinVisitor<D, K, T> vis(v, base, base + P::WIN + 2 * NV);
-    visit_row(L, tb, comp, idx, vis);
-    base[P::WIN + NV + l] = base[P::WIN + l] - vis.acc;
+    const T* cw = base + P::WIN + NV + P::NVT;
+    T* res = base + P::WIN + NV;
+    if (interior) {
+      using V = typename Vec16<T>::type;
+      T acc[RR];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) acc[r] = T(0);
+#pragma unroll 8
+      for (int w = 0; w < P::WIN; ++w) {
+        const V c4 = *reinterpret_cast<const V*>(s_R0 + w * P::NVT + rg * RR);
+        const T xw = base[w];
+        const T* cc = reinterpret_cast<const T*>(&c4);
+#pragma unroll
+        for (int r = 0; r < RR; ++r) acc[r] += cc[r] * xw;
+      }
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const int l = rg * RR + r;
+        if (l < NV) {
+          int idx[D];
+          const int comp = patch_local_decode<D, K>(v, l, idx);
+          T m = T(0);
+          if (comp < D) m = mass_row(L, tb, v, comp, idx, base, cw);
+          res[l] = base[P::WIN + l] - acc[r] - m;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < RR; ++r) {
+        const int l = rg * RR + r;
+        if (l < NV) {
+          int idx[D];
+          const int comp = patch_local_decode<D, K>(v, l, idx);
+          WinVisitor<D, K, T> vis(v, base, cw);
+          visit_row(L, tb, comp, idx, vis);
+          res[l] = base[P::WIN + l] - vis.acc;
+        }
+      }
+    }
   }
   __syncwarp();
   // 4. wait for the inverses (bounded), then delta = S_v r
@@ -614,7 +768,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       for (int r = 0; r < RG; ++r) acc[r] += sv[r] * rj;
     }
     int v[D];
-    patch_vertex<D>(L.n, colour, pw + g, v);
+#pragma unroll
+    for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
 #pragma unroll
     for (int r = 0; r < RG; ++r) {
       const int row = q * RG + r;

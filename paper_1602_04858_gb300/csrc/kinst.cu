@@ -124,8 +124,8 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S, (T*)x,
-                     (const T*)b, h.s_evict_first, err, h.ndof);
+  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S,
+                     (const T*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
 void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
@@ -133,6 +133,18 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
   if (prec == P64) colour_pass_t<double, double>(h, colour, S, x, b, err, nrhs, s);
   else if (prec == P32) colour_pass_t<float, float>(h, colour, S, x, b, err, nrhs, s);
   else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, err, nrhs, s);
+}
+
+int64_t template_elems(int sprec) {
+  if (sprec == P64) return PassShape<D, K, double, double>::TPL;
+  if (sprec == P32) return PassShape<D, K, float, float>::TPL;
+  return PassShape<D, K, float, __nv_bfloat16>::TPL;
+}
+
+void build_template(const HostLevel& h, int sprec, void* R0, cudaStream_t s) {
+  if (sprec == P64) k_build_template<D, K, double, double><<<1, 256, 0, s>>>(mk<double>(h), tab<double>(), (double*)R0);
+  else if (sprec == P32) k_build_template<D, K, float, float><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), (float*)R0);
+  else k_build_template<D, K, float, __nv_bfloat16><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), (float*)R0);
 }
 
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
@@ -178,6 +190,8 @@ DKOps make_ops() {
   o.coarse_assemble = coarse_assemble;
   o.copy_constrained = copy_constrained;
   o.residual_norm = residual_norm;
+  o.template_elems = template_elems;
+  o.build_template = build_template;
   return o;
 }
 

@@ -21,6 +21,7 @@ struct HostLevel {
   float* c32;
   int sprec;             // storage precision of the patch inverses (Prec)
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
+  void* R0;              // interior-patch template of the colour pass (working precision), or null
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision
@@ -49,6 +50,9 @@ struct DKOps {
   // the patch inverses sets *err = 2
   void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, int* err,
                       int nrhs, cudaStream_t);
+  // interior-patch template of the colour pass (entries for storage precision sprec)
+  int64_t (*template_elems)(int sprec);
+  void (*build_template)(const HostLevel&, int sprec, void* R0, cudaStream_t);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);
