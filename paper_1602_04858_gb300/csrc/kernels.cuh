@@ -432,7 +432,7 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 // the stencil visitor.  Finally S_v is applied: LPP lanes per patch, lane q
 // owning RG consecutive rows of delta.
 // ---------------------------------------------------------------------------
-template <int D, int K, typename T, typename TS>
+template <int D, int K, typename T, typename TS, int NR = 1>
 struct PassShape {
   using PS = PatchShape<D, K>;
   static constexpr int K1 = K + 1;
@@ -442,7 +442,7 @@ struct PassShape {
   static constexpr int NVP = SL::NVP;
   static constexpr int LPP = NVP / RG;      // lanes per patch in the product
   static constexpr int GPW = 32 / LPP;      // patches per warp
-  static constexpr int WARPS = 4;
+  static constexpr int WARPS = (NR == 1) ? 4 : 2;
   static constexpr int PPB = WARPS * GPW;   // patches per block
   static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
   // window of x: velocity component i spans WA nodes along x_i and WB across,
@@ -458,7 +458,7 @@ struct PassShape {
   static constexpr int NRG = NVT / RR;
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  static constexpr int T_PER_PATCH = WIN + NV + NVT + NC;   // window, b rows, residual, c
+  static constexpr int T_PER_PATCH = NR * (WIN + NV + NVT) + NC;   // per rhs: window, b rows, residual; c
   static constexpr int TPL = WIN * NVT;                     // template entries
   static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + (size_t)TPL * sizeof(T) +
                                  (size_t)PPB * T_PER_PATCH * sizeof(T) + (size_t)PPB * D * sizeof(int) +
@@ -594,15 +594,18 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; };
 template <> struct Vec16<double> { using type = double2; };
 
-template <int D, int K, typename T, typename TS>
+// NR right-hand sides share each S_v (vectors vs apart); blockIdx.y selects
+// a group of NR vectors.
+template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
                                                      int colour, int64_t count, const TS* __restrict__ S,
                                                      const T* __restrict__ R0g, T* x, const T* __restrict__ b,
                                                      int evict_first, int* __restrict__ err, int64_t vs) {
-  using P = PassShape<D, K, T, TS>;
+  using P = PassShape<D, K, T, TS, NR>;
   constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB, RR = P::RR;
-  x += blockIdx.y * vs;
-  b += blockIdx.y * vs;
+  constexpr int WIN = P::WIN, NVT = P::NVT;
+  x += (int64_t)blockIdx.y * NR * vs;
+  b += (int64_t)blockIdx.y * NR * vs;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* s_inv = smem;                                                   // PPB x S_BYTES
   float* s_scale = reinterpret_cast<float*>(smem + (size_t)PPB * P::S_BYTES);    // PPB x NVP (BF16 only)
@@ -664,7 +667,10 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
         const int hi = (C < D && e == C) ? L.N : L.N - 1;
         inside = inside && idx[e] >= 0 && idx[e] <= hi;
       }
-      tw[g * P::T_PER_PATCH + BASE + w] = inside ? x[flat_index(L, C, idx)] : T(0);
+      const int64_t f = inside ? flat_index(L, C, idx) : 0;
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+        tw[g * P::T_PER_PATCH + rr * WIN + BASE + w] = inside ? x[f + rr * vs] : T(0);
     }
   };
   gather(std::integral_constant<int, 0>{});
@@ -676,21 +682,24 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     int v[D];
 #pragma unroll
     for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
-    T* base = tw + g * P::T_PER_PATCH + P::WIN;
+    T* pbase = tw + g * P::T_PER_PATCH;
     if (l < NV) {
       int idx[D];
       const int comp = patch_local_decode<D, K>(v, l, idx);
-      base[l] = b[flat_index(L, comp, idx)];
+      const int64_t f = flat_index(L, comp, idx);
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) pbase[NR * WIN + rr * NV + l] = b[f + rr * vs];
     } else {
       const int cl = l - NV;
       int cell[D];
 #pragma unroll
       for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cl >> e) & 1);
-      base[NV + P::NVT + cl] = L.c[cell_linear(L, cell)];
+      pbase[NR * (WIN + NV + NVT) + cl] = L.c[cell_linear(L, cell)];
     }
   }
   __syncwarp();
-  // 3. local residual rows (b - A x)|_v
+  // 3. local residual rows (b - A x)|_v; per patch: NR windows, NR b-row
+  //    blocks, NR residual blocks, then the cell coefficients
   for (int q = lane; q < nmine * P::NRG; q += 32) {
     const int g = q / P::NRG, rg = q - g * P::NRG;
     int v[D];
@@ -700,21 +709,25 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       v[e] = wv[g * D + e];
       interior = interior && v[e] >= 2 && v[e] <= L.n - 2;
     }
-    T* base = tw + g * P::T_PER_PATCH;
-    const T* cw = base + P::WIN + NV + P::NVT;
-    T* res = base + P::WIN + NV;
+    T* pbase = tw + g * P::T_PER_PATCH;
+    const T* cw = pbase + NR * (WIN + NV + NVT);
     if (interior) {
       using V = typename Vec16<T>::type;
-      T acc[RR];
+      T acc[RR][NR];
 #pragma unroll
-      for (int r = 0; r < RR; ++r) acc[r] = T(0);
+      for (int r = 0; r < RR; ++r)
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
 #pragma unroll 8
-      for (int w = 0; w < P::WIN; ++w) {
-        const V c4 = *reinterpret_cast<const V*>(s_R0 + w * P::NVT + rg * RR);
-        const T xw = base[w];
+      for (int w = 0; w < WIN; ++w) {
+        const V c4 = *reinterpret_cast<const V*>(s_R0 + w * NVT + rg * RR);
         const T* cc = reinterpret_cast<const T*>(&c4);
 #pragma unroll
-        for (int r = 0; r < RR; ++r) acc[r] += cc[r] * xw;
+        for (int rr = 0; rr < NR; ++rr) {
+          const T xw = pbase[rr * WIN + w];
+#pragma unroll
+          for (int r = 0; r < RR; ++r) acc[r][rr] += cc[r] * xw;
+        }
       }
 #pragma unroll
       for (int r = 0; r < RR; ++r) {
@@ -722,9 +735,12 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
         if (l < NV) {
           int idx[D];
           const int comp = patch_local_decode<D, K>(v, l, idx);
-          T m = T(0);
-          if (comp < D) m = mass_row(L, tb, v, comp, idx, base, cw);
-          res[l] = base[P::WIN + l] - acc[r] - m;
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            const T* win = pbase + rr * WIN;
+            const T m = (comp < D) ? mass_row(L, tb, v, comp, idx, win, cw) : T(0);
+            pbase[NR * WIN + NR * NV + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - acc[r][rr] - m;
+          }
         }
       }
     } else {
@@ -734,9 +750,12 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
         if (l < NV) {
           int idx[D];
           const int comp = patch_local_decode<D, K>(v, l, idx);
-          WinVisitor<D, K, T> vis(v, base, cw);
-          visit_row(L, tb, comp, idx, vis);
-          res[l] = base[P::WIN + l] - vis.acc;
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
+            visit_row(L, tb, comp, idx, vis);
+            pbase[NR * WIN + NR * NV + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
+          }
         }
       }
     }
@@ -753,19 +772,24 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   if (g < nmine) {
     const int slot = warp * GPW + g;
     const TS* Sg = reinterpret_cast<const TS*>(s_inv + (size_t)slot * P::S_BYTES) + q * RG;
-    const T* rv = tw + g * P::T_PER_PATCH + P::WIN + NV;
+    const T* rv = tw + g * P::T_PER_PATCH + NR * (WIN + NV);
     const float* sc = s_scale + (size_t)slot * NVP;
-    T acc[RG];
+    T acc[RG][NR];
 #pragma unroll
-    for (int r = 0; r < RG; ++r) acc[r] = T(0);
+    for (int r = 0; r < RG; ++r)
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
 #pragma unroll 4
     for (int j = 0; j < NV; ++j) {
       T sv[RG];
       load_rg_smem<TS, T>(Sg + j * NVP, sv);
-      T rj = rv[j];
-      if constexpr (P::BF) rj *= sc[j];
 #pragma unroll
-      for (int r = 0; r < RG; ++r) acc[r] += sv[r] * rj;
+      for (int rr = 0; rr < NR; ++rr) {
+        T rj = rv[rr * NVT + j];
+        if constexpr (P::BF) rj *= sc[j];
+#pragma unroll
+        for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+      }
     }
     int v[D];
 #pragma unroll
@@ -776,9 +800,10 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       if (row < NV) {
         int idx[D];
         const int comp = patch_local_decode<D, K>(v, row, idx);
-        T dv = acc[r];
-        if constexpr (P::BF) dv *= sc[row];
-        x[flat_index(L, comp, idx)] += dv;
+        const int64_t f = flat_index(L, comp, idx);
+        const T sr = P::BF ? (T)sc[row] : T(1);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) x[f + rr * vs] += P::BF ? acc[r][rr] * sr : acc[r][rr];
       }
     }
   }

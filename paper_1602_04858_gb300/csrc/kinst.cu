@@ -103,19 +103,17 @@ void patch_setup(const HostLevel& h, int colour, int sprec, void* S, int* fail, 
   else patch_setup_t<__nv_bfloat16>(h, colour, S, fail, s);
 }
 
-template <typename T, typename TS>
-void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
-                   cudaStream_t s) {
-  using P = PassShape<D, K, T, TS>;
-  const int64_t cnt = h.count[colour];
-  if (cnt == 0) return;
+template <typename T, typename TS, int NR>
+void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
+                    cudaStream_t s) {
+  using P = PassShape<D, K, T, TS, NR>;
   static bool attr = [] {
-    cudaFuncSetAttribute(k_colour_pass<D, K, T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+    cudaFuncSetAttribute(k_colour_pass<D, K, T, TS, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
     return true;
   }();
   (void)attr;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocks(cnt, P::PPB), nrhs);
+  cfg.gridDim = dim3(blocks(h.count[colour], P::PPB), groups);
   cfg.blockDim = dim3(32 * P::WARPS);
   cfg.dynamicSmemBytes = P::SMEM;
   cfg.stream = s;
@@ -124,8 +122,21 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S,
-                     (const T*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), tab<T>(), colour, h.count[colour],
+                     (const TS*)S, (const T*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+}
+
+// Right-hand sides in groups of four share each S_v load; the rest one by one.
+template <typename T, typename TS>
+void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
+                   cudaStream_t s) {
+  if (h.count[colour] == 0) return;
+  const int g4 = nrhs / 4, rest = nrhs - 4 * g4;
+  if (g4 > 0) colour_pass_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+  if (rest > 0) {
+    const size_t off = (size_t)4 * g4 * h.ndof;
+    colour_pass_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+  }
 }
 
 void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
@@ -136,9 +147,9 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
 }
 
 int64_t template_elems(int sprec) {
-  if (sprec == P64) return PassShape<D, K, double, double>::TPL;
-  if (sprec == P32) return PassShape<D, K, float, float>::TPL;
-  return PassShape<D, K, float, __nv_bfloat16>::TPL;
+  if (sprec == P64) return PassShape<D, K, double, double, 1>::TPL;
+  if (sprec == P32) return PassShape<D, K, float, float, 1>::TPL;
+  return PassShape<D, K, float, __nv_bfloat16, 1>::TPL;
 }
 
 void build_template(const HostLevel& h, int sprec, void* R0, cudaStream_t s) {
