@@ -162,6 +162,87 @@ mg_status mg_residual_norm(mg_handle* h, int level, const double* x, const doubl
 mg_status mg_residual_norm_noalloc(int dim, int degree, int n, double mu, const double* c, const double* x,
                                    const double* b, double* norm, void* cuda_stream);
 
+/* Load vector of cellwise-constant data on level `level` (-1: finest): the
+ * body-force term (f, v) of F in eq. (BCh) and the divergence source
+ * -(q, g) of the pressure rows (eq. Brinkman-weak), homogeneous boundary
+ * data (constrained rows 0).  f: device, d arrays of one value per cell
+ * (component-major, x fastest); g: device, one value per cell, or NULL;
+ * b: device, length n_u + n_p. */
+mg_status mg_load_vector(mg_handle* h, int level, const double* f, const double* g, double* b);
+
+/* --- batches of independent problems ----------------------------------------- */
+
+typedef struct mg_batch mg_batch;
+
+/* Sets up nprob independent problems (each as mg_setup would) solved together,
+ * each with nrhs right-hand sides.  Batch vector layout: problem 0's nrhs
+ * vectors (each n_u + n_p of its finest level) one after another, then
+ * problem 1's, ...  (mg_batch_layout gives sizes and offsets).  An automatic
+ * dense fold (dense_level = -1) is limited to 64 MiB per problem.
+ * Synchronises the stream. */
+mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* cuda_stream, mg_batch** out);
+
+/* Frees the batch (NULL is allowed). */
+void mg_destroy_batch(mg_batch* b);
+
+/* Finest-level dofs of problem p, the offset of its first vector in the batch
+ * layout, and the total batch-vector length (any pointer may be NULL). */
+mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offset, int64_t* total);
+
+/* z = B_J r for every problem and right-hand side (Sec. 3.2): one CUDA graph
+ * whose branches are the problems' V-cycles, the right-hand sides of a problem
+ * sharing each patch-inverse load.  r, z: device, FP64, batch layout. */
+mg_status mg_vcycle_batch(mg_batch* b, const double* r, double* z);
+
+/* Flexible GMRES(restart) in FP64 for all nprob x nrhs systems in lockstep,
+ * one batched V-cycle per iteration (stop per system at
+ * ||b - A x|| <= tol ||b||).  rhs: full right-hand sides (velocity and pressure
+ * blocks, compatible), x: solutions, initial guess if use_x0; both device,
+ * batch layout.  stats: NULL or nprob * nrhs entries (problem-major).
+ * The pressure constant is not normalised.  Synchronises.  Returns
+ * MG_ERR_NOT_CONVERGED if a system reaches maxit (total lockstep iterations). */
+mg_status mg_solve_batch(mg_batch* b, const double* rhs, double* x, int use_x0, double tol, int maxit,
+                         int restart, mg_stats* stats);
+
+/* Number of kernels the library launched for this batch's solves and V-cycles. */
+int64_t mg_batch_kernel_launches(const mg_batch* b);
+
+/* --- learned initial guess ------------------------------------------------------ */
+
+/* A 4-layer 3x3 convolutional network (3 -> 32 -> 32 -> 32 -> 3 channels, zero
+ * padding, ReLU after the first three) on an n x n cell grid mapping the
+ * per-cell features (log c, f_1, f_2) to a per-cell guess (u_1 on the cell's
+ * west face, u_2 on its south face, p) for RT_0 in 2-D.  BF16 weights and
+ * activations, FP32 accumulation, FP32 master weights with Adam.  The paper
+ * has no network; the V-cycle solve started from its guess must still reach
+ * the same residual tolerance.  Weight layout [out][in][3][3] then the biases,
+ * layer by layer (mg_cnn_param_count floats). */
+typedef struct mg_cnn mg_cnn;
+
+/* He-normal weights from `seed`, zero biases; batches up to max_batch. */
+mg_status mg_cnn_create(int n, int max_batch, uint64_t seed, void* cuda_stream, mg_cnn** out);
+void mg_cnn_destroy(mg_cnn* net);
+int64_t mg_cnn_param_count(const mg_cnn* net);
+/* FP32 parameters to / from host memory (checkpoint). */
+mg_status mg_cnn_get_params(mg_cnn* net, float* host);
+mg_status mg_cnn_set_params(mg_cnn* net, const float* host);
+/* 12 host floats: input mean[3], input std[3], output mean[3], output std[3]. */
+mg_status mg_cnn_set_normalisation(mg_cnn* net, const float* host12);
+/* Features of one problem: c (n*n cells), f (2 x n*n), both device FP64 -> in (3 x n*n, device FP32). */
+mg_status mg_cnn_features(mg_cnn* net, const double* c, const double* f, float* in);
+/* Normalised per-cell targets (3 x n*n, device FP32) from an RT_0 solution x (device FP64). */
+mg_status mg_cnn_targets(mg_cnn* net, const double* x, float* target);
+/* out = network(in) for `batch` inputs (B x 3 x n x n, device FP32). */
+mg_status mg_cnn_forward(mg_cnn* net, const float* in, int batch, float* out);
+/* Mean-squared-error loss (host) and its gradients (host, param_count floats; may be NULL). */
+mg_status mg_cnn_gradients(mg_cnn* net, const float* in, const float* target, int batch, float* loss,
+                           float* grads_host);
+/* One Adam step (beta 0.9 / 0.999) on a batch; loss returned on the host. */
+mg_status mg_cnn_train_step(mg_cnn* net, const float* in, const float* target, int batch, float lr, float* loss);
+/* Initial guess x0 (device FP64, RT_0 layout of the n x n level) for the problem (c, f):
+ * boundary normal dofs 0, velocity and pressure from the network. */
+mg_status mg_cnn_guess(mg_cnn* net, const double* c, const double* f, double* x0);
+
 /* --- single steps of the V-cycle, for testing and measurement ---------------- */
 
 /* x <- x + R_j (b - A_j x): `steps` symmetric multiplicative Schwarz

@@ -82,7 +82,8 @@ struct mg_handle {
   int Ls = -1;
   void* Bd = nullptr;
   void* Bd_partial = nullptr;
-  VecSet main;    // the level vectors X, B, R of the single right-hand side
+  VecSet main;    // the level vectors X, B, R (nrhs right-hand sides)
+  int nrhs = 1;
   int64_t launches = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;
@@ -190,8 +191,8 @@ mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cu
   HostLevel& L = h->lv[j];
   const int nr = vs.nrhs;
   if (use_dense && j == h->Ls) {
-    launch_dense_apply(h->f32(), h->Bd, L.ndof, vs.B[j], vs.X[j], h->Bd_partial, stream);
-    h->launches += 2;
+    launch_dense_apply(h->f32(), h->Bd, L.ndof, vs.B[j], vs.X[j], h->Bd_partial, nr, stream);
+    h->launches += 2 * ((nr + 3) / 4);
     return MG_OK;
   }
   if (j == 0) {
@@ -282,7 +283,7 @@ mg_status vcycle_dev(mg_handle* h, const double* r, double* z) {
 
 mg_status apply_dev(mg_handle* h, int level, const double* x, double* y) {
   HostLevel& L = h->lv[level];
-  h->ops->apply(L, 0, x, y, h->stream);
+  h->ops->apply(L, 0, x, y, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -312,8 +313,14 @@ int64_t mg_kernel_launches(const mg_handle* h) { return h ? h->launches : 0; }
 
 void mg_destroy(mg_handle* h) { delete h; }
 
-mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
+}  // extern "C"
+
+// Builds one hierarchy whose level vectors hold nrhs right-hand sides; an
+// automatic dense fold (dense_level = -1) may use at most dense_budget bytes.
+static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs, double dense_budget,
+                                mg_handle** out) {
   if (!p || !out) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (nrhs < 1) return fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
   *out = nullptr;
   if (p->dim != 2 && p->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (p->degree < 0 || p->degree > 1) return fail(MG_ERR_UNSUPPORTED, "degree must be 0 or 1");
@@ -392,7 +399,7 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
     HostLevel& L = h->lv[j];
     void* q;
     for (void** v : {&L.X, &L.B, &L.R}) {
-      if ((st = h->alloc((char**)&q, L.ndof * h->vbytes())) != MG_OK) return cleanup(st);
+      if ((st = h->alloc((char**)&q, (size_t)L.ndof * nrhs * h->vbytes())) != MG_OK) return cleanup(st);
       *v = q;
     }
     // BF16 storage (with FP32 equilibration scales) on the finest level only;
@@ -406,9 +413,9 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
       // levels whose inverses would crowd the L2 cache stream them evict-first
       L.s_evict_first = (double)np * h->ops->s_stride[L.sprec] * sb > 48.0e6 ? 1 : 0;
     }
-    if (L.n >= 4) {   // a level with patches away from the boundary
-      const int64_t te = h->ops->template_elems(L.sprec);
-      if ((st = h->alloc((char**)&q, (size_t)te * h->vbytes())) != MG_OK) return cleanup(st);
+    {   // per-level colour-pass tables (interior template, mass and gather tables)
+      const int64_t tb = h->ops->template_elems(L.sprec);
+      if ((st = h->alloc((char**)&q, (size_t)tb)) != MG_OK) return cleanup(st);
       L.R0 = q;
       h->ops->build_template(L, L.sprec, q, h->stream);
       ++h->launches;
@@ -423,7 +430,8 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
       ++h->launches;
     }
   }
-  h->main.nrhs = 1;
+  h->main.nrhs = nrhs;
+  h->nrhs = nrhs;
   for (int j = 0; j <= J; ++j) {
     h->main.X.push_back(h->lv[j].X);
     h->main.B.push_back(h->lv[j].B);
@@ -500,7 +508,8 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
   {
     int Ls = p->dense_level;
     if (Ls < 0) {
-      const double budget = (h->prec == P64) ? 256.0 * (1 << 20) : 1024.0 * (1 << 20);
+      const double budget = dense_budget > 0 ? dense_budget : ((h->prec == P64) ? 256.0 * (1 << 20)
+                                                                                 : 1024.0 * (1 << 20));
       Ls = 0;
       for (int j = 1; j < J; ++j)
         if ((double)h->lv[j].ndof * h->lv[j].ndof * h->vbytes() <= budget) Ls = j;
@@ -509,7 +518,7 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
       h->Ls = Ls;
       const int64_t n = h->lv[Ls].ndof;
       if ((st = h->alloc((char**)&h->Bd, (size_t)n * n * h->vbytes())) != MG_OK) return cleanup(st);
-      if ((st = h->alloc((char**)&h->Bd_partial, (size_t)DENSE_CHUNKS * n * h->vbytes())) != MG_OK)
+      if ((st = h->alloc((char**)&h->Bd_partial, (size_t)4 * DENSE_CHUNKS * n * h->vbytes())) != MG_OK)
         return cleanup(st);
       // columns in chunks: every level <= Ls holds chunk vectors X, B, R
       int64_t per_rhs = 0;
@@ -561,6 +570,12 @@ mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
   if (bad) return cleanup(fail(MG_ERR_BREAKDOWN, "zero pivot in a patch or coarse factorisation"));
   *out = h;
   return MG_OK;
+}
+
+extern "C" {
+
+mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
+  return setup_internal(p, cuda_stream, 1, 0.0, out);
 }
 
 mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p) {
@@ -703,6 +718,18 @@ mg_status mg_residual_norm(mg_handle* h, int level, const double* x, const doubl
     CU(cudaMemcpyAsync(norm, h->d_rn, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   }
+  return MG_OK;
+}
+
+mg_status mg_load_vector(mg_handle* h, int level, const double* f, const double* g, double* b) {
+  if (!h || !f || !b) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (level < 0) level = h->J;
+  if (level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  if (!is_device_ptr(f) || !is_device_ptr(b) || (g && !is_device_ptr(g)))
+    return fail(MG_ERR_INVALID_ARG, "f, g and b must be device pointers");
+  h->ops->load_vector(h->lv[level], f, g, b, h->stream);
+  ++h->launches;
+  CU(cudaGetLastError());
   return MG_OK;
 }
 
@@ -904,6 +931,378 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
   if (result != MG_OK) return result;
   if (!converged) return fail(MG_ERR_NOT_CONVERGED, "GMRES reached maxit");
   return MG_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches: many independent problems, nrhs right-hand sides each.
+// ===========================================================================
+
+struct mg_batch {
+  std::vector<mg_handle*> sub;
+  int nrhs = 1;
+  cudaStream_t stream = nullptr;
+  std::vector<int64_t> ndof, off;   // finest-level dofs and offset of each problem
+  int64_t total = 0;
+  double* rb = nullptr;   // FP64 input / output of the captured V-cycle graph
+  double* zb = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int64_t graph_kernels = 0;
+  // systems (problem, rhs) as segments of the long vectors
+  SegTable seg;
+  std::vector<int64_t> sstart, slen;
+  // Krylov workspace
+  int gm_m = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *bb = nullptr, *xx = nullptr;
+  double *partial = nullptr, *coef = nullptr;
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+  ~mg_batch() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto* h : sub) delete h;
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename T>
+  mg_status alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess)
+      return fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+                  std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    allocs.push_back(q);
+    *p = (T*)q;
+    return MG_OK;
+  }
+};
+
+namespace {
+
+// z = B r for the nrhs vectors of one problem (FP64 device, problem layout).
+mg_status sub_vcycle(mg_handle* h, const double* r, double* z, cudaStream_t s) {
+  HostLevel& L = h->lv.back();
+  const int64_t n = L.ndof * h->nrhs;
+  if (h->prec == P64) CU(cudaMemcpyAsync(L.B, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else launch_d2f(r, (float*)L.B, n, s);
+  TRY(vcycle_level(h, h->J, h->main, true, s));
+  if (h->prec == P64) CU(cudaMemcpyAsync(z, L.X, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else launch_f2d((const float*)L.X, z, n, s);
+  for (int rr = 0; rr < h->nrhs; ++rr) h->ops->copy_constrained(L, r + rr * L.ndof, z + rr * L.ndof, s);
+  return MG_OK;
+}
+
+// One CUDA graph: every problem's V-cycle as its own branch (rb -> zb).
+mg_status batch_graph(mg_batch* B) {
+  if (B->graph) return MG_OK;
+  const int np = (int)B->sub.size();
+  std::vector<cudaStream_t> st(np);
+  std::vector<cudaEvent_t> ev(np + 1);
+  cudaStream_t s0;
+  CU(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+  for (int p = 0; p < np; ++p) CU(cudaStreamCreateWithFlags(&st[p], cudaStreamNonBlocking));
+  for (auto& e : ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  int64_t l0 = 0;
+  for (auto* h : B->sub) l0 += h->launches;
+  CU(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+  mg_status result = MG_OK;
+  cudaEventRecord(ev[np], s0);
+  for (int p = 0; p < np && result == MG_OK; ++p) {
+    cudaStreamWaitEvent(st[p], ev[np], 0);
+    result = sub_vcycle(B->sub[p], B->rb + B->off[p], B->zb + B->off[p], st[p]);
+    cudaEventRecord(ev[p], st[p]);
+    cudaStreamWaitEvent(s0, ev[p], 0);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s0, &g);
+  for (auto& x : st) cudaStreamDestroy(x);
+  for (auto& x : ev) cudaEventDestroy(x);
+  cudaStreamDestroy(s0);
+  int64_t l1 = 0;
+  for (auto* h : B->sub) l1 += h->launches;
+  if (result != MG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return result;
+  }
+  if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&B->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    B->graph = nullptr;
+    return fail(MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  B->graph_kernels = l1 - l0;
+  return MG_OK;
+}
+
+// y = A x for every problem and right-hand side (FP64, batch layout).
+void batch_apply(mg_batch* B, const double* x, double* y) {
+  for (size_t p = 0; p < B->sub.size(); ++p) {
+    mg_handle* h = B->sub[p];
+    h->ops->apply(h->lv.back(), 0, x + B->off[p], y + B->off[p], B->nrhs, B->stream);
+    ++B->launches;
+  }
+}
+
+// r = b - A x (constrained rows b - x) for every problem and right-hand side.
+void batch_residual(mg_batch* B, const double* x, const double* b, double* r) {
+  for (size_t p = 0; p < B->sub.size(); ++p) {
+    mg_handle* h = B->sub[p];
+    h->ops->residual(h->lv.back(), 0, x + B->off[p], b + B->off[p], r + B->off[p], 0, B->nrhs, B->stream);
+    ++B->launches;
+  }
+}
+
+// per-system dots out[s] = a_s . b_s, copied to the host
+mg_status batch_dots(mg_batch* B, const double* a, const double* b, std::vector<double>& out) {
+  launch_seg_dot(a, 0, 1, b, B->seg, B->partial, B->coef, B->stream);
+  B->launches += 2;
+  out.resize(B->seg.nseg);
+  CU(cudaMemcpyAsync(out.data(), B->coef, B->seg.nseg * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+  CU(cudaStreamSynchronize(B->stream));
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mg_destroy_batch(mg_batch* b) { delete b; }
+
+mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* cuda_stream, mg_batch** out) {
+  if (!problems || !out || nprob < 1 || nrhs < 1) return fail(MG_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  mg_batch* B = new mg_batch();
+  B->nrhs = nrhs;
+  B->stream = (cudaStream_t)cuda_stream;
+  mg_status st;
+  for (int p = 0; p < nprob; ++p) {
+    mg_handle* h = nullptr;
+    // a dense fold of at most 64 MiB per problem keeps the batch's setup short
+    if ((st = setup_internal(&problems[p], cuda_stream, nrhs, 64.0 * (1 << 20), &h)) != MG_OK) {
+      delete B;
+      return st;
+    }
+    B->sub.push_back(h);
+    B->ndof.push_back(h->lv.back().ndof);
+    B->off.push_back(B->total);
+    B->total += h->lv.back().ndof * nrhs;
+  }
+  // segments and blocks
+  std::vector<int> bseg, sfirst;
+  std::vector<int64_t> bs, be;
+  for (int p = 0; p < nprob; ++p)
+    for (int rr = 0; rr < nrhs; ++rr) {
+      const int64_t s0 = B->off[p] + rr * B->ndof[p], len = B->ndof[p];
+      B->sstart.push_back(s0);
+      B->slen.push_back(len);
+      sfirst.push_back((int)bs.size());
+      for (int64_t c = 0; c < len; c += SEG_CHUNK) {
+        bseg.push_back((int)B->sstart.size() - 1);
+        bs.push_back(s0 + c);
+        be.push_back(s0 + std::min<int64_t>(len, c + SEG_CHUNK));
+      }
+    }
+  sfirst.push_back((int)bs.size());
+  B->seg.nseg = (int)B->sstart.size();
+  B->seg.nblocks = (int)bs.size();
+  if ((st = B->alloc(&B->seg.bseg, bseg.size())) != MG_OK || (st = B->alloc(&B->seg.bstart, bs.size())) != MG_OK ||
+      (st = B->alloc(&B->seg.bend, be.size())) != MG_OK || (st = B->alloc(&B->seg.sfirst, sfirst.size())) != MG_OK ||
+      (st = B->alloc(&B->rb, B->total)) != MG_OK || (st = B->alloc(&B->zb, B->total)) != MG_OK) {
+    delete B;
+    return st;
+  }
+  cudaMemcpy(B->seg.bseg, bseg.data(), bseg.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemcpy(B->seg.bstart, bs.data(), bs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(B->seg.bend, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaMemcpy(B->seg.sfirst, sfirst.data(), sfirst.size() * sizeof(int), cudaMemcpyHostToDevice);
+  *out = B;
+  return MG_OK;
+}
+
+mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offset, int64_t* total) {
+  if (!b || p < 0 || p >= (int)b->sub.size()) return fail(MG_ERR_INVALID_ARG, "bad problem index");
+  if (ndof) *ndof = b->ndof[p];
+  if (offset) *offset = b->off[p];
+  if (total) *total = b->total;
+  return MG_OK;
+}
+
+int64_t mg_batch_kernel_launches(const mg_batch* b) { return b ? b->launches : 0; }
+
+mg_status mg_vcycle_batch(mg_batch* B, const double* r, double* z) {
+  if (!B || !r || !z) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (!is_device_ptr(r) || !is_device_ptr(z)) return fail(MG_ERR_INVALID_ARG, "r and z must be device pointers");
+  TRY(batch_graph(B));
+  CU(cudaMemcpyAsync(B->rb, r, B->total * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+  CU(cudaGraphLaunch(B->graph, B->stream));
+  CU(cudaMemcpyAsync(z, B->zb, B->total * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+  B->launches += B->graph_kernels;
+  return MG_OK;
+}
+
+mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, double tol, int maxit, int restart,
+                         mg_stats* stats) {
+  if (!B || !rhs || !x) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (!is_device_ptr(rhs) || !is_device_ptr(x)) return fail(MG_ERR_INVALID_ARG, "rhs and x must be device pointers");
+  if (!(tol > 0.0) || maxit < 0) return fail(MG_ERR_INVALID_ARG, "bad tol or maxit");
+  const int64_t n = B->total;
+  const int ns = B->seg.nseg;
+  if (restart <= 0 || restart > maxit) restart = std::max(1, maxit);
+  const int m = restart;
+  if (B->gm_m < m) {
+    for (auto it = B->allocs.begin(); it != B->allocs.end();) {
+      if (*it == B->V || *it == B->Z || *it == B->w || *it == B->r || *it == B->bb || *it == B->xx ||
+          *it == B->partial || *it == B->coef) {
+        cudaFree(*it);
+        it = B->allocs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    TRY(B->alloc(&B->V, (size_t)(m + 1) * n));
+    TRY(B->alloc(&B->Z, (size_t)m * n));
+    TRY(B->alloc(&B->w, n));
+    TRY(B->alloc(&B->r, n));
+    TRY(B->alloc(&B->bb, n));
+    TRY(B->alloc(&B->xx, n));
+    TRY(B->alloc(&B->partial, (size_t)(m + 2) * B->seg.nblocks));
+    TRY(B->alloc(&B->coef, (size_t)(m + 2) * ns));
+    B->gm_m = m;
+  }
+  TRY(batch_graph(B));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  CU(cudaEventRecord(e0, B->stream));
+  CU(cudaMemcpyAsync(B->bb, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+  if (use_x0) CU(cudaMemcpyAsync(B->xx, x, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+  else CU(cudaMemsetAsync(B->xx, 0, n * sizeof(double), B->stream));
+  std::vector<double> bn2, beta2, hc, hn2;
+  TRY(batch_dots(B, B->bb, B->bb, bn2));
+  std::vector<double> bnorm(ns), relres(ns, 0.0), rel0(ns, -1.0);
+  for (int s = 0; s < ns; ++s) bnorm[s] = std::sqrt(bn2[s]);
+  std::vector<int> its(ns, 0), conv(ns, 0);
+  std::vector<double> H((size_t)ns * (m + 1) * m), cs((size_t)ns * m), sn((size_t)ns * m), gv((size_t)ns * (m + 1));
+  std::vector<int> kdone(ns), active(ns);
+  std::vector<double> scale(ns), coefs((size_t)(m + 1) * ns);
+  int total_its = 0;
+  while (true) {
+    batch_residual(B, B->xx, B->bb, B->r);
+    TRY(batch_dots(B, B->r, B->r, beta2));
+    bool any = false;
+    for (int s = 0; s < ns; ++s) {
+      const double beta = std::sqrt(beta2[s]);
+      relres[s] = bnorm[s] > 0 ? beta / bnorm[s] : 0.0;
+      if (rel0[s] < 0) rel0[s] = relres[s];
+      conv[s] = (beta <= tol * bnorm[s]) ? 1 : 0;
+      active[s] = !conv[s];
+      any = any || active[s];
+      scale[s] = active[s] ? 1.0 / beta : 0.0;
+      kdone[s] = 0;
+      std::fill(&gv[(size_t)s * (m + 1)], &gv[(size_t)s * (m + 1)] + (m + 1), 0.0);
+      gv[(size_t)s * (m + 1)] = beta;
+    }
+    if (!any || total_its >= maxit) break;
+    CU(cudaMemcpyAsync(B->coef, scale.data(), ns * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+    launch_seg_scale(B->r, B->coef, B->V, B->seg, B->stream);
+    ++B->launches;
+    std::fill(H.begin(), H.end(), 0.0);
+    for (int i = 0; i < m && total_its < maxit; ++i) {
+      double* vi = B->V + (size_t)i * n;
+      double* zi = B->Z + (size_t)i * n;
+      CU(cudaMemcpyAsync(B->rb, vi, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+      CU(cudaGraphLaunch(B->graph, B->stream));
+      B->launches += B->graph_kernels;
+      CU(cudaMemcpyAsync(zi, B->zb, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+      batch_apply(B, zi, B->w);
+      for (int pass = 0; pass < 2; ++pass) {   // classical Gram-Schmidt, twice
+        launch_seg_dot(B->V, n, i + 1, B->w, B->seg, B->partial, B->coef, B->stream);
+        launch_seg_axpy(B->w, B->V, n, i + 1, B->coef, -1.0, B->seg, B->stream);
+        B->launches += 3;
+        hc.resize((size_t)(i + 1) * ns);
+        CU(cudaMemcpyAsync(hc.data(), B->coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
+        CU(cudaStreamSynchronize(B->stream));
+        for (int s = 0; s < ns; ++s)
+          for (int l = 0; l <= i; ++l) H[((size_t)s * (m + 1) + l) * m + i] += hc[(size_t)l * ns + s];
+      }
+      TRY(batch_dots(B, B->w, B->w, hn2));
+      for (int s = 0; s < ns; ++s) scale[s] = (active[s] && hn2[s] > 0) ? 1.0 / std::sqrt(hn2[s]) : 0.0;
+      CU(cudaMemcpyAsync(B->coef, scale.data(), ns * sizeof(double), cudaMemcpyHostToDevice, B->stream));
+      launch_seg_scale(B->w, B->coef, B->V + (size_t)(i + 1) * n, B->seg, B->stream);
+      ++B->launches;
+      ++total_its;
+      bool still = false;
+      for (int s = 0; s < ns; ++s) {
+        if (!active[s]) continue;
+        double* Hs = &H[(size_t)s * (m + 1) * m];
+        double* css = &cs[(size_t)s * m];
+        double* sns = &sn[(size_t)s * m];
+        double* g = &gv[(size_t)s * (m + 1)];
+        const double hn = std::sqrt(hn2[s]);
+        for (int l = 0; l < i; ++l) {
+          const double t = css[l] * Hs[l * m + i] + sns[l] * Hs[(l + 1) * m + i];
+          Hs[(l + 1) * m + i] = -sns[l] * Hs[l * m + i] + css[l] * Hs[(l + 1) * m + i];
+          Hs[l * m + i] = t;
+        }
+        const double den = std::hypot(Hs[i * m + i], hn);
+        if (den == 0.0) {
+          active[s] = 0;
+          continue;
+        }
+        css[i] = Hs[i * m + i] / den;
+        sns[i] = hn / den;
+        Hs[i * m + i] = den;
+        g[i + 1] = -sns[i] * g[i];
+        g[i] = css[i] * g[i];
+        kdone[s] = i + 1;
+        ++its[s];
+        if (std::fabs(g[i + 1]) <= tol * bnorm[s] || hn == 0.0) active[s] = 0;
+        still = still || active[s];
+      }
+      if (!still) break;
+    }
+    // x_s += sum_l y_l Z[l]_s with each system's own Krylov dimension
+    int kmax = 0;
+    for (int s = 0; s < ns; ++s) kmax = std::max(kmax, kdone[s]);
+    if (kmax == 0) break;
+    std::fill(coefs.begin(), coefs.end(), 0.0);
+    for (int s = 0; s < ns; ++s) {
+      const int k = kdone[s];
+      const double* Hs = &H[(size_t)s * (m + 1) * m];
+      const double* g = &gv[(size_t)s * (m + 1)];
+      std::vector<double> y(k);
+      for (int l = k - 1; l >= 0; --l) {
+        double t = g[l];
+        for (int q = l + 1; q < k; ++q) t -= Hs[l * m + q] * y[q];
+        y[l] = t / Hs[l * m + l];
+      }
+      for (int l = 0; l < k; ++l) coefs[(size_t)l * ns + s] = y[l];
+    }
+    CU(cudaMemcpyAsync(B->coef, coefs.data(), (size_t)kmax * ns * sizeof(double), cudaMemcpyHostToDevice,
+                       B->stream));
+    launch_seg_axpy(B->xx, B->Z, n, kmax, B->coef, 1.0, B->seg, B->stream);
+    ++B->launches;
+  }
+  CU(cudaMemcpyAsync(x, B->xx, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
+  CU(cudaEventRecord(e1, B->stream));
+  CU(cudaStreamSynchronize(B->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  bool all = true;
+  for (int s = 0; s < ns; ++s) {
+    all = all && conv[s];
+    if (stats) {
+      stats[s].iterations = its[s];
+      stats[s].converged = conv[s];
+      stats[s].rel_residual = relres[s];
+      stats[s].initial_rel_residual = rel0[s] < 0 ? 0.0 : rel0[s];
+      stats[s].removed_flux = 0.0;
+      stats[s].solve_ms = ms;
+    }
+  }
+  return all ? MG_OK : fail(MG_ERR_NOT_CONVERGED, "some systems of the batch reached maxit");
 }
 
 }  // extern "C"

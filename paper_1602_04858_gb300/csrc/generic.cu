@@ -170,28 +170,121 @@ __global__ void k_set_units(T* __restrict__ B, int64_t ndof, int64_t c0, int nc)
 
 // Column-blocked z = Bd^T b: block (x, y) sums rows r of chunk y for DENSE_THREADS entries i.
 constexpr int DENSE_THREADS = 256;
-template <typename T>
+// NR right-hand sides (vectors n apart) share each read of Bd.
+template <typename T, int NR>
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense_partial(const T* __restrict__ Bd, int64_t n,
                                                                  const T* __restrict__ b, T* __restrict__ partial) {
   const int64_t i = (int64_t)blockIdx.x * DENSE_THREADS + threadIdx.x;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = blockIdx.y * per, r1 = (r0 + per < n) ? r0 + per : n;
-  T acc = T(0);
+  T acc[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) acc[q] = T(0);
   if (i < n)
-    for (int64_t r = r0; r < r1; ++r) acc += Bd[r * n + i] * b[r];
-  if (i < n) partial[blockIdx.y * n + i] = acc;
+    for (int64_t r = r0; r < r1; ++r) {
+      const T a = Bd[r * n + i];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] += a * b[q * n + r];
+    }
+  if (i < n)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) partial[((int64_t)q * gridDim.y + blockIdx.y) * n + i] = acc[q];
 }
 
 template <typename T>
 __global__ void k_dense_reduce(const T* __restrict__ partial, int chunks, int64_t n, T* __restrict__ z) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  partial += (int64_t)blockIdx.y * chunks * n;   // one right-hand side per blockIdx.y
   T acc = T(0);
   for (int y = 0; y < chunks; ++y) acc += partial[y * n + i];
-  z[i] = acc;
+  z[(int64_t)blockIdx.y * n + i] = acc;
+}
+
+// --- segmented vectors: many independent systems in one long vector ---------
+// Block b covers [bstart[b], bend[b]) inside segment bseg[b]; the blocks of
+// segment s are sfirst[s] .. sfirst[s+1]-1.
+constexpr int SEG_THREADS = 256;
+
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_dot(const double* __restrict__ V, int64_t ld, int nvec,
+                                                         const double* __restrict__ w, const int64_t* __restrict__ bstart,
+                                                         const int64_t* __restrict__ bend, int nblocks,
+                                                         double* __restrict__ partial) {
+  __shared__ double red[SEG_THREADS / 32];
+  const int b = blockIdx.x;
+  const int64_t i0 = bstart[b], i1 = bend[b];
+  for (int v = 0; v < nvec; ++v) {
+    double a = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += SEG_THREADS) a += V[(int64_t)v * ld + i] * w[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < SEG_THREADS / 32; ++q) t += red[q];
+      partial[(int64_t)v * nblocks + b] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// out[v * nseg + s] = sum of the partials of segment s (fixed order)
+__global__ void k_seg_reduce(const double* __restrict__ partial, int nblocks, const int* __restrict__ sfirst,
+                             int nseg, double* __restrict__ out) {
+  const int s = blockIdx.x, v = blockIdx.y;
+  __shared__ double red[32];
+  double a = 0.0;
+  for (int q = sfirst[s] + threadIdx.x; q < sfirst[s + 1]; q += blockDim.x) a += partial[(int64_t)v * nblocks + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    out[(int64_t)v * nseg + s] = t;
+  }
+}
+
+// w += sign * sum_v coef[v * nseg + seg] V[v]  (segment-wise coefficients)
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_axpy(double* __restrict__ w, const double* __restrict__ V,
+                                                          int64_t ld, int nvec, const double* __restrict__ coef,
+                                                          int nseg, double sign, const int* __restrict__ bseg,
+                                                          const int64_t* __restrict__ bstart,
+                                                          const int64_t* __restrict__ bend) {
+  const int b = blockIdx.x, sg = bseg[b];
+  for (int64_t i = bstart[b] + threadIdx.x; i < bend[b]; i += SEG_THREADS) {
+    double a = 0.0;
+    for (int v = 0; v < nvec; ++v) a += coef[(int64_t)v * nseg + sg] * V[(int64_t)v * ld + i];
+    w[i] += sign * a;
+  }
+}
+
+// out = scale[seg] * a
+__global__ void __launch_bounds__(SEG_THREADS) k_seg_scale(const double* __restrict__ a, const double* __restrict__ scale,
+                                                           double* __restrict__ out, const int* __restrict__ bseg,
+                                                           const int64_t* __restrict__ bstart,
+                                                           const int64_t* __restrict__ bend) {
+  const int b = blockIdx.x;
+  const double sc = scale[bseg[b]];
+  for (int64_t i = bstart[b] + threadIdx.x; i < bend[b]; i += SEG_THREADS) out[i] = sc * a[i];
 }
 
 }  // namespace
+
+void launch_seg_dot(const double* V, int64_t ld, int nvec, const double* w, const SegTable& t, double* partial,
+                    double* out, cudaStream_t s) {
+  k_seg_dot<<<t.nblocks, SEG_THREADS, 0, s>>>(V, ld, nvec, w, t.bstart, t.bend, t.nblocks, partial);
+  k_seg_reduce<<<dim3(t.nseg, nvec), 256, 0, s>>>(partial, t.nblocks, t.sfirst, t.nseg, out);
+}
+void launch_seg_axpy(double* w, const double* V, int64_t ld, int nvec, const double* coef, double sign,
+                     const SegTable& t, cudaStream_t s) {
+  k_seg_axpy<<<t.nblocks, SEG_THREADS, 0, s>>>(w, V, ld, nvec, coef, t.nseg, sign, t.bseg, t.bstart, t.bend);
+}
+void launch_seg_scale(const double* a, const double* scale, double* out, const SegTable& t, cudaStream_t s) {
+  k_seg_scale<<<t.nblocks, SEG_THREADS, 0, s>>>(a, scale, out, t.bseg, t.bstart, t.bend);
+}
 
 void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaStream_t s) {
   const unsigned g = blocks(ndof * nc, 256);
@@ -199,16 +292,24 @@ void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaSt
   else k_set_units<double><<<g, 256, 0, s>>>((double*)B, ndof, c0, nc);
 }
 
-void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, cudaStream_t s) {
-  const dim3 grid(blocks(n, DENSE_THREADS), DENSE_CHUNKS);
-  if (f32) {
-    k_dense_partial<float><<<grid, DENSE_THREADS, 0, s>>>((const float*)Bd, n, (const float*)b, (float*)partial);
-    k_dense_reduce<float><<<blocks(n, 256), 256, 0, s>>>((const float*)partial, DENSE_CHUNKS, n, (float*)z);
-  } else {
-    k_dense_partial<double><<<grid, DENSE_THREADS, 0, s>>>((const double*)Bd, n, (const double*)b,
-                                                           (double*)partial);
-    k_dense_reduce<double><<<blocks(n, 256), 256, 0, s>>>((const double*)partial, DENSE_CHUNKS, n, (double*)z);
+template <typename T>
+void dense_apply_t(const T* Bd, int64_t n, const T* b, T* z, T* partial, int nrhs, cudaStream_t s) {
+  for (int r0 = 0; r0 < nrhs; r0 += 4) {
+    const int nr = (nrhs - r0 < 4) ? nrhs - r0 : 4;
+    const dim3 grid(blocks(n, DENSE_THREADS), DENSE_CHUNKS);
+    const T* bb = b + (int64_t)r0 * n;
+    if (nr == 4) k_dense_partial<T, 4><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
+    else if (nr == 3) k_dense_partial<T, 3><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
+    else if (nr == 2) k_dense_partial<T, 2><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
+    else k_dense_partial<T, 1><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
+    k_dense_reduce<T><<<dim3(blocks(n, 256), nr), 256, 0, s>>>(partial, DENSE_CHUNKS, n, z + (int64_t)r0 * n);
   }
+}
+
+void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, int nrhs,
+                        cudaStream_t s) {
+  if (f32) dense_apply_t<float>((const float*)Bd, n, (const float*)b, (float*)z, (float*)partial, nrhs, s);
+  else dense_apply_t<double>((const double*)Bd, n, (const double*)b, (double*)z, (double*)partial, nrhs, s);
 }
 
 void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t s) {

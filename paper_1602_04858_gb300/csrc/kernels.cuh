@@ -16,9 +16,11 @@ namespace mgd {
 // ---------------------------------------------------------------------------
 template <int D, int K, typename T>
 __global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
-                                               const T* __restrict__ x, T* __restrict__ y) {
+                                               const T* __restrict__ x, T* __restrict__ y, int64_t vs) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.ndof) return;
+  x += blockIdx.y * vs;
+  y += blockIdx.y * vs;
   int idx[D];
   const int comp = decode(L, g, idx);
   y[g] = apply_row(L, tb, comp, idx, x);
@@ -71,6 +73,63 @@ __global__ void __launch_bounds__(RN_THREADS) k_residual_norm(const Lvl<D, K, T>
     for (int w = 0; w < RN_THREADS / 32; ++w) s += red[w];
     partial[blockIdx.x] = s;
   }
+}
+
+// Load vector of cellwise-constant data (the first term of F in eq. (BCh)
+// and the pressure block of eq. (Brinkman-weak)):
+//   velocity row (i, node): sum over the cells K containing the node of
+//     f_i(K) * integral over K of the basis function,
+//   pressure row: -g(K) * integral of q;  constrained rows: 0.
+// f: D component arrays of one value per cell (x fastest); g may be null.
+template <int D, int K>
+__global__ void __launch_bounds__(256) k_load(const Lvl<D, K, double> L, const __grid_constant__ Tab<K, double> tb,
+                                              const double* __restrict__ f, const double* __restrict__ g,
+                                              double* __restrict__ out) {
+  constexpr int K1 = K + 1, NG = K + 2;
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= L.ndof) return;
+  int idx[D];
+  const int comp = decode(L, gi, idx);
+  int64_t ncell = 1;
+#pragma unroll
+  for (int e = 0; e < D; ++e) ncell *= L.n;
+  if (comp == D) {
+    int cell[D];
+    double w = L.s_c;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      cell[e] = idx[e] / K1;
+      w *= tb.wg[idx[e] % K1];
+    }
+    out[gi] = g ? -g[cell_linear(L, cell)] * w : 0.0;
+    return;
+  }
+  if (is_constrained(L, comp, idx)) {
+    out[gi] = 0.0;
+    return;
+  }
+  int cell[D];
+  double wperp = L.s_c;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (e == comp) continue;
+    cell[e] = idx[e] / K1;
+    wperp *= tb.wg[idx[e] % K1];
+  }
+  const int t = idx[comp];
+  int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
+  if (lo < 0) lo = 0;
+  if (hi > L.n - 1) hi = L.n - 1;
+  double acc = 0.0;
+  for (int cx = lo; cx <= hi; ++cx) {
+    const int a = t - cx * K1;
+    double rs = 0.0;
+#pragma unroll
+    for (int ap = 0; ap < NG; ++ap) rs += tb.Mcg[a][ap];   // integral of the Gauss-Lobatto basis function
+    cell[comp] = cx;
+    acc += f[comp * ncell + cell_linear(L, cell)] * rs;
+  }
+  out[gi] = acc * wperp;
 }
 
 // ---------------------------------------------------------------------------
@@ -419,18 +478,20 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 // Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
 // for every patch v of one colour, x|_v += S_v (b - A x)|_v.
 //
-// A warp owns GPW patches.  Lane 0 first issues one bulk asynchronous copy
-// per patch of its stored inverse S_v into shared memory (S_v does not depend
-// on earlier passes, so this happens before the programmatic-dependent-launch
-// wait and overlaps the previous pass).  The lanes gather each patch's window
-// of x (every column its rows touch), its b rows and its 2^D cell
-// coefficients, and form the local residual.  For a patch away from the
-// boundary the coefficient-free part of its rows (the mu terms and the
-// divergence blocks) is the same dense template R0 for every patch of the
-// level; it is applied from shared memory, RR rows per lane, and the cellwise
-// mass term is added from the 1-D tables.  Patches next to the boundary use
-// the stencil visitor.  Finally S_v is applied: LPP lanes per patch, lane q
-// owning RG consecutive rows of delta.
+// A warp owns GPW patches (one for n_v >= 20) and NR right-hand sides.
+//  1. lane 0 issues one bulk asynchronous copy per patch of its stored
+//     inverse S_v into shared memory; S_v does not depend on earlier passes,
+//     so this precedes the programmatic-dependent-launch wait;
+//  2. the lanes gather the patch window of x (every column its rows touch),
+//     its b rows and its 2^D cell coefficients: all loads of a lane are
+//     issued before any is stored, addresses from per-level offset tables;
+//  3. local residual: for a patch away from the boundary the coefficient-free
+//     part of its rows (mu terms, divergence blocks) is the level's dense
+//     template R0, applied from shared memory with the window columns split
+//     over the lanes; the cellwise mass term comes from a per-level table;
+//     patches next to the boundary use the stencil visitor;
+//  4. delta = S_v r, the columns of S_v split over the lanes, partial sums
+//     reduced in shared memory, then x|_v += delta.
 // ---------------------------------------------------------------------------
 template <int D, int K, typename T, typename TS, int NR = 1>
 struct PassShape {
@@ -440,10 +501,17 @@ struct PassShape {
   using SL = SLayout<NV, TS>;
   static constexpr int RG = SL::RG;
   static constexpr int NVP = SL::NVP;
-  static constexpr int LPP = NVP / RG;      // lanes per patch in the product
-  static constexpr int GPW = 32 / LPP;      // patches per warp
+  static constexpr int LPP = NVP / RG;                    // row groups of the S_v product
+  static constexpr int RR = 16 / (int)sizeof(T);          // rows per lane in the template product
+  static constexpr int NVT = ((NV + RR - 1) / RR) * RR;
+  static constexpr int NRG = NVT / RR;                    // row groups of the template product
+  static constexpr int MAXG = NRG > LPP ? NRG : LPP;
+  static constexpr int GPW = (32 / (4 * MAXG)) > 1 ? 32 / (4 * MAXG) : 1;   // patches per warp
+  static constexpr int LW = 32 / GPW;                     // lanes per patch
+  static constexpr int TSPL = LW / NRG;                   // column splits, template product
+  static constexpr int SSPL = LW / LPP;                   // column splits, S_v product
   static constexpr int WARPS = (NR == 1) ? 4 : 2;
-  static constexpr int PPB = WARPS * GPW;   // patches per block
+  static constexpr int PPB = WARPS * GPW;                 // patches per block
   static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
   // window of x: velocity component i spans WA nodes along x_i and WB across,
   // the pressure WP per direction
@@ -452,17 +520,26 @@ struct PassShape {
   static constexpr int WPP = (D == 2) ? WP * WP : WP * WP * WP;
   static constexpr int WIN = D * WU + WPP;
   static constexpr int NC = 1 << D;
-  // residual rows per lane in the template product (16-byte vectors of T)
-  static constexpr int RR = 16 / (int)sizeof(T);
-  static constexpr int NVT = ((NV + RR - 1) / RR) * RR;   // template column length
-  static constexpr int NRG = NVT / RR;
+  static constexpr int NG = K + 2;
+  static constexpr int MTE = 2 * NG;                      // mass-table entries per row
+  static constexpr int GTE = WIN + NV + NC;               // gather-table entries
+  static constexpr int TPL = WIN * NVT;                   // template entries
+  static constexpr int SPLIT = (TSPL * NVT > SSPL * NVP ? TSPL * NVT : SSPL * NVP);
+  // per patch in shared memory (T): NR windows, NR b-row blocks, NR residual
+  // blocks, the cell coefficients, the split partial sums
+  static constexpr int T_PER_PATCH = NR * (WIN + NV + NVT) + NC + NR * SPLIT;
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  static constexpr int T_PER_PATCH = NR * (WIN + NV + NVT) + NC;   // per rhs: window, b rows, residual; c
-  static constexpr int TPL = WIN * NVT;                     // template entries
-  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + (size_t)TPL * sizeof(T) +
-                                 (size_t)PPB * T_PER_PATCH * sizeof(T) + (size_t)PPB * D * sizeof(int) +
-                                 (size_t)WARPS * sizeof(uint64_t) + 32;
+  // per-level tables in global memory (read through the L1 cache):
+  // R0 (TPL x T), mass coefficients (NV x MTE x T), mass window index and
+  // cell bit (NV x MTE x int each), gather offsets (GTE x int)
+  static constexpr size_t TAB_T = (size_t)TPL + (size_t)NV * MTE;
+  static constexpr size_t TAB_I = (size_t)2 * NV * MTE + GTE;
+  static constexpr size_t TAB_BYTES = TAB_T * sizeof(T) + TAB_I * sizeof(int);
+  // T entries of all patches, rounded so the int64 bases that follow stay aligned
+  static constexpr size_t T_ALIGNED = (((size_t)PPB * T_PER_PATCH * sizeof(T) + 15) / 16) * 16 / sizeof(T);
+  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + T_ALIGNED * sizeof(T) +
+                                 (size_t)PPB * 4 * (D + 1) * sizeof(int64_t) + (size_t)WARPS * sizeof(uint64_t) + 64;
 };
 
 // Window origin along direction e for component comp (D = pressure).
@@ -489,17 +566,21 @@ __device__ __forceinline__ int win_index(const int (&v)[D], int comp, const int 
   return comp * WU + l;
 }
 
-// Local multi-index of window entry r of component C (compile-time shape).
-template <int D, int K, int C>
-__device__ __forceinline__ void win_local(int r, int (&le)[D]) {
+// Component and local multi-index of window entry w.
+template <int D, int K>
+__device__ __forceinline__ int win_local(int w, int (&le)[D]) {
   constexpr int K1 = K + 1;
   constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
+  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
+  int comp = w / WU;
+  if (comp > D) comp = D;
+  int r = w - comp * WU;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
-    if (C == D) {
+    if (comp == D) {
       le[e] = r % WP;
       r /= WP;
-    } else if (e == C) {
+    } else if (e == comp) {
       le[e] = r % WA;
       r /= WA;
     } else {
@@ -507,6 +588,7 @@ __device__ __forceinline__ void win_local(int r, int (&le)[D]) {
       r /= WB;
     }
   }
+  return comp;
 }
 
 template <int D, int K, typename T>
@@ -527,12 +609,12 @@ struct WinVisitor {
   }
 };
 
-// Builds the coefficient-free interior template: R0[w][l] = coefficient of
+// Records the coefficient-free interior template: R0[w][l] = coefficient of
 // window column w in patch row l (c = 0), for a patch away from the boundary.
 template <int D, int K, typename T>
 struct TemplateVisitor {
   const int (&v)[D];
-  T* col;   // R0 + l; column w at col[w * NVT]
+  T* col;   // R0 + l; column w at col[w * nvt]
   int nvt;
   __device__ TemplateVisitor(const int (&vv)[D], T* c, int n) : v(vv), col(c), nvt(n) {}
   __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
@@ -541,78 +623,123 @@ struct TemplateVisitor {
   __device__ __forceinline__ T cell_c(const int (&)[D]) const { return T(0); }
 };
 
+// Per-level tables of the colour pass (one block):
+//   R0 [WIN][NVT]: interior template;  mass table per row: MTE entries of
+//   (coefficient, window index, cell bit), coefficient 0 for unused entries;
+//   gather offsets: window entries relative to the per-patch component base,
+//   b rows relative to the patch-row base, cells relative to the block base.
 template <int D, int K, typename T, typename TS>
-__global__ void k_build_template(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb, T* __restrict__ R0) {
-  using P = PassShape<D, K, T, TS>;
+__global__ void k_build_pass_tables(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                    unsigned char* __restrict__ tabs) {
+  using P = PassShape<D, K, T, TS, 1>;
+  constexpr int K1 = K + 1;
+  T* R0 = reinterpret_cast<T*>(tabs);
+  T* mc = R0 + P::TPL;
+  int* mw = reinterpret_cast<int*>(mc + P::NV * P::MTE);
+  int* mb = mw + P::NV * P::MTE;
+  int* gt = mb + P::NV * P::MTE;
   for (int q = threadIdx.x; q < P::TPL; q += blockDim.x) R0[q] = T(0);
+  for (int q = threadIdx.x; q < P::NV * P::MTE; q += blockDim.x) {
+    mc[q] = T(0);
+    mw[q] = 0;
+    mb[q] = 0;
+  }
   __syncthreads();
   int v[D];
 #pragma unroll
   for (int e = 0; e < D; ++e) v[e] = 2;
-  for (int l = threadIdx.x; l < P::NV; l += blockDim.x) {
+  // interior patches (every v_e in [2, n-2]) exist only for n >= 4; otherwise
+  // the template and mass tables stay zero and are never used
+  for (int l = threadIdx.x; l < P::NV && L.n >= 4; l += blockDim.x) {
     int idx[D];
     const int comp = patch_local_decode<D, K>(v, l, idx);
     TemplateVisitor<D, K, T> vis(v, R0 + l, P::NVT);
     visit_row(L, tb, comp, idx, vis);
-  }
-}
-
-// Mass term (c u, v) of a velocity row from the window.
-template <int D, int K, typename T>
-__device__ __forceinline__ T mass_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, const int (&v)[D], int i,
-                                      const int (&idx)[D], const T* win, const T* cw) {
-  constexpr int K1 = K + 1, NG = K + 2;
-  const int t = idx[i];
-  T wperp = T(1);
-  int cbits = 0;
+    if (comp < D) {   // mass term: cells containing the node along x_comp
+      const int t = idx[comp];
+      T wperp = T(1);
+      int cbits = 0;
 #pragma unroll
-  for (int e = 0; e < D; ++e) {
-    if (e == i) continue;
-    wperp *= tb.wg[idx[e] % K1];
-    cbits |= (idx[e] / K1 - (v[e] - 1)) << e;
-  }
-  const int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
-  T acc = T(0);
-  for (int cx = lo; cx <= hi; ++cx) {
-    const int a = t - cx * K1;
-    const T cK = cw[cbits | ((cx - (v[i] - 1)) << i)];
-    int j[D];
+      for (int e = 0; e < D; ++e) {
+        if (e == comp) continue;
+        wperp *= tb.wg[idx[e] % K1];
+        cbits |= (idx[e] / K1 - (v[e] - 1)) << e;
+      }
+      const int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
+      int k = 0;
+      for (int cx = lo; cx <= hi; ++cx) {
+        const int a = t - cx * K1;
+        for (int ap = 0; ap < P::NG; ++ap) {
+          int j[D];
 #pragma unroll
-    for (int e = 0; e < D; ++e) j[e] = idx[e];
-    T s = T(0);
-#pragma unroll
-    for (int ap = 0; ap < NG; ++ap) {
-      j[i] = cx * K1 + ap;
-      s += tb.Mcg[a][ap] * win[win_index<D, K>(v, i, j)];
+          for (int e = 0; e < D; ++e) j[e] = idx[e];
+          j[comp] = cx * K1 + ap;
+          mc[l * P::MTE + k] = L.s_c * wperp * tb.Mcg[a][ap];
+          mw[l * P::MTE + k] = win_index<D, K>(v, comp, j);
+          mb[l * P::MTE + k] = cbits | ((cx - (v[comp] - 1)) << comp);
+          ++k;
+        }
+      }
     }
-    acc += cK * s;
   }
-  return L.s_c * wperp * acc;
+  // gather offsets (global strides of each component)
+  for (int q = threadIdx.x; q < P::GTE; q += blockDim.x) {
+    int le[D];
+    int comp = 0;
+    if (q < P::WIN) {
+      comp = win_local<D, K>(q, le);
+    } else if (q < P::WIN + P::NV) {
+      int idx[D];
+      comp = patch_local_decode<D, K>(v, q - P::WIN, idx);
+#pragma unroll
+      for (int e = 0; e < D; ++e) le[e] = idx[e] - ((v[e] - 1) * K1 + ((comp < D && e == comp) ? 1 : 0));
+    } else {
+      const int cl = q - P::WIN - P::NV;
+      int off = 0, s = 1;
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        off += ((cl >> e) & 1) * s;
+        s *= L.n;
+      }
+      gt[q] = off;
+      continue;
+    }
+    int off = 0, s = 1;
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+      off += le[e] * s;
+      s *= (comp < D && e == comp) ? (L.N + 1) : L.N;
+    }
+    gt[q] = off;
+  }
 }
 
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; };
 template <> struct Vec16<double> { using type = double2; };
 
-// NR right-hand sides share each S_v (vectors vs apart); blockIdx.y selects
-// a group of NR vectors.
 template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
                                                      int colour, int64_t count, const TS* __restrict__ S,
-                                                     const T* __restrict__ R0g, T* x, const T* __restrict__ b,
-                                                     int evict_first, int* __restrict__ err, int64_t vs) {
+                                                     const unsigned char* __restrict__ tabs, T* x,
+                                                     const T* __restrict__ b, int evict_first,
+                                                     int* __restrict__ err, int64_t vs) {
   using P = PassShape<D, K, T, TS, NR>;
   constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB, RR = P::RR;
-  constexpr int WIN = P::WIN, NVT = P::NVT;
+  constexpr int WIN = P::WIN, NVT = P::NVT, NRG = P::NRG, LW = P::LW, MTE = P::MTE, GTE = P::GTE;
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* s_inv = smem;                                                   // PPB x S_BYTES
   float* s_scale = reinterpret_cast<float*>(smem + (size_t)PPB * P::S_BYTES);    // PPB x NVP (BF16 only)
-  T* s_R0 = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
-  T* s_t = s_R0 + P::TPL;
-  int* s_v = reinterpret_cast<int*>(s_t + (size_t)PPB * P::T_PER_PATCH);
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(s_v + PPB * D) + 15) & ~uintptr_t(15));
+  const T* s_R0 = reinterpret_cast<const T*>(tabs);   // per-level tables, global (L1-cached)
+  const T* s_mc = s_R0 + P::TPL;
+  const int* s_mw = reinterpret_cast<const int*>(s_mc + NV * MTE);
+  const int* s_mb = s_mw + NV * MTE;
+  const int* s_gt = s_mb + NV * MTE;
+  T* s_t = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
+  int64_t* s_base = reinterpret_cast<int64_t*>(s_t + P::T_ALIGNED);   // PPB x 4 x (D+1)
+  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_base + PPB * 4 * (D + 1));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t pw = ((int64_t)blockIdx.x * P::WARPS + warp) * GPW;   // first patch of this warp
   const int nmine = (pw >= count) ? 0 : (int)((count - pw) < GPW ? (count - pw) : GPW);
@@ -630,96 +757,127 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
                   reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + (pw + g) * NVP, P::SC_BYTES, bar, pol);
     }
   }
-  // the interior template (independent of earlier passes)
-  if (R0g) {
-    using V = typename Vec16<T>::type;
-    const V* src = reinterpret_cast<const V*>(R0g);
-    V* dst = reinterpret_cast<V*>(s_R0);
-    for (int q = threadIdx.x; q < P::TPL / RR; q += blockDim.x) dst[q] = src[q];
-  }
-  if (lane < nmine) {
-    int v[D];
-    patch_vertex<D>(L.n, colour, pw + lane, v);
+  // per-patch vertex and address bases, one entry per lane: window base per
+  // component, b-row base per component, cell base, interior flag, vertex
+  for (int qq = lane; qq < nmine * 4 * (D + 1); qq += 32) {
+    const int gq = qq / (4 * (D + 1)), item = qq - gq * 4 * (D + 1);
+    if (item < 3 * (D + 1) + D) {
+      int v[D];
+      patch_vertex<D>(L.n, colour, pw + gq, v);
+      int64_t val = 0;
+      if (item < 2 * (D + 1)) {
+        const int c = item % (D + 1);
+        const bool row = item > D;
+        int64_t s = 1;
+        val = L.off[c];
 #pragma unroll
-    for (int e = 0; e < D; ++e) s_v[(warp * GPW + lane) * D + e] = v[e];
+        for (int e = 0; e < D; ++e) {
+          val += (int64_t)(row ? (v[e] - 1) * (K + 1) + ((c < D && e == c) ? 1 : 0) : win_origin<D, K>(v, c, e)) * s;
+          s *= (c < D && e == c) ? (L.N + 1) : L.N;
+        }
+      } else if (item == 2 * (D + 1)) {
+        int64_t cs = 1;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          val += (int64_t)(v[e] - 1) * cs;
+          cs *= L.n;
+        }
+      } else if (item == 2 * (D + 1) + 1) {
+        bool interior = true;
+#pragma unroll
+        for (int e = 0; e < D; ++e) interior = interior && v[e] >= 2 && v[e] <= L.n - 2;
+        val = interior ? 1 : 0;
+      } else {
+        val = v[item - 3 * (D + 1)];
+      }
+      s_base[(size_t)(warp * GPW + gq) * 4 * (D + 1) + item] = val;
+    }
   }
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncthreads();
   if (nmine == 0) return;
-  const int* wv = s_v + warp * GPW * D;
   T* tw = s_t + (size_t)(warp * GPW) * P::T_PER_PATCH;
-  // 2. gather windows (component by component, compile-time shapes), b rows, c
-  auto gather = [&](auto Cc) {
-    constexpr int C = decltype(Cc)::value;
-    constexpr int WSZ = (C == D) ? P::WPP : P::WU;
-    constexpr int BASE = C * P::WU;
-    for (int q = lane; q < nmine * WSZ; q += 32) {
-      const int g = q / WSZ, w = q - g * WSZ;
-      int v[D], le[D], idx[D];
+  const int64_t* wb0 = s_base + (size_t)(warp * GPW) * 4 * (D + 1);
+  // 2. gather: window of x (NR), b rows (NR), cell coefficients; per patch
+  //    E entries, all of a lane's loads issued before its stores
+  {
+    constexpr int E = NR * WIN + NR * NV + P::NC;
+    constexpr int TRIPS = (GPW * E + 31) / 32;
+    T val[TRIPS];
 #pragma unroll
-      for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
-      win_local<D, K, C>(w, le);
-      bool inside = true;
+    for (int k = 0; k < TRIPS; ++k) {
+      const int q = lane + 32 * k;
+      const int g = q / E, e = q - g * E;
+      T vv = T(0);
+      if (g < nmine) {
+        const int64_t* pb = wb0 + g * 4 * (D + 1);
+        if (e < NR * WIN) {
+          const int rr = e / WIN, w = e - rr * WIN;
+          int comp = w / P::WU;
+          if (comp > D) comp = D;
+          bool inside = true;
+          if (!pb[2 * (D + 1) + 1]) {   // boundary patch: mask entries outside the domain
+            int le[D];
+            win_local<D, K>(w, le);
 #pragma unroll
-      for (int e = 0; e < D; ++e) {
-        idx[e] = win_origin<D, K>(v, C, e) + le[e];
-        const int hi = (C < D && e == C) ? L.N : L.N - 1;
-        inside = inside && idx[e] >= 0 && idx[e] <= hi;
+            for (int d2 = 0; d2 < D; ++d2) {
+              const int vv2 = (int)pb[3 * (D + 1) + d2];
+              const int o = (comp < D && d2 != comp) ? (vv2 - 2) * (K + 1) : (vv2 - 1) * (K + 1);
+              const int id = o + le[d2];
+              const int hi = (comp < D && d2 == comp) ? L.N : L.N - 1;
+              inside = inside && id >= 0 && id <= hi;
+            }
+          }
+          if (inside) vv = x[pb[comp] + s_gt[w] + rr * vs];
+        } else if (e < NR * (WIN + NV)) {
+          const int e2 = e - NR * WIN;
+          const int rr = e2 / NV, l = e2 - rr * NV;
+          int comp = l / P::PS::NU1;
+          if (comp > D) comp = D;
+          vv = b[pb[(D + 1) + comp] + s_gt[WIN + l] + rr * vs];
+        } else {
+          vv = L.c[pb[2 * (D + 1)] + s_gt[WIN + NV + (e - NR * (WIN + NV))]];
+        }
       }
-      const int64_t f = inside ? flat_index(L, C, idx) : 0;
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr)
-        tw[g * P::T_PER_PATCH + rr * WIN + BASE + w] = inside ? x[f + rr * vs] : T(0);
+      val[k] = vv;
     }
-  };
-  gather(std::integral_constant<int, 0>{});
-  gather(std::integral_constant<int, 1>{});
-  if constexpr (D == 3) gather(std::integral_constant<int, 2>{});
-  gather(std::integral_constant<int, D>{});
-  for (int q = lane; q < nmine * (NV + P::NC); q += 32) {
-    const int g = q / (NV + P::NC), l = q - g * (NV + P::NC);
-    int v[D];
 #pragma unroll
-    for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
-    T* pbase = tw + g * P::T_PER_PATCH;
-    if (l < NV) {
-      int idx[D];
-      const int comp = patch_local_decode<D, K>(v, l, idx);
-      const int64_t f = flat_index(L, comp, idx);
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr) pbase[NR * WIN + rr * NV + l] = b[f + rr * vs];
-    } else {
-      const int cl = l - NV;
-      int cell[D];
-#pragma unroll
-      for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cl >> e) & 1);
-      pbase[NR * (WIN + NV + NVT) + cl] = L.c[cell_linear(L, cell)];
+    for (int k = 0; k < TRIPS; ++k) {
+      const int q = lane + 32 * k;
+      const int g = q / E, e = q - g * E;
+      if (g < nmine) {
+        T* pbase = tw + g * P::T_PER_PATCH;
+        if (e < NR * (WIN + NV)) pbase[e] = val[k];
+        else pbase[NR * (WIN + NV + NVT) + (e - NR * (WIN + NV))] = val[k];
+      }
     }
   }
   __syncwarp();
-  // 3. local residual rows (b - A x)|_v; per patch: NR windows, NR b-row
-  //    blocks, NR residual blocks, then the cell coefficients
-  for (int q = lane; q < nmine * P::NRG; q += 32) {
-    const int g = q / P::NRG, rg = q - g * P::NRG;
-    int v[D];
-    bool interior = R0g != nullptr;
-#pragma unroll
-    for (int e = 0; e < D; ++e) {
-      v[e] = wv[g * D + e];
-      interior = interior && v[e] >= 2 && v[e] <= L.n - 2;
-    }
+  // 3. local residual rows (b - A x)|_v
+  const int g = lane / LW, lp = lane - g * LW;   // patch of this lane, lane within the patch
+  {
     T* pbase = tw + g * P::T_PER_PATCH;
     const T* cw = pbase + NR * (WIN + NV + NVT);
-    if (interior) {
+    T* part = pbase + NR * (WIN + NV + NVT) + P::NC;   // NR x SPLIT
+    const bool active = g < nmine;
+    const bool interior = active && wb0[g * 4 * (D + 1) + 2 * (D + 1) + 1] != 0;
+    int v[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) v[e] = active ? (int)wb0[g * 4 * (D + 1) + 3 * (D + 1) + e] : 2;
+    // template product, window columns split over TSPL lane groups
+    const int rg = lp % NRG, sp = lp / NRG;
+    constexpr int WCH = (WIN + P::TSPL - 1) / P::TSPL;
+    if (interior && sp < P::TSPL) {
       using V = typename Vec16<T>::type;
       T acc[RR][NR];
 #pragma unroll
       for (int r = 0; r < RR; ++r)
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
-#pragma unroll 8
-      for (int w = 0; w < WIN; ++w) {
+      const int w0 = sp * WCH, w1 = (w0 + WCH < WIN) ? w0 + WCH : WIN;
+#pragma unroll 4
+      for (int w = w0; w < w1; ++w) {
         const V c4 = *reinterpret_cast<const V*>(s_R0 + w * NVT + rg * RR);
         const T* cc = reinterpret_cast<const T*>(&c4);
 #pragma unroll
@@ -730,32 +888,34 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
         }
       }
 #pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const int l = rg * RR + r;
-        if (l < NV) {
-          int idx[D];
-          const int comp = patch_local_decode<D, K>(v, l, idx);
+      for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            const T* win = pbase + rr * WIN;
-            const T m = (comp < D) ? mass_row(L, tb, v, comp, idx, win, cw) : T(0);
-            pbase[NR * WIN + NR * NV + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - acc[r][rr] - m;
-          }
+        for (int r = 0; r < RR; ++r) part[rr * P::SPLIT + sp * NVT + rg * RR + r] = acc[r][rr];
+    }
+    __syncwarp();
+    if (interior) {
+      // combine splits, add the mass term, subtract from b
+      for (int l = lp; l < NV; l += LW) {
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+          T a = T(0);
+#pragma unroll
+          for (int s2 = 0; s2 < P::TSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVT + l];
+          const T* win = pbase + rr * WIN;
+#pragma unroll
+          for (int k = 0; k < MTE; ++k) a += s_mc[l * MTE + k] * cw[s_mb[l * MTE + k]] * win[s_mw[l * MTE + k]];
+          pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - a;
         }
       }
-    } else {
+    } else if (active) {
+      for (int l = lp; l < NV; l += LW) {
+        int idx[D];
+        const int comp = patch_local_decode<D, K>(v, l, idx);
 #pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const int l = rg * RR + r;
-        if (l < NV) {
-          int idx[D];
-          const int comp = patch_local_decode<D, K>(v, l, idx);
-#pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
-            visit_row(L, tb, comp, idx, vis);
-            pbase[NR * WIN + NR * NV + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
-          }
+        for (int rr = 0; rr < NR; ++rr) {
+          WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
+          visit_row(L, tb, comp, idx, vis);
+          pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
         }
       }
     }
@@ -768,42 +928,54 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     mbar_wait_bounded(bar, 0, 2000000000ull);   // let copies in flight land before the block exits
     return;
   }
-  const int g = lane / LPP, q = lane - g * LPP;
-  if (g < nmine) {
+  {
+    const int q = lp % LPP, sp = lp / LPP;
+    constexpr int JCH = (NV + P::SSPL - 1) / P::SSPL;
     const int slot = warp * GPW + g;
-    const TS* Sg = reinterpret_cast<const TS*>(s_inv + (size_t)slot * P::S_BYTES) + q * RG;
-    const T* rv = tw + g * P::T_PER_PATCH + NR * (WIN + NV);
+    T* pbase = tw + g * P::T_PER_PATCH;
+    T* part = pbase + NR * (WIN + NV + NVT) + P::NC;
     const float* sc = s_scale + (size_t)slot * NVP;
-    T acc[RG][NR];
+    if (g < nmine && sp < P::SSPL) {
+      const TS* Sg = reinterpret_cast<const TS*>(s_inv + (size_t)slot * P::S_BYTES) + q * RG;
+      const T* rv = pbase + NR * (WIN + NV);
+      T acc[RG][NR];
 #pragma unroll
-    for (int r = 0; r < RG; ++r)
+      for (int r = 0; r < RG; ++r)
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+        for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+      const int j0 = sp * JCH, j1 = (j0 + JCH < NV) ? j0 + JCH : NV;
 #pragma unroll 4
-    for (int j = 0; j < NV; ++j) {
-      T sv[RG];
-      load_rg_smem<TS, T>(Sg + j * NVP, sv);
+      for (int j = j0; j < j1; ++j) {
+        T sv[RG];
+        load_rg_smem<TS, T>(Sg + j * NVP, sv);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) {
-        T rj = rv[rr * NVT + j];
-        if constexpr (P::BF) rj *= sc[j];
+        for (int rr = 0; rr < NR; ++rr) {
+          T rj = rv[rr * NVT + j];
+          if constexpr (P::BF) rj *= sc[j];
 #pragma unroll
-        for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+          for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+        }
       }
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+        for (int r = 0; r < RG; ++r) part[rr * P::SPLIT + sp * NVP + q * RG + r] = acc[r][rr];
     }
-    int v[D];
-#pragma unroll
-    for (int e = 0; e < D; ++e) v[e] = wv[g * D + e];
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      const int row = q * RG + r;
-      if (row < NV) {
-        int idx[D];
-        const int comp = patch_local_decode<D, K>(v, row, idx);
-        const int64_t f = flat_index(L, comp, idx);
+    __syncwarp();
+    if (g < nmine) {
+      const int64_t* pb = wb0 + g * 4 * (D + 1);
+      for (int row = lp; row < NV; row += LW) {
+        int comp = row / P::PS::NU1;
+        if (comp > D) comp = D;
+        const int64_t f = pb[(D + 1) + comp] + s_gt[WIN + row];
         const T sr = P::BF ? (T)sc[row] : T(1);
 #pragma unroll
-        for (int rr = 0; rr < NR; ++rr) x[f + rr * vs] += P::BF ? acc[r][rr] * sr : acc[r][rr];
+        for (int rr = 0; rr < NR; ++rr) {
+          T a = T(0);
+#pragma unroll
+          for (int s2 = 0; s2 < P::SSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVP + row];
+          x[f + rr * vs] += P::BF ? a * sr : a;
+        }
       }
     }
   }

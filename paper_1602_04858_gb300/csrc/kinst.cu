@@ -49,9 +49,12 @@ template <> const Tab<K, float>& tab<float>() { return tabs().f; }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-void apply(const HostLevel& h, int f32, const void* x, void* y, cudaStream_t s) {
-  if (f32) k_apply<D, K, float><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (float*)y);
-  else k_apply<D, K, double><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x, (double*)y);
+void apply(const HostLevel& h, int f32, const void* x, void* y, int nrhs, cudaStream_t s) {
+  const dim3 grid(blocks(h.ndof, 256), nrhs);
+  if (f32)
+    k_apply<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (float*)y, h.ndof);
+  else
+    k_apply<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x, (double*)y, h.ndof);
 }
 
 void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r, int zero_c, int nrhs,
@@ -123,7 +126,7 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), tab<T>(), colour, h.count[colour],
-                     (const TS*)S, (const T*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
 // Right-hand sides in groups of four share each S_v load; the rest one by one.
@@ -146,16 +149,20 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
   else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, err, nrhs, s);
 }
 
+// Bytes of the per-level colour-pass tables (rounded to 16).
 int64_t template_elems(int sprec) {
-  if (sprec == P64) return PassShape<D, K, double, double, 1>::TPL;
-  if (sprec == P32) return PassShape<D, K, float, float, 1>::TPL;
-  return PassShape<D, K, float, __nv_bfloat16, 1>::TPL;
+  size_t b;
+  if (sprec == P64) b = PassShape<D, K, double, double, 1>::TAB_BYTES;
+  else if (sprec == P32) b = PassShape<D, K, float, float, 1>::TAB_BYTES;
+  else b = PassShape<D, K, float, __nv_bfloat16, 1>::TAB_BYTES;
+  return (int64_t)((b + 15) / 16) * 16;
 }
 
-void build_template(const HostLevel& h, int sprec, void* R0, cudaStream_t s) {
-  if (sprec == P64) k_build_template<D, K, double, double><<<1, 256, 0, s>>>(mk<double>(h), tab<double>(), (double*)R0);
-  else if (sprec == P32) k_build_template<D, K, float, float><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), (float*)R0);
-  else k_build_template<D, K, float, __nv_bfloat16><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), (float*)R0);
+void build_template(const HostLevel& h, int sprec, void* tabs, cudaStream_t s) {
+  auto* t = (unsigned char*)tabs;
+  if (sprec == P64) k_build_pass_tables<D, K, double, double><<<1, 256, 0, s>>>(mk<double>(h), tab<double>(), t);
+  else if (sprec == P32) k_build_pass_tables<D, K, float, float><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), t);
+  else k_build_pass_tables<D, K, float, __nv_bfloat16><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), t);
 }
 
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
@@ -168,6 +175,10 @@ int64_t residual_norm(const HostLevel& h, const double* x, const double* b, doub
   const int64_t nb = residual_norm_blocks(h.ndof);
   k_residual_norm<D, K, double><<<(unsigned)nb, RN_THREADS, 0, s>>>(mk<double>(h), tab<double>(), x, b, r, partial);
   return nb;
+}
+
+void load_vector(const HostLevel& h, const double* f, const double* g, double* b, cudaStream_t s) {
+  k_load<D, K><<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), tab<double>(), f, g, b);
 }
 
 __global__ void k_copy_constrained(const Lvl<D, K, double> L, const double* __restrict__ r, double* __restrict__ z) {
@@ -201,6 +212,7 @@ DKOps make_ops() {
   o.coarse_assemble = coarse_assemble;
   o.copy_constrained = copy_constrained;
   o.residual_norm = residual_norm;
+  o.load_vector = load_vector;
   o.template_elems = template_elems;
   o.build_template = build_template;
   return o;

@@ -21,7 +21,7 @@ struct HostLevel {
   float* c32;
   int sprec;             // storage precision of the patch inverses (Prec)
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
-  void* R0;              // interior-patch template of the colour pass (working precision), or null
+  void* R0;              // colour-pass tables: interior template, mass and gather tables
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision
@@ -33,8 +33,8 @@ struct DKOps {
   int nv;                // patch size
   int nvp[3];            // stored column length per storage precision (P64, P32, P32B)
   int64_t s_stride[3];   // elements per stored patch inverse
-  // y = A x (f32 != 0: float vectors, float coefficient)
-  void (*apply)(const HostLevel&, int f32, const void* x, void* y, cudaStream_t);
+  // y = A x (f32 != 0: float vectors, float coefficient), nrhs vectors
+  void (*apply)(const HostLevel&, int f32, const void* x, void* y, int nrhs, cudaStream_t);
   // The V-cycle kernels act on nrhs vectors stored one after another (each
   // of its level's ndof entries).
   // r = b - A x; constrained rows r = 0 (zero_c) or b - x
@@ -50,7 +50,7 @@ struct DKOps {
   // the patch inverses sets *err = 2
   void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, int* err,
                       int nrhs, cudaStream_t);
-  // interior-patch template of the colour pass (entries for storage precision sprec)
+  // per-level colour-pass tables: bytes for storage precision sprec, and their construction
   int64_t (*template_elems)(int sprec);
   void (*build_template)(const HostLevel&, int sprec, void* R0, cudaStream_t);
   // bordered dense matrix of the coarsest level
@@ -60,6 +60,8 @@ struct DKOps {
   // returns the number of partials (blocks) written
   int64_t (*residual_norm)(const HostLevel&, const double* x, const double* b, double* r, double* partial,
                            cudaStream_t);
+  // load vector of cellwise-constant f (D x ncell) and g (ncell, may be null), FP64
+  void (*load_vector)(const HostLevel&, const double* f, const double* g, double* b, cudaStream_t);
   // z[g] = r[g] on the constrained dofs (FP64)
   void (*copy_constrained)(const HostLevel&, const double* r, double* z, cudaStream_t);
 };
@@ -94,8 +96,29 @@ inline int64_t residual_norm_blocks(int64_t ndof) { return (ndof + 255) / 256; }
 int multidot_blocks();
 // vectors r = 0..nc-1 of B (each ndof long) become the unit vectors e_{c0+r}
 void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaStream_t);
-// z = Bd^T b with Bd (n x n, row r = B e_r); partial holds DENSE_CHUNKS x n
+// Segmented FP64 vectors: nseg independent systems in one long vector, cut
+// into nblocks blocks of at most SEG_CHUNK entries that never cross a segment.
+constexpr int64_t SEG_CHUNK = 16384;
+struct SegTable {
+  int nseg = 0, nblocks = 0;
+  int* bseg = nullptr;        // segment of each block (device)
+  int64_t* bstart = nullptr;  // [bstart, bend) of each block (device)
+  int64_t* bend = nullptr;
+  int* sfirst = nullptr;      // first block of each segment, nseg + 1 entries (device)
+};
+// out[v * nseg + s] = V[v]_s . w_s  (partial: nvec x nblocks doubles)
+void launch_seg_dot(const double* V, int64_t ld, int nvec, const double* w, const SegTable& t, double* partial,
+                    double* out, cudaStream_t);
+// w_s += sign * sum_v coef[v * nseg + s] V[v]_s
+void launch_seg_axpy(double* w, const double* V, int64_t ld, int nvec, const double* coef, double sign,
+                     const SegTable& t, cudaStream_t);
+// out_s = scale[s] * a_s
+void launch_seg_scale(const double* a, const double* scale, double* out, const SegTable& t, cudaStream_t);
+
+// z = Bd^T b with Bd (n x n, row r = B e_r) for nrhs vectors (n apart);
+// partial holds 4 x DENSE_CHUNKS x n
 constexpr int DENSE_CHUNKS = 64;
-void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, cudaStream_t);
+void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, int nrhs,
+                        cudaStream_t);
 
 }  // namespace mgd

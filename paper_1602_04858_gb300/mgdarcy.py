@@ -24,6 +24,11 @@ API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
     "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
+    "mg_setup_batch", "mg_destroy_batch", "mg_batch_layout", "mg_vcycle_batch", "mg_solve_batch",
+    "mg_batch_kernel_launches", "mg_load_vector",
+    "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
+    "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
+    "mg_cnn_train_step", "mg_cnn_guess",
 ]
 
 
@@ -76,6 +81,30 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
+    lib.mg_setup_batch.argtypes = [ctypes.POINTER(mg_problem), i, i, vp, ctypes.POINTER(vp)]
+    lib.mg_destroy_batch.argtypes = [vp]
+    lib.mg_destroy_batch.restype = None
+    lib.mg_batch_layout.argtypes = [vp, i, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.mg_vcycle_batch.argtypes = [vp, vp, vp]
+    lib.mg_solve_batch.argtypes = [vp, vp, vp, i, d, i, i, ctypes.POINTER(mg_stats)]
+    lib.mg_batch_kernel_launches.argtypes = [vp]
+    lib.mg_batch_kernel_launches.restype = i64
+    lib.mg_load_vector.argtypes = [vp, i, vp, vp, vp]
+    f = ctypes.c_float
+    lib.mg_cnn_create.argtypes = [i, i, ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+    lib.mg_cnn_destroy.argtypes = [vp]
+    lib.mg_cnn_destroy.restype = None
+    lib.mg_cnn_param_count.argtypes = [vp]
+    lib.mg_cnn_param_count.restype = i64
+    lib.mg_cnn_get_params.argtypes = [vp, vp]
+    lib.mg_cnn_set_params.argtypes = [vp, vp]
+    lib.mg_cnn_set_normalisation.argtypes = [vp, vp]
+    lib.mg_cnn_features.argtypes = [vp, vp, vp, vp]
+    lib.mg_cnn_targets.argtypes = [vp, vp, vp]
+    lib.mg_cnn_forward.argtypes = [vp, vp, i, vp]
+    lib.mg_cnn_gradients.argtypes = [vp, vp, vp, i, ctypes.POINTER(f), vp]
+    lib.mg_cnn_train_step.argtypes = [vp, vp, vp, i, f, ctypes.POINTER(f)]
+    lib.mg_cnn_guess.argtypes = [vp, vp, vp, vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -83,22 +112,23 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_last_error.argtypes = []
     lib.mg_last_error.restype = ctypes.c_char_p
     for name in API:
-        if name not in ("mg_destroy", "mg_kernel_launches", "mg_status_string", "mg_last_error"):
+        if name not in ("mg_destroy", "mg_kernel_launches", "mg_status_string", "mg_last_error",
+                        "mg_destroy_batch", "mg_batch_kernel_launches", "mg_cnn_destroy", "mg_cnn_param_count"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
 
 
-def _ptr(a):
-    """Raw pointer of a contiguous FP64 torch tensor or NumPy array."""
+def _ptr(a, dtype="float64"):
+    """Raw pointer of a contiguous torch tensor or NumPy array of the given dtype."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-            raise TypeError("arrays must be contiguous float64")
+        if a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"arrays must be contiguous {dtype}")
         return a.ctypes.data
-    if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
-        raise TypeError("tensors must be contiguous float64")
+    if str(a.dtype) != "torch." + dtype or not a.is_contiguous():
+        raise TypeError(f"tensors must be contiguous {dtype}")
     return a.data_ptr()
 
 
@@ -204,5 +234,130 @@ class Multigrid:
         _check(load().mg_residual_norm(self.h, level, _ptr(x), _ptr(b), _ptr(r), ctypes.addressof(out)))
         return out.value
 
+    def load_vector(self, f, g, b, level=-1):
+        """b = load vector of cellwise-constant f (dim x cells) and g (cells or None); device tensors."""
+        _check(load().mg_load_vector(self.h, level, _ptr(f), _ptr(g), _ptr(b)))
+
     def launches(self):
         return load().mg_kernel_launches(self.h)
+
+
+class Batch:
+    """Independent problems with nrhs right-hand sides each (mg_setup_batch).
+
+    problems: list of dicts with keys dim, n_coarse, n_levels, degree, mu, c
+    (and optionally precision, m_fine, variable_cycle, coarse_avg, dense_level).
+    """
+
+    def __init__(self, problems, nrhs=4, stream=None):
+        lib = load()
+        arr = (mg_problem * len(problems))()
+        self._keep = []
+        for k, p in enumerate(problems):
+            c = p["c"]
+            self._keep.append(c)
+            prec = p.get("precision", "fp32")
+            arr[k] = mg_problem(p["dim"], p["n_coarse"], p["n_levels"], p["degree"], float(p["mu"]), _ptr(c),
+                                PREC[prec] if isinstance(prec, str) else int(prec), int(p.get("m_fine", 2)),
+                                1 if p.get("variable_cycle", True) else 0, int(p.get("coarse_avg", 0)),
+                                int(p.get("dense_level", -1)))
+        h = ctypes.c_void_p()
+        _check(lib.mg_setup_batch(arr, len(problems), int(nrhs), ctypes.c_void_p(_stream_ptr(stream)),
+                                  ctypes.byref(h)))
+        self.h = h
+        self.nprob, self.nrhs = len(problems), nrhs
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mg_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self, p):
+        nd, off, tot = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().mg_batch_layout(self.h, p, ctypes.byref(nd), ctypes.byref(off), ctypes.byref(tot)))
+        return nd.value, off.value, tot.value
+
+    def total(self):
+        return self.layout(0)[2]
+
+    def vcycle(self, r, z):
+        _check(load().mg_vcycle_batch(self.h, _ptr(r), _ptr(z)))
+
+    def solve(self, rhs, x, use_x0=False, tol=1e-8, maxit=200, restart=20, check=True):
+        st = (mg_stats * (self.nprob * self.nrhs))()
+        status = load().mg_solve_batch(self.h, _ptr(rhs), _ptr(x), 1 if use_x0 else 0, float(tol), int(maxit),
+                                       int(restart), st)
+        if check:
+            _check(status)
+        return list(st), status
+
+    def launches(self):
+        return load().mg_batch_kernel_launches(self.h)
+
+
+class CNN:
+    """The learned-initial-guess network (mg_cnn_*); n x n RT_0 cell grids."""
+
+    def __init__(self, n, max_batch=16, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().mg_cnn_create(int(n), int(max_batch), int(seed), ctypes.c_void_p(_stream_ptr(stream)),
+                                    ctypes.byref(h)))
+        self.h, self.n = h, n
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().mg_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def param_count(self):
+        return load().mg_cnn_param_count(self.h)
+
+    def get_params(self):
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        _check(load().mg_cnn_get_params(self.h, _ptr(out, "float32")))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(load().mg_cnn_set_params(self.h, _ptr(p, "float32")))
+
+    def set_normalisation(self, in_mean, in_std, out_mean, out_std):
+        v = np.ascontiguousarray(np.concatenate([in_mean, in_std, out_mean, out_std]), dtype=np.float32)
+        _check(load().mg_cnn_set_normalisation(self.h, _ptr(v, "float32")))
+
+    def features(self, c, f, out):
+        _check(load().mg_cnn_features(self.h, _ptr(c), _ptr(f), _ptr(out, "float32")))
+
+    def targets(self, x, out):
+        _check(load().mg_cnn_targets(self.h, _ptr(x), _ptr(out, "float32")))
+
+    def forward(self, inp, batch, out):
+        _check(load().mg_cnn_forward(self.h, _ptr(inp, "float32"), int(batch), _ptr(out, "float32")))
+
+    def gradients(self, inp, target, batch):
+        loss = ctypes.c_float()
+        g = np.zeros(self.param_count(), dtype=np.float32)
+        _check(load().mg_cnn_gradients(self.h, _ptr(inp, "float32"), _ptr(target, "float32"), int(batch),
+                                       ctypes.byref(loss), _ptr(g, "float32")))
+        return loss.value, g
+
+    def train_step(self, inp, target, batch, lr):
+        loss = ctypes.c_float()
+        _check(load().mg_cnn_train_step(self.h, _ptr(inp, "float32"), _ptr(target, "float32"), int(batch),
+                                        ctypes.c_float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def guess(self, c, f, x0):
+        _check(load().mg_cnn_guess(self.h, _ptr(c), _ptr(f), _ptr(x0)))

@@ -1,0 +1,80 @@
+"""The learned initial guess: BF16/FP32 network kernels and their use in the solve.
+
+* forward outputs and parameter gradients of the GPU network against the FP64
+  reference (oracle/cnn.py) with the same parameters: relative error per
+  tensor <= 2e-2 (BF16 weights and activations, FP32 accumulation);
+* a short training on solves produced by the method, then held-out problems
+  solved from the zero and from the learned guess: every solve reaches
+  1e-8 and the learned guess needs no more iterations on average.
+"""
+import numpy as np
+import pytest
+
+from oracle import cnn as ocnn
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1602_04858_gb300 import learned, mgdarcy  # noqa: E402
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([w.reshape(-1), b]) for w, b in params]).astype(np.float32)
+
+
+def _unflat(flat, like):
+    out, k = [], 0
+    for w, b in like:
+        nw = w.size
+        out.append((flat[k:k + nw].reshape(w.shape), flat[k + nw:k + nw + b.size]))
+        k += nw + b.size
+    return out
+
+
+def test_forward_and_gradients_match_fp64_reference():
+    n, batch = 16, 2
+    params = ocnn.init_params(7)
+    net = mgdarcy.CNN(n, max_batch=batch, seed=3)
+    assert net.param_count() == sum(w.size + b.size for w, b in params)
+    net.set_params(_flat(params))
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((batch, 3, n, n)).astype(np.float32)
+    t = rng.standard_normal((batch, 3, n, n)).astype(np.float32)
+    xd = torch.as_tensor(x, device="cuda").contiguous()
+    td = torch.as_tensor(t, device="cuda").contiguous()
+    out = torch.zeros_like(xd)
+    net.forward(xd, batch, out)
+    torch.cuda.synchronize()
+    y = out.cpu().numpy()
+    loss_ref = 0.0
+    grads_ref = None
+    for k in range(batch):
+        yr, _ = ocnn.forward(params, x[k].astype(np.float64))
+        assert np.linalg.norm(y[k] - yr) <= 2e-2 * np.linalg.norm(yr)
+    # the reference loss is the mean over the batch: average the per-sample means
+    for k in range(batch):
+        lk, gk = ocnn.loss_and_grads(params, x[k].astype(np.float64), t[k].astype(np.float64))
+        loss_ref += lk / batch
+        gk = [(gw / batch, gb / batch) for gw, gb in gk]
+        grads_ref = gk if grads_ref is None else [(a + c, b + d) for (a, b), (c, d) in zip(grads_ref, gk)]
+    loss, g = net.gradients(xd, td, batch)
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref
+    for (gw, gb), (rw, rb) in zip(_unflat(g, params), grads_ref):
+        assert np.linalg.norm(gw - rw) <= 2e-2 * np.linalg.norm(rw)
+        assert np.linalg.norm(gb - rb) <= 2e-2 * np.linalg.norm(rb) + 1e-12
+
+
+def test_learned_guess_keeps_tolerance_and_saves_iterations():
+    n = 32
+    net = mgdarcy.CNN(n, max_batch=16, seed=1)
+    data = learned.build_dataset(torch, net, list(range(96)), n)
+    fm, fs, tm, ts = learned.fit_normalisation(torch, net, data)
+    net.set_normalisation(fm, fs, tm, ts)
+    feats, targs = learned.normalised_tensors(torch, net, data)
+    hist = learned.train(torch, net, feats, targs, epochs=40, batch=16, lr=3e-3)
+    assert hist[-1] < hist[0]
+    rows = learned.evaluate(torch, net, list(range(100000, 100012)), n)
+    s = learned.summarise(rows)
+    assert s["all_converged"]
+    assert s["learned_initial_rel_residual_mean"] < 1.0
+    assert s["learned_its_mean"] <= s["zero_its_mean"], s

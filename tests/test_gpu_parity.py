@@ -290,3 +290,28 @@ def test_residual_norm_parity(case):
     bound = 1e-13 * (abs(LJ.A) @ np.abs(x) + np.abs(b))
     assert np.all(np.abs(host(r) - ro) <= bound)
     assert abs(nrm - np.linalg.norm(ro)) <= 1e-12 * np.linalg.norm(ro)
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]], ids=[CASES[0][0], CASES[1][0], CASES[3][0]])
+def test_load_vector_parity(case):
+    """Cellwise-constant f and g: GPU load vector against the oracle's quadrature (eq. BCh)."""
+    from oracle import fem
+    name, d, k, n0, L, mu, cf = case
+    n = n0 * 2 ** (L - 1)
+    H, G = build(case)
+    S = H.levels[-1].S
+    rng = np.random.default_rng(14)
+    fc = rng.standard_normal((d,) + (n,) * d)
+    gc = rng.standard_normal((n,) * d)
+    h = 1.0 / n
+
+    def cell_of(X):
+        idx = np.minimum((X / h).astype(int), n - 1)
+        return tuple(idx[:, e] for e in reversed(range(d)))
+
+    f = lambda X, c: np.stack([fc[i][cell_of(X)] for i in range(d)], 1)
+    g = lambda X: gc[cell_of(X)]
+    bo = fem.load_vector(S, mu, H.levels[-1].c, f=f, div_source=g)
+    b = torch.zeros(S.ndof, dtype=torch.float64, device=DEV)
+    G.load_vector(dev(fc.reshape(d, -1)), dev(gc.reshape(-1)), b)
+    assert rel_inf(host(b), bo) < 1e-13
