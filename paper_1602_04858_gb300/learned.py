@@ -37,8 +37,14 @@ def hierarchy_args(n: int):
     return dict(dim=2, n_coarse=n_coarse, n_levels=levels, degree=0, mu=0.01)
 
 
-def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp32"):
-    """Sets up and solves one problem; returns (stats, x, c_dev, f_dev, setup_ms)."""
+def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp32", smooth_steps=1):
+    """Sets up and solves one problem; returns (stats, x, c_dev, f_dev, setup_ms).
+
+    With x0_fn the solve starts from its guess after `smooth_steps` symmetric
+    Schwarz smoothing steps on the finest level (each about 1/8 of a variable
+    V-cycle with m(J) = 2): the network is accurate in the smooth part of the
+    solution, the smoother removes the rest.
+    """
     c, f = problem(seed, n)
     cd = torch.as_tensor(c, device="cuda")
     fd = torch.as_tensor(f.reshape(2, -1), device="cuda").contiguous()
@@ -55,6 +61,8 @@ def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp
     use_x0 = False
     if x0_fn is not None:
         x0_fn(cd, fd, x)
+        if smooth_steps > 0:
+            G.smooth(a["n_levels"] - 1, x, b, steps=smooth_steps)
         use_x0 = True
     st, status = G.solve(b[:nu].contiguous(), b[nu:].contiguous(), x, use_x0=use_x0, tol=tol, maxit=maxit,
                          check=False)
@@ -123,12 +131,13 @@ def train(torch, net, feats, targs, epochs=30, batch=16, lr=2e-3, seed=0, log=No
     return hist
 
 
-def evaluate(torch, net, seeds, n, tol=1e-8):
-    """Iterations and solve time from the zero and from the learned guess."""
+def evaluate(torch, net, seeds, n, tol=1e-8, smooth_steps=1):
+    """Iterations and solve time from the zero and from the (smoothed) learned guess."""
     rows = []
     for s in seeds:
         st0, _, _, _, _ = solve_problem(torch, s, n, tol=tol)
-        st1, _, _, _, _ = solve_problem(torch, s, n, x0_fn=lambda c, f, x: net.guess(c, f, x), tol=tol)
+        st1, _, _, _, _ = solve_problem(torch, s, n, x0_fn=lambda c, f, x: net.guess(c, f, x), tol=tol,
+                                        smooth_steps=smooth_steps)
         rows.append(dict(seed=s, zero_its=st0.iterations, zero_ms=st0.solve_ms, zero_conv=st0.converged,
                          learned_its=st1.iterations, learned_ms=st1.solve_ms, learned_conv=st1.converged,
                          learned_initial_rel_residual=st1.initial_rel_residual))
