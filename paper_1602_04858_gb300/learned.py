@@ -32,9 +32,11 @@ def problem(seed: int, n: int, sigma: float = 2.0, ell: float = 8.0):
 
 
 def hierarchy_args(n: int):
+    """Levels 4x4 -> n x n; the sub-cycle three levels below the finest is folded
+    (dense operator of at most a few tens of MB, cheap to set up per problem)."""
     n_coarse = 4
     levels = int(np.log2(n // n_coarse)) + 1
-    return dict(dim=2, n_coarse=n_coarse, n_levels=levels, degree=0, mu=0.01)
+    return dict(dim=2, n_coarse=n_coarse, n_levels=levels, degree=0, mu=0.01, dense_level=max(0, levels - 4))
 
 
 def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp32", smooth_steps=1):
@@ -51,7 +53,7 @@ def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp
     a = hierarchy_args(n)
     t0 = time.perf_counter()
     G = mgdarcy.Multigrid(a["dim"], a["n_coarse"], a["n_levels"], a["degree"], a["mu"], cd,
-                          precision=precision, dense_level=-1)
+                          precision=precision, dense_level=a["dense_level"])
     torch.cuda.synchronize()
     setup_ms = 1e3 * (time.perf_counter() - t0)
     nu, np_ = G.sizes()
@@ -69,12 +71,15 @@ def solve_problem(torch, seed, n, x0_fn=None, tol=1e-8, maxit=200, precision="fp
     return st, x, cd, fd, setup_ms
 
 
-def build_dataset(torch, net, seeds, n, tol=1e-10):
+def build_dataset(torch, net, seeds, n, tol=1e-10, log=None):
     """Solves the seeded problems; returns their (c, f, x) on the device."""
     data = []
-    for s in seeds:
+    t0 = time.perf_counter()
+    for k, s in enumerate(seeds):
         st, x, cd, fd, _ = solve_problem(torch, s, n, tol=tol, maxit=400)
         data.append((cd, fd, x))
+        if log and (k + 1) % 250 == 0:
+            log(f"{k + 1} solves, {time.perf_counter() - t0:.1f} s")
     torch.cuda.synchronize()
     return data
 
@@ -168,13 +173,13 @@ def main():
     args = ap.parse_args()
     net = mgdarcy.CNN(args.n, max_batch=16, seed=1)
     t0 = time.perf_counter()
-    data = build_dataset(torch, net, list(range(args.train)), args.n)
+    data = build_dataset(torch, net, list(range(args.train)), args.n, log=lambda m: print(m, flush=True))
     gen_s = time.perf_counter() - t0
     fm, fs, tm, ts = fit_normalisation(torch, net, data)
     net.set_normalisation(fm, fs, tm, ts)
     feats, targs = normalised_tensors(torch, net, data)
     t0 = time.perf_counter()
-    hist = train(torch, net, feats, targs, epochs=args.epochs, log=print)
+    hist = train(torch, net, feats, targs, epochs=args.epochs, log=lambda m: print(m, flush=True))
     train_s = time.perf_counter() - t0
     rows = evaluate(torch, net, list(range(100000, 100000 + args.test)), args.n)
     summary = summarise(rows)

@@ -54,3 +54,41 @@ def test_fullsize_vcycle(workload, prec, tol):
     zo = mg.vcycle(H, r, m_fine=2, variable=True)
     err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
     assert err < tol, err
+
+
+@pytest.fixture(scope="module")
+def darcy3d():
+    """3-D Darcy, RT_0, 32^3 cells (levels 2^3 -> 32^3), c = exp(G), G ~ GRF(sigma=3, ell=4 cells)."""
+    n = 32
+    c = inputs.lognormal_c(n, 3, 3.0, 4.0, 3)
+    H = mg.Hierarchy(3, 2, 5, 0, 0.0, c)
+    return c, H
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_3d_vcycle(darcy3d, prec, tol):
+    c, H = darcy3d
+    G = mgdarcy.Multigrid(3, 2, 5, 0, 0.0, torch.as_tensor(c, device="cuda"), precision=prec)
+    LJ = H.levels[-1]
+    r = np.random.default_rng(4).standard_normal(LJ.S.ndof)
+    z = torch.zeros(LJ.S.ndof, dtype=torch.float64, device="cuda")
+    G.vcycle(torch.as_tensor(r, device="cuda"), z)
+    zo = mg.vcycle(H, r)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_bf16inv"])
+def test_3d_solve_reaches_1e8(darcy3d, prec):
+    """Random Gaussian load (u.n = 0, g = 0): every precision mode reaches 1e-8 (FP64 residual)."""
+    c, H = darcy3d
+    LJ = H.levels[-1]
+    G = mgdarcy.Multigrid(3, 2, 5, 0, 0.0, torch.as_tensor(c, device="cuda"), precision=prec)
+    b = np.random.default_rng(5).standard_normal(LJ.S.ndof)
+    b[LJ.cm] = 0.0
+    b[LJ.S.n_u:] = 0.0
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    st, _ = G.solve(bd[:LJ.S.n_u].contiguous(), bd[LJ.S.n_u:].contiguous(), x, tol=1e-8, maxit=200)
+    res = np.linalg.norm(LJ.A @ x.cpu().numpy() - b) / np.linalg.norm(b)
+    assert st.converged == 1 and res <= 1.01e-8
