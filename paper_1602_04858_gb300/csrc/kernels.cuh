@@ -536,10 +536,12 @@ struct PassShape {
   static constexpr size_t TAB_T = (size_t)TPL + (size_t)NV * MTE;
   static constexpr size_t TAB_I = (size_t)2 * NV * MTE + GTE;
   static constexpr size_t TAB_BYTES = TAB_T * sizeof(T) + TAB_I * sizeof(int);
-  // T entries of all patches, rounded so the int64 bases that follow stay aligned
-  static constexpr size_t T_ALIGNED = (((size_t)PPB * T_PER_PATCH * sizeof(T) + 15) / 16) * 16 / sizeof(T);
-  static constexpr size_t SMEM = (size_t)PPB * (S_BYTES + SC_BYTES) + T_ALIGNED * sizeof(T) +
-                                 (size_t)PPB * 4 * (D + 1) * sizeof(int64_t) + (size_t)WARPS * sizeof(uint64_t) + 64;
+  // one pipeline stage of a warp: inverses, per-patch T data, address bases
+  static constexpr size_t STAGE_S = (size_t)GPW * (S_BYTES + SC_BYTES);
+  static constexpr size_t STAGE_T = (((size_t)GPW * T_PER_PATCH * sizeof(T) + 15) / 16) * 16;
+  static constexpr size_t STAGE_B = (size_t)GPW * 4 * (D + 1) * sizeof(int64_t);
+  static constexpr size_t STAGE = STAGE_S + STAGE_T + STAGE_B;
+  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE + (size_t)WARPS * 2 * sizeof(uint64_t) + 16;
 };
 
 // Window origin along direction e for component comp (D = pressure).
@@ -725,55 +727,62 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
                                                      const T* __restrict__ b, int evict_first,
                                                      int* __restrict__ err, int64_t vs) {
   using P = PassShape<D, K, T, TS, NR>;
-  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, PPB = P::PPB, RR = P::RR;
-  constexpr int WIN = P::WIN, NVT = P::NVT, NRG = P::NRG, LW = P::LW, MTE = P::MTE, GTE = P::GTE;
+  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, RR = P::RR;
+  constexpr int WIN = P::WIN, NVT = P::NVT, NRG = P::NRG, LW = P::LW, MTE = P::MTE;
+  constexpr int E = NR * WIN + NR * NV + P::NC;   // gathered entries per patch
+  constexpr int NB = 4 * (D + 1);                  // int64 bases per patch
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* s_inv = smem;                                                   // PPB x S_BYTES
-  float* s_scale = reinterpret_cast<float*>(smem + (size_t)PPB * P::S_BYTES);    // PPB x NVP (BF16 only)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * 2 * P::STAGE) + warp * 2;
   const T* s_R0 = reinterpret_cast<const T*>(tabs);   // per-level tables, global (L1-cached)
   const T* s_mc = s_R0 + P::TPL;
   const int* s_mw = reinterpret_cast<const int*>(s_mc + NV * MTE);
   const int* s_mb = s_mw + NV * MTE;
   const int* s_gt = s_mb + NV * MTE;
-  T* s_t = reinterpret_cast<T*>(smem + (size_t)PPB * (P::S_BYTES + P::SC_BYTES));
-  int64_t* s_base = reinterpret_cast<int64_t*>(s_t + P::T_ALIGNED);   // PPB x 4 x (D+1)
-  uint64_t* s_bar = reinterpret_cast<uint64_t*>(s_base + PPB * 4 * (D + 1));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t pw = ((int64_t)blockIdx.x * P::WARPS + warp) * GPW;   // first patch of this warp
-  const int nmine = (pw >= count) ? 0 : (int)((count - pw) < GPW ? (count - pw) : GPW);
-  uint64_t* bar = s_bar + warp;
-  // 1. stream the inverses of this warp's patches into shared memory
-  if (lane == 0 && nmine > 0) {
-    mbar_init(bar, 1);
-    const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
-    mbar_arrive_expect_tx(bar, (uint32_t)(nmine * (P::S_BYTES + P::SC_BYTES)));
-    for (int g = 0; g < nmine; ++g) {
-      const int slot = warp * GPW + g;
-      bulk_load(s_inv + (size_t)slot * P::S_BYTES, S + (pw + g) * P::SL::STRIDE, P::S_BYTES, bar, pol);
+  const int64_t ngroups = (count + GPW - 1) / GPW;
+  const int64_t W = (int64_t)gridDim.x * P::WARPS;
+  const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
+
+  auto st_S = [&](int bi) { return smem + ((size_t)warp * 2 + bi) * P::STAGE; };
+  auto st_T = [&](int bi) { return reinterpret_cast<T*>(st_S(bi) + P::STAGE_S); };
+  auto st_B = [&](int bi) { return reinterpret_cast<int64_t*>(st_S(bi) + P::STAGE_S + P::STAGE_T); };
+  auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
+
+  // (a) bulk copies of the inverses of patch group pg into stage bi (lane 0)
+  auto issue_S = [&](int bi, int64_t pg) {
+    const int np = npat(pg);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bars + bi, (uint32_t)(np * (P::S_BYTES + P::SC_BYTES)));
+    for (int g = 0; g < np; ++g) {
+      const int64_t p = pg * GPW + g;
+      bulk_load(st_S(bi) + (size_t)g * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bars + bi, pol);
       if constexpr (P::BF)
-        bulk_load(s_scale + (size_t)slot * NVP,
-                  reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + (pw + g) * NVP, P::SC_BYTES, bar, pol);
+        bulk_load(st_S(bi) + (size_t)GPW * P::S_BYTES + (size_t)g * P::SC_BYTES,
+                  reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + p * NVP, P::SC_BYTES, bars + bi, pol);
     }
-  }
-  // per-patch vertex and address bases, one entry per lane: window base per
-  // component, b-row base per component, cell base, interior flag, vertex
-  for (int qq = lane; qq < nmine * 4 * (D + 1); qq += 32) {
-    const int gq = qq / (4 * (D + 1)), item = qq - gq * 4 * (D + 1);
-    if (item < 3 * (D + 1) + D) {
+  };
+  // (b) per-patch address bases: window base per component, b-row base per
+  //     component, cell base, interior flag, vertex
+  auto compute_bases = [&](int bi, int64_t pg) {
+    const int np = npat(pg);
+    int64_t* pbs = st_B(bi);
+    for (int qq = lane; qq < np * NB; qq += 32) {
+      const int gq = qq / NB, item = qq - gq * NB;
+      if (item >= 3 * (D + 1) + D) continue;
       int v[D];
-      patch_vertex<D>(L.n, colour, pw + gq, v);
+      patch_vertex<D>(L.n, colour, pg * GPW + gq, v);
       int64_t val = 0;
       if (item < 2 * (D + 1)) {
         const int c = item % (D + 1);
         const bool row = item > D;
-        int64_t s = 1;
+        int64_t sstr = 1;
         val = L.off[c];
 #pragma unroll
         for (int e = 0; e < D; ++e) {
-          val += (int64_t)(row ? (v[e] - 1) * (K + 1) + ((c < D && e == c) ? 1 : 0) : win_origin<D, K>(v, c, e)) * s;
-          s *= (c < D && e == c) ? (L.N + 1) : L.N;
+          val += (int64_t)(row ? (v[e] - 1) * (K + 1) + ((c < D && e == c) ? 1 : 0) : win_origin<D, K>(v, c, e)) * sstr;
+          sstr *= (c < D && e == c) ? (L.N + 1) : L.N;
         }
       } else if (item == 2 * (D + 1)) {
         int64_t cs = 1;
@@ -790,194 +799,208 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       } else {
         val = v[item - 3 * (D + 1)];
       }
-      s_base[(size_t)(warp * GPW + gq) * 4 * (D + 1) + item] = val;
+      pbs[gq * NB + item] = val;
     }
+  };
+  // (c) asynchronous gather of windows, b rows and cell coefficients (needs the bases)
+  auto issue_window = [&](int bi, int64_t pg) {
+    const int np = npat(pg);
+    const int64_t* pbs = st_B(bi);
+    T* tw = st_T(bi);
+    for (int q = lane; q < np * E; q += 32) {
+      const int g = q / E, e = q - g * E;
+      const int64_t* pb = pbs + g * NB;
+      const T* src = x;
+      bool ok = true;
+      int dst;
+      if (e < NR * WIN) {
+        const int rr = e / WIN, w = e - rr * WIN;
+        int comp = w / P::WU;
+        if (comp > D) comp = D;
+        if (!pb[2 * (D + 1) + 1]) {   // boundary patch: entries outside the domain are zero
+          int le[D];
+          win_local<D, K>(w, le);
+#pragma unroll
+          for (int d2 = 0; d2 < D; ++d2) {
+            const int vv2 = (int)pb[3 * (D + 1) + d2];
+            const int o = (comp < D && d2 != comp) ? (vv2 - 2) * (K + 1) : (vv2 - 1) * (K + 1);
+            const int id = o + le[d2];
+            const int hi = (comp < D && d2 == comp) ? L.N : L.N - 1;
+            ok = ok && id >= 0 && id <= hi;
+          }
+        }
+        if (ok) src = x + pb[comp] + s_gt[w] + rr * vs;
+        dst = e;
+      } else if (e < NR * (WIN + NV)) {
+        const int e2 = e - NR * WIN;
+        const int rr = e2 / NV, l = e2 - rr * NV;
+        int comp = l / P::PS::NU1;
+        if (comp > D) comp = D;
+        src = b + pb[(D + 1) + comp] + s_gt[WIN + l] + rr * vs;
+        dst = e;
+      } else {
+        src = L.c + pb[2 * (D + 1)] + s_gt[WIN + NV + (e - NR * (WIN + NV))];
+        dst = NR * (WIN + NV + NVT) + (e - NR * (WIN + NV));
+      }
+      T* d = tw + g * P::T_PER_PATCH + dst;
+      if constexpr (sizeof(T) == 8) cp_async8(d, src, ok ? 8u : 0u);
+      else cp_async4(d, src, ok ? 4u : 0u);
+    }
+    cp_async_commit();
+  };
+
+  int64_t pg = (int64_t)blockIdx.x * P::WARPS + warp;
+  if (lane == 0) {
+    mbar_init(bars + 0, 1);
+    mbar_init(bars + 1, 1);
+  }
+  __syncwarp();
+  if (pg < ngroups) {
+    if (lane == 0) issue_S(0, pg);   // the inverses do not depend on earlier passes
+    compute_bases(0, pg);
   }
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
-  __syncthreads();
-  if (nmine == 0) return;
-  T* tw = s_t + (size_t)(warp * GPW) * P::T_PER_PATCH;
-  const int64_t* wb0 = s_base + (size_t)(warp * GPW) * 4 * (D + 1);
-  // 2. gather: window of x (NR), b rows (NR), cell coefficients; per patch
-  //    E entries, all of a lane's loads issued before its stores
-  {
-    constexpr int E = NR * WIN + NR * NV + P::NC;
-    constexpr int TRIPS = (GPW * E + 31) / 32;
-    T val[TRIPS];
+  __syncwarp();
+  if (pg < ngroups) issue_window(0, pg);
+  for (int k = 0; pg < ngroups; ++k, pg += W) {
+    const int bi = k & 1;
+    const int64_t pn = pg + W;
+    if (pn < ngroups) {   // stage the next group while this one is computed
+      if (lane == 0) issue_S(bi ^ 1, pn);
+      compute_bases(bi ^ 1, pn);
+      __syncwarp();
+      issue_window(bi ^ 1, pn);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const int nmine = npat(pg);
+    T* tw = st_T(bi);
+    const int64_t* wb0 = st_B(bi);
+    // local residual rows (b - A x)|_v
+    const int g = lane / LW, lp = lane - g * LW;
+    {
+      T* pbase = tw + g * P::T_PER_PATCH;
+      const T* cw = pbase + NR * (WIN + NV + NVT);
+      T* part = pbase + NR * (WIN + NV + NVT) + P::NC;   // NR x SPLIT
+      const bool active = g < nmine;
+      const bool interior = active && wb0[g * NB + 2 * (D + 1) + 1] != 0;
+      int v[D];
 #pragma unroll
-    for (int k = 0; k < TRIPS; ++k) {
-      const int q = lane + 32 * k;
-      const int g = q / E, e = q - g * E;
-      T vv = T(0);
-      if (g < nmine) {
-        const int64_t* pb = wb0 + g * 4 * (D + 1);
-        if (e < NR * WIN) {
-          const int rr = e / WIN, w = e - rr * WIN;
-          int comp = w / P::WU;
-          if (comp > D) comp = D;
-          bool inside = true;
-          if (!pb[2 * (D + 1) + 1]) {   // boundary patch: mask entries outside the domain
-            int le[D];
-            win_local<D, K>(w, le);
+      for (int e = 0; e < D; ++e) v[e] = active ? (int)wb0[g * NB + 3 * (D + 1) + e] : 2;
+      const int rg = lp % NRG, sp = lp / NRG;
+      constexpr int WCH = (WIN + P::TSPL - 1) / P::TSPL;
+      if (interior && sp < P::TSPL) {
+        using V = typename Vec16<T>::type;
+        T acc[RR][NR];
 #pragma unroll
-            for (int d2 = 0; d2 < D; ++d2) {
-              const int vv2 = (int)pb[3 * (D + 1) + d2];
-              const int o = (comp < D && d2 != comp) ? (vv2 - 2) * (K + 1) : (vv2 - 1) * (K + 1);
-              const int id = o + le[d2];
-              const int hi = (comp < D && d2 == comp) ? L.N : L.N - 1;
-              inside = inside && id >= 0 && id <= hi;
-            }
+        for (int r = 0; r < RR; ++r)
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+        const int w0 = sp * WCH, w1 = (w0 + WCH < WIN) ? w0 + WCH : WIN;
+#pragma unroll 4
+        for (int w = w0; w < w1; ++w) {
+          const V c4 = __ldg(reinterpret_cast<const V*>(s_R0 + w * NVT + rg * RR));
+          const T* cc = reinterpret_cast<const T*>(&c4);
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            const T xw = pbase[rr * WIN + w];
+#pragma unroll
+            for (int r = 0; r < RR; ++r) acc[r][rr] += cc[r] * xw;
           }
-          if (inside) vv = x[pb[comp] + s_gt[w] + rr * vs];
-        } else if (e < NR * (WIN + NV)) {
-          const int e2 = e - NR * WIN;
-          const int rr = e2 / NV, l = e2 - rr * NV;
-          int comp = l / P::PS::NU1;
-          if (comp > D) comp = D;
-          vv = b[pb[(D + 1) + comp] + s_gt[WIN + l] + rr * vs];
-        } else {
-          vv = L.c[pb[2 * (D + 1)] + s_gt[WIN + NV + (e - NR * (WIN + NV))]];
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+          for (int r = 0; r < RR; ++r) part[rr * P::SPLIT + sp * NVT + rg * RR + r] = acc[r][rr];
+      }
+      __syncwarp();
+      if (interior) {
+        for (int l = lp; l < NV; l += LW) {
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            T a = T(0);
+#pragma unroll
+            for (int s2 = 0; s2 < P::TSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVT + l];
+            const T* win = pbase + rr * WIN;
+#pragma unroll
+            for (int kk = 0; kk < MTE; ++kk)
+              a += __ldg(s_mc + l * MTE + kk) * cw[__ldg(s_mb + l * MTE + kk)] * win[__ldg(s_mw + l * MTE + kk)];
+            pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - a;
+          }
+        }
+      } else if (active) {
+        for (int l = lp; l < NV; l += LW) {
+          int idx[D];
+          const int comp = patch_local_decode<D, K>(v, l, idx);
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
+            visit_row(L, tb, comp, idx, vis);
+            pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
+          }
         }
       }
-      val[k] = vv;
     }
+    __syncwarp();
+    // wait for the inverses of this group (bounded), then delta = S_v r
+    if (!mbar_wait_bounded(bars + bi, (uint32_t)((k >> 1) & 1), 2000000000ull)) {
+      if (lane == 0) atomicExch(err, 2);
+      continue;
+    }
+    {
+      const int q = lp % LPP, sp = lp / LPP;
+      constexpr int JCH = (NV + P::SSPL - 1) / P::SSPL;
+      T* pbase = tw + g * P::T_PER_PATCH;
+      T* part = pbase + NR * (WIN + NV + NVT) + P::NC;
+      const float* sc = reinterpret_cast<const float*>(st_S(bi) + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
+      if (g < nmine && sp < P::SSPL) {
+        const TS* Sg = reinterpret_cast<const TS*>(st_S(bi) + (size_t)g * P::S_BYTES) + q * RG;
+        const T* rv = pbase + NR * (WIN + NV);
+        T acc[RG][NR];
 #pragma unroll
-    for (int k = 0; k < TRIPS; ++k) {
-      const int q = lane + 32 * k;
-      const int g = q / E, e = q - g * E;
+        for (int r = 0; r < RG; ++r)
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+        const int j0 = sp * JCH, j1 = (j0 + JCH < NV) ? j0 + JCH : NV;
+#pragma unroll 4
+        for (int j = j0; j < j1; ++j) {
+          T sv[RG];
+          load_rg_smem<TS, T>(Sg + j * NVP, sv);
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr) {
+            T rj = rv[rr * NVT + j];
+            if constexpr (P::BF) rj *= sc[j];
+#pragma unroll
+            for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+          }
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+          for (int r = 0; r < RG; ++r) part[rr * P::SPLIT + sp * NVP + q * RG + r] = acc[r][rr];
+      }
+      __syncwarp();
       if (g < nmine) {
-        T* pbase = tw + g * P::T_PER_PATCH;
-        if (e < NR * (WIN + NV)) pbase[e] = val[k];
-        else pbase[NR * (WIN + NV + NVT) + (e - NR * (WIN + NV))] = val[k];
-      }
-    }
-  }
-  __syncwarp();
-  // 3. local residual rows (b - A x)|_v
-  const int g = lane / LW, lp = lane - g * LW;   // patch of this lane, lane within the patch
-  {
-    T* pbase = tw + g * P::T_PER_PATCH;
-    const T* cw = pbase + NR * (WIN + NV + NVT);
-    T* part = pbase + NR * (WIN + NV + NVT) + P::NC;   // NR x SPLIT
-    const bool active = g < nmine;
-    const bool interior = active && wb0[g * 4 * (D + 1) + 2 * (D + 1) + 1] != 0;
-    int v[D];
+        const int64_t* pb = wb0 + g * NB;
+        for (int row = lp; row < NV; row += LW) {
+          int comp = row / P::PS::NU1;
+          if (comp > D) comp = D;
+          const int64_t f = pb[(D + 1) + comp] + s_gt[WIN + row];
+          const T sr = P::BF ? (T)sc[row] : T(1);
 #pragma unroll
-    for (int e = 0; e < D; ++e) v[e] = active ? (int)wb0[g * 4 * (D + 1) + 3 * (D + 1) + e] : 2;
-    // template product, window columns split over TSPL lane groups
-    const int rg = lp % NRG, sp = lp / NRG;
-    constexpr int WCH = (WIN + P::TSPL - 1) / P::TSPL;
-    if (interior && sp < P::TSPL) {
-      using V = typename Vec16<T>::type;
-      T acc[RR][NR];
+          for (int rr = 0; rr < NR; ++rr) {
+            T a = T(0);
 #pragma unroll
-      for (int r = 0; r < RR; ++r)
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
-      const int w0 = sp * WCH, w1 = (w0 + WCH < WIN) ? w0 + WCH : WIN;
-#pragma unroll 4
-      for (int w = w0; w < w1; ++w) {
-        const V c4 = *reinterpret_cast<const V*>(s_R0 + w * NVT + rg * RR);
-        const T* cc = reinterpret_cast<const T*>(&c4);
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          const T xw = pbase[rr * WIN + w];
-#pragma unroll
-          for (int r = 0; r < RR; ++r) acc[r][rr] += cc[r] * xw;
+            for (int s2 = 0; s2 < P::SSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVP + row];
+            x[f + rr * vs] += P::BF ? a * sr : a;
+          }
         }
       }
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr)
-#pragma unroll
-        for (int r = 0; r < RR; ++r) part[rr * P::SPLIT + sp * NVT + rg * RR + r] = acc[r][rr];
     }
     __syncwarp();
-    if (interior) {
-      // combine splits, add the mass term, subtract from b
-      for (int l = lp; l < NV; l += LW) {
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          T a = T(0);
-#pragma unroll
-          for (int s2 = 0; s2 < P::TSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVT + l];
-          const T* win = pbase + rr * WIN;
-#pragma unroll
-          for (int k = 0; k < MTE; ++k) a += s_mc[l * MTE + k] * cw[s_mb[l * MTE + k]] * win[s_mw[l * MTE + k]];
-          pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - a;
-        }
-      }
-    } else if (active) {
-      for (int l = lp; l < NV; l += LW) {
-        int idx[D];
-        const int comp = patch_local_decode<D, K>(v, l, idx);
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
-          visit_row(L, tb, comp, idx, vis);
-          pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
-        }
-      }
-    }
-  }
-  __syncwarp();
-  // 4. wait for the inverses (bounded), then delta = S_v r
-  const bool ok = mbar_wait_bounded(bar, 0, 2000000000ull);
-  if (!ok) {
-    if (lane == 0) atomicExch(err, 2);
-    mbar_wait_bounded(bar, 0, 2000000000ull);   // let copies in flight land before the block exits
-    return;
-  }
-  {
-    const int q = lp % LPP, sp = lp / LPP;
-    constexpr int JCH = (NV + P::SSPL - 1) / P::SSPL;
-    const int slot = warp * GPW + g;
-    T* pbase = tw + g * P::T_PER_PATCH;
-    T* part = pbase + NR * (WIN + NV + NVT) + P::NC;
-    const float* sc = s_scale + (size_t)slot * NVP;
-    if (g < nmine && sp < P::SSPL) {
-      const TS* Sg = reinterpret_cast<const TS*>(s_inv + (size_t)slot * P::S_BYTES) + q * RG;
-      const T* rv = pbase + NR * (WIN + NV);
-      T acc[RG][NR];
-#pragma unroll
-      for (int r = 0; r < RG; ++r)
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
-      const int j0 = sp * JCH, j1 = (j0 + JCH < NV) ? j0 + JCH : NV;
-#pragma unroll 4
-      for (int j = j0; j < j1; ++j) {
-        T sv[RG];
-        load_rg_smem<TS, T>(Sg + j * NVP, sv);
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          T rj = rv[rr * NVT + j];
-          if constexpr (P::BF) rj *= sc[j];
-#pragma unroll
-          for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
-        }
-      }
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr)
-#pragma unroll
-        for (int r = 0; r < RG; ++r) part[rr * P::SPLIT + sp * NVP + q * RG + r] = acc[r][rr];
-    }
-    __syncwarp();
-    if (g < nmine) {
-      const int64_t* pb = wb0 + g * 4 * (D + 1);
-      for (int row = lp; row < NV; row += LW) {
-        int comp = row / P::PS::NU1;
-        if (comp > D) comp = D;
-        const int64_t f = pb[(D + 1) + comp] + s_gt[WIN + row];
-        const T sr = P::BF ? (T)sc[row] : T(1);
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          T a = T(0);
-#pragma unroll
-          for (int s2 = 0; s2 < P::SSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVP + row];
-          x[f + rr * vs] += P::BF ? a * sr : a;
-        }
-      }
-    }
   }
 }
 

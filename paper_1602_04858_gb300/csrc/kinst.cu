@@ -115,8 +115,20 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
     return true;
   }();
   (void)attr;
+  // persistent: at most as many blocks as fit on the device at once; each
+  // warp then walks a strided sequence of patch groups
+  static int cap = [] {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass<D, K, T, TS, NR>, 32 * P::WARPS, P::SMEM);
+    return (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
+  }();
+  const int64_t groups_total = (h.count[colour] + P::GPW - 1) / P::GPW;
+  int64_t nb = (groups_total + P::WARPS - 1) / P::WARPS;
+  if (nb > cap) nb = cap;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(blocks(h.count[colour], P::PPB), groups);
+  cfg.gridDim = dim3((unsigned)nb, groups);
   cfg.blockDim = dim3(32 * P::WARPS);
   cfg.dynamicSmemBytes = P::SMEM;
   cfg.stream = s;
