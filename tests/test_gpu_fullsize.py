@@ -92,3 +92,65 @@ def test_3d_solve_reaches_1e8(darcy3d, prec):
     st, _ = G.solve(bd[:LJ.S.n_u].contiguous(), bd[LJ.S.n_u:].contiguous(), x, tol=1e-8, maxit=200)
     res = np.linalg.norm(LJ.A @ x.cpu().numpy() - b) / np.linalg.norm(b)
     assert st.converged == 1 and res <= 1.01e-8
+
+
+@pytest.fixture(scope="module")
+def darcy3d_64():
+    w = inputs.workload("lognormal_3d_64")
+    return w
+
+
+def test_3d_64_vcycle_symmetric(darcy3d_64):
+    """Properties at the full 64^3 size: (r1, B r2) = (r2, B r1) for the FP64 V-cycle
+    on the free dofs (symmetric smoother, Sec. 3.3), and B r = r on the constrained dofs."""
+    w = darcy3d_64
+    G = mgdarcy.Multigrid(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"],
+                          torch.as_tensor(w["c"], device="cuda"), precision="fp64")
+    n = G.ndof()
+    rng = np.random.default_rng(6)
+    r1 = torch.as_tensor(rng.standard_normal(n), device="cuda")
+    r2 = torch.as_tensor(rng.standard_normal(n), device="cuda")
+    z1, z2 = torch.zeros_like(r1), torch.zeros_like(r2)
+    G.vcycle(r1, z1)
+    G.vcycle(r2, z2)
+    # remove the constrained (identity) part before comparing the bilinear forms
+    nu, _ = G.sizes()
+    N = 64
+    free = torch.ones(n, dtype=torch.bool, device="cuda")
+    ux = free[:(N + 1) * N * N].view(N, N, N + 1)
+    ux[:, :, 0] = False
+    ux[:, :, N] = False
+    uy = free[(N + 1) * N * N:2 * (N + 1) * N * N].view(N, N + 1, N)
+    uy[:, 0, :] = False
+    uy[:, N, :] = False
+    uz = free[2 * (N + 1) * N * N:nu].view(N + 1, N, N)
+    uz[0] = False
+    uz[N] = False
+    a = float((r1[free] * z2[free]).sum())
+    b = float((r2[free] * z1[free]).sum())
+    assert abs(a - b) <= 1e-9 * max(abs(a), abs(b))
+    assert torch.equal(z1[~free], r1[~free])
+
+
+@pytest.mark.parametrize("prec", ["fp32_bf16inv", "fp32"])
+def test_3d_64_solve_reaches_1e8(darcy3d_64, prec):
+    """The 64^3 workload with a random Gaussian load reaches 1e-8 (FP64 residual by mg_residual_norm)."""
+    w = darcy3d_64
+    G = mgdarcy.Multigrid(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"],
+                          torch.as_tensor(w["c"], device="cuda"), precision=prec)
+    nu, np_ = G.sizes()
+    N = 64
+    f = torch.as_tensor(np.random.default_rng(33).standard_normal(nu), device="cuda")
+    for comp, shape in enumerate([(N, N, N + 1), (N, N + 1, N), (N + 1, N, N)]):
+        blk = f[comp * (N + 1) * N * N:(comp + 1) * (N + 1) * N * N].view(*shape)
+        idx = [slice(None)] * 3
+        idx[2 - comp] = 0
+        blk[tuple(idx)] = 0.0
+        idx[2 - comp] = N
+        blk[tuple(idx)] = 0.0
+    g = torch.zeros(np_, dtype=torch.float64, device="cuda")
+    x = torch.zeros(nu + np_, dtype=torch.float64, device="cuda")
+    st, _ = G.solve(f, g, x, tol=1e-8, maxit=300)
+    b = torch.cat([f, g])
+    res = G.residual_norm(x, b) / float(torch.linalg.vector_norm(b))
+    assert st.converged == 1 and res <= 1.01e-8
