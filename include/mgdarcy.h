@@ -281,6 +281,17 @@ int64_t mg_kernel_launches(const mg_handle* h);
 const char* mg_status_string(mg_status s);
 const char* mg_last_error(void);
 
+/* Host-only check (no GPU, no handle) of the colour-pass tables that
+ * mg_setup builds for an n^dim level of RT_degree with viscosity mu and the
+ * given storage precision (mg_precision) of the patch inverses (Sec. 3.3):
+ * every row of every patch type is reproduced exactly by its lane plan, the
+ * plan evaluated on a random window agrees with the row of the operator, and
+ * every gather segment addresses the window column, patch row or cell it
+ * stands for (zero outside the domain).  Returns 0 if all hold, 1 with a
+ * reason in msg (msg_len bytes, may be null) otherwise, 2 for unsupported
+ * arguments. */
+int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -313,6 +313,19 @@ int64_t mg_kernel_launches(const mg_handle* h) { return h ? h->launches : 0; }
 
 void mg_destroy(mg_handle* h) { delete h; }
 
+int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len) {
+  if (!((dim == 2 && (degree == 0 || degree == 1)) || (dim == 3 && degree == 0)) || precision < 0 ||
+      precision > 2 || n < 2 || !(mu >= 0.0)) {
+    if (msg && msg_len > 0) std::snprintf(msg, (size_t)msg_len, "unsupported arguments");
+    return 2;
+  }
+  const DKOps* o = (dim == 2) ? (degree == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
+  std::string why;
+  const int r = o->plan_selftest(precision, n, mu, &why);
+  if (msg && msg_len > 0) std::snprintf(msg, (size_t)msg_len, "%s", why.c_str());
+  return r;
+}
+
 }  // extern "C"
 
 // Builds one hierarchy whose level vectors hold nrhs right-hand sides; an
@@ -413,12 +426,13 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
       // levels whose inverses would crowd the L2 cache stream them evict-first
       L.s_evict_first = (double)np * h->ops->s_stride[L.sprec] * sb > 48.0e6 ? 1 : 0;
     }
-    {   // per-level colour-pass tables (interior template, mass and gather tables)
+    {   // per-level colour-pass tables (gather segments, lane plans, row maps)
       const int64_t tb = h->ops->template_elems(L.sprec);
       if ((st = h->alloc((char**)&q, (size_t)tb)) != MG_OK) return cleanup(st);
       L.R0 = q;
-      h->ops->build_template(L, L.sprec, q, h->stream);
-      ++h->launches;
+      std::string why;
+      const int r = h->ops->build_template(L, L.sprec, q, h->stream, &why);
+      if (r != 0) return cleanup(fail(r == 1 ? MG_ERR_UNSUPPORTED : MG_ERR_CUDA, why));
     }
     for (int col = 0; col < C; ++col) {
       if (L.count[col] == 0) continue;

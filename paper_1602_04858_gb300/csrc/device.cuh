@@ -82,7 +82,7 @@ __host__ __device__ __forceinline__ int64_t comp_size(int N, int comp) {
 }
 
 template <int D, int K, typename T>
-__device__ __forceinline__ int64_t flat_index(const Lvl<D, K, T>& L, int comp, const int (&idx)[D]) {
+__host__ __device__ __forceinline__ int64_t flat_index(const Lvl<D, K, T>& L, int comp, const int (&idx)[D]) {
   int64_t f = 0, stride = 1;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
@@ -94,7 +94,7 @@ __device__ __forceinline__ int64_t flat_index(const Lvl<D, K, T>& L, int comp, c
 
 // Decode a level-vector index into (component, node multi-index).
 template <int D, int K, typename T>
-__device__ __forceinline__ int decode(const Lvl<D, K, T>& L, int64_t g, int (&idx)[D]) {
+__host__ __device__ __forceinline__ int decode(const Lvl<D, K, T>& L, int64_t g, int (&idx)[D]) {
   int comp = D;
 #pragma unroll
   for (int c = 0; c < D; ++c)
@@ -110,14 +110,14 @@ __device__ __forceinline__ int decode(const Lvl<D, K, T>& L, int64_t g, int (&id
 }
 
 template <int D, int K, typename T>
-__device__ __forceinline__ bool is_constrained(const Lvl<D, K, T>& L, int comp, const int (&idx)[D]) {
+__host__ __device__ __forceinline__ bool is_constrained(const Lvl<D, K, T>& L, int comp, const int (&idx)[D]) {
   if (comp >= D) return false;
   const int t = idx[comp];
   return t == 0 || t == L.N;
 }
 
 template <int D, int K, typename T>
-__device__ __forceinline__ int64_t cell_linear(const Lvl<D, K, T>& L, const int (&cell)[D]) {
+__host__ __device__ __forceinline__ int64_t cell_linear(const Lvl<D, K, T>& L, const int (&cell)[D]) {
   int64_t f = 0, s = 1;
 #pragma unroll
   for (int e = 0; e < D; ++e) { f += (int64_t)cell[e] * s; s *= L.n; }
@@ -127,7 +127,7 @@ __device__ __forceinline__ int64_t cell_linear(const Lvl<D, K, T>& L, const int 
 // Visits every (column, coefficient) of the row of velocity dof (i, idx)
 // (free row).  vis(comp, idx, coef) may be called more than once per column.
 template <int D, int K, typename T, class Vis>
-__device__ __forceinline__ void visit_u_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, int i,
+__host__ __device__ __forceinline__ void visit_u_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, int i,
                                             const int (&idx)[D], Vis& vis) {
   constexpr int K1 = K + 1, NG = K + 2;
   const int t = idx[i];
@@ -194,7 +194,7 @@ __device__ __forceinline__ void visit_u_row(const Lvl<D, K, T>& L, const Tab<K, 
 
 // Row of pressure dof idx: -(q, div u).
 template <int D, int K, typename T, class Vis>
-__device__ __forceinline__ void visit_p_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb,
+__host__ __device__ __forceinline__ void visit_p_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb,
                                             const int (&idx)[D], Vis& vis) {
   constexpr int K1 = K + 1, NG = K + 2;
 #pragma unroll
@@ -218,7 +218,7 @@ __device__ __forceinline__ void visit_p_row(const Lvl<D, K, T>& L, const Tab<K, 
 }
 
 template <int D, int K, typename T, class Vis>
-__device__ __forceinline__ void visit_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, int comp,
+__host__ __device__ __forceinline__ void visit_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, int comp,
                                           const int (&idx)[D], Vis& vis) {
   if (comp < D) visit_u_row(L, tb, comp, idx, vis);
   else visit_p_row(L, tb, idx, vis);
@@ -261,7 +261,7 @@ __host__ __device__ __forceinline__ int colour_count(int n, int r) {
 
 // Vertex of patch p (0-based, x fastest) of colour `colour` (digits base 3, x first).
 template <int D>
-__device__ __forceinline__ void patch_vertex(int n, int colour, int64_t p, int (&v)[D]) {
+__host__ __device__ __forceinline__ void patch_vertex(int n, int colour, int64_t p, int (&v)[D]) {
   int r = colour;
 #pragma unroll
   for (int e = 0; e < D; ++e) {
@@ -278,7 +278,7 @@ __device__ __forceinline__ void patch_vertex(int n, int colour, int64_t p, int (
 // spans UA nodes along x_i starting one node past the block's lower face, UB
 // Gauss nodes along the other directions; the pressure spans UB^D nodes.
 template <int D, int K>
-__device__ __forceinline__ int patch_local_decode(const int (&v)[D], int l, int (&idx)[D]) {
+__host__ __device__ __forceinline__ int patch_local_decode(const int (&v)[D], int l, int (&idx)[D]) {
   using PS = PatchShape<D, K>;
   constexpr int K1 = K + 1;
   int comp = l / PS::NU1;
@@ -307,7 +307,7 @@ __device__ __forceinline__ int patch_local_decode(const int (&v)[D], int l, int 
 
 // Global (component, node) -> local patch dof, or -1 if outside the patch.
 template <int D, int K>
-__device__ __forceinline__ int patch_local_index(const int (&v)[D], int comp, const int (&idx)[D]) {
+__host__ __device__ __forceinline__ int patch_local_index(const int (&v)[D], int comp, const int (&idx)[D]) {
   using PS = PatchShape<D, K>;
   constexpr int K1 = K + 1;
   int l = 0, stride = 1;

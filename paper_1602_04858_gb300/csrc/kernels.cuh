@@ -8,6 +8,7 @@
 #include "async.cuh"
 #include "device.cuh"
 #include "ops.h"
+#include "passplan.cuh"
 
 namespace mgd {
 
@@ -478,529 +479,334 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 // Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
 // for every patch v of one colour, x|_v += S_v (b - A x)|_v.
 //
-// A warp owns GPW patches (one for n_v >= 20) and NR right-hand sides.
-//  1. lane 0 issues one bulk asynchronous copy per patch of its stored
-//     inverse S_v into shared memory; S_v does not depend on earlier passes,
-//     so this precedes the programmatic-dependent-launch wait;
-//  2. the lanes gather the patch window of x (every column its rows touch),
-//     its b rows and its 2^D cell coefficients: all loads of a lane are
-//     issued before any is stored, addresses from per-level offset tables;
-//  3. local residual: for a patch away from the boundary the coefficient-free
-//     part of its rows (mu terms, divergence blocks) is the level's dense
-//     template R0, applied from shared memory with the window columns split
-//     over the lanes; the cellwise mass term comes from a per-level table;
-//     patches next to the boundary use the stencil visitor;
-//  4. delta = S_v r, the columns of S_v split over the lanes, partial sums
-//     reduced in shared memory, then x|_v += delta.
+// A warp owns GPW patches (one for n_v >= 20) and NR right-hand sides and walks
+// a strided sequence of patch groups; while it computes one group it stages the
+// next (two stages per warp):
+//  1. lane 0 bulk-copies the stored inverses S_v into shared memory; they do
+//     not depend on earlier passes, so the first copy precedes the wait for the
+//     preceding kernel (programmatic dependent launch);
+//  2. the lanes gather the window of x, the patch rows of b and the 2^D cell
+//     coefficients by contiguous segments (cp.async, zero outside the domain);
+//  3. local residual (b - A x)|_v from the lane plan of the patch's type: each
+//     lane accumulates its pieces, the row map adds the pieces of a row;
+//  4. delta = S_v r, the columns of S_v split over the lanes (FP32: packed
+//     pair FMAs), partial sums reduced in shared memory;
+//  5. x|_v = (window copy of x|_v) + delta, stored by patch-row segments.
 // ---------------------------------------------------------------------------
-template <int D, int K, typename T, typename TS, int NR = 1>
-struct PassShape {
-  using PS = PatchShape<D, K>;
-  static constexpr int K1 = K + 1;
-  static constexpr int NV = PS::NV;
-  using SL = SLayout<NV, TS>;
-  static constexpr int RG = SL::RG;
-  static constexpr int NVP = SL::NVP;
-  static constexpr int LPP = NVP / RG;                    // row groups of the S_v product
-  static constexpr int RR = 16 / (int)sizeof(T);          // rows per lane in the template product
-  static constexpr int NVT = ((NV + RR - 1) / RR) * RR;
-  static constexpr int NRG = NVT / RR;                    // row groups of the template product
-  static constexpr int MAXG = NRG > LPP ? NRG : LPP;
-  static constexpr int GPW = (32 / (4 * MAXG)) > 1 ? 32 / (4 * MAXG) : 1;   // patches per warp
-  static constexpr int LW = 32 / GPW;                     // lanes per patch
-  static constexpr int TSPL = LW / NRG;                   // column splits, template product
-  static constexpr int SSPL = LW / LPP;                   // column splits, S_v product
-  static constexpr int WARPS = (NR == 1) ? 4 : 2;
-  static constexpr int PPB = WARPS * GPW;                 // patches per block
-  static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
-  // window of x: velocity component i spans WA nodes along x_i and WB across,
-  // the pressure WP per direction
-  static constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
-  static constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
-  static constexpr int WPP = (D == 2) ? WP * WP : WP * WP * WP;
-  static constexpr int WIN = D * WU + WPP;
-  static constexpr int NC = 1 << D;
-  static constexpr int NG = K + 2;
-  static constexpr int MTE = 2 * NG;                      // mass-table entries per row
-  static constexpr int GTE = WIN + NV + NC;               // gather-table entries
-  static constexpr int TPL = WIN * NVT;                   // template entries
-  static constexpr int SPLIT = (TSPL * NVT > SSPL * NVP ? TSPL * NVT : SSPL * NVP);
-  // per patch in shared memory (T): NR windows, NR b-row blocks, NR residual
-  // blocks, the cell coefficients, the split partial sums
-  static constexpr int T_PER_PATCH = NR * (WIN + NV + NVT) + NC + NR * SPLIT;
-  static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
-  static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  // per-level tables in global memory (read through the L1 cache):
-  // R0 (TPL x T), mass coefficients (NV x MTE x T), mass window index and
-  // cell bit (NV x MTE x int each), gather offsets (GTE x int)
-  static constexpr size_t TAB_T = (size_t)TPL + (size_t)NV * MTE;
-  static constexpr size_t TAB_I = (size_t)2 * NV * MTE + GTE;
-  static constexpr size_t TAB_BYTES = TAB_T * sizeof(T) + TAB_I * sizeof(int);
-  // one pipeline stage of a warp: inverses, per-patch T data, address bases
-  static constexpr size_t STAGE_S = (size_t)GPW * (S_BYTES + SC_BYTES);
-  static constexpr size_t STAGE_T = (((size_t)GPW * T_PER_PATCH * sizeof(T) + 15) / 16) * 16;
-  static constexpr size_t STAGE_B = (size_t)GPW * 4 * (D + 1) * sizeof(int64_t);
-  static constexpr size_t STAGE = STAGE_S + STAGE_T + STAGE_B;
-  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE + (size_t)WARPS * 2 * sizeof(uint64_t) + 16;
+template <typename T> struct PlainLd;
+template <> struct PlainLd<float> {
+  static __device__ __forceinline__ void get(const unsigned char* p, float& c, int& w) {
+    const float2 r = __ldg(reinterpret_cast<const float2*>(p));
+    c = r.x;
+    w = __float_as_int(r.y);
+  }
 };
-
-// Window origin along direction e for component comp (D = pressure).
-template <int D, int K>
-__device__ __forceinline__ int win_origin(const int (&v)[D], int comp, int e) {
-  constexpr int K1 = K + 1;
-  return (comp < D && e != comp) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
-}
-
-// Window position of (comp, idx) for the patch at vertex v.
-template <int D, int K>
-__device__ __forceinline__ int win_index(const int (&v)[D], int comp, const int (&idx)[D]) {
-  constexpr int K1 = K + 1;
-  constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
-  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
-  int l = 0, stride = 1;
-#pragma unroll
-  for (int e = 0; e < D; ++e) {
-    const bool own = comp < D && e == comp;
-    const int m = (comp == D) ? WP : (own ? WA : WB);
-    l += (idx[e] - win_origin<D, K>(v, comp, e)) * stride;
-    stride *= m;
+template <> struct PlainLd<double> {
+  static __device__ __forceinline__ void get(const unsigned char* p, double& c, int& w) {
+    const double2 r = __ldg(reinterpret_cast<const double2*>(p));
+    c = r.x;
+    w = (int)__double_as_longlong(r.y);
   }
-  return comp * WU + l;
-}
-
-// Component and local multi-index of window entry w.
-template <int D, int K>
-__device__ __forceinline__ int win_local(int w, int (&le)[D]) {
-  constexpr int K1 = K + 1;
-  constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
-  constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
-  int comp = w / WU;
-  if (comp > D) comp = D;
-  int r = w - comp * WU;
-#pragma unroll
-  for (int e = 0; e < D; ++e) {
-    if (comp == D) {
-      le[e] = r % WP;
-      r /= WP;
-    } else if (e == comp) {
-      le[e] = r % WA;
-      r /= WA;
-    } else {
-      le[e] = r % WB;
-      r /= WB;
-    }
+};
+template <typename T> struct MassLd;
+template <> struct MassLd<float> {
+  static __device__ __forceinline__ void get(const unsigned char* p, float& c, int& w, int& cell) {
+    const float4 r = __ldg(reinterpret_cast<const float4*>(p));
+    c = r.x;
+    w = __float_as_int(r.y);
+    cell = __float_as_int(r.z);
   }
-  return comp;
-}
-
-template <int D, int K, typename T>
-struct WinVisitor {
-  const int (&v)[D];
-  const T* win;
-  const T* cw;
-  T acc;
-  __device__ WinVisitor(const int (&vv)[D], const T* w, const T* c) : v(vv), win(w), cw(c), acc(T(0)) {}
-  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
-    acc += coef * win[win_index<D, K>(v, comp, j)];
-  }
-  __device__ __forceinline__ T cell_c(const int (&cell)[D]) const {
-    int l = 0;
-#pragma unroll
-    for (int e = 0; e < D; ++e) l |= (cell[e] - (v[e] - 1)) << e;
-    return cw[l];
+};
+template <> struct MassLd<double> {
+  static __device__ __forceinline__ void get(const unsigned char* p, double& c, int& w, int& cell) {
+    const double2 r = __ldg(reinterpret_cast<const double2*>(p));
+    const long long q = __double_as_longlong(r.y);
+    c = r.x;
+    w = (int)(q & 0xffffffffll);
+    cell = (int)(q >> 32);
   }
 };
 
-// Records the coefficient-free interior template: R0[w][l] = coefficient of
-// window column w in patch row l (c = 0), for a patch away from the boundary.
-template <int D, int K, typename T>
-struct TemplateVisitor {
-  const int (&v)[D];
-  T* col;   // R0 + l; column w at col[w * nvt]
-  int nvt;
-  __device__ TemplateVisitor(const int (&vv)[D], T* c, int n) : v(vv), col(c), nvt(n) {}
-  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], T coef) {
-    col[(size_t)win_index<D, K>(v, comp, j) * nvt] += coef;
-  }
-  __device__ __forceinline__ T cell_c(const int (&)[D]) const { return T(0); }
-};
-
-// Per-level tables of the colour pass (one block):
-//   R0 [WIN][NVT]: interior template;  mass table per row: MTE entries of
-//   (coefficient, window index, cell bit), coefficient 0 for unused entries;
-//   gather offsets: window entries relative to the per-patch component base,
-//   b rows relative to the patch-row base, cells relative to the block base.
-template <int D, int K, typename T, typename TS>
-__global__ void k_build_pass_tables(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
-                                    unsigned char* __restrict__ tabs) {
-  using P = PassShape<D, K, T, TS, 1>;
-  constexpr int K1 = K + 1;
-  T* R0 = reinterpret_cast<T*>(tabs);
-  T* mc = R0 + P::TPL;
-  int* mw = reinterpret_cast<int*>(mc + P::NV * P::MTE);
-  int* mb = mw + P::NV * P::MTE;
-  int* gt = mb + P::NV * P::MTE;
-  for (int q = threadIdx.x; q < P::TPL; q += blockDim.x) R0[q] = T(0);
-  for (int q = threadIdx.x; q < P::NV * P::MTE; q += blockDim.x) {
-    mc[q] = T(0);
-    mw[q] = 0;
-    mb[q] = 0;
-  }
-  __syncthreads();
-  int v[D];
-#pragma unroll
-  for (int e = 0; e < D; ++e) v[e] = 2;
-  // interior patches (every v_e in [2, n-2]) exist only for n >= 4; otherwise
-  // the template and mass tables stay zero and are never used
-  for (int l = threadIdx.x; l < P::NV && L.n >= 4; l += blockDim.x) {
-    int idx[D];
-    const int comp = patch_local_decode<D, K>(v, l, idx);
-    TemplateVisitor<D, K, T> vis(v, R0 + l, P::NVT);
-    visit_row(L, tb, comp, idx, vis);
-    if (comp < D) {   // mass term: cells containing the node along x_comp
-      const int t = idx[comp];
-      T wperp = T(1);
-      int cbits = 0;
-#pragma unroll
-      for (int e = 0; e < D; ++e) {
-        if (e == comp) continue;
-        wperp *= tb.wg[idx[e] % K1];
-        cbits |= (idx[e] / K1 - (v[e] - 1)) << e;
-      }
-      const int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
-      int k = 0;
-      for (int cx = lo; cx <= hi; ++cx) {
-        const int a = t - cx * K1;
-        for (int ap = 0; ap < P::NG; ++ap) {
-          int j[D];
-#pragma unroll
-          for (int e = 0; e < D; ++e) j[e] = idx[e];
-          j[comp] = cx * K1 + ap;
-          mc[l * P::MTE + k] = L.s_c * wperp * tb.Mcg[a][ap];
-          mw[l * P::MTE + k] = win_index<D, K>(v, comp, j);
-          mb[l * P::MTE + k] = cbits | ((cx - (v[comp] - 1)) << comp);
-          ++k;
-        }
-      }
-    }
-  }
-  // gather offsets (global strides of each component)
-  for (int q = threadIdx.x; q < P::GTE; q += blockDim.x) {
-    int le[D];
-    int comp = 0;
-    if (q < P::WIN) {
-      comp = win_local<D, K>(q, le);
-    } else if (q < P::WIN + P::NV) {
-      int idx[D];
-      comp = patch_local_decode<D, K>(v, q - P::WIN, idx);
-#pragma unroll
-      for (int e = 0; e < D; ++e) le[e] = idx[e] - ((v[e] - 1) * K1 + ((comp < D && e == comp) ? 1 : 0));
-    } else {
-      const int cl = q - P::WIN - P::NV;
-      int off = 0, s = 1;
-#pragma unroll
-      for (int e = 0; e < D; ++e) {
-        off += ((cl >> e) & 1) * s;
-        s *= L.n;
-      }
-      gt[q] = off;
-      continue;
-    }
-    int off = 0, s = 1;
-#pragma unroll
-    for (int e = 0; e < D; ++e) {
-      off += le[e] * s;
-      s *= (comp < D && e == comp) ? (L.N + 1) : L.N;
-    }
-    gt[q] = off;
-  }
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* dst, const T* src, bool ok) {
+  if constexpr (sizeof(T) == 8) cp_async8(dst, src, ok ? 8u : 0u);
+  else cp_async4(dst, src, ok ? 4u : 0u);
 }
-
-template <typename T> struct Vec16;
-template <> struct Vec16<float> { using type = float4; };
-template <> struct Vec16<double> { using type = double2; };
 
 template <int D, int K, typename T, typename TS, int NR>
-__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
-                                                     int colour, int64_t count, const TS* __restrict__ S,
-                                                     const unsigned char* __restrict__ tabs, T* x,
-                                                     const T* __restrict__ b, int evict_first,
+__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int colour, int64_t count,
+                                                     const TS* __restrict__ S, const unsigned char* __restrict__ tabs,
+                                                     T* x, const T* __restrict__ b, int evict_first,
                                                      int* __restrict__ err, int64_t vs) {
   using P = PassShape<D, K, T, TS, NR>;
-  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, RR = P::RR;
-  constexpr int WIN = P::WIN, NVT = P::NVT, NRG = P::NRG, LW = P::LW, MTE = P::MTE;
-  constexpr int E = NR * WIN + NR * NV + P::NC;   // gathered entries per patch
-  constexpr int NB = 4 * (D + 1);                  // int64 bases per patch
+  using PL = typename P::PL;
+  using PSum = typename P::PSum;
+  constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, LW = P::LW;
+  constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>();
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / LW, lp = lane - g * LW;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * 2 * P::STAGE) + warp * 2;
-  const T* s_R0 = reinterpret_cast<const T*>(tabs);   // per-level tables, global (L1-cached)
-  const T* s_mc = s_R0 + P::TPL;
-  const int* s_mw = reinterpret_cast<const int*>(s_mc + NV * MTE);
-  const int* s_mb = s_mw + NV * MTE;
-  const int* s_gt = s_mb + NV * MTE;
+  const int4* segs = reinterpret_cast<const int4*>(tabs + P::TB_SEG);
+  const unsigned char* plan_p = tabs + P::TB_PLAIN;
+  const unsigned char* plan_m = tabs + P::TB_MASS;
+  const uint32_t* rowp = reinterpret_cast<const uint32_t*>(tabs + P::TB_ROWP);
   const int64_t ngroups = (count + GPW - 1) / GPW;
   const int64_t W = (int64_t)gridDim.x * P::WARPS;
   const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
 
   auto st_S = [&](int bi) { return smem + ((size_t)warp * 2 + bi) * P::STAGE; };
-  auto st_T = [&](int bi) { return reinterpret_cast<T*>(st_S(bi) + P::STAGE_S); };
-  auto st_B = [&](int bi) { return reinterpret_cast<int64_t*>(st_S(bi) + P::STAGE_S + P::STAGE_T); };
+  auto st_T = [&](int bi) { return reinterpret_cast<T*>(st_S(bi) + P::STAGE_S) + g * P::T_PER_PATCH; };
+  auto st_B = [&](int bi) {
+    return reinterpret_cast<int64_t*>(st_S(bi) + P::STAGE_S + P::STAGE_T) + g * P::NSEGB;
+  };
   auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
 
-  // (a) bulk copies of the inverses of patch group pg into stage bi (lane 0)
+  // (1) bulk copies of the inverses of patch group pg into stage bi (lane 0)
   auto issue_S = [&](int bi, int64_t pg) {
     const int np = npat(pg);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bars + bi, (uint32_t)(np * (P::S_BYTES + P::SC_BYTES)));
-    for (int g = 0; g < np; ++g) {
-      const int64_t p = pg * GPW + g;
-      bulk_load(st_S(bi) + (size_t)g * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bars + bi, pol);
+    for (int q = 0; q < np; ++q) {
+      const int64_t p = pg * GPW + q;
+      bulk_load(st_S(bi) + (size_t)q * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bars + bi, pol);
       if constexpr (P::BF)
-        bulk_load(st_S(bi) + (size_t)GPW * P::S_BYTES + (size_t)g * P::SC_BYTES,
+        bulk_load(st_S(bi) + (size_t)GPW * P::S_BYTES + (size_t)q * P::SC_BYTES,
                   reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + p * NVP, P::SC_BYTES, bars + bi, pol);
     }
   };
-  // (b) per-patch address bases: window base per component, b-row base per
-  //     component, cell base, interior flag, vertex
-  auto compute_bases = [&](int bi, int64_t pg) {
-    const int np = npat(pg);
-    int64_t* pbs = st_B(bi);
-    for (int qq = lane; qq < np * NB; qq += 32) {
-      const int gq = qq / NB, item = qq - gq * NB;
-      if (item >= 3 * (D + 1) + D) continue;
-      int v[D];
-      patch_vertex<D>(L.n, colour, pg * GPW + gq, v);
-      int64_t val = 0;
-      if (item < 2 * (D + 1)) {
-        const int c = item % (D + 1);
-        const bool row = item > D;
-        int64_t sstr = 1;
-        val = L.off[c];
-#pragma unroll
-        for (int e = 0; e < D; ++e) {
-          val += (int64_t)(row ? (v[e] - 1) * (K + 1) + ((c < D && e == c) ? 1 : 0) : win_origin<D, K>(v, c, e)) * sstr;
-          sstr *= (c < D && e == c) ? (L.N + 1) : L.N;
-        }
-      } else if (item == 2 * (D + 1)) {
-        int64_t cs = 1;
-#pragma unroll
-        for (int e = 0; e < D; ++e) {
-          val += (int64_t)(v[e] - 1) * cs;
-          cs *= L.n;
-        }
-      } else if (item == 2 * (D + 1) + 1) {
-        bool interior = true;
-#pragma unroll
-        for (int e = 0; e < D; ++e) interior = interior && v[e] >= 2 && v[e] <= L.n - 2;
-        val = interior ? 1 : 0;
-      } else {
-        val = v[item - 3 * (D + 1)];
-      }
-      pbs[gq * NB + item] = val;
+  // vertex of this lane's patch in group pg; false past the last patch
+  auto vertex = [&](int64_t pg, int (&v)[D]) {
+    const int64_t p = pg * GPW + g;
+    if (p < count) {
+      patch_vertex<D>(L.n, colour, p, v);
+      return true;
     }
-  };
-  // (c) asynchronous gather of windows, b rows and cell coefficients (needs the bases)
-  auto issue_window = [&](int bi, int64_t pg) {
-    const int np = npat(pg);
-    const int64_t* pbs = st_B(bi);
-    T* tw = st_T(bi);
-    for (int q = lane; q < np * E; q += 32) {
-      const int g = q / E, e = q - g * E;
-      const int64_t* pb = pbs + g * NB;
-      const T* src = x;
-      bool ok = true;
-      int dst;
-      if (e < NR * WIN) {
-        const int rr = e / WIN, w = e - rr * WIN;
-        int comp = w / P::WU;
-        if (comp > D) comp = D;
-        if (!pb[2 * (D + 1) + 1]) {   // boundary patch: entries outside the domain are zero
-          int le[D];
-          win_local<D, K>(w, le);
 #pragma unroll
-          for (int d2 = 0; d2 < D; ++d2) {
-            const int vv2 = (int)pb[3 * (D + 1) + d2];
-            const int o = (comp < D && d2 != comp) ? (vv2 - 2) * (K + 1) : (vv2 - 1) * (K + 1);
-            const int id = o + le[d2];
-            const int hi = (comp < D && d2 == comp) ? L.N : L.N - 1;
-            ok = ok && id >= 0 && id <= hi;
-          }
+    for (int e = 0; e < D; ++e) v[e] = 2;
+    return false;
+  };
+  // (2) asynchronous gather of the window, the patch rows of b and the cells
+  auto issue_gather = [&](int bi, const int (&v)[D], bool act) {
+    T* tw = st_T(bi);
+    int64_t* bb = st_B(bi);
+    if (act) {
+      for (int s = lp; s < P::NSEG; s += LW) {
+        const int4 d0 = __ldg(segs + 4 * s), d1 = __ldg(segs + 4 * s + 1);
+        const int4 d2 = __ldg(segs + 4 * s + 2), d3 = __ldg(segs + 4 * s + 3);
+        int64_t src = (int64_t)d0.w + (int64_t)v[0] * d1.x + (int64_t)v[1] * d1.y;
+        if constexpr (D == 3) src += (int64_t)v[2] * d1.z;
+        const int m = d1.w;
+        bool okr;
+        {
+          const int ix = m * v[1] + d2.y;
+          okr = ix >= 0 && ix <= d3.x;
         }
-        if (ok) src = x + pb[comp] + s_gt[w] + rr * vs;
-        dst = e;
-      } else if (e < NR * (WIN + NV)) {
-        const int e2 = e - NR * WIN;
-        const int rr = e2 / NV, l = e2 - rr * NV;
-        int comp = l / P::PS::NU1;
-        if (comp > D) comp = D;
-        src = b + pb[(D + 1) + comp] + s_gt[WIN + l] + rr * vs;
-        dst = e;
-      } else {
-        src = L.c + pb[2 * (D + 1)] + s_gt[WIN + NV + (e - NR * (WIN + NV))];
-        dst = NR * (WIN + NV + NVT) + (e - NR * (WIN + NV));
+        if constexpr (D == 3) {
+          const int ix = m * v[2] + d2.z;
+          okr = okr && ix >= 0 && ix <= d3.y;
+        }
+        const int i0 = m * v[0] + d2.x, hi0 = d2.w;
+        const int kind = d0.x, len = d0.y, dst = d0.z;
+        if (kind == 2) {
+#pragma unroll
+          for (int i = 0; i < 2; ++i) cp_async_t(tw + P::OFF_C + dst + i, L.c + src + i, true);
+        } else {
+          const T* base = (kind == 0) ? x : b;
+          T* dd = tw + ((kind == 0) ? P::OFF_W : P::OFF_B) + dst;
+          const int rs = (kind == 0) ? WIN : NV;
+          if (kind == 1) bb[d3.w] = src;
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+            for (int i = 0; i < P::LMAX; ++i)
+              if (i < len) {
+                const bool ok = okr && (unsigned)(i0 + i) <= (unsigned)hi0;
+                cp_async_t(dd + rr * rs + i, ok ? base + (src + rr * vs + i) : base, ok);
+              }
+        }
       }
-      T* d = tw + g * P::T_PER_PATCH + dst;
-      if constexpr (sizeof(T) == 8) cp_async8(d, src, ok ? 8u : 0u);
-      else cp_async4(d, src, ok ? 4u : 0u);
     }
     cp_async_commit();
   };
 
   int64_t pg = (int64_t)blockIdx.x * P::WARPS + warp;
+  int vc[D];
+  bool actc = vertex(pg, vc);
   if (lane == 0) {
     mbar_init(bars + 0, 1);
     mbar_init(bars + 1, 1);
   }
   __syncwarp();
-  if (pg < ngroups) {
-    if (lane == 0) issue_S(0, pg);   // the inverses do not depend on earlier passes
-    compute_bases(0, pg);
-  }
+  if (pg < ngroups && lane == 0) issue_S(0, pg);   // the inverses do not depend on earlier passes
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncwarp();
-  if (pg < ngroups) issue_window(0, pg);
+  if (pg < ngroups) issue_gather(0, vc, actc);
   for (int k = 0; pg < ngroups; ++k, pg += W) {
     const int bi = k & 1;
     const int64_t pn = pg + W;
+    int vn[D];
+    const bool actn = vertex(pn, vn);
     if (pn < ngroups) {   // stage the next group while this one is computed
       if (lane == 0) issue_S(bi ^ 1, pn);
-      compute_bases(bi ^ 1, pn);
-      __syncwarp();
-      issue_window(bi ^ 1, pn);
+      issue_gather(bi ^ 1, vn, actn);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncwarp();
-    const int nmine = npat(pg);
-    T* tw = st_T(bi);
-    const int64_t* wb0 = st_B(bi);
-    // local residual rows (b - A x)|_v
-    const int g = lane / LW, lp = lane - g * LW;
-    {
-      T* pbase = tw + g * P::T_PER_PATCH;
-      const T* cw = pbase + NR * (WIN + NV + NVT);
-      T* part = pbase + NR * (WIN + NV + NVT) + P::NC;   // NR x SPLIT
-      const bool active = g < nmine;
-      const bool interior = active && wb0[g * NB + 2 * (D + 1) + 1] != 0;
-      int v[D];
+    T* pb = st_T(bi);
+    const T* win = pb + P::OFF_W;
+    const T* cw = pb + P::OFF_C;
+    T* part = pb + P::OFF_P;
+    const int type = patch_type<D>(vc, L.n);
+    // (3a) lane pieces of the local residual
+    if (actc) {
+      const unsigned char* pp = plan_p + ((size_t)type * PSum::ZP * LW + lp) * PB;
+      const unsigned char* pm = plan_m + ((size_t)type * PSum::ZM * LW + lp) * MASS_BYTES;
 #pragma unroll
-      for (int e = 0; e < D; ++e) v[e] = active ? (int)wb0[g * NB + 3 * (D + 1) + e] : 2;
-      const int rg = lp % NRG, sp = lp / NRG;
-      constexpr int WCH = (WIN + P::TSPL - 1) / P::TSPL;
-      if (interior && sp < P::TSPL) {
-        using V = typename Vec16<T>::type;
-        T acc[RR][NR];
+      for (int p = 0; p < PL::NP; ++p) {
+        T acc[NR];
 #pragma unroll
-        for (int r = 0; r < RR; ++r)
+        for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
-        const int w0 = sp * WCH, w1 = (w0 + WCH < WIN) ? w0 + WCH : WIN;
-#pragma unroll 4
-        for (int w = w0; w < w1; ++w) {
-          const V c4 = __ldg(reinterpret_cast<const V*>(s_R0 + w * NVT + rg * RR));
-          const T* cc = reinterpret_cast<const T*>(&c4);
+        for (int s = 0; s < PL::z(p); ++s) {
+          T c;
+          int w;
+          PlainLd<T>::get(pp + (size_t)(PSum::zoff(p) + s) * LW * PB, c, w);
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            const T xw = pbase[rr * WIN + w];
-#pragma unroll
-            for (int r = 0; r < RR; ++r) acc[r][rr] += cc[r] * xw;
-          }
+          for (int rr = 0; rr < NR; ++rr) acc[rr] += c * win[rr * WIN + w];
         }
 #pragma unroll
-        for (int rr = 0; rr < NR; ++rr)
+        for (int s = 0; s < PL::zm(p); ++s) {
+          T c;
+          int w, cell;
+          MassLd<T>::get(pm + (size_t)(PSum::zmoff(p) + s) * LW * MASS_BYTES, c, w, cell);
+          const T cc = c * cw[cell];
 #pragma unroll
-          for (int r = 0; r < RR; ++r) part[rr * P::SPLIT + sp * NVT + rg * RR + r] = acc[r][rr];
+          for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * win[rr * WIN + w];
+        }
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) part[rr * PARTS + p * LW + lp] = acc[rr];
       }
-      __syncwarp();
-      if (interior) {
-        for (int l = lp; l < NV; l += LW) {
+      if (lp == 0) {
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            T a = T(0);
+        for (int rr = 0; rr < NR; ++rr) part[rr * PARTS + P::ZSLOT] = T(0);
+      }
+    }
+    __syncwarp();
+    // (3b) wait for the inverses of this group (bounded); rows of the residual
+    const bool have_S = mbar_wait_bounded(bars + bi, (uint32_t)((k >> 1) & 1), 2000000000ull);
+    if (!have_S && lane == 0) atomicExch(err, 2);
+    const float* sc = reinterpret_cast<const float*>(st_S(bi) + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
+    if (actc && have_S) {
+      for (int l = lp; l < NV; l += LW) {
+        const uint32_t rp = __ldg(rowp + (size_t)type * NV + l);
 #pragma unroll
-            for (int s2 = 0; s2 < P::TSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVT + l];
-            const T* win = pbase + rr * WIN;
+        for (int rr = 0; rr < NR; ++rr) {
+          T sum = part[rr * PARTS + (rp & 0xffu)];
 #pragma unroll
-            for (int kk = 0; kk < MTE; ++kk)
-              a += __ldg(s_mc + l * MTE + kk) * cw[__ldg(s_mb + l * MTE + kk)] * win[__ldg(s_mw + l * MTE + kk)];
-            pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - a;
-          }
-        }
-      } else if (active) {
-        for (int l = lp; l < NV; l += LW) {
-          int idx[D];
-          const int comp = patch_local_decode<D, K>(v, l, idx);
-#pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            WinVisitor<D, K, T> vis(v, pbase + rr * WIN, cw);
-            visit_row(L, tb, comp, idx, vis);
-            pbase[NR * (WIN + NV) + rr * NVT + l] = pbase[NR * WIN + rr * NV + l] - vis.acc;
-          }
+          for (int k2 = 1; k2 < PL::MAXP; ++k2) sum += part[rr * PARTS + ((rp >> (8 * k2)) & 0xffu)];
+          T r = pb[P::OFF_B + rr * NV + l] - sum;
+          if constexpr (P::BF) r *= sc[l];
+          if constexpr (P::F2) reinterpret_cast<float2*>(pb + P::OFF_R + rr * 2 * NV)[l] = make_float2(r, r);
+          else pb[P::OFF_R + rr * NV + l] = r;
         }
       }
     }
     __syncwarp();
-    // wait for the inverses of this group (bounded), then delta = S_v r
-    if (!mbar_wait_bounded(bars + bi, (uint32_t)((k >> 1) & 1), 2000000000ull)) {
-      if (lane == 0) atomicExch(err, 2);
-      continue;
-    }
+    // (4) delta = S_v r: row group q, column split sp
     {
       const int q = lp % LPP, sp = lp / LPP;
-      constexpr int JCH = (NV + P::SSPL - 1) / P::SSPL;
-      T* pbase = tw + g * P::T_PER_PATCH;
-      T* part = pbase + NR * (WIN + NV + NVT) + P::NC;
-      const float* sc = reinterpret_cast<const float*>(st_S(bi) + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
-      if (g < nmine && sp < P::SSPL) {
+      if (actc && have_S && sp < SSPL) {
         const TS* Sg = reinterpret_cast<const TS*>(st_S(bi) + (size_t)g * P::S_BYTES) + q * RG;
-        const T* rv = pbase + NR * (WIN + NV);
-        T acc[RG][NR];
+        if constexpr (P::F2) {
+          float2 acc[RG / 2][NR];
 #pragma unroll
-        for (int r = 0; r < RG; ++r)
+          for (int h = 0; h < RG / 2; ++h)
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
-        const int j0 = sp * JCH, j1 = (j0 + JCH < NV) ? j0 + JCH : NV;
-#pragma unroll 4
-        for (int j = j0; j < j1; ++j) {
-          T sv[RG];
-          load_rg_smem<TS, T>(Sg + j * NVP, sv);
+            for (int rr = 0; rr < NR; ++rr) acc[h][rr] = make_float2(0.f, 0.f);
+          const float2* rv = reinterpret_cast<const float2*>(pb + P::OFF_R);
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            T rj = rv[rr * NVT + j];
-            if constexpr (P::BF) rj *= sc[j];
+          for (int jj = 0; jj < P::JCH; ++jj) {
+            const int j = sp * P::JCH + jj;
+            if (j < NV) {
+              float sv[RG];
+              load_rg_smem<TS, float>(Sg + (size_t)j * NVP, sv);
 #pragma unroll
-            for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+              for (int rr = 0; rr < NR; ++rr) {
+                const float2 rj = rv[rr * NV + j];
+#pragma unroll
+                for (int h = 0; h < RG / 2; ++h)
+                  acc[h][rr] = __ffma2_rn(make_float2(sv[2 * h], sv[2 * h + 1]), rj, acc[h][rr]);
+              }
+            }
           }
-        }
 #pragma unroll
-        for (int rr = 0; rr < NR; ++rr)
+          for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-          for (int r = 0; r < RG; ++r) part[rr * P::SPLIT + sp * NVP + q * RG + r] = acc[r][rr];
-      }
-      __syncwarp();
-      if (g < nmine) {
-        const int64_t* pb = wb0 + g * NB;
-        for (int row = lp; row < NV; row += LW) {
-          int comp = row / P::PS::NU1;
-          if (comp > D) comp = D;
-          const int64_t f = pb[(D + 1) + comp] + s_gt[WIN + row];
-          const T sr = P::BF ? (T)sc[row] : T(1);
+            for (int h = 0; h < RG / 2; ++h) {
+              part[rr * PARTS + sp * NVP + q * RG + 2 * h] = acc[h][rr].x;
+              part[rr * PARTS + sp * NVP + q * RG + 2 * h + 1] = acc[h][rr].y;
+            }
+        } else {
+          T acc[RG][NR];
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr) {
-            T a = T(0);
+          for (int r = 0; r < RG; ++r)
 #pragma unroll
-            for (int s2 = 0; s2 < P::SSPL; ++s2) a += part[rr * P::SPLIT + s2 * NVP + row];
-            x[f + rr * vs] += P::BF ? a * sr : a;
+            for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+          const T* rv = pb + P::OFF_R;
+#pragma unroll
+          for (int jj = 0; jj < P::JCH; ++jj) {
+            const int j = sp * P::JCH + jj;
+            if (j < NV) {
+              T sv[RG];
+              load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
+#pragma unroll
+              for (int rr = 0; rr < NR; ++rr) {
+                const T rj = rv[rr * NV + j];
+#pragma unroll
+                for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+              }
+            }
           }
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) part[rr * PARTS + sp * NVP + q * RG + r] = acc[r][rr];
         }
       }
     }
     __syncwarp();
+    // (5) x|_v = window copy of x|_v + delta, by patch-row segments
+    if (actc && have_S) {
+      const int64_t* bb = st_B(bi);
+      for (int s = lp; s < P::NSEGB; s += LW) {
+        const int4 d0 = __ldg(segs + 4 * (P::NSEGX + s)), d3 = __ldg(segs + 4 * (P::NSEGX + s) + 3);
+        const int len = d0.y, l0 = d0.z, wst = d3.z;
+        const int64_t base = bb[s];
+#pragma unroll
+        for (int i = 0; i < P::LMAXB; ++i)
+          if (i < len) {
+            const int l = l0 + i;
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr) {
+              T a = part[rr * PARTS + l];
+#pragma unroll
+              for (int s2 = 1; s2 < SSPL; ++s2) a += part[rr * PARTS + s2 * NVP + l];
+              if constexpr (P::BF) a *= (T)sc[l];
+              x[base + rr * vs + i] = win[rr * WIN + wst + i] + a;
+            }
+          }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < D; ++e) vc[e] = vn[e];
+    actc = actn;
   }
 }
 

@@ -4,6 +4,8 @@
 #include "tables.h"
 
 #include <cmath>
+#include <string>
+#include <vector>
 
 #ifndef MG_D
 #error "MG_D must be defined"
@@ -137,8 +139,8 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), tab<T>(), colour, h.count[colour],
-                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), colour, h.count[colour], (const TS*)S,
+                     (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
 // Right-hand sides in groups of four share each S_v load; the rest one by one.
@@ -161,7 +163,7 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
   else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, err, nrhs, s);
 }
 
-// Bytes of the per-level colour-pass tables (rounded to 16).
+// Bytes of the per-level colour-pass tables (segments, lane plans, row maps).
 int64_t template_elems(int sprec) {
   size_t b;
   if (sprec == P64) b = PassShape<D, K, double, double, 1>::TAB_BYTES;
@@ -170,11 +172,57 @@ int64_t template_elems(int sprec) {
   return (int64_t)((b + 15) / 16) * 16;
 }
 
-void build_template(const HostLevel& h, int sprec, void* tabs, cudaStream_t s) {
-  auto* t = (unsigned char*)tabs;
-  if (sprec == P64) k_build_pass_tables<D, K, double, double><<<1, 256, 0, s>>>(mk<double>(h), tab<double>(), t);
-  else if (sprec == P32) k_build_pass_tables<D, K, float, float><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), t);
-  else k_build_pass_tables<D, K, float, __nv_bfloat16><<<1, 256, 0, s>>>(mk<float>(h), tab<float>(), t);
+template <typename T, typename TS>
+int build_template_t(const HostLevel& h, void* tabs, cudaStream_t s, std::string* why) {
+  std::vector<unsigned char> blob;
+  std::string msg;
+  if (!build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg)) {
+    if (why) *why = "colour-pass tables of the " + std::to_string(h.n) + "^" + std::to_string(D) + " level: " + msg;
+    return 1;
+  }
+  if (cudaMemcpyAsync(tabs, blob.data(), blob.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    if (why) *why = "upload of the colour-pass tables failed";
+    return 2;
+  }
+  return 0;
+}
+
+// Builds the colour-pass tables on the host and uploads them; nonzero (with
+// a reason) if the rows of a patch type do not fit the lane plan.
+int build_template(const HostLevel& h, int sprec, void* tabs, cudaStream_t s, std::string* why) {
+  if (sprec == P64) return build_template_t<double, double>(h, tabs, s, why);
+  if (sprec == P32) return build_template_t<float, float>(h, tabs, s, why);
+  return build_template_t<float, __nv_bfloat16>(h, tabs, s, why);
+}
+
+// Host check of the colour-pass tables of an n^D level (no GPU needed).
+template <typename T, typename TS>
+int plan_selftest_t(int n, double mu, std::string& why) {
+  HostLevel h = {};
+  h.d = D;
+  h.k = K;
+  h.n = n;
+  h.N = n * (K + 1);
+  int64_t o = 0;
+  for (int c = 0; c <= D; ++c) {
+    h.off[c] = o;
+    o += comp_size<D>(h.N, c);
+  }
+  h.ndof = o;
+  h.h = 1.0 / n;
+  h.mu = mu;
+  return check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+}
+
+int plan_selftest(int sprec, int n, double mu, std::string* why) {
+  std::string msg;
+  int r;
+  if (sprec == P64) r = plan_selftest_t<double, double>(n, mu, msg);
+  else if (sprec == P32) r = plan_selftest_t<float, float>(n, mu, msg);
+  else r = plan_selftest_t<float, __nv_bfloat16>(n, mu, msg);
+  if (why) *why = msg;
+  return r;
 }
 
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
@@ -227,6 +275,7 @@ DKOps make_ops() {
   o.load_vector = load_vector;
   o.template_elems = template_elems;
   o.build_template = build_template;
+  o.plan_selftest = plan_selftest;
   return o;
 }
 

@@ -21,7 +21,7 @@ struct HostLevel {
   float* c32;
   int sprec;             // storage precision of the patch inverses (Prec)
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
-  void* R0;              // colour-pass tables: interior template, mass and gather tables
+  void* R0;              // colour-pass tables: gather segments, lane plans and row maps
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision
@@ -50,9 +50,12 @@ struct DKOps {
   // the patch inverses sets *err = 2
   void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, int* err,
                       int nrhs, cudaStream_t);
-  // per-level colour-pass tables: bytes for storage precision sprec, and their construction
+  // per-level colour-pass tables: bytes for storage precision sprec, and their
+  // construction on the host (nonzero with a reason if the level is not supported)
   int64_t (*template_elems)(int sprec);
-  void (*build_template)(const HostLevel&, int sprec, void* R0, cudaStream_t);
+  int (*build_template)(const HostLevel&, int sprec, void* R0, cudaStream_t, std::string* why);
+  // host check of the tables of an n^d level (no GPU); nonzero with a reason on failure
+  int (*plan_selftest)(int sprec, int n, double mu, std::string* why);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);

@@ -1,0 +1,745 @@
+// passplan.cuh -- geometry and per-level tables of the colour pass of the
+// multiplicative Schwarz smoother (Sec. 3.3), and their host-side construction.
+//
+// A colour pass computes, for every vertex patch v of one colour,
+//     x|_v += S_v (b - A x)|_v.
+// The rows of A restricted to the patch dofs touch a fixed window of x around
+// the vertex.  The coefficient-free part of those rows (mu terms, interior
+// penalty and Nitsche terms, divergence blocks) depends only on where the
+// patch sits relative to the boundary: per direction the vertex is next to the
+// lower boundary (v = 1), interior (2 <= v <= n-2), next to the upper boundary
+// (v = n-1), or both (n = 2).  Each of these patch types gets a sparse "lane
+// plan": the nonzeros of its rows, distributed over the lanes of the warp that
+// owns the patch, in slots whose number is fixed at compile time.  The cell
+// coefficient enters through separate mass slots (coefficient, window column,
+// cell) of the velocity mass term.
+//
+// Per level the table blob holds
+//   segment descriptors: contiguous runs (along x_0) of the window of x, of
+//     the patch rows of b and of the patch cells, relative to the vertex;
+//   plain plan:  [type][slot][lane] (coefficient, window column);
+//   mass plan:   [type][mass slot][lane] (coefficient, window column, cell);
+//   row map:     [type][row] the partial sums (lane pieces) that make up a row.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "device.cuh"
+
+namespace mgd {
+
+// --- window geometry ---------------------------------------------------------
+// Velocity component i spans WA = 2K+3 nodes along x_i (from the face below the
+// patch block to the face above it) and WB = 4(K+1) Gauss nodes across
+// (cells v-2 .. v+1); the pressure spans WP = 2(K+1) nodes per direction.
+
+template <int D, int K>
+__host__ __device__ __forceinline__ int win_origin(const int (&v)[D], int comp, int e) {
+  constexpr int K1 = K + 1;
+  return (comp < D && e != comp) ? (v[e] - 2) * K1 : (v[e] - 1) * K1;
+}
+
+template <int D, int K>
+__host__ __device__ __forceinline__ int win_extent(int comp, int e) {
+  constexpr int K1 = K + 1;
+  return (comp == D) ? 2 * K1 : ((e == comp) ? 2 * K1 + 1 : 4 * K1);
+}
+
+// Window position of (comp, idx) for the patch at vertex v.
+template <int D, int K>
+__host__ __device__ __forceinline__ int win_index(const int (&v)[D], int comp, const int (&idx)[D]) {
+  constexpr int K1 = K + 1;
+  constexpr int WU = (D == 2) ? (2 * K1 + 1) * 4 * K1 : (2 * K1 + 1) * 16 * K1 * K1;
+  int l = 0, stride = 1;
+  for (int e = 0; e < D; ++e) {
+    l += (idx[e] - win_origin<D, K>(v, comp, e)) * stride;
+    stride *= win_extent<D, K>(comp, e);
+  }
+  return comp * WU + l;
+}
+
+// Patch type code per direction: 0 lower boundary, 1 interior, 2 upper
+// boundary, 3 both (n = 2); the type of a patch is sum_e code_e 4^e.
+__host__ __device__ __forceinline__ int type_code(int ve, int n) {
+  return n == 2 ? 3 : (ve == 1 ? 0 : (ve == n - 1 ? 2 : 1));
+}
+template <int D>
+__host__ __device__ __forceinline__ int patch_type(const int (&v)[D], int n) {
+  int t = 0;
+  for (int e = D - 1; e >= 0; --e) t = 4 * t + type_code(v[e], n);
+  return t;
+}
+
+// --- lane plans ----------------------------------------------------------------
+// NP pieces per lane; piece p has z(p) plain and zm(p) mass slots and yields one
+// partial sum.  A row is the sum of at most MAXP pieces.  The shapes cover the
+// Brinkman (mu > 0) and Darcy (mu = 0) rows of every patch type; the host
+// builder rejects a level whose rows do not fit.
+template <int D, int K, int LW> struct PlanShape;
+template <> struct PlanShape<2, 1, 32> {
+  static constexpr int NP = 2, MAXP = 2;
+  static constexpr int z(int p) { return p == 0 ? 22 : 12; }
+  static constexpr int zm(int p) { return p == 0 ? 6 : 0; }
+};
+template <> struct PlanShape<2, 0, 4> {
+  static constexpr int NP = 2, MAXP = 2;
+  static constexpr int z(int p) { return p == 0 ? 11 : 4; }
+  static constexpr int zm(int p) { return p == 0 ? 4 : 0; }
+};
+template <> struct PlanShape<2, 0, 8> {
+  static constexpr int NP = 2, MAXP = 2;
+  static constexpr int z(int p) { return p == 0 ? 6 : 4; }
+  static constexpr int zm(int p) { return p == 0 ? 2 : 0; }
+};
+template <> struct PlanShape<2, 0, 16> {
+  static constexpr int NP = 1, MAXP = 2;
+  static constexpr int z(int) { return 6; }
+  static constexpr int zm(int) { return 2; }
+};
+template <> struct PlanShape<3, 0, 32> {
+  static constexpr int NP = 1, MAXP = 2;
+  static constexpr int z(int) { return 9; }
+  static constexpr int zm(int) { return 4; }
+};
+template <> struct PlanShape<3, 0, 16> {
+  static constexpr int NP = 2, MAXP = 2;
+  static constexpr int z(int) { return 9; }
+  static constexpr int zm(int) { return 2; }
+};
+
+template <class PL>
+struct PlanSums {
+  static constexpr int zoff(int p) { return p == 0 ? 0 : zoff(p - 1) + PL::z(p - 1); }
+  static constexpr int zmoff(int p) { return p == 0 ? 0 : zmoff(p - 1) + PL::zm(p - 1); }
+  static constexpr int ZP = zoff(PL::NP);
+  static constexpr int ZM = zmoff(PL::NP);
+};
+
+// Plan entries as stored (and loaded as one 8- or 16-byte vector).
+//   plain, float:  {coef, w}             plain, double: {coef, (int64) w}
+//   mass,  float:  {coef, w, cell, 0}    mass,  double: {coef, w | cell << 32}
+template <typename T> constexpr int plain_bytes() { return sizeof(T) == 4 ? 8 : 16; }
+constexpr int MASS_BYTES = 16;
+constexpr int SEG_INTS = 16;
+
+// --- colour-pass shape ---------------------------------------------------------
+template <int D, int K, typename T, typename TS, int NR = 1>
+struct PassShape {
+  using PS = PatchShape<D, K>;
+  static constexpr int K1 = K + 1;
+  static constexpr int NV = PS::NV;
+  using SL = SLayout<NV, TS>;
+  static constexpr int RG = SL::RG;
+  static constexpr int NVP = SL::NVP;
+  static constexpr int LPP = NVP / RG;                    // row groups of the S_v product
+  static constexpr int GPW = (32 / (4 * LPP)) > 1 ? 32 / (4 * LPP) : 1;   // patches per warp
+  static constexpr int LW = 32 / GPW;                     // lanes per patch
+  static constexpr int SSPL = LW / LPP;                   // column splits of the S_v product
+  static constexpr int JCH = (NV + SSPL - 1) / SSPL;      // columns per split
+  static constexpr int WARPS = (NR == 1) ? 4 : 2;
+  static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
+  static constexpr bool F2 = sizeof(T) == 4;              // FP32: residual stored as (r, r) pairs
+  using PL = PlanShape<D, K, LW>;
+  using PSum = PlanSums<PL>;
+  // window
+  static constexpr int WA = 2 * K1 + 1, WB = 4 * K1, WP = 2 * K1;
+  static constexpr int WU = (D == 2) ? WA * WB : WA * WB * WB;
+  static constexpr int WPP = (D == 2) ? WP * WP : WP * WP * WP;
+  static constexpr int WIN = D * WU + WPP;
+  static constexpr int NC = 1 << D;
+  // segments: rows of the window along x_0, rows of the patch block along x_0, cell pairs
+  static constexpr int pw(int b, int e) { return e == 0 ? 1 : b * pw(b, e - 1); }
+  static constexpr int NSEGX = (D == 2) ? (WB + WA + WP) : (WB * WB + 2 * WA * WB + WP * WP);
+  static constexpr int NSEGB = (D == 2) ? (PS::UB + PS::UA + PS::UB) : (PS::UB * PS::UB + 2 * PS::UA * PS::UB + PS::UB * PS::UB);
+  static constexpr int NSEGC = NC / 2;
+  static constexpr int NSEG = NSEGX + NSEGB + NSEGC;
+  static constexpr int LMAX = WB;                          // longest segment
+  static constexpr int LMAXB = PS::UB;                     // longest patch-row segment
+  // partial sums: residual pieces (NP x LW) and S_v splits (SSPL x NVP), + a zero slot
+  static constexpr int PARTS = ((SSPL * NVP > PL::NP * LW) ? SSPL * NVP : PL::NP * LW) + 1;
+  static constexpr int ZSLOT = PARTS - 1;
+  // per patch in shared memory (T): windows, b rows, residual, cell coefficients, partials
+  static constexpr int OFF_W = 0;
+  static constexpr int OFF_B = NR * WIN;
+  static constexpr int OFF_R = OFF_B + NR * NV;
+  static constexpr int RSZ = F2 ? 2 * NV : NV;
+  static constexpr int OFF_C = OFF_R + NR * RSZ;
+  static constexpr int OFF_P = OFF_C + NC;
+  static constexpr int T_PER_PATCH = ((OFF_P + NR * PARTS + 3) / 4) * 4;
+  static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
+  static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
+  // one pipeline stage of a warp: inverses, per-patch T data, patch-row bases
+  static constexpr size_t STAGE_S = (size_t)GPW * (S_BYTES + SC_BYTES);
+  static constexpr size_t STAGE_T = (((size_t)GPW * T_PER_PATCH * sizeof(T) + 15) / 16) * 16;
+  static constexpr size_t STAGE_B = (((size_t)GPW * NSEGB * sizeof(int64_t) + 15) / 16) * 16;
+  static constexpr size_t STAGE = STAGE_S + STAGE_T + STAGE_B;
+  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE + (size_t)WARPS * 2 * sizeof(uint64_t) + 16;
+  // per-level tables
+  static constexpr int NTYPE = (D == 2) ? 16 : 64;
+  static constexpr size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+  static constexpr size_t TB_SEG = 0;
+  static constexpr size_t TB_PLAIN = al16((size_t)NSEG * SEG_INTS * 4);
+  static constexpr size_t TB_MASS = TB_PLAIN + al16((size_t)NTYPE * PSum::ZP * LW * plain_bytes<T>());
+  static constexpr size_t TB_ROWP = TB_MASS + al16((size_t)NTYPE * PSum::ZM * LW * MASS_BYTES);
+  static constexpr size_t TAB_BYTES = TB_ROWP + al16((size_t)NTYPE * NV * 4);
+  static_assert(PL::MAXP <= 4, "row map holds four pieces");
+  static_assert(PARTS <= 256, "piece indices are bytes");
+  static_assert((OFF_R % 2) == 0, "residual pairs need 8-byte alignment");
+};
+
+// --- host construction -----------------------------------------------------------
+
+// Records the coefficient-free part of one row: row[w] += coef.
+template <int D, int K, typename T>
+struct HostRowVisitor {
+  const int (&v)[D];
+  T* row;
+  HostRowVisitor(const int (&vv)[D], T* r) : v(vv), row(r) {}
+  void operator()(int comp, const int (&j)[D], T coef) { row[win_index<D, K>(v, comp, j)] += coef; }
+  T cell_c(const int (&)[D]) const { return T(0); }
+};
+
+// Evaluates a full row on a window (cell coefficients cw by cell bit).
+template <int D, int K>
+struct HostEvalVisitor {
+  const int (&v)[D];
+  const double* win;
+  const double* cw;
+  double acc = 0, mag = 0;
+  HostEvalVisitor(const int (&vv)[D], const double* w, const double* c) : v(vv), win(w), cw(c) {}
+  void operator()(int comp, const int (&j)[D], double coef) {
+    const double t = coef * win[win_index<D, K>(v, comp, j)];
+    acc += t;
+    mag += std::fabs(t);
+  }
+  double cell_c(const int (&cell)[D]) const {
+    int l = 0;
+    for (int e = 0; e < D; ++e) l |= (cell[e] - (v[e] - 1)) << e;
+    return cw[l];
+  }
+};
+
+template <typename T>
+struct PlanRow {
+  std::vector<std::pair<int, T>> pl;            // (window column, coefficient)
+  std::vector<std::pair<std::pair<int, int>, T>> ms;   // ((window column, cell), coefficient)
+};
+
+// Plain and mass entries of the rows of the patch at vertex v.
+template <int D, int K, typename T>
+void plan_rows(const Lvl<D, K, T>& L, const Tab<K, T>& tb, const int (&v)[D], std::vector<PlanRow<T>>& rows) {
+  using P = PassShape<D, K, T, T, 1>;
+  constexpr int K1 = K + 1, NG = K + 2;
+  rows.assign(P::NV, PlanRow<T>());
+  std::vector<T> dense(P::WIN);
+  for (int l = 0; l < P::NV; ++l) {
+    int idx[D];
+    const int comp = patch_local_decode<D, K>(v, l, idx);
+    std::fill(dense.begin(), dense.end(), T(0));
+    HostRowVisitor<D, K, T> vis(v, dense.data());
+    visit_row(L, tb, comp, idx, vis);
+    for (int w = 0; w < P::WIN; ++w)
+      if (dense[w] != T(0)) rows[l].pl.push_back({w, dense[w]});
+    if (comp < D) {   // velocity mass term: the cells along x_comp that contain the node
+      const int t = idx[comp];
+      T wperp = T(1);
+      int cbits = 0;
+      for (int e = 0; e < D; ++e) {
+        if (e == comp) continue;
+        wperp *= tb.wg[idx[e] % K1];
+        cbits |= (idx[e] / K1 - (v[e] - 1)) << e;
+      }
+      const int lo = (t % K1 == 0) ? t / K1 - 1 : t / K1, hi = t / K1;
+      for (int cx = lo; cx <= hi; ++cx) {
+        const int a = t - cx * K1;
+        for (int ap = 0; ap < NG; ++ap) {
+          const int tp = cx * K1 + ap;
+          if (tp == 0 || tp == L.N) continue;   // constrained column
+          int j[D];
+          for (int e = 0; e < D; ++e) j[e] = idx[e];
+          j[comp] = tp;
+          const T coef = L.s_c * tb.Mcg[a][ap] * wperp;
+          if (coef == T(0)) continue;
+          rows[l].ms.push_back({{win_index<D, K>(v, comp, j), cbits | ((cx - (v[comp] - 1)) << comp)}, coef});
+        }
+      }
+    }
+  }
+}
+
+// Representative vertex of a patch type on a level of n cells per direction.
+template <int D>
+void type_vertex(int type, int n, int (&v)[D]) {
+  for (int e = 0; e < D; ++e) {
+    const int code = (type >> (2 * e)) & 3;
+    v[e] = code == 0 ? 1 : (code == 1 ? 2 : (code == 2 ? n - 1 : 1));
+  }
+}
+
+// Types that occur on a level of n cells per direction.
+template <int D>
+bool type_present(int type, int n) {
+  for (int e = 0; e < D; ++e) {
+    const int code = (type >> (2 * e)) & 3;
+    if (n < 2) return false;
+    if (n == 2 && code != 3) return false;
+    if (n == 3 && code != 0 && code != 2) return false;
+    if (n >= 4 && code == 3) return false;
+  }
+  return true;
+}
+
+// Assigns the rows of one patch type to lane pieces.  Rows are taken longest
+// first; each is split into the fewest parts (1 .. MAXP) that fit free pieces,
+// each part into the smallest piece shape that holds it.  Writes the plain and
+// mass slots of the type and its row map; false if a row does not fit.
+template <int D, int K, typename T, typename TS>
+bool plan_type(const std::vector<PlanRow<T>>& rows, unsigned char* plain, unsigned char* mass, uint32_t* rowp,
+               std::string& why) {
+  using P = PassShape<D, K, T, TS, 1>;
+  using PL = typename P::PL;
+  using PSum = typename P::PSum;
+  constexpr int LW = P::LW, NP = PL::NP;
+  std::vector<int> used(NP * LW, 0);
+  std::vector<int> order(P::NV);
+  for (int l = 0; l < P::NV; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (rows[a].pl.size() != rows[b].pl.size()) return rows[a].pl.size() > rows[b].pl.size();
+    return rows[a].ms.size() > rows[b].ms.size();
+  });
+  std::vector<int> ptypes(NP);
+  for (int p = 0; p < NP; ++p) ptypes[p] = p;
+  std::stable_sort(ptypes.begin(), ptypes.end(),
+                   [](int a, int b) { return PL::z(a) + PL::zm(a) < PL::z(b) + PL::zm(b); });
+  for (int l : order) {
+    const int a = (int)rows[l].pl.size(), bm = (int)rows[l].ms.size();
+    bool placed = false;
+    for (int m = 1; m <= PL::MAXP && !placed; ++m) {
+      std::vector<int> bins;
+      std::vector<int> tmp = used;
+      bool ok = true;
+      for (int i = 0; i < m && ok; ++i) {
+        const int ai = a / m + (i < a % m ? 1 : 0), bi = bm / m + (bm % m > i ? 1 : 0);
+        int found = -1;
+        for (int pp = 0; pp < NP && found < 0; ++pp) {
+          const int p = ptypes[pp];
+          if (PL::z(p) < ai || PL::zm(p) < bi) continue;
+          for (int lam = 0; lam < LW; ++lam)
+            if (!tmp[p * LW + lam]) {
+              found = p * LW + lam;
+              break;
+            }
+        }
+        if (found < 0) ok = false;
+        else {
+          tmp[found] = 1;
+          bins.push_back(found);
+        }
+      }
+      if (!ok) continue;
+      used = tmp;
+      placed = true;
+      uint32_t rp = 0;
+      for (int k = 0; k < PL::MAXP; ++k) rp |= (uint32_t)P::ZSLOT << (8 * k);
+      int pa = 0, pb = 0;
+      for (int i = 0; i < m; ++i) {
+        const int ai = a / m + (i < a % m ? 1 : 0), bi = bm / m + (bm % m > i ? 1 : 0);
+        const int bin = bins[i], p = bin / LW, lam = bin % LW;
+        rp = (rp & ~(0xffu << (8 * i))) | ((uint32_t)bin << (8 * i));
+        for (int s = 0; s < ai; ++s, ++pa) {
+          unsigned char* e = plain + ((size_t)(PSum::zoff(p) + s) * LW + lam) * plain_bytes<T>();
+          const T c = rows[l].pl[pa].second;
+          std::memcpy(e, &c, sizeof(T));
+          if (sizeof(T) == 4) {
+            const int32_t w = rows[l].pl[pa].first;
+            std::memcpy(e + 4, &w, 4);
+          } else {
+            const int64_t w = rows[l].pl[pa].first;
+            std::memcpy(e + 8, &w, 8);
+          }
+        }
+        for (int s = 0; s < bi; ++s, ++pb) {
+          unsigned char* e = mass + ((size_t)(PSum::zmoff(p) + s) * LW + lam) * MASS_BYTES;
+          const T c = rows[l].ms[pb].second;
+          const int32_t w = rows[l].ms[pb].first.first, cell = rows[l].ms[pb].first.second;
+          std::memcpy(e, &c, sizeof(T));
+          std::memcpy(e + sizeof(T), &w, 4);
+          std::memcpy(e + sizeof(T) + 4, &cell, 4);
+        }
+      }
+      rowp[l] = rp;
+    }
+    if (!placed) {
+      why = "patch row " + std::to_string(l) + " (" + std::to_string(a) + " + " + std::to_string(bm) +
+            " entries) does not fit the lane plan";
+      return false;
+    }
+  }
+  return true;
+}
+
+// Segment descriptors (SEG_INTS ints each):
+//  [0] kind (0 window of x, 1 patch rows of b, 2 cells)  [1] length  [2] first
+//  entry in its block (window column, patch row or cell bit)  [3] array index at
+//  v = 0  [4..6] index step per unit of v_e  [7] index multiplier m (node index
+//  along x_e is m v_e + a_e)  [8..10] a_e  [11..13] largest valid index along x_e
+//  [14] window column of the first entry (patch rows)  [15] patch-row segment number
+template <int D, int K, typename T, typename TS>
+void make_segments(const Lvl<D, K, T>& L, int* out) {
+  using P = PassShape<D, K, T, TS, 1>;
+  using PS = PatchShape<D, K>;
+  constexpr int K1 = K + 1;
+  const int N = L.N, n = L.n;
+  auto stride = [&](int c, int e) {
+    int64_t s = 1;
+    for (int f = 0; f < e; ++f) s *= (c < D && f == c) ? (N + 1) : N;
+    return s;
+  };
+  int ns = 0, nb = 0;
+  auto emit = [&](int kind, int len, int dst, int64_t base, const int64_t* cv, int m, const int* a, const int* hi,
+                  int wst, int bseg) {
+    int* d = out + (size_t)ns * SEG_INTS;
+    for (int q = 0; q < SEG_INTS; ++q) d[q] = 0;
+    d[0] = kind;
+    d[1] = len;
+    d[2] = dst;
+    d[3] = (int)base;
+    for (int e = 0; e < D; ++e) {
+      d[4 + e] = (int)cv[e];
+      d[8 + e] = a[e];
+      d[11 + e] = hi[e];
+    }
+    d[7] = m;
+    d[14] = wst;
+    d[15] = bseg;
+    ++ns;
+  };
+  // window of x
+  for (int c = 0; c <= D; ++c) {
+    int ext[D], a0[D], hi[D];
+    int64_t cv[D];
+    for (int e = 0; e < D; ++e) {
+      ext[e] = win_extent<D, K>(c, e);
+      a0[e] = (c < D && e != c) ? -2 * K1 : -K1;
+      hi[e] = (c < D && e == c) ? N : N - 1;
+      cv[e] = (int64_t)K1 * stride(c, e);
+    }
+    const int rowsn = (D == 2) ? ext[1] : ext[1] * ext[2];
+    for (int r = 0; r < rowsn; ++r) {
+      int le[D] = {};
+      int rr = r;
+      for (int e = 1; e < D; ++e) {
+        le[e] = rr % ext[e];
+        rr /= ext[e];
+      }
+      int a[D];
+      int64_t base = L.off[c];
+      int dst = 0, sw = 1;
+      for (int e = 0; e < D; ++e) {
+        a[e] = a0[e] + le[e];
+        base += (int64_t)a[e] * stride(c, e);
+        dst += le[e] * sw;
+        sw *= ext[e];
+      }
+      emit(0, ext[0], c * P::WU + dst, base, cv, K1, a, hi, 0, -1);
+    }
+  }
+  // patch rows of b
+  for (int c = 0; c <= D; ++c) {
+    int ext[D], a0[D], hi[D];
+    int64_t cv[D];
+    for (int e = 0; e < D; ++e) {
+      const bool own = c < D && e == c;
+      ext[e] = (c == D) ? PS::UB : (own ? PS::UA : PS::UB);
+      a0[e] = -K1 + (own ? 1 : 0);
+      hi[e] = 1 << 29;
+      cv[e] = (int64_t)K1 * stride(c, e);
+    }
+    const int rowsn = (D == 2) ? ext[1] : ext[1] * ext[2];
+    for (int r = 0; r < rowsn; ++r) {
+      int le[D] = {};
+      int rr = r;
+      for (int e = 1; e < D; ++e) {
+        le[e] = rr % ext[e];
+        rr /= ext[e];
+      }
+      int a[D];
+      int64_t base = L.off[c];
+      int dst = 0, sw = 1, wst = 0, sww = 1;
+      for (int e = 0; e < D; ++e) {
+        a[e] = a0[e] + le[e];
+        base += (int64_t)a[e] * stride(c, e);
+        dst += le[e] * sw;
+        sw *= ext[e];
+        const int wa = (c < D && e != c) ? -2 * K1 : -K1;   // window origin offset
+        wst += (a[e] - wa) * sww;
+        sww *= win_extent<D, K>(c, e);
+      }
+      emit(1, ext[0], (c < D ? c * PS::NU1 : D * PS::NU1) + dst, base, cv, K1, a, hi, c * P::WU + wst, nb++);
+    }
+  }
+  // cells, in pairs along x_0
+  {
+    int64_t cv[D];
+    int hi[D];
+    int64_t cs = 1;
+    for (int e = 0; e < D; ++e) {
+      cv[e] = cs;
+      cs *= n;
+      hi[e] = n - 1;
+    }
+    for (int r = 0; r < P::NSEGC; ++r) {
+      int le[D] = {};
+      for (int e = 1; e < D; ++e) le[e] = (r >> (e - 1)) & 1;
+      int a[D];
+      int64_t base = 0;
+      int dst = 0;
+      for (int e = 0; e < D; ++e) {
+        a[e] = -1 + le[e];
+        base += (int64_t)a[e] * cv[e];
+        dst |= le[e] << e;
+      }
+      emit(2, 2, dst, base, cv, 1, a, hi, 0, -1);
+    }
+  }
+}
+
+// Builds the colour-pass tables of one level into blob (P::TAB_BYTES bytes).
+template <int D, int K, typename T, typename TS>
+bool build_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<unsigned char>& blob,
+                       std::string& why) {
+  using P = PassShape<D, K, T, TS, 1>;
+  using PSum = typename P::PSum;
+  blob.assign(P::TAB_BYTES, 0);
+  make_segments<D, K, T, TS>(L, reinterpret_cast<int*>(blob.data() + P::TB_SEG));
+  uint32_t* rowp = reinterpret_cast<uint32_t*>(blob.data() + P::TB_ROWP);
+  for (int t = 0; t < P::NTYPE; ++t) {
+    if (!type_present<D>(t, L.n)) continue;
+    int v[D];
+    type_vertex<D>(t, L.n, v);
+    std::vector<PlanRow<T>> rows;
+    plan_rows(L, tb, v, rows);
+    unsigned char* pl = blob.data() + P::TB_PLAIN + (size_t)t * PSum::ZP * P::LW * plain_bytes<T>();
+    unsigned char* ms = blob.data() + P::TB_MASS + (size_t)t * PSum::ZM * P::LW * MASS_BYTES;
+    if (!plan_type<D, K, T, TS>(rows, pl, ms, rowp + (size_t)t * P::NV, why)) {
+      why = "patch type " + std::to_string(t) + ": " + why;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Host check of the tables of one level (no GPU): (1) every row of every type
+// is reproduced exactly by its pieces; (2) the plan evaluated on a random
+// window matches the row visitor; (3) every segment entry addresses the
+// window column, patch row or cell it is meant to, zero outside the domain.
+// Returns 0, or 1 with a message in why.
+template <int D, int K, typename T, typename TS>
+int check_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& why) {
+  using P = PassShape<D, K, T, TS, 1>;
+  using PL = typename P::PL;
+  using PSum = typename P::PSum;
+  using PS = PatchShape<D, K>;
+  constexpr int LW = P::LW;
+  std::vector<unsigned char> blob;
+  if (!build_pass_tables<D, K, T, TS>(L, tb, blob, why)) return 1;
+  const uint32_t* rowp = reinterpret_cast<const uint32_t*>(blob.data() + P::TB_ROWP);
+  uint64_t rng = 0x9E3779B97F4A7C15ull;
+  auto urand = [&]() {
+    rng ^= rng << 13;
+    rng ^= rng >> 7;
+    rng ^= rng << 17;
+    return (double)(rng >> 11) * (1.0 / 9007199254740992.0);
+  };
+  // Lvl and tables in double for the reference evaluation
+  Lvl<D, K, double> Ld;
+  Ld.n = L.n;
+  Ld.N = L.N;
+  for (int e = 0; e <= D; ++e) Ld.off[e] = L.off[e];
+  Ld.ndof = L.ndof;
+  Ld.s_mu = (double)L.s_mu;
+  Ld.s_c = (double)L.s_c;
+  Ld.s_b = (double)L.s_b;
+  Ld.c = nullptr;
+  Tab<K, double> tbd;
+  {
+    const T* src = reinterpret_cast<const T*>(&tb);
+    double* dst = reinterpret_cast<double*>(&tbd);
+    for (size_t q = 0; q < sizeof(tb) / sizeof(T); ++q) dst[q] = (double)src[q];
+  }
+  for (int t = 0; t < P::NTYPE; ++t) {
+    if (!type_present<D>(t, L.n)) continue;
+    int v[D];
+    type_vertex<D>(t, L.n, v);
+    std::vector<PlanRow<T>> rows;
+    plan_rows(L, tb, v, rows);
+    const unsigned char* pl = blob.data() + P::TB_PLAIN + (size_t)t * PSum::ZP * LW * plain_bytes<T>();
+    const unsigned char* ms = blob.data() + P::TB_MASS + (size_t)t * PSum::ZM * LW * MASS_BYTES;
+    std::vector<double> win(P::WIN), cw(P::NC);
+    for (auto& w : win) w = 2.0 * urand() - 1.0;
+    for (auto& c : cw) c = std::exp(6.0 * urand() - 3.0);
+    // partial sums of every piece
+    std::vector<double> part(P::PARTS, 0.0);
+    std::vector<std::vector<std::pair<int, double>>> got_pl(P::PARTS);
+    std::vector<std::vector<std::pair<std::pair<int, int>, double>>> got_ms(P::PARTS);
+    for (int p = 0; p < PL::NP; ++p)
+      for (int lam = 0; lam < LW; ++lam) {
+        double acc = 0;
+        for (int s = 0; s < PL::z(p); ++s) {
+          const unsigned char* e = pl + ((size_t)(PSum::zoff(p) + s) * LW + lam) * plain_bytes<T>();
+          T c;
+          std::memcpy(&c, e, sizeof(T));
+          int64_t w = 0;
+          if (sizeof(T) == 4) {
+            int32_t w32;
+            std::memcpy(&w32, e + 4, 4);
+            w = w32;
+          } else {
+            std::memcpy(&w, e + 8, 8);
+          }
+          if (w < 0 || w >= P::WIN) { why = "plain column out of the window"; return 1; }
+          acc += (double)c * win[w];
+          if (c != T(0)) got_pl[p * LW + lam].push_back({(int)w, (double)c});
+        }
+        for (int s = 0; s < PL::zm(p); ++s) {
+          const unsigned char* e = ms + ((size_t)(PSum::zmoff(p) + s) * LW + lam) * MASS_BYTES;
+          T c;
+          int32_t w, cell;
+          std::memcpy(&c, e, sizeof(T));
+          std::memcpy(&w, e + sizeof(T), 4);
+          std::memcpy(&cell, e + sizeof(T) + 4, 4);
+          if (w < 0 || w >= P::WIN || cell < 0 || cell >= P::NC) { why = "mass entry out of range"; return 1; }
+          acc += (double)c * cw[cell] * win[w];
+          if (c != T(0)) got_ms[p * LW + lam].push_back({{w, cell}, (double)c});
+        }
+        part[p * LW + lam] = acc;
+      }
+    for (int l = 0; l < P::NV; ++l) {
+      std::vector<std::pair<int, double>> gp;
+      std::vector<std::pair<std::pair<int, int>, double>> gm;
+      double r = 0;
+      for (int k = 0; k < PL::MAXP; ++k) {
+        const int q = (rowp[(size_t)t * P::NV + l] >> (8 * k)) & 0xff;
+        if (q == P::ZSLOT) continue;
+        if (q >= PL::NP * LW) { why = "row map index out of range"; return 1; }
+        r += part[q];
+        gp.insert(gp.end(), got_pl[q].begin(), got_pl[q].end());
+        gm.insert(gm.end(), got_ms[q].begin(), got_ms[q].end());
+      }
+      std::vector<std::pair<int, double>> ep;
+      for (auto& e : rows[l].pl) ep.push_back({e.first, (double)e.second});
+      std::vector<std::pair<std::pair<int, int>, double>> em;
+      for (auto& e : rows[l].ms) em.push_back({e.first, (double)e.second});
+      std::sort(gp.begin(), gp.end());
+      std::sort(ep.begin(), ep.end());
+      std::sort(gm.begin(), gm.end());
+      std::sort(em.begin(), em.end());
+      if (gp != ep || gm != em) {
+        why = "type " + std::to_string(t) + " row " + std::to_string(l) + ": plan does not reproduce the row";
+        return 1;
+      }
+      int idx[D];
+      const int comp = patch_local_decode<D, K>(v, l, idx);
+      HostEvalVisitor<D, K> ev(v, win.data(), cw.data());
+      visit_row(Ld, tbd, comp, idx, ev);
+      const double tol = (sizeof(T) == 4 ? 1e-5 : 1e-12) * (ev.mag + 1e-300);
+      if (std::fabs(r - ev.acc) > tol) {
+        why = "type " + std::to_string(t) + " row " + std::to_string(l) + ": plan value " + std::to_string(r) +
+              " differs from the row value " + std::to_string(ev.acc);
+        return 1;
+      }
+    }
+  }
+  // segments: emulate the gather for one vertex of each type on x[g] = g + 1
+  const int* seg = reinterpret_cast<const int*>(blob.data() + P::TB_SEG);
+  for (int t = 0; t < P::NTYPE; ++t) {
+    if (!type_present<D>(t, L.n)) continue;
+    int v[D];
+    type_vertex<D>(t, L.n, v);
+    std::vector<double> win(P::WIN, -1.0), brow(P::NV, -1.0), cells(P::NC, -1.0);
+    std::vector<int> seen_b(P::NV, 0);
+    for (int s = 0; s < P::NSEG; ++s) {
+      const int* d = seg + (size_t)s * SEG_INTS;
+      int64_t src = d[3];
+      bool okr = true;
+      for (int e = 0; e < D; ++e) src += (int64_t)v[e] * d[4 + e];
+      for (int e = 1; e < D; ++e) {
+        const int ix = d[7] * v[e] + d[8 + e];
+        okr = okr && ix >= 0 && ix <= d[11 + e];
+      }
+      const int i0 = d[7] * v[0] + d[8];
+      for (int i = 0; i < d[1]; ++i) {
+        const bool ok = okr && i0 + i >= 0 && i0 + i <= d[11];
+        const double val = ok ? (double)(src + i + 1) : 0.0;
+        if (d[0] == 0) {
+          if (d[2] + i >= P::WIN) { why = "window segment past the window"; return 1; }
+          win[d[2] + i] = val;
+        } else if (d[0] == 1) {
+          if (d[2] + i >= P::NV) { why = "row segment past the patch"; return 1; }
+          brow[d[2] + i] = val;
+          ++seen_b[d[2] + i];
+        } else {
+          cells[d[2] + i] = (double)(src + i);
+        }
+      }
+    }
+    // window: every column of every component, in or out of the domain
+    for (int c = 0; c <= D; ++c) {
+      int ext[D];
+      int tot = 1;
+      for (int e = 0; e < D; ++e) {
+        ext[e] = win_extent<D, K>(c, e);
+        tot *= ext[e];
+      }
+      for (int q = 0; q < tot; ++q) {
+        int idx[D], rr = q;
+        bool in = true;
+        for (int e = 0; e < D; ++e) {
+          idx[e] = win_origin<D, K>(v, c, e) + rr % ext[e];
+          rr /= ext[e];
+          const int hi = (c < D && e == c) ? L.N : L.N - 1;
+          in = in && idx[e] >= 0 && idx[e] <= hi;
+        }
+        const double expect = in ? (double)(flat_index(L, c, idx) + 1) : 0.0;
+        if (win[win_index<D, K>(v, c, idx)] != expect) {
+          why = "type " + std::to_string(t) + ": window column " + std::to_string(win_index<D, K>(v, c, idx)) +
+                " gathers the wrong entry";
+          return 1;
+        }
+      }
+    }
+    for (int l = 0; l < P::NV; ++l) {
+      int idx[D];
+      const int comp = patch_local_decode<D, K>(v, l, idx);
+      if (seen_b[l] != 1 || brow[l] != (double)(flat_index(L, comp, idx) + 1)) {
+        why = "type " + std::to_string(t) + ": patch row " + std::to_string(l) + " gathers the wrong entry";
+        return 1;
+      }
+    }
+    for (int cb = 0; cb < P::NC; ++cb) {
+      int cell[D];
+      for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cb >> e) & 1);
+      if (cells[cb] != (double)cell_linear(L, cell)) { why = "cell gather wrong"; return 1; }
+    }
+    // patch-row segments: window column of each row (used to update x)
+    for (int s = P::NSEGX; s < P::NSEGX + P::NSEGB; ++s) {
+      const int* d = seg + (size_t)s * SEG_INTS;
+      for (int i = 0; i < d[1]; ++i) {
+        int idx[D];
+        const int comp = patch_local_decode<D, K>(v, d[2] + i, idx);
+        if (d[14] + i != win_index<D, K>(v, comp, idx)) { why = "row segment window column wrong"; return 1; }
+      }
+      if (d[15] != s - P::NSEGX) { why = "row segment numbering wrong"; return 1; }
+    }
+  }
+  (void)sizeof(PS);
+  return 0;
+}
+
+}  // namespace mgd

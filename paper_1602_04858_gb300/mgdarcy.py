@@ -28,7 +28,7 @@ API = [
     "mg_batch_kernel_launches", "mg_load_vector",
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
-    "mg_cnn_train_step", "mg_cnn_guess",
+    "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
 ]
 
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_cnn_gradients.argtypes = [vp, vp, vp, i, ctypes.POINTER(f), vp]
     lib.mg_cnn_train_step.argtypes = [vp, vp, vp, i, f, ctypes.POINTER(f)]
     lib.mg_cnn_guess.argtypes = [vp, vp, vp, vp]
+    lib.mg_pass_tables_check.argtypes = [i, i, i, i, d, ctypes.c_char_p, i]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -117,6 +118,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             getattr(lib, name).restype = i
     _lib = lib
     return lib
+
+
+def pass_tables_check(dim, degree, precision, n, mu):
+    """mg_pass_tables_check: host check of the colour-pass tables of an n^dim
+    level (no GPU).  Returns (code, message); code 0 means every check held."""
+    prec = PREC[precision] if isinstance(precision, str) else int(precision)
+    buf = ctypes.create_string_buffer(512)
+    r = load().mg_pass_tables_check(int(dim), int(degree), prec, int(n), float(mu), buf, len(buf))
+    return r, buf.value.decode()
 
 
 def _ptr(a, dtype="float64"):
