@@ -533,8 +533,50 @@ __device__ __forceinline__ void cp_async_t(T* dst, const T* src, bool ok) {
   else cp_async4(dst, src, ok ? 4u : 0u);
 }
 
+// Plan entries of one lane for one patch type, held in registers.
+template <class P, typename T>
+struct PlanRegs {
+  static constexpr int ZP = P::PSum::ZP, ZM = P::PSum::ZM;
+  T pc[ZP > 0 ? ZP : 1];
+  int pw[ZP > 0 ? ZP : 1];
+  T mc[ZM > 0 ? ZM : 1];
+  int mw[ZM > 0 ? ZM : 1], mcell[ZM > 0 ? ZM : 1];
+  __device__ __forceinline__ void load(const unsigned char* pp, const unsigned char* pm) {
+    constexpr int LW = P::LW, PB = plain_bytes<T>();
+#pragma unroll
+    for (int s = 0; s < ZP; ++s) PlainLd<T>::get(pp + (size_t)s * LW * PB, pc[s], pw[s]);
+#pragma unroll
+    for (int s = 0; s < ZM; ++s) MassLd<T>::get(pm + (size_t)s * LW * MASS_BYTES, mc[s], mw[s], mcell[s]);
+  }
+};
+
+// Lane pieces of the local residual: piece PI accumulates its plain slots
+// (coefficient x window column) and mass slots (coefficient x cell
+// coefficient x window column) into one partial sum.
+template <int PI, class P, typename T, int NR>
+__device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* win, const T* cw, T* part, int lp) {
+  using PL = typename P::PL;
+  using PSum = typename P::PSum;
+  T acc[NR];
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
+#pragma unroll
+  for (int s = PSum::zoff(PI); s < PSum::zoff(PI) + PL::z(PI); ++s)
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc[rr] += R.pc[s] * win[rr * P::WIN + R.pw[s]];
+#pragma unroll
+  for (int s = PSum::zmoff(PI); s < PSum::zmoff(PI) + PL::zm(PI); ++s) {
+    const T cc = R.mc[s] * cw[R.mcell[s]];
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * win[rr * P::WIN + R.mw[s]];
+  }
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) part[rr * P::PARTS + PI * P::LW + lp] = acc[rr];
+  if constexpr (PI + 1 < PL::NP) plan_pieces<PI + 1, P, T, NR>(R, win, cw, part, lp);
+}
+
 template <int D, int K, typename T, typename TS, int NR>
-__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int colour, int64_t count,
+__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const ColourGeom cg, int64_t count,
                                                      const TS* __restrict__ S, const unsigned char* __restrict__ tabs,
                                                      T* x, const T* __restrict__ b, int evict_first,
                                                      int* __restrict__ err, int64_t vs) {
@@ -542,60 +584,85 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
   using PL = typename P::PL;
   using PSum = typename P::PSum;
   constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, LW = P::LW;
-  constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>();
+  constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>(), NSI = P::NSI;
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / LW, lp = lane - g * LW;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * 2 * P::STAGE) + warp * 2;
+  unsigned char* wbase = smem + (size_t)warp * P::WARP_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * P::WARP_BYTES) + warp;
   const int4* segs = reinterpret_cast<const int4*>(tabs + P::TB_SEG);
-  const unsigned char* plan_p = tabs + P::TB_PLAIN;
-  const unsigned char* plan_m = tabs + P::TB_MASS;
+  const unsigned char* plan_p = tabs + P::TB_PLAIN + (size_t)lp * PB;
+  const unsigned char* plan_m = tabs + P::TB_MASS + (size_t)lp * MASS_BYTES;
   const uint32_t* rowp = reinterpret_cast<const uint32_t*>(tabs + P::TB_ROWP);
   const int64_t ngroups = (count + GPW - 1) / GPW;
   const int64_t W = (int64_t)gridDim.x * P::WARPS;
   const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
 
-  auto st_S = [&](int bi) { return smem + ((size_t)warp * 2 + bi) * P::STAGE; };
-  auto st_T = [&](int bi) { return reinterpret_cast<T*>(st_S(bi) + P::STAGE_S) + g * P::T_PER_PATCH; };
-  auto st_B = [&](int bi) {
-    return reinterpret_cast<int64_t*>(st_S(bi) + P::STAGE_S + P::STAGE_T) + g * P::NSEGB;
+  auto st_T = [&](int bi) {
+    return reinterpret_cast<T*>(wbase + P::STAGE_S + (size_t)bi * P::STAGE_T) + g * P::T_PER_PATCH;
+  };
+  auto st_Bb = [&](int bi) {   // patch-row segment bases
+    return reinterpret_cast<int64_t*>(wbase + P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B) + g * P::NSEGB;
+  };
+  auto st_Bi = [&](int bi) {   // patch-row segment (length, first row, window column)
+    return reinterpret_cast<int4*>(wbase + P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B + P::STAGE_BI) +
+           g * P::NSEGB;
   };
   auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
 
-  // (1) bulk copies of the inverses of patch group pg into stage bi (lane 0)
-  auto issue_S = [&](int bi, int64_t pg) {
+  // (1) bulk copies of the inverses of patch group pg (lane 0)
+  auto issue_S = [&](int64_t pg) {
     const int np = npat(pg);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(bars + bi, (uint32_t)(np * (P::S_BYTES + P::SC_BYTES)));
+    mbar_arrive_expect_tx(bar, (uint32_t)(np * (P::S_BYTES + P::SC_BYTES)));
     for (int q = 0; q < np; ++q) {
       const int64_t p = pg * GPW + q;
-      bulk_load(st_S(bi) + (size_t)q * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bars + bi, pol);
+      bulk_load(wbase + (size_t)q * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bar, pol);
       if constexpr (P::BF)
-        bulk_load(st_S(bi) + (size_t)GPW * P::S_BYTES + (size_t)q * P::SC_BYTES,
-                  reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + p * NVP, P::SC_BYTES, bars + bi, pol);
+        bulk_load(wbase + (size_t)GPW * P::S_BYTES + (size_t)q * P::SC_BYTES,
+                  reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + p * NVP, P::SC_BYTES, bar, pol);
     }
   };
   // vertex of this lane's patch in group pg; false past the last patch
   auto vertex = [&](int64_t pg, int (&v)[D]) {
     const int64_t p = pg * GPW + g;
     if (p < count) {
-      patch_vertex<D>(L.n, colour, p, v);
+      geom_vertex<D>(cg, (uint32_t)p, v);
       return true;
     }
 #pragma unroll
     for (int e = 0; e < D; ++e) v[e] = 2;
     return false;
   };
-  // (2) asynchronous gather of the window, the patch rows of b and the cells
+  // this lane's gather segments (the same for every patch), kept in registers
+  int4 sd0[NSI], sd1[NSI], sd2[NSI], sd3[NSI];
+#pragma unroll
+  for (int i = 0; i < NSI; ++i) {
+    const int s = lp + i * LW;
+    if (s < P::NSEG) {
+      sd0[i] = __ldg(segs + 4 * s);
+      sd1[i] = __ldg(segs + 4 * s + 1);
+      sd2[i] = __ldg(segs + 4 * s + 2);
+      sd3[i] = __ldg(segs + 4 * s + 3);
+    } else {
+      sd0[i] = make_int4(-1, 0, 0, 0);
+      sd1[i] = sd2[i] = sd3[i] = make_int4(0, 0, 0, 0);
+    }
+  }
+  // (2) asynchronous gather of the window, the patch rows of b and the cells;
+  //     window entries outside the domain are zero
   auto issue_gather = [&](int bi, const int (&v)[D], bool act) {
     T* tw = st_T(bi);
-    int64_t* bb = st_B(bi);
+    int64_t* bb = st_Bb(bi);
+    int4* binf = st_Bi(bi);
     if (act) {
-      for (int s = lp; s < P::NSEG; s += LW) {
-        const int4 d0 = __ldg(segs + 4 * s), d1 = __ldg(segs + 4 * s + 1);
-        const int4 d2 = __ldg(segs + 4 * s + 2), d3 = __ldg(segs + 4 * s + 3);
+#pragma unroll
+      for (int si = 0; si < NSI; ++si) {
+        const int4 d0 = sd0[si], d1 = sd1[si], d2 = sd2[si], d3 = sd3[si];
+        const int kind = d0.x, len = d0.y, dst = d0.z;
+        if (kind < 0) continue;
         int64_t src = (int64_t)d0.w + (int64_t)v[0] * d1.x + (int64_t)v[1] * d1.y;
         if constexpr (D == 3) src += (int64_t)v[2] * d1.z;
         const int m = d1.w;
@@ -609,22 +676,27 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
           okr = okr && ix >= 0 && ix <= d3.y;
         }
         const int i0 = m * v[0] + d2.x, hi0 = d2.w;
-        const int kind = d0.x, len = d0.y, dst = d0.z;
+        // entries [ilo, ihi) of the segment lie in the domain
+        const int ilo = okr ? (i0 < 0 ? -i0 : 0) : len;
+        const int ihi = (hi0 - i0 + 1 < len) ? hi0 - i0 + 1 : len;
         if (kind == 2) {
 #pragma unroll
-          for (int i = 0; i < 2; ++i) cp_async_t(tw + P::OFF_C + dst + i, L.c + src + i, true);
+          for (int i = 0; i < 2; ++i) cp_async_t(tw + P::OFF_C + dst + i, L.c + (src + i), true);
         } else {
           const T* base = (kind == 0) ? x : b;
           T* dd = tw + ((kind == 0) ? P::OFF_W : P::OFF_B) + dst;
           const int rs = (kind == 0) ? WIN : NV;
-          if (kind == 1) bb[d3.w] = src;
+          if (kind == 1) {
+            bb[d3.w] = src;
+            binf[d3.w] = make_int4(len, dst, d3.z, 0);
+          }
 #pragma unroll
           for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
             for (int i = 0; i < P::LMAX; ++i)
               if (i < len) {
-                const bool ok = okr && (unsigned)(i0 + i) <= (unsigned)hi0;
-                cp_async_t(dd + rr * rs + i, ok ? base + (src + rr * vs + i) : base, ok);
+                if (i >= ilo && i < ihi) cp_async_t(dd + rr * rs + i, base + (src + rr * vs + i), true);
+                else dd[rr * rs + i] = T(0);
               }
         }
       }
@@ -635,12 +707,14 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
   int64_t pg = (int64_t)blockIdx.x * P::WARPS + warp;
   int vc[D];
   bool actc = vertex(pg, vc);
-  if (lane == 0) {
-    mbar_init(bars + 0, 1);
-    mbar_init(bars + 1, 1);
-  }
+  // plan of the first group's patch type, loaded before the wait for the
+  // preceding kernel (the tables do not depend on it)
+  PlanRegs<P, T> R;
+  int rtype = patch_type<D>(vc, L.n);
+  R.load(plan_p + (size_t)rtype * PSum::ZP * LW * PB, plan_m + (size_t)rtype * PSum::ZM * LW * MASS_BYTES);
+  if (lane == 0) mbar_init(bar, 1);
   __syncwarp();
-  if (pg < ngroups && lane == 0) issue_S(0, pg);   // the inverses do not depend on earlier passes
+  if (pg < ngroups && lane == 0) issue_S(pg);   // the inverses do not depend on earlier passes
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncwarp();
@@ -650,48 +724,30 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
     const int64_t pn = pg + W;
     int vn[D];
     const bool actn = vertex(pn, vn);
-    if (pn < ngroups) {   // stage the next group while this one is computed
-      if (lane == 0) issue_S(bi ^ 1, pn);
+    if (pn < ngroups) {   // gather the next group while this one is computed
       issue_gather(bi ^ 1, vn, actn);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
+    const int type = patch_type<D>(vc, L.n);
+    if (type != rtype) {
+      R.load(plan_p + (size_t)type * PSum::ZP * LW * PB, plan_m + (size_t)type * PSum::ZM * LW * MASS_BYTES);
+      rtype = type;
+    }
+    uint32_t rps[P::NROWIT];
+#pragma unroll
+    for (int it = 0; it < P::NROWIT; ++it) {
+      const int l = lp + it * LW;
+      rps[it] = (l < NV) ? __ldg(rowp + (size_t)type * NV + l) : 0u;
+    }
     __syncwarp();
     T* pb = st_T(bi);
     const T* win = pb + P::OFF_W;
-    const T* cw = pb + P::OFF_C;
     T* part = pb + P::OFF_P;
-    const int type = patch_type<D>(vc, L.n);
     // (3a) lane pieces of the local residual
     if (actc) {
-      const unsigned char* pp = plan_p + ((size_t)type * PSum::ZP * LW + lp) * PB;
-      const unsigned char* pm = plan_m + ((size_t)type * PSum::ZM * LW + lp) * MASS_BYTES;
-#pragma unroll
-      for (int p = 0; p < PL::NP; ++p) {
-        T acc[NR];
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
-#pragma unroll
-        for (int s = 0; s < PL::z(p); ++s) {
-          T c;
-          int w;
-          PlainLd<T>::get(pp + (size_t)(PSum::zoff(p) + s) * LW * PB, c, w);
-#pragma unroll
-          for (int rr = 0; rr < NR; ++rr) acc[rr] += c * win[rr * WIN + w];
-        }
-#pragma unroll
-        for (int s = 0; s < PL::zm(p); ++s) {
-          T c;
-          int w, cell;
-          MassLd<T>::get(pm + (size_t)(PSum::zmoff(p) + s) * LW * MASS_BYTES, c, w, cell);
-          const T cc = c * cw[cell];
-#pragma unroll
-          for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * win[rr * WIN + w];
-        }
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr) part[rr * PARTS + p * LW + lp] = acc[rr];
-      }
+      plan_pieces<0, P, T, NR>(R, win, pb + P::OFF_C, part, lp);
       if (lp == 0) {
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) part[rr * PARTS + P::ZSLOT] = T(0);
@@ -699,21 +755,33 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
     }
     __syncwarp();
     // (3b) wait for the inverses of this group (bounded); rows of the residual
-    const bool have_S = mbar_wait_bounded(bars + bi, (uint32_t)((k >> 1) & 1), 2000000000ull);
-    if (!have_S && lane == 0) atomicExch(err, 2);
-    const float* sc = reinterpret_cast<const float*>(st_S(bi) + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
-    if (actc && have_S) {
-      for (int l = lp; l < NV; l += LW) {
-        const uint32_t rp = __ldg(rowp + (size_t)type * NV + l);
+    if (!mbar_wait_bounded(bar, (uint32_t)(k & 1), 2000000000ull)) {
+      if (lane == 0) atomicExch(err, 2);
+      cp_async_wait<0>();
+      break;
+    }
+    const float* sc = reinterpret_cast<const float*>(wbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
+    if (actc) {
 #pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          T sum = part[rr * PARTS + (rp & 0xffu)];
+      for (int it = 0; it < P::NROWIT; ++it) {
+        const int l = lp + it * LW;
+        if (l < NV) {
+          const uint32_t rp = rps[it];
+          T srow = T(1);
+          if constexpr (P::BF) {
+            srow = (T)sc[l];
+            pb[P::OFF_SC + l] = srow;
+          }
 #pragma unroll
-          for (int k2 = 1; k2 < PL::MAXP; ++k2) sum += part[rr * PARTS + ((rp >> (8 * k2)) & 0xffu)];
-          T r = pb[P::OFF_B + rr * NV + l] - sum;
-          if constexpr (P::BF) r *= sc[l];
-          if constexpr (P::F2) reinterpret_cast<float2*>(pb + P::OFF_R + rr * 2 * NV)[l] = make_float2(r, r);
-          else pb[P::OFF_R + rr * NV + l] = r;
+          for (int rr = 0; rr < NR; ++rr) {
+            T sum = part[rr * PARTS + (rp & 0xffu)];
+#pragma unroll
+            for (int k2 = 1; k2 < PL::MAXP; ++k2) sum += part[rr * PARTS + ((rp >> (8 * k2)) & 0xffu)];
+            T r = pb[P::OFF_B + rr * NV + l] - sum;
+            if constexpr (P::BF) r *= srow;
+            if constexpr (P::F2) reinterpret_cast<float2*>(pb + P::OFF_R + rr * 2 * NV)[l] = make_float2(r, r);
+            else pb[P::OFF_R + rr * NV + l] = r;
+          }
         }
       }
     }
@@ -721,8 +789,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
     // (4) delta = S_v r: row group q, column split sp
     {
       const int q = lp % LPP, sp = lp / LPP;
-      if (actc && have_S && sp < SSPL) {
-        const TS* Sg = reinterpret_cast<const TS*>(st_S(bi) + (size_t)g * P::S_BYTES) + q * RG;
+      if (actc && sp < SSPL) {
+        const TS* Sg = reinterpret_cast<const TS*>(wbase + (size_t)g * P::S_BYTES) + q * RG;
         if constexpr (P::F2) {
           float2 acc[RG / 2][NR];
 #pragma unroll
@@ -748,10 +816,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
 #pragma unroll
           for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-            for (int h = 0; h < RG / 2; ++h) {
-              part[rr * PARTS + sp * NVP + q * RG + 2 * h] = acc[h][rr].x;
-              part[rr * PARTS + sp * NVP + q * RG + 2 * h + 1] = acc[h][rr].y;
-            }
+            for (int h = 0; h < RG / 2; ++h)
+              *reinterpret_cast<float2*>(part + rr * PARTS + sp * NVP + q * RG + 2 * h) = acc[h][rr];
         } else {
           T acc[RG][NR];
 #pragma unroll
@@ -781,24 +847,28 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, int c
       }
     }
     __syncwarp();
+    // the inverses are consumed: copy those of the next group
+    if (pn < ngroups && lane == 0) issue_S(pn);
     // (5) x|_v = window copy of x|_v + delta, by patch-row segments
-    if (actc && have_S) {
-      const int64_t* bb = st_B(bi);
+    if (actc) {
+      const int64_t* bb = st_Bb(bi);
+      const int4* binf = st_Bi(bi);
       for (int s = lp; s < P::NSEGB; s += LW) {
-        const int4 d0 = __ldg(segs + 4 * (P::NSEGX + s)), d3 = __ldg(segs + 4 * (P::NSEGX + s) + 3);
-        const int len = d0.y, l0 = d0.z, wst = d3.z;
-        const int64_t base = bb[s];
+        const int4 inf = binf[s];
+        const int len = inf.x, l0 = inf.y, wst = inf.z;
+        T* xs = x + bb[s];
+        const T* ws = win + wst;
+        const T* ps = part + l0;
 #pragma unroll
         for (int i = 0; i < P::LMAXB; ++i)
           if (i < len) {
-            const int l = l0 + i;
 #pragma unroll
             for (int rr = 0; rr < NR; ++rr) {
-              T a = part[rr * PARTS + l];
+              T a = ps[rr * PARTS + i];
 #pragma unroll
-              for (int s2 = 1; s2 < SSPL; ++s2) a += part[rr * PARTS + s2 * NVP + l];
-              if constexpr (P::BF) a *= (T)sc[l];
-              x[base + rr * vs + i] = win[rr * WIN + wst + i] + a;
+              for (int s2 = 1; s2 < SSPL; ++s2) a += ps[rr * PARTS + s2 * NVP + i];
+              if constexpr (P::BF) a *= pb[P::OFF_SC + l0 + i];
+              xs[rr * vs + i] = ws[rr * WIN + i] + a;
             }
           }
       }

@@ -139,8 +139,8 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), colour, h.count[colour], (const TS*)S,
-                     (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+  cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour), h.count[colour],
+                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
 // Right-hand sides in groups of four share each S_v load; the rest one by one.

@@ -76,6 +76,43 @@ __host__ __device__ __forceinline__ int patch_type(const int (&v)[D], int n) {
   return t;
 }
 
+// --- patches of one colour ------------------------------------------------------
+// Patch p of a colour has vertex v_e = first_e + 3 q_e, where q_e are the digits
+// of p in the mixed radix (cnt_0, cnt_1, ...), x_0 fastest.  The kernels divide
+// by cnt_e with a multiply and shift: q = floor(p * ceil(2^40 / cnt) / 2^40),
+// exact while p * cnt < 2^40 (then the rounding-up excess of the multiplier,
+// below cnt, moves p * magic by less than 2^40 / cnt).
+struct ColourGeom {
+  int first[3];
+  int cnt[3];
+  unsigned long long magic[3];
+};
+
+inline ColourGeom colour_geom(int d, int n, int colour) {
+  ColourGeom g = {};
+  int r = colour;
+  for (int e = 0; e < 3; ++e) {
+    const int re = r % 3;
+    r /= 3;
+    g.first[e] = colour_first(re);
+    g.cnt[e] = e < d ? colour_count(n, re) : 1;
+    const unsigned long long c = g.cnt[e] > 0 ? (unsigned long long)g.cnt[e] : 1ull;
+    g.magic[e] = ((1ull << 40) + c - 1) / c;
+  }
+  return g;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ void geom_vertex(const ColourGeom& g, uint32_t p, int (&v)[D]) {
+#pragma unroll
+  for (int e = 0; e < D - 1; ++e) {
+    const uint32_t q = (uint32_t)(((unsigned long long)p * g.magic[e]) >> 40);
+    v[e] = g.first[e] + 3 * (int)(p - q * (uint32_t)g.cnt[e]);
+    p = q;
+  }
+  v[D - 1] = g.first[D - 1] + 3 * (int)p;
+}
+
 // --- lane plans ----------------------------------------------------------------
 // NP pieces per lane; piece p has z(p) plain and zm(p) mass slots and yields one
 // partial sum.  A row is the sum of at most MAXP pieces.  The shapes cover the
@@ -154,7 +191,6 @@ struct PassShape {
   static constexpr int WIN = D * WU + WPP;
   static constexpr int NC = 1 << D;
   // segments: rows of the window along x_0, rows of the patch block along x_0, cell pairs
-  static constexpr int pw(int b, int e) { return e == 0 ? 1 : b * pw(b, e - 1); }
   static constexpr int NSEGX = (D == 2) ? (WB + WA + WP) : (WB * WB + 2 * WA * WB + WP * WP);
   static constexpr int NSEGB = (D == 2) ? (PS::UB + PS::UA + PS::UB) : (PS::UB * PS::UB + 2 * PS::UA * PS::UB + PS::UB * PS::UB);
   static constexpr int NSEGC = NC / 2;
@@ -162,24 +198,33 @@ struct PassShape {
   static constexpr int LMAX = WB;                          // longest segment
   static constexpr int LMAXB = PS::UB;                     // longest patch-row segment
   // partial sums: residual pieces (NP x LW) and S_v splits (SSPL x NVP), + a zero slot
-  static constexpr int PARTS = ((SSPL * NVP > PL::NP * LW) ? SSPL * NVP : PL::NP * LW) + 1;
+  static constexpr int PARTS = (((SSPL * NVP > PL::NP * LW) ? SSPL * NVP : PL::NP * LW) + 2) / 2 * 2;   // even
   static constexpr int ZSLOT = PARTS - 1;
-  // per patch in shared memory (T): windows, b rows, residual, cell coefficients, partials
+  static constexpr int NROWIT = (NV + LW - 1) / LW;        // patch rows per lane
+  // per patch in shared memory (T): windows, b rows, residual, cell
+  // coefficients, row scales of BF16 inverses, partial sums
   static constexpr int OFF_W = 0;
   static constexpr int OFF_B = NR * WIN;
   static constexpr int OFF_R = OFF_B + NR * NV;
   static constexpr int RSZ = F2 ? 2 * NV : NV;
   static constexpr int OFF_C = OFF_R + NR * RSZ;
-  static constexpr int OFF_P = OFF_C + NC;
+  static constexpr int OFF_SC = OFF_C + NC;
+  static constexpr int OFF_P = OFF_SC + (BF ? NV : 0);
   static constexpr int T_PER_PATCH = ((OFF_P + NR * PARTS + 3) / 4) * 4;
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  // one pipeline stage of a warp: inverses, per-patch T data, patch-row bases
+  // per warp: one buffer of inverses, two stages of per-patch T data and
+  // patch-row bases (the window of the next group is gathered while the
+  // current one is computed; its inverses are copied once the current
+  // product is done)
   static constexpr size_t STAGE_S = (size_t)GPW * (S_BYTES + SC_BYTES);
   static constexpr size_t STAGE_T = (((size_t)GPW * T_PER_PATCH * sizeof(T) + 15) / 16) * 16;
-  static constexpr size_t STAGE_B = (((size_t)GPW * NSEGB * sizeof(int64_t) + 15) / 16) * 16;
-  static constexpr size_t STAGE = STAGE_S + STAGE_T + STAGE_B;
-  static constexpr size_t SMEM = (size_t)WARPS * 2 * STAGE + (size_t)WARPS * 2 * sizeof(uint64_t) + 16;
+  // patch-row segments of each patch: array bases (int64), then (length, first row, window column) as int4
+  static constexpr size_t STAGE_BI = (((size_t)GPW * NSEGB * sizeof(int64_t) + 15) / 16) * 16;
+  static constexpr size_t STAGE_B = STAGE_BI + (size_t)GPW * NSEGB * 16;
+  static constexpr int NSI = (NSEG + LW - 1) / LW;         // gather segments per lane
+  static constexpr size_t WARP_BYTES = STAGE_S + 2 * (STAGE_T + STAGE_B);
+  static constexpr size_t SMEM = (size_t)WARPS * WARP_BYTES + (size_t)WARPS * sizeof(uint64_t) + 16;
   // per-level tables
   static constexpr int NTYPE = (D == 2) ? 16 : 64;
   static constexpr size_t al16(size_t b) { return (b + 15) / 16 * 16; }
@@ -189,6 +234,11 @@ struct PassShape {
   static constexpr size_t TB_ROWP = TB_MASS + al16((size_t)NTYPE * PSum::ZM * LW * MASS_BYTES);
   static constexpr size_t TAB_BYTES = TB_ROWP + al16((size_t)NTYPE * NV * 4);
   static_assert(PL::MAXP <= 4, "row map holds four pieces");
+  static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(STAGE_S % 16 == 0 && STAGE_T % 16 == 0 && STAGE_B % 16 == 0 && WARP_BYTES % 16 == 0,
+                "shared-memory stages start on 16-byte boundaries");
+  static_assert(((size_t)T_PER_PATCH * sizeof(T)) % 16 == 0, "per-patch data starts on 16-byte boundaries");
+  static_assert((OFF_P % 2) == 0 && (PARTS % 2) == 0 && (NVP % 2) == 0, "partial-sum pairs need 8-byte alignment");
   static_assert(PARTS <= 256, "piece indices are bytes");
   static_assert((OFF_R % 2) == 0, "residual pairs need 8-byte alignment");
 };
@@ -200,9 +250,9 @@ template <int D, int K, typename T>
 struct HostRowVisitor {
   const int (&v)[D];
   T* row;
-  HostRowVisitor(const int (&vv)[D], T* r) : v(vv), row(r) {}
-  void operator()(int comp, const int (&j)[D], T coef) { row[win_index<D, K>(v, comp, j)] += coef; }
-  T cell_c(const int (&)[D]) const { return T(0); }
+  __host__ __device__ HostRowVisitor(const int (&vv)[D], T* r) : v(vv), row(r) {}
+  __host__ __device__ void operator()(int comp, const int (&j)[D], T coef) { row[win_index<D, K>(v, comp, j)] += coef; }
+  __host__ __device__ T cell_c(const int (&)[D]) const { return T(0); }
 };
 
 // Evaluates a full row on a window (cell coefficients cw by cell bit).
@@ -212,13 +262,13 @@ struct HostEvalVisitor {
   const double* win;
   const double* cw;
   double acc = 0, mag = 0;
-  HostEvalVisitor(const int (&vv)[D], const double* w, const double* c) : v(vv), win(w), cw(c) {}
-  void operator()(int comp, const int (&j)[D], double coef) {
+  __host__ __device__ HostEvalVisitor(const int (&vv)[D], const double* w, const double* c) : v(vv), win(w), cw(c) {}
+  __host__ __device__ void operator()(int comp, const int (&j)[D], double coef) {
     const double t = coef * win[win_index<D, K>(v, comp, j)];
     acc += t;
-    mag += std::fabs(t);
+    mag += fabs(t);
   }
-  double cell_c(const int (&cell)[D]) const {
+  __host__ __device__ double cell_c(const int (&cell)[D]) const {
     int l = 0;
     for (int e = 0; e < D; ++e) l |= (cell[e] - (v[e] - 1)) << e;
     return cw[l];
@@ -736,6 +786,19 @@ int check_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& w
         if (d[14] + i != win_index<D, K>(v, comp, idx)) { why = "row segment window column wrong"; return 1; }
       }
       if (d[15] != s - P::NSEGX) { why = "row segment numbering wrong"; return 1; }
+    }
+  }
+  // patch vertices by multiply-shift division agree with plain division
+  for (int col = 0; col < (D == 2 ? 9 : 27); ++col) {
+    const ColourGeom cg = colour_geom(D, L.n, col);
+    int64_t cnt = 1;
+    for (int e = 0; e < D; ++e) cnt *= cg.cnt[e];
+    for (int64_t p = 0; p < cnt; ++p) {
+      int v1[D], v2[D];
+      patch_vertex<D>(L.n, col, p, v1);
+      geom_vertex<D>(cg, (uint32_t)p, v2);
+      for (int e = 0; e < D; ++e)
+        if (v1[e] != v2[e]) { why = "colour " + std::to_string(col) + ": vertex of patch " + std::to_string(p) + " wrong"; return 1; }
     }
   }
   (void)sizeof(PS);
