@@ -591,7 +591,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / LW, lp = lane - g * LW;
   unsigned char* wbase = smem + (size_t)warp * P::WARP_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * P::WARP_BYTES) + warp;
+  constexpr int NSB = P::NSB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * P::WARP_BYTES) + warp * NSB;
   const int4* segs = reinterpret_cast<const int4*>(tabs + P::TB_SEG);
   const unsigned char* plan_p = tabs + P::TB_PLAIN + (size_t)lp * PB;
   const unsigned char* plan_m = tabs + P::TB_MASS + (size_t)lp * MASS_BYTES;
@@ -601,27 +602,31 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
 
   auto st_T = [&](int bi) {
-    return reinterpret_cast<T*>(wbase + P::STAGE_S + (size_t)bi * P::STAGE_T) + g * P::T_PER_PATCH;
+    return reinterpret_cast<T*>(wbase + NSB * P::STAGE_S + (size_t)bi * P::STAGE_T) + g * P::T_PER_PATCH;
   };
   auto st_Bb = [&](int bi) {   // patch-row segment bases
-    return reinterpret_cast<int64_t*>(wbase + P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B) + g * P::NSEGB;
+    return reinterpret_cast<int64_t*>(wbase + NSB * P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B) +
+           g * P::NSEGB;
   };
   auto st_Bi = [&](int bi) {   // patch-row segment (length, first row, window column)
-    return reinterpret_cast<int4*>(wbase + P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B + P::STAGE_BI) +
+    return reinterpret_cast<int4*>(wbase + NSB * P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B +
+                                   P::STAGE_BI) +
            g * P::NSEGB;
   };
   auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
 
-  // (1) bulk copies of the inverses of patch group pg (lane 0)
-  auto issue_S = [&](int64_t pg) {
+  // (1) bulk copies of the inverses of patch group pg into buffer sb (lane 0)
+  auto issue_S = [&](int64_t pg, int sb) {
     const int np = npat(pg);
+    unsigned char* sbase = wbase + (size_t)sb * P::STAGE_S;
+    uint64_t* bar = bars + sb;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(bar, (uint32_t)(np * (P::S_BYTES + P::SC_BYTES)));
     for (int q = 0; q < np; ++q) {
       const int64_t p = pg * GPW + q;
-      bulk_load(wbase + (size_t)q * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bar, pol);
+      bulk_load(sbase + (size_t)q * P::S_BYTES, S + p * P::SL::STRIDE, P::S_BYTES, bar, pol);
       if constexpr (P::BF)
-        bulk_load(wbase + (size_t)GPW * P::S_BYTES + (size_t)q * P::SC_BYTES,
+        bulk_load(sbase + (size_t)GPW * P::S_BYTES + (size_t)q * P::SC_BYTES,
                   reinterpret_cast<const float*>(S + count * P::SL::STRIDE) + p * NVP, P::SC_BYTES, bar, pol);
     }
   };
@@ -712,18 +717,37 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   PlanRegs<P, T> R;
   int rtype = patch_type<D>(vc, L.n);
   R.load(plan_p + (size_t)rtype * PSum::ZP * LW * PB, plan_m + (size_t)rtype * PSum::ZM * LW * MASS_BYTES);
-  if (lane == 0) mbar_init(bar, 1);
+  // row maps of this lane's patch rows, for the current group; those of the
+  // next group are loaded while the current one is computed
+  uint32_t rps[P::NROWIT];
+  auto load_rowmap = [&](int type, uint32_t (&o)[P::NROWIT]) {
+#pragma unroll
+    for (int it = 0; it < P::NROWIT; ++it) {
+      const int l = lp + it * LW;
+      o[it] = (l < NV) ? __ldg(rowp + (size_t)type * NV + l) : 0u;
+    }
+  };
+  load_rowmap(rtype, rps);
+  if (lane == 0)
+#pragma unroll
+    for (int sb = 0; sb < NSB; ++sb) mbar_init(bars + sb, 1);
   __syncwarp();
-  if (pg < ngroups && lane == 0) issue_S(pg);   // the inverses do not depend on earlier passes
+  if (lane == 0)   // the inverses do not depend on earlier passes
+#pragma unroll
+    for (int sb = 0; sb < NSB; ++sb)
+      if (pg + sb * W < ngroups) issue_S(pg + sb * W, sb);
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncwarp();
   if (pg < ngroups) issue_gather(0, vc, actc);
   for (int k = 0; pg < ngroups; ++k, pg += W) {
     const int bi = k & 1;
+    const int sb = (NSB == 1) ? 0 : (k % NSB);
     const int64_t pn = pg + W;
     int vn[D];
     const bool actn = vertex(pn, vn);
+    uint32_t rpn[P::NROWIT];
+    load_rowmap(patch_type<D>(vn, L.n), rpn);
     if (pn < ngroups) {   // gather the next group while this one is computed
       issue_gather(bi ^ 1, vn, actn);
       cp_async_wait<1>();
@@ -734,12 +758,6 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     if (type != rtype) {
       R.load(plan_p + (size_t)type * PSum::ZP * LW * PB, plan_m + (size_t)type * PSum::ZM * LW * MASS_BYTES);
       rtype = type;
-    }
-    uint32_t rps[P::NROWIT];
-#pragma unroll
-    for (int it = 0; it < P::NROWIT; ++it) {
-      const int l = lp + it * LW;
-      rps[it] = (l < NV) ? __ldg(rowp + (size_t)type * NV + l) : 0u;
     }
     __syncwarp();
     T* pb = st_T(bi);
@@ -755,12 +773,15 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     }
     __syncwarp();
     // (3b) wait for the inverses of this group (bounded); rows of the residual
-    if (!mbar_wait_bounded(bar, (uint32_t)(k & 1), 2000000000ull)) {
+    if (!mbar_wait_bounded(bars + sb, (uint32_t)((k / NSB) & 1), 2000000000ull)) {
       if (lane == 0) atomicExch(err, 2);
       cp_async_wait<0>();
+      // the copy into the other buffer (group k+1) may still be in flight
+      if (NSB > 1 && pn < ngroups) mbar_wait_bounded(bars + (sb ^ 1), (uint32_t)(((k + 1) / NSB) & 1), 100000000ull);
       break;
     }
-    const float* sc = reinterpret_cast<const float*>(wbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
+    const unsigned char* sbase = wbase + (size_t)sb * P::STAGE_S;
+    const float* sc = reinterpret_cast<const float*>(sbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
     if (actc) {
 #pragma unroll
       for (int it = 0; it < P::NROWIT; ++it) {
@@ -790,7 +811,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     {
       const int q = lp % LPP, sp = lp / LPP;
       if (actc && sp < SSPL) {
-        const TS* Sg = reinterpret_cast<const TS*>(wbase + (size_t)g * P::S_BYTES) + q * RG;
+        const TS* Sg = reinterpret_cast<const TS*>(sbase + (size_t)g * P::S_BYTES) + q * RG;
         if constexpr (P::F2) {
           float2 acc[RG / 2][NR];
 #pragma unroll
@@ -847,8 +868,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
       }
     }
     __syncwarp();
-    // the inverses are consumed: copy those of the next group
-    if (pn < ngroups && lane == 0) issue_S(pn);
+    // the inverses are consumed: copy those of the group NSB iterations ahead
+    if (lane == 0 && pg + NSB * W < ngroups) issue_S(pg + NSB * W, sb);
     // (5) x|_v = window copy of x|_v + delta, by patch-row segments
     if (actc) {
       const int64_t* bb = st_Bb(bi);
@@ -876,6 +897,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
     __syncwarp();
 #pragma unroll
     for (int e = 0; e < D; ++e) vc[e] = vn[e];
+#pragma unroll
+    for (int it = 0; it < P::NROWIT; ++it) rps[it] = rpn[it];
     actc = actn;
   }
 }

@@ -213,18 +213,21 @@ struct PassShape {
   static constexpr int T_PER_PATCH = ((OFF_P + NR * PARTS + 3) / 4) * 4;
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  // per warp: one buffer of inverses, two stages of per-patch T data and
-  // patch-row bases (the window of the next group is gathered while the
-  // current one is computed; its inverses are copied once the current
-  // product is done)
+  // per warp: NSB buffers of inverses and two stages of per-patch T data and
+  // patch-row bases.  The window of the next group is gathered while the
+  // current one is computed; with two inverse buffers the copy of group k+2
+  // starts as soon as the product of group k is done, so a copy has about two
+  // iterations to land (one buffer where the inverses are FP64: 12.8 KB per
+  // patch at n_v = 40 would cost occupancy).
+  static constexpr int NSB = (sizeof(TS) == 8) ? 1 : 2;
   static constexpr size_t STAGE_S = (size_t)GPW * (S_BYTES + SC_BYTES);
   static constexpr size_t STAGE_T = (((size_t)GPW * T_PER_PATCH * sizeof(T) + 15) / 16) * 16;
   // patch-row segments of each patch: array bases (int64), then (length, first row, window column) as int4
   static constexpr size_t STAGE_BI = (((size_t)GPW * NSEGB * sizeof(int64_t) + 15) / 16) * 16;
   static constexpr size_t STAGE_B = STAGE_BI + (size_t)GPW * NSEGB * 16;
   static constexpr int NSI = (NSEG + LW - 1) / LW;         // gather segments per lane
-  static constexpr size_t WARP_BYTES = STAGE_S + 2 * (STAGE_T + STAGE_B);
-  static constexpr size_t SMEM = (size_t)WARPS * WARP_BYTES + (size_t)WARPS * sizeof(uint64_t) + 16;
+  static constexpr size_t WARP_BYTES = NSB * STAGE_S + 2 * (STAGE_T + STAGE_B);
+  static constexpr size_t SMEM = (size_t)WARPS * WARP_BYTES + (size_t)WARPS * NSB * sizeof(uint64_t) + 16;
   // per-level tables
   static constexpr int NTYPE = (D == 2) ? 16 : 64;
   static constexpr size_t al16(size_t b) { return (b + 15) / 16 * 16; }
