@@ -82,6 +82,11 @@ typedef struct {
                            rounding).  -1: automatic (the largest j < J whose
                            matrix fits 1 GiB in FP32 / 256 MiB in FP64 modes),
                            0: never, j >= 1: level j.                          */
+  int pass_kernel;      /* kernel of the colour passes of the smoother (same
+                           update up to rounding): 0: chosen per level at
+                           setup by timing both on this device, 1: one warp
+                           per patch (persistent), 2: one thread block per
+                           patch.                                              */
 } mg_problem;
 
 typedef struct {

@@ -11,6 +11,8 @@
 #include "tables.h"
 
 #include <algorithm>
+#include <mutex>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -185,6 +187,63 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, i
 
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
+// Picks the colour-pass kernel of every level (mode 0), or sets the one asked
+// for (1: warp per patch, 2: block per patch).  Both compute the same update
+// up to rounding.  A warp per patch, persistent over the colour, keeps the
+// copies of the patch inverses streaming and suits levels whose passes fill
+// the GPU; a block per patch shortens the latency of one patch update, which
+// is what a pass costs on coarse levels.  Mode 0 times three symmetric
+// smoothing steps of each on the level's own vectors (after one untimed step)
+// and keeps the faster; the choice is cached per level shape and device.
+mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
+  static std::mutex mu;
+  static std::map<std::vector<int>, int> cache;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const int64_t l0 = h->launches;
+  for (int j = 1; j <= h->J; ++j) {
+    HostLevel& L = h->lv[j];
+    if (mode != 0) {
+      L.pass_cta = (mode == 2) ? 1 : 0;
+      continue;
+    }
+    const std::vector<int> key = {h->device, h->d, h->k, L.n, L.sprec, h->prec, nrhs, L.mu == 0.0 ? 1 : 0};
+    {
+      std::lock_guard<std::mutex> g(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        L.pass_cta = it->second;
+        continue;
+      }
+    }
+    if (!e0) {
+      CU(cudaEventCreate(&e0));
+      CU(cudaEventCreate(&e1));
+    }
+    const size_t bytes = (size_t)L.ndof * nrhs * h->vbytes();
+    float ms[2] = {0.f, 0.f};
+    for (int var = 0; var < 2; ++var) {
+      L.pass_cta = var;
+      CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
+      CU(cudaMemsetAsync(L.B, 0, bytes, h->stream));
+      TRY(smooth_steps(h, j, L.X, L.B, 1, nrhs, h->stream));
+      CU(cudaEventRecord(e0, h->stream));
+      TRY(smooth_steps(h, j, L.X, L.B, 3, nrhs, h->stream));
+      CU(cudaEventRecord(e1, h->stream));
+      CU(cudaEventSynchronize(e1));
+      CU(cudaEventElapsedTime(&ms[var], e0, e1));
+    }
+    L.pass_cta = ms[1] < ms[0] ? 1 : 0;
+    CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = L.pass_cta;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->launches = l0;
+  CU(cudaGetLastError());
+  return MG_OK;
+}
+
 // B_j b_j for the nrhs vectors of vs.B[j]; result in vs.X[j] (Sec. 3.2).  With
 // use_dense, the sub-cycle at level Ls is the precomputed dense operator.
 mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cudaStream_t stream) {
@@ -345,6 +404,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
+  if (p->pass_kernel < 0 || p->pass_kernel > 2) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -444,6 +504,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
       ++h->launches;
     }
   }
+  if ((st = tune_passes(h, p->pass_kernel, nrhs)) != MG_OK) return cleanup(st);
   h->main.nrhs = nrhs;
   h->nrhs = nrhs;
   for (int j = 0; j <= J; ++j) {

@@ -903,6 +903,12 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   }
 }
 
+}  // namespace mgd
+
+#include "passcta.cuh"
+
+namespace mgd {
+
 // ---------------------------------------------------------------------------
 // Coarsest level: dense bordered inverse of A_0 on the free dofs (FP64).
 // ---------------------------------------------------------------------------

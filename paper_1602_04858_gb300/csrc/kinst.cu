@@ -4,6 +4,7 @@
 #include "tables.h"
 
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -143,17 +144,46 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
                      (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
 }
 
+// Byte offset of the block-per-patch tables inside a level's table blob.
+template <typename T, typename TS>
+constexpr size_t cta_tables_offset() {
+  return (PassShape<D, K, T, TS, 1>::TAB_BYTES + 255) / 256 * 256;
+}
+
+// One block per patch: grid = patches of the colour x right-hand-side groups.
+template <typename T, typename TS, int NR>
+void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
+                        cudaStream_t s) {
+  using C = PassShapeC<D, K, T, TS, NR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h.count[colour], groups);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
+  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour),
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+}
+
 // Right-hand sides in groups of four share each S_v load; the rest one by one.
 template <typename T, typename TS>
 void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
                    cudaStream_t s) {
   if (h.count[colour] == 0) return;
   const int g4 = nrhs / 4, rest = nrhs - 4 * g4;
-  if (g4 > 0) colour_pass_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
-  if (rest > 0) {
-    const size_t off = (size_t)4 * g4 * h.ndof;
-    colour_pass_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+  const size_t off = (size_t)4 * g4 * h.ndof;
+  if (h.pass_cta) {
+    if (g4 > 0) colour_pass_cta_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+    if (rest > 0) colour_pass_cta_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+    return;
   }
+  if (g4 > 0) colour_pass_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+  if (rest > 0) colour_pass_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
 }
 
 void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
@@ -163,23 +193,32 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
   else colour_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, err, nrhs, s);
 }
 
-// Bytes of the per-level colour-pass tables (segments, lane plans, row maps).
+// Bytes of the per-level colour-pass tables: those of the warp-per-patch
+// pass (segments, lane plans, row maps), then those of the block-per-patch
+// pass (gather descriptors, block plans).
+template <typename T, typename TS>
+size_t tables_bytes() {
+  return cta_tables_offset<T, TS>() + (PassShapeC<D, K, T, TS, 1>::TAB_BYTES + 15) / 16 * 16;
+}
 int64_t template_elems(int sprec) {
   size_t b;
-  if (sprec == P64) b = PassShape<D, K, double, double, 1>::TAB_BYTES;
-  else if (sprec == P32) b = PassShape<D, K, float, float, 1>::TAB_BYTES;
-  else b = PassShape<D, K, float, __nv_bfloat16, 1>::TAB_BYTES;
-  return (int64_t)((b + 15) / 16) * 16;
+  if (sprec == P64) b = tables_bytes<double, double>();
+  else if (sprec == P32) b = tables_bytes<float, float>();
+  else b = tables_bytes<float, __nv_bfloat16>();
+  return (int64_t)b;
 }
 
 template <typename T, typename TS>
 int build_template_t(const HostLevel& h, void* tabs, cudaStream_t s, std::string* why) {
-  std::vector<unsigned char> blob;
+  std::vector<unsigned char> blob, blob_c;
   std::string msg;
-  if (!build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg)) {
+  if (!build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg) ||
+      !build_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob_c, msg)) {
     if (why) *why = "colour-pass tables of the " + std::to_string(h.n) + "^" + std::to_string(D) + " level: " + msg;
     return 1;
   }
+  blob.resize(tables_bytes<T, TS>(), 0);
+  std::memcpy(blob.data() + cta_tables_offset<T, TS>(), blob_c.data(), blob_c.size());
   if (cudaMemcpyAsync(tabs, blob.data(), blob.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     if (why) *why = "upload of the colour-pass tables failed";
@@ -212,7 +251,9 @@ int plan_selftest_t(int n, double mu, std::string& why) {
   h.ndof = o;
   h.h = 1.0 / n;
   h.mu = mu;
-  return check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+  const int r = check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+  if (r != 0) return r;
+  return check_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
 }
 
 int plan_selftest(int sprec, int n, double mu, std::string* why) {

@@ -21,7 +21,9 @@ struct HostLevel {
   float* c32;
   int sprec;             // storage precision of the patch inverses (Prec)
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
-  void* R0;              // colour-pass tables: gather segments, lane plans and row maps
+  void* R0;              // colour-pass tables: gather segments, lane plans and row maps of the
+                         // warp-per-patch pass, followed by those of the block-per-patch pass
+  int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision

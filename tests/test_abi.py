@@ -43,7 +43,8 @@ def _setup(lib, **kw):
     c = kw.pop("c", np.ones((8, 8)))
     p = mgdarcy.mg_problem(kw.get("dim", 2), kw.get("n_coarse", 2), kw.get("n_levels", 3), kw.get("degree", 0),
                            kw.get("mu", 1.0), c.ctypes.data if c is not None else None, kw.get("precision", 0),
-                           kw.get("m_fine", 2), 1, kw.get("coarse_avg", 0), kw.get("dense_level", 0))
+                           kw.get("m_fine", 2), 1, kw.get("coarse_avg", 0), kw.get("dense_level", 0),
+                           kw.get("pass_kernel", 0))
     h = ctypes.c_void_p()
     return lib.mg_setup(ctypes.byref(p), None, ctypes.byref(h))
 
@@ -62,6 +63,8 @@ def _setup(lib, **kw):
     (dict(c=None), 1),
     (dict(dense_level=3), 1),
     (dict(dense_level=-2), 1),
+    (dict(pass_kernel=3), 1),
+    (dict(pass_kernel=-1), 1),
 ])
 def test_setup_rejects_bad_arguments(lib, kw, status):
     assert _setup(lib, **kw) == status

@@ -22,13 +22,13 @@ NRHS = 4
 SPECS = [(4, 2, 1, 0.01, 1.0, 11), (4, 3, 1, 0.01, 2.0, 12), (4, 4, 1, 0.01, 3.0, 13)]
 
 
-def _problems(precision):
+def _problems(precision, pass_kernel=0):
     probs, hier = [], []
     for n0, L, k, mu, sig, seed in SPECS:
         n = n0 * 2 ** (L - 1)
         c = inputs.lognormal_c(n, 2, sig, n / 8, seed)
         probs.append(dict(dim=2, n_coarse=n0, n_levels=L, degree=k, mu=mu, c=torch.as_tensor(c, device="cuda"),
-                          precision=precision))
+                          precision=precision, pass_kernel=pass_kernel))
         hier.append(mg.Hierarchy(2, n0, L, k, mu, c))
     return probs, hier
 
@@ -38,9 +38,10 @@ def oracle_hierarchies():
     return _problems("fp64")[1]
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2], ids=["tuned", "warp", "block"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
-def test_batched_vcycle_matches_oracle(precision, tol, oracle_hierarchies):
-    probs, _ = _problems(precision)
+def test_batched_vcycle_matches_oracle(precision, tol, kernel, oracle_hierarchies):
+    probs, _ = _problems(precision, kernel)
     B = mgdarcy.Batch(probs, nrhs=NRHS)
     total = B.total()
     rng = np.random.default_rng(4)

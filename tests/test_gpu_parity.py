@@ -55,7 +55,12 @@ def physical_rhs(L, seed):
 _cache = {}
 
 
-def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1):
+# colour-pass kernels: 1 one warp per patch, 2 one thread block per patch
+KERNELS = [1, 2]
+KERNEL_IDS = ["warp", "block"]
+
+
+def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_kernel=0):
     name, d, k, n0, L, mu, cf = case
     nf = n0 * 2 ** (L - 1)
     c = cf(nf)
@@ -64,7 +69,7 @@ def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1):
         _cache[key] = mg.Hierarchy(d, n0, L, k, mu, c)
     H = _cache[key]
     G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, m_fine=m_fine, variable_cycle=variable,
-                          dense_level=dense_level)
+                          dense_level=dense_level, pass_kernel=pass_kernel)
     return H, G
 
 
@@ -126,9 +131,10 @@ def test_coarse_solve_parity(case):
     assert rel_inf(host(x), mg.coarse_solve(H, b)) < 1e-11
 
 
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_smoothing_step_parity_fp64(case):
-    H, G = build(case)
+def test_smoothing_step_parity_fp64(case, kernel):
+    H, G = build(case, pass_kernel=kernel)
     rng = np.random.default_rng(4)
     for j in range(1, len(H.levels)):
         L = H.levels[j]
@@ -154,6 +160,58 @@ def test_vcycle_parity_fp64(case, variable, dense_level):
     G.vcycle(dev(r), z)
     zo = mg.vcycle(H, r, m_fine=2 if variable else 1, variable=variable)
     assert rel_inf(host(z), zo) < 1e-10
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_vcycle_parity_fp64_each_kernel(case, kernel):
+    """One variable V-cycle with every level's colour passes on one kernel."""
+    H, G = build(case, dense_level=0, pass_kernel=kernel)
+    LJ = H.levels[-1]
+    r = np.random.default_rng(15).standard_normal(LJ.S.ndof)
+    z = torch.zeros_like(dev(r))
+    G.vcycle(dev(r), z)
+    assert rel_inf(host(z), mg.vcycle(H, r)) < 1e-10
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
+def test_smoothing_step_fp32_each_kernel(case, kernel):
+    """A symmetric FP32 smoothing step on every level against the FP64 oracle
+    step: relative error of the update within the FP32 bound FP32_VCYCLE_TOL."""
+    H, G = build(case, precision="fp32", pass_kernel=kernel)
+    tol = FP32_VCYCLE_TOL.get(case[0], 1e-5)
+    rng = np.random.default_rng(16)
+    for j in range(1, len(H.levels)):
+        L = H.levels[j]
+        x0 = rng.standard_normal(L.S.ndof)
+        b = rng.standard_normal(L.S.ndof)
+        x = dev(x0)
+        G.smooth(j, x, dev(b), steps=1)
+        d_gpu, d_ora = host(x) - x0, mg.smooth_step(L, x0, b) - x0
+        err = np.linalg.norm(d_gpu - d_ora) / np.linalg.norm(d_ora)
+        assert err < tol, f"level {j}: {err}"
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
+def test_colour_pass_kernels_agree(case, precision):
+    """Both kernels read the same stored inverses (BF16 ones included) and
+    differ only in FP32 summation order, so their smoothing steps agree within
+    twice the FP32 bound FP32_VCYCLE_TOL."""
+    _, Gw = build(case, precision=precision, pass_kernel=1)
+    _, Gb = build(case, precision=precision, pass_kernel=2)
+    tol = 2.0 * FP32_VCYCLE_TOL.get(case[0], 1e-5)
+    rng = np.random.default_rng(17)
+    for j in range(1, case[4]):
+        nd = Gw.ndof(j)
+        x0 = rng.standard_normal(nd)
+        b = rng.standard_normal(nd)
+        xw, xb = dev(x0), dev(x0)
+        Gw.smooth(j, xw, dev(b), steps=1)
+        Gb.smooth(j, xb, dev(b), steps=1)
+        dw, db = host(xw) - x0, host(xb) - x0
+        assert np.linalg.norm(dw - db) <= tol * np.linalg.norm(dw), f"level {j}"
 
 
 def test_config1_vcycle_and_solve():
@@ -217,11 +275,12 @@ def test_solve_fp64_matches_oracle(case):
     assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) < SOLVE_TOL.get(case[0], 1e-8)
 
 
+@pytest.mark.parametrize("kernel", [0, 2], ids=["tuned", "block"])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
-def test_mixed_precision_solve_reaches_1e8(case, precision):
+def test_mixed_precision_solve_reaches_1e8(case, precision, kernel):
     """FP32 / BF16-inverse V-cycle inside FP64 flexible GMRES reaches 1e-8 (FP64 residual)."""
-    H, G = build(case, precision=precision)
+    H, G = build(case, precision=precision, pass_kernel=kernel)
     LJ = H.levels[-1]
     S = LJ.S
     b = physical_rhs(LJ, 8)
@@ -232,10 +291,11 @@ def test_mixed_precision_solve_reaches_1e8(case, precision):
     assert np.linalg.norm(LJ.A @ xg - b) <= 1.01e-8 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
 @pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
-def test_vcycle_fp32_error(case):
+def test_vcycle_fp32_error(case, kernel):
     """FP32 V-cycle vs the FP64 oracle V-cycle, bound FP32_VCYCLE_TOL."""
-    H, G = build(case, precision="fp32")
+    H, G = build(case, precision="fp32", pass_kernel=kernel)
     LJ = H.levels[-1]
     rng = np.random.default_rng(9)
     r = rng.standard_normal(LJ.S.ndof)
