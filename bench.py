@@ -182,6 +182,13 @@ def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
     return dofs * steps * world / (ms_max / 1e3), ms_max
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the warp-per-patch FP32 colour pass on the finest level of this workload
+# (7,225 patches), from an ncu capture of the kernel as it stands; it has to be
+# taken again whenever that kernel changes.
+FINEST_PASS_DRAM_BYTES = 51.024e6 + 0.044e6
+
+
 def colour_pass_bytes(count, nv, s_inv, s_v):
     """Algorithmic bytes of one colour pass: each patch streams its n_v x n_v
     inverse once and reads b_v, x_v and writes x_v (3 n_v vector entries)."""
@@ -334,6 +341,7 @@ def main():
                                  precision=prec, m_fine=2, variable_cycle=True, stream=stream.cuda_stream)
 
     G = make("fp32")
+    pass_kernels = {j: ("warp" if G.pass_kernel(j) == 1 else "block") for j in range(1, w["n_levels"])}
     nu, npr = G.sizes()
     N = nu + npr
     rng = np.random.default_rng(11 + rank)
@@ -448,12 +456,13 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(),
+                "config": dict(workload_config(), pass_kernel_by_level=pass_kernels),
                 "e2e": ({"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
                         if e2e_value is not None else None),
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                             "frac": achieved / hbm, "traffic": None,
+                             "frac": achieved / hbm,
+                             "traffic": FINEST_PASS_DRAM_BYTES if pass_kernels[J] == "warp" else None,
                              "kernel": "k_colour_pass<2,1,float,float> (finest level)",
                              "peak_kind": peak_kind, "avg_launch_ms": avg_launch_ms,
                              "bytes_per_launch": per_launch_bytes, "isolated_launch_ms": isolated_launch_ms,

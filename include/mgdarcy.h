@@ -80,13 +80,16 @@ typedef struct {
                            vectors, and apply it in one product instead of its
                            sequential smoothing passes (same operator up to
                            rounding).  -1: automatic (the largest j < J whose
-                           matrix fits 1 GiB in FP32 / 256 MiB in FP64 modes),
+                           matrix fits 2.5 GiB in the working precision),
                            0: never, j >= 1: level j.                          */
   int pass_kernel;      /* kernel of the colour passes of the smoother (same
-                           update up to rounding): 0: chosen per level at
-                           setup by timing both on this device, 1: one warp
-                           per patch (persistent), 2: one thread block per
-                           patch.                                              */
+                           update up to rounding): 1: one warp per patch
+                           (persistent), 2: one thread block per patch,
+                           0: per level, the block kernel where the largest
+                           colour holds at most 10,000 inverse entries
+                           (n_v^2 per patch) per SM, else the warp kernel,
+                           3: per level, the faster of the two in a timed
+                           trial at setup.                                     */
 } mg_problem;
 
 typedef struct {
@@ -279,6 +282,11 @@ mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
 
 /* Patch counts: number of patches of `colour` on `level` and their size n_v. */
 mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v);
+
+/* Colour-pass kernel chosen for `level` (1 <= level <= J) at setup, see
+ * mg_problem.pass_kernel: *kernel = 1 (warp per patch) or 2 (block per
+ * patch).  Host only. */
+mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel);
 
 /* Number of kernels the library launched on this handle so far. */
 int64_t mg_kernel_launches(const mg_handle* h);

@@ -187,14 +187,19 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, i
 
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
-// Picks the colour-pass kernel of every level (mode 0), or sets the one asked
-// for (1: warp per patch, 2: block per patch).  Both compute the same update
+// Sets the colour-pass kernel of every level.  Both compute the same update
 // up to rounding.  A warp per patch, persistent over the colour, keeps the
 // copies of the patch inverses streaming and suits levels whose passes fill
 // the GPU; a block per patch shortens the latency of one patch update, which
-// is what a pass costs on coarse levels.  Mode 0 times three symmetric
-// smoothing steps of each on the level's own vectors (after one untimed step)
-// and keeps the faster; the choice is cached per level shape and device.
+// is what a pass costs on coarse levels.  Modes: 1 warp per patch, 2 block
+// per patch everywhere; 0 (default) block per patch on levels whose largest
+// colour holds at most 10,000 inverse entries (n_v^2 per patch) per SM, warp
+// per patch elsewhere (the crossover measured on GB300: 2-D RT_1 colours of
+// 441 patches and 3-D RT_0 colours of 1,103 favour the block, 2-D RT_1
+// colours of 1,800 patches the warp); 3 times three symmetric smoothing steps of each on
+// the level's own vectors (after one untimed step) and keeps the faster, the
+// choice cached per level shape and device (timings taken under a profiler
+// that serialises kernels can flip it).
 mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   static std::mutex mu;
   static std::map<std::vector<int>, int> cache;
@@ -202,8 +207,17 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   const int64_t l0 = h->launches;
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
-    if (mode != 0) {
-      L.pass_cta = (mode == 2) ? 1 : 0;
+    if (mode != 3) {
+      if (mode == 0) {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        int64_t mx = 0;
+        for (int col = 0; col < num_colours(h->d); ++col) mx = std::max(mx, L.count[col]);
+        const int64_t nv = h->ops->nv;
+        L.pass_cta = (mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
+      } else {
+        L.pass_cta = (mode == 2) ? 1 : 0;
+      }
       continue;
     }
     const std::vector<int> key = {h->device, h->d, h->k, L.n, L.sprec, h->prec, nrhs, L.mu == 0.0 ? 1 : 0};
@@ -404,7 +418,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
-  if (p->pass_kernel < 0 || p->pass_kernel > 2) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (p->pass_kernel < 0 || p->pass_kernel > 3) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -583,8 +597,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   {
     int Ls = p->dense_level;
     if (Ls < 0) {
-      const double budget = dense_budget > 0 ? dense_budget : ((h->prec == P64) ? 256.0 * (1 << 20)
-                                                                                 : 1024.0 * (1 << 20));
+      const double budget = dense_budget > 0 ? dense_budget : 2560.0 * (1 << 20);
       Ls = 0;
       for (int j = 1; j < J; ++j)
         if ((double)h->lv[j].ndof * h->lv[j].ndof * h->vbytes() <= budget) Ls = j;
@@ -667,6 +680,12 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
     return fail(MG_ERR_INVALID_ARG, "bad level or colour");
   if (count) *count = h->lv[level].count[colour];
   if (n_v) *n_v = h->ops->nv;
+  return MG_OK;
+}
+
+mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
+  if (!h || level < 1 || level > h->J || !kernel) return fail(MG_ERR_INVALID_ARG, "bad level or argument");
+  *kernel = h->lv[level].pass_cta ? 2 : 1;
   return MG_OK;
 }
 

@@ -23,7 +23,7 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
+    "mg_level_pass_kernel", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
     "mg_setup_batch", "mg_destroy_batch", "mg_batch_layout", "mg_vcycle_batch", "mg_solve_batch",
     "mg_batch_kernel_launches", "mg_load_vector",
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_prolong_add.argtypes = [vp, i, vp, vp]
     lib.mg_coarse_solve.argtypes = [vp, vp, vp]
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
+    lib.mg_level_pass_kernel.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
     lib.mg_setup_batch.argtypes = [ctypes.POINTER(mg_problem), i, i, vp, ctypes.POINTER(vp)]
@@ -237,6 +238,12 @@ class Multigrid:
         cnt, nv = ctypes.c_int64(), ctypes.c_int()
         _check(load().mg_patch_info(self.h, level, colour, ctypes.byref(cnt), ctypes.byref(nv)))
         return cnt.value, nv.value
+
+    def pass_kernel(self, level):
+        """Colour-pass kernel of a level: 1 warp per patch, 2 block per patch."""
+        k = ctypes.c_int()
+        _check(load().mg_level_pass_kernel(self.h, level, ctypes.byref(k)))
+        return k.value
 
     def residual_norm(self, x, b, r=None, level=-1):
         """||b - A x||_2 (FP64) of device tensors; also stores r = b - A x if given."""

@@ -275,7 +275,7 @@ def test_solve_fp64_matches_oracle(case):
     assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) < SOLVE_TOL.get(case[0], 1e-8)
 
 
-@pytest.mark.parametrize("kernel", [0, 2], ids=["tuned", "block"])
+@pytest.mark.parametrize("kernel", [0, 3], ids=["rule", "timed"])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
 def test_mixed_precision_solve_reaches_1e8(case, precision, kernel):
@@ -304,6 +304,22 @@ def test_vcycle_fp32_error(case, kernel):
     zo = mg.vcycle(H, r)
     err = np.linalg.norm(host(z) - zo) / np.linalg.norm(zo)
     assert err < FP32_VCYCLE_TOL.get(case[0], 1e-5), err
+
+
+def test_pass_kernel_choice():
+    """Explicit choices are kept; the default rule takes the block kernel
+    where a level's largest colour holds at most 10,000 inverse entries per SM."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    case = CASES[1]
+    for pk, want in ((1, 1), (2, 2)):
+        _, G = build(case, pass_kernel=pk)
+        assert all(G.pass_kernel(j) == want for j in range(1, case[4]))
+    _, G = build(case)
+    for j in range(1, case[4]):
+        mx, nv = max(G.patch_info(j, c) for c in range(9))
+        assert G.pass_kernel(j) == (2 if mx * nv * nv <= 10000 * nsm else 1)
+    with pytest.raises(mgdarcy.MGError):
+        G.pass_kernel(0)
 
 
 def test_host_pointers_give_the_same_vcycle():
