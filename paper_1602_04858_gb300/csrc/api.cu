@@ -86,6 +86,11 @@ struct mg_handle {
   void* Bd_partial = nullptr;
   VecSet main;    // the level vectors X, B, R (nrhs right-hand sides)
   int nrhs = 1;
+  // a group of grp_nprob problems of one shape run as one (batches): nrhs
+  // counts the vectors of all of them, the dense operators are bd_stride
+  // elements apart; the storage belongs to the batch
+  int grp_nprob = 1;
+  int64_t bd_stride = 0;
   int64_t launches = 0;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;
@@ -264,8 +269,15 @@ mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cu
   HostLevel& L = h->lv[j];
   const int nr = vs.nrhs;
   if (use_dense && j == h->Ls) {
-    launch_dense_apply(h->f32(), h->Bd, L.ndof, vs.B[j], vs.X[j], h->Bd_partial, nr, stream);
-    h->launches += 2 * ((nr + 3) / 4);
+    if (h->grp_nprob > 1) {
+      const int rhs = nr / h->grp_nprob;
+      launch_dense_apply_grouped(h->f32(), h->Bd, h->bd_stride, L.ndof, vs.B[j], vs.X[j], h->Bd_partial,
+                                 h->grp_nprob, rhs, stream);
+      h->launches += 2 * ((rhs + 3) / 4);
+    } else {
+      launch_dense_apply(h->f32(), h->Bd, L.ndof, vs.B[j], vs.X[j], h->Bd_partial, nr, stream);
+      h->launches += 2 * ((nr + 3) / 4);
+    }
     return MG_OK;
   }
   if (j == 0) {
@@ -348,7 +360,7 @@ mg_status vcycle_dev(mg_handle* h, const double* r, double* z) {
     launch_f2d((const float*)L.X, z, L.ndof, h->stream);
     ++h->launches;
   }
-  h->ops->copy_constrained(L, r, z, h->stream);
+  h->ops->copy_constrained(L, r, z, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -1035,6 +1047,12 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
 
 struct mg_batch {
   std::vector<mg_handle*> sub;
+  // groups of problems of one shape whose V-cycles run as one (their storage
+  // one after another, each kernel launched once for the whole group);
+  // grp[g] is null for a group of one problem, which runs on its own handle
+  std::vector<std::vector<int>> grp_mem;
+  std::vector<mg_handle*> grp;
+  std::vector<int> grp_contig;   // the group's FP64 vectors follow one another in the batch layout
   int nrhs = 1;
   cudaStream_t stream = nullptr;
   std::vector<int64_t> ndof, off;   // finest-level dofs and offset of each problem
@@ -1054,6 +1072,7 @@ struct mg_batch {
   std::vector<void*> allocs;
   ~mg_batch() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto* h : grp) delete h;   // owns no device memory
     for (auto* h : sub) delete h;
     for (void* p : allocs) cudaFree(p);
   }
@@ -1077,49 +1096,249 @@ mg_status sub_vcycle(mg_handle* h, const double* r, double* z, cudaStream_t s) {
   HostLevel& L = h->lv.back();
   const int64_t n = L.ndof * h->nrhs;
   if (h->prec == P64) CU(cudaMemcpyAsync(L.B, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  else launch_d2f(r, (float*)L.B, n, s);
+  else {
+    launch_d2f(r, (float*)L.B, n, s);
+    ++h->launches;
+  }
   TRY(vcycle_level(h, h->J, h->main, true, s));
   if (h->prec == P64) CU(cudaMemcpyAsync(z, L.X, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  else launch_f2d((const float*)L.X, z, n, s);
-  for (int rr = 0; rr < h->nrhs; ++rr) h->ops->copy_constrained(L, r + rr * L.ndof, z + rr * L.ndof, s);
+  else {
+    launch_f2d((const float*)L.X, z, n, s);
+    ++h->launches;
+  }
+  h->ops->copy_constrained(L, r, z, h->nrhs, s);
+  ++h->launches;
   return MG_OK;
 }
 
-// One CUDA graph: every problem's V-cycle as its own branch (rb -> zb).
+// Frees one of the handle's allocations (storage moved elsewhere).
+void release(mg_handle* h, void* p) {
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) {
+    cudaFree(p);
+    h->allocs.erase(it);
+  }
+}
+
+bool same_shape(const mg_handle* a, const mg_handle* b) {
+  if (a->d != b->d || a->k != b->k || a->J != b->J || a->prec != b->prec || a->m_fine != b->m_fine ||
+      a->variable != b->variable || a->mu != b->mu || a->Ls != b->Ls || a->nrhs != b->nrhs ||
+      a->lv[0].n != b->lv[0].n)
+    return false;
+  for (int j = 0; j <= a->J; ++j)
+    if (a->lv[j].pass_cta != b->lv[j].pass_cta || a->lv[j].sprec != b->lv[j].sprec) return false;
+  return true;
+}
+
+// Moves the members' per-level vectors, coefficients, patch inverses and dense
+// operators into group storage (member i's part at i times the per-problem
+// size) and makes the handle that runs the group's V-cycle.
+mg_status build_group(mg_batch* B, const std::vector<int>& mem, mg_handle** out) {
+  const int G = (int)mem.size();
+  mg_handle* h0 = B->sub[mem[0]];
+  const int C = num_colours(h0->d);
+  const size_t vb = h0->vbytes();
+  std::vector<std::pair<mg_handle*, void*>> old;
+  auto gather = [&](size_t per, std::vector<void**> slots, bool copy, char** base) -> mg_status {
+    TRY(B->alloc(base, per * G));
+    for (int i = 0; i < G; ++i) {
+      void* src = *slots[i];
+      if (copy) CU(cudaMemcpyAsync(*base + per * i, src, per, cudaMemcpyDeviceToDevice, B->stream));
+      old.push_back({B->sub[mem[i]], src});
+      *slots[i] = *base + per * i;
+    }
+    return MG_OK;
+  };
+  mg_handle* gh = new mg_handle(*h0);
+  gh->allocs.clear();
+  gh->graph_exec = nullptr;
+  gh->graph_kernels = 0;
+  gh->launches = 0;
+  auto fail_out = [&](mg_status st) {
+    delete gh;
+    return st;
+  };
+  mg_status st;
+  for (int j = 0; j <= h0->J; ++j) {
+    HostLevel& Lg = gh->lv[j];
+    const HostLevel& L0 = h0->lv[j];
+    int64_t ncell = 1;
+    for (int e = 0; e < h0->d; ++e) ncell *= L0.n;
+    char* base = nullptr;
+    const size_t per_v = (size_t)L0.ndof * h0->nrhs * vb;
+    for (int w = 0; w < 3; ++w) {
+      std::vector<void**> sl;
+      for (int i = 0; i < G; ++i) {
+        HostLevel& Lm = B->sub[mem[i]]->lv[j];
+        sl.push_back(w == 0 ? &Lm.X : (w == 1 ? &Lm.B : &Lm.R));
+      }
+      if ((st = gather(per_v, sl, false, &base)) != MG_OK) return fail_out(st);
+      (w == 0 ? Lg.X : (w == 1 ? Lg.B : Lg.R)) = base;
+    }
+    {
+      std::vector<void**> s64, s32;
+      for (int i = 0; i < G; ++i) {
+        s64.push_back((void**)&B->sub[mem[i]]->lv[j].c64);
+        s32.push_back((void**)&B->sub[mem[i]]->lv[j].c32);
+      }
+      if ((st = gather(ncell * sizeof(double), s64, true, &base)) != MG_OK) return fail_out(st);
+      Lg.c64 = (double*)base;
+      if ((st = gather(ncell * sizeof(float), s32, true, &base)) != MG_OK) return fail_out(st);
+      Lg.c32 = (float*)base;
+    }
+    Lg.c_prob = ncell;
+    Lg.rhs_prob = h0->nrhs;
+    if (j >= 1)
+      for (int col = 0; col < C; ++col) {
+        if (L0.count[col] == 0) continue;
+        const size_t sb = (L0.sprec == P64) ? 8 : (L0.sprec == P32 ? 4 : 2);
+        size_t bytes = (size_t)L0.count[col] * h0->ops->s_stride[L0.sprec] * sb;
+        if (L0.sprec == P32B) bytes += (size_t)L0.count[col] * h0->ops->nvp[P32B] * sizeof(float);
+        std::vector<void**> sl;
+        for (int i = 0; i < G; ++i) sl.push_back(&B->sub[mem[i]]->lv[j].S[col]);
+        if ((st = gather(bytes, sl, true, &base)) != MG_OK) return fail_out(st);
+        Lg.S[col] = base;
+        Lg.s_prob[col] = (int64_t)bytes;
+      }
+  }
+  {   // dense operators of the sub-cycle at level Ls
+    const int64_t n = h0->lv[h0->Ls].ndof;
+    std::vector<void**> sl;
+    for (int i = 0; i < G; ++i) sl.push_back(&B->sub[mem[i]]->Bd);
+    char* base = nullptr;
+    if ((st = gather((size_t)n * n * vb, sl, true, &base)) != MG_OK) return fail_out(st);
+    gh->Bd = base;
+    gh->bd_stride = n * n;
+    if ((st = B->alloc((char**)&gh->Bd_partial, (size_t)G * 4 * DENSE_CHUNKS * n * vb)) != MG_OK) return fail_out(st);
+  }
+  if (cudaStreamSynchronize(B->stream) != cudaSuccess) return fail_out(fail(MG_ERR_CUDA, "copy of group storage failed"));
+  for (auto& pr : old) release(pr.first, pr.second);
+  // the members' level-vector lists follow their moved vectors
+  for (int i = 0; i < G; ++i) {
+    mg_handle* hm = B->sub[mem[i]];
+    for (int j = 0; j <= hm->J; ++j) {
+      hm->main.X[j] = hm->lv[j].X;
+      hm->main.B[j] = hm->lv[j].B;
+      hm->main.R[j] = hm->lv[j].R;
+    }
+  }
+  gh->grp_nprob = G;
+  gh->nrhs = G * h0->nrhs;
+  gh->main.nrhs = gh->nrhs;
+  for (int j = 0; j <= gh->J; ++j) {
+    gh->main.X[j] = gh->lv[j].X;
+    gh->main.B[j] = gh->lv[j].B;
+    gh->main.R[j] = gh->lv[j].R;
+  }
+  *out = gh;
+  return MG_OK;
+}
+
+// Groups the batch's problems by shape (dimension, degree, levels, viscosity,
+// precision, cycle, dense level, kernels); groups of several problems with a
+// dense sub-cycle get group storage and a group handle.
+mg_status make_groups(mg_batch* B) {
+  const int np = (int)B->sub.size();
+  std::vector<int> done(np, 0);
+  for (int p = 0; p < np; ++p) {
+    if (done[p]) continue;
+    std::vector<int> mem = {p};
+    done[p] = 1;
+    for (int q = p + 1; q < np; ++q)
+      if (!done[q] && same_shape(B->sub[p], B->sub[q])) {
+        mem.push_back(q);
+        done[q] = 1;
+      }
+    mg_handle* gh = nullptr;
+    if (mem.size() > 1 && B->sub[p]->Ls >= 1) TRY(build_group(B, mem, &gh));
+    int contig = 1;
+    for (size_t i = 1; i < mem.size(); ++i)
+      if (B->off[mem[i]] != B->off[mem[i - 1]] + B->ndof[mem[i - 1]] * B->nrhs) contig = 0;
+    B->grp_mem.push_back(mem);
+    B->grp.push_back(gh);
+    B->grp_contig.push_back(contig);
+  }
+  return MG_OK;
+}
+
+// z = B r for every problem of group g (FP64 device, batch layout).
+mg_status group_vcycle(mg_batch* B, int g, const double* r, double* z, cudaStream_t s) {
+  mg_handle* gh = B->grp[g];
+  const std::vector<int>& mem = B->grp_mem[g];
+  if (!gh) {
+    for (int p : mem) TRY(sub_vcycle(B->sub[p], r + B->off[p], z + B->off[p], s));
+    return MG_OK;
+  }
+  HostLevel& L = gh->lv.back();
+  const int rhs = gh->nrhs / gh->grp_nprob;
+  const int64_t per = L.ndof * rhs;
+  // (contiguous members: one conversion for all)
+  const int nseg = B->grp_contig[g] ? 1 : (int)mem.size();
+  const int64_t seg_len = B->grp_contig[g] ? per * (int64_t)mem.size() : per;
+  for (int i = 0; i < nseg; ++i) {
+    const double* ri = r + B->off[mem[i]];
+    if (gh->prec == P64)
+      CU(cudaMemcpyAsync((double*)L.B + i * per, ri, seg_len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else {
+      launch_d2f(ri, (float*)L.B + i * per, seg_len, s);
+      ++gh->launches;
+    }
+  }
+  TRY(vcycle_level(gh, gh->J, gh->main, true, s));
+  for (int i = 0; i < nseg; ++i) {
+    double* zi = z + B->off[mem[i]];
+    if (gh->prec == P64)
+      CU(cudaMemcpyAsync(zi, (double*)L.X + i * per, seg_len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else {
+      launch_f2d((const float*)L.X + i * per, zi, seg_len, s);
+      ++gh->launches;
+    }
+    gh->ops->copy_constrained(L, r + B->off[mem[i]], zi, (int)(seg_len / L.ndof), s);
+    ++gh->launches;
+  }
+  return MG_OK;
+}
+
+// One CUDA graph: every group's V-cycle as its own branch (rb -> zb).
 mg_status batch_graph(mg_batch* B) {
   if (B->graph) return MG_OK;
-  const int np = (int)B->sub.size();
-  std::vector<cudaStream_t> st(np);
-  std::vector<cudaEvent_t> ev(np + 1);
+  const int ng = (int)B->grp_mem.size();
+  std::vector<cudaStream_t> st(ng);
+  std::vector<cudaEvent_t> ev(ng + 1);
   cudaStream_t s0;
   CU(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
-  for (int p = 0; p < np; ++p) CU(cudaStreamCreateWithFlags(&st[p], cudaStreamNonBlocking));
+  for (int g = 0; g < ng; ++g) CU(cudaStreamCreateWithFlags(&st[g], cudaStreamNonBlocking));
   for (auto& e : ev) CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  int64_t l0 = 0;
-  for (auto* h : B->sub) l0 += h->launches;
+  auto count = [&]() {
+    int64_t l = 0;
+    for (auto* h : B->sub) l += h->launches;
+    for (auto* h : B->grp)
+      if (h) l += h->launches;
+    return l;
+  };
+  const int64_t l0 = count();
   CU(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
   mg_status result = MG_OK;
-  cudaEventRecord(ev[np], s0);
-  for (int p = 0; p < np && result == MG_OK; ++p) {
-    cudaStreamWaitEvent(st[p], ev[np], 0);
-    result = sub_vcycle(B->sub[p], B->rb + B->off[p], B->zb + B->off[p], st[p]);
-    cudaEventRecord(ev[p], st[p]);
-    cudaStreamWaitEvent(s0, ev[p], 0);
+  cudaEventRecord(ev[ng], s0);
+  for (int g = 0; g < ng && result == MG_OK; ++g) {
+    cudaStreamWaitEvent(st[g], ev[ng], 0);
+    result = group_vcycle(B, g, B->rb, B->zb, st[g]);
+    cudaEventRecord(ev[g], st[g]);
+    cudaStreamWaitEvent(s0, ev[g], 0);
   }
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s0, &g);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s0, &gr);
   for (auto& x : st) cudaStreamDestroy(x);
   for (auto& x : ev) cudaEventDestroy(x);
   cudaStreamDestroy(s0);
-  int64_t l1 = 0;
-  for (auto* h : B->sub) l1 += h->launches;
+  const int64_t l1 = count();
   if (result != MG_OK) {
-    if (g) cudaGraphDestroy(g);
+    if (gr) cudaGraphDestroy(gr);
     return result;
   }
   if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&B->graph, g, 0);
-  cudaGraphDestroy(g);
+  e = cudaGraphInstantiate(&B->graph, gr, 0);
+  cudaGraphDestroy(gr);
   if (e != cudaSuccess) {
     B->graph = nullptr;
     return fail(MG_ERR_CUDA, std::string("batch graph: ") + cudaGetErrorString(e));
@@ -1180,6 +1399,10 @@ mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* 
     B->ndof.push_back(h->lv.back().ndof);
     B->off.push_back(B->total);
     B->total += h->lv.back().ndof * nrhs;
+  }
+  if ((st = make_groups(B)) != MG_OK) {
+    delete B;
+    return st;
   }
   // segments and blocks
   std::vector<int> bseg, sfirst;

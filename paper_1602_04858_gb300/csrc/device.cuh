@@ -61,6 +61,17 @@ struct Lvl {
   const T* c;       // per-cell coefficient, x fastest
 };
 
+// Problems of one shape solved together: their vectors follow one another
+// (rhs per problem), and so do their per-level coefficients (c elements apart)
+// and their patch inverses of a colour (s_bytes apart).  rhs = 0: one problem.
+struct ProbStride {
+  int64_t s_bytes;
+  int64_t c;
+  int rhs;
+  // problem of vector (group of vectors) v
+  __host__ __device__ __forceinline__ int64_t of(int64_t v) const { return rhs > 0 ? v / rhs : 0; }
+};
+
 // Number of patch dofs of an interior-vertex patch: D (2K+1)(2K+2)^(D-1)
 // velocity dofs (supported inside the 2^D block) + (2K+2)^D pressure dofs.
 template <int D, int K>

@@ -168,12 +168,18 @@ __global__ void k_set_units(T* __restrict__ B, int64_t ndof, int64_t c0, int nc)
   B[g] = (i == c0 + r) ? T(1) : T(0);
 }
 
-// Column-blocked z = Bd^T b: block (x, y) sums rows r of chunk y for DENSE_THREADS entries i.
+// Column-blocked z = Bd^T b: block (x, y) sums rows r of chunk y for
+// DENSE_THREADS entries i; blockIdx.z selects the problem (matrix Bd + z bd_stride,
+// right-hand sides b + z bvs, partial sums partial + z pstride).
 constexpr int DENSE_THREADS = 256;
 // NR right-hand sides (vectors n apart) share each read of Bd.
 template <typename T, int NR>
 __global__ void __launch_bounds__(DENSE_THREADS) k_dense_partial(const T* __restrict__ Bd, int64_t n,
-                                                                 const T* __restrict__ b, T* __restrict__ partial) {
+                                                                 const T* __restrict__ b, T* __restrict__ partial,
+                                                                 int64_t bd_stride, int64_t bvs, int64_t pstride) {
+  Bd += blockIdx.z * bd_stride;
+  b += blockIdx.z * bvs;
+  partial += blockIdx.z * pstride;
   const int64_t i = (int64_t)blockIdx.x * DENSE_THREADS + threadIdx.x;
   const int64_t per = (n + gridDim.y - 1) / gridDim.y;
   const int64_t r0 = blockIdx.y * per, r1 = (r0 + per < n) ? r0 + per : n;
@@ -192,10 +198,12 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense_partial(const T* __rest
 }
 
 template <typename T>
-__global__ void k_dense_reduce(const T* __restrict__ partial, int chunks, int64_t n, T* __restrict__ z) {
+__global__ void k_dense_reduce(const T* __restrict__ partial, int chunks, int64_t n, T* __restrict__ z,
+                               int64_t zvs, int64_t pstride) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  partial += (int64_t)blockIdx.y * chunks * n;   // one right-hand side per blockIdx.y
+  partial += blockIdx.z * pstride + (int64_t)blockIdx.y * chunks * n;   // one right-hand side per blockIdx.y
+  z += blockIdx.z * zvs;
   T acc = T(0);
   for (int y = 0; y < chunks; ++y) acc += partial[y * n + i];
   z[(int64_t)blockIdx.y * n + i] = acc;
@@ -293,23 +301,36 @@ void launch_set_units(int f32, void* B, int64_t ndof, int64_t c0, int nc, cudaSt
 }
 
 template <typename T>
-void dense_apply_t(const T* Bd, int64_t n, const T* b, T* z, T* partial, int nrhs, cudaStream_t s) {
-  for (int r0 = 0; r0 < nrhs; r0 += 4) {
-    const int nr = (nrhs - r0 < 4) ? nrhs - r0 : 4;
-    const dim3 grid(blocks(n, DENSE_THREADS), DENSE_CHUNKS);
+void dense_apply_t(const T* Bd, int64_t bd_stride, int64_t n, const T* b, T* z, T* partial, int nprob, int rhs,
+                   cudaStream_t s) {
+  const int64_t pstride = (int64_t)4 * DENSE_CHUNKS * n, vs = (int64_t)rhs * n;
+  for (int r0 = 0; r0 < rhs; r0 += 4) {
+    const int nr = (rhs - r0 < 4) ? rhs - r0 : 4;
+    const dim3 grid(blocks(n, DENSE_THREADS), DENSE_CHUNKS, nprob);
     const T* bb = b + (int64_t)r0 * n;
-    if (nr == 4) k_dense_partial<T, 4><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
-    else if (nr == 3) k_dense_partial<T, 3><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
-    else if (nr == 2) k_dense_partial<T, 2><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
-    else k_dense_partial<T, 1><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial);
-    k_dense_reduce<T><<<dim3(blocks(n, 256), nr), 256, 0, s>>>(partial, DENSE_CHUNKS, n, z + (int64_t)r0 * n);
+    if (nr == 4) k_dense_partial<T, 4><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial, bd_stride, vs, pstride);
+    else if (nr == 3) k_dense_partial<T, 3><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial, bd_stride, vs, pstride);
+    else if (nr == 2) k_dense_partial<T, 2><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial, bd_stride, vs, pstride);
+    else k_dense_partial<T, 1><<<grid, DENSE_THREADS, 0, s>>>(Bd, n, bb, partial, bd_stride, vs, pstride);
+    k_dense_reduce<T><<<dim3(blocks(n, 256), nr, nprob), 256, 0, s>>>(partial, DENSE_CHUNKS, n,
+                                                                      z + (int64_t)r0 * n, vs, pstride);
   }
 }
 
 void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, int nrhs,
                         cudaStream_t s) {
-  if (f32) dense_apply_t<float>((const float*)Bd, n, (const float*)b, (float*)z, (float*)partial, nrhs, s);
-  else dense_apply_t<double>((const double*)Bd, n, (const double*)b, (double*)z, (double*)partial, nrhs, s);
+  if (f32) dense_apply_t<float>((const float*)Bd, 0, n, (const float*)b, (float*)z, (float*)partial, 1, nrhs, s);
+  else dense_apply_t<double>((const double*)Bd, 0, n, (const double*)b, (double*)z, (double*)partial, 1, nrhs, s);
+}
+
+void launch_dense_apply_grouped(int f32, const void* Bd, int64_t bd_stride, int64_t n, const void* b, void* z,
+                                void* partial, int nprob, int rhs_prob, cudaStream_t s) {
+  if (f32)
+    dense_apply_t<float>((const float*)Bd, bd_stride, n, (const float*)b, (float*)z, (float*)partial, nprob,
+                         rhs_prob, s);
+  else
+    dense_apply_t<double>((const double*)Bd, bd_stride, n, (const double*)b, (double*)z, (double*)partial, nprob,
+                          rhs_prob, s);
 }
 
 void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t s) {

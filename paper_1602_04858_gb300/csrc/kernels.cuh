@@ -30,11 +30,13 @@ __global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const __gri
 // r = b - A x on free rows; constrained rows: r = 0 (zero_c) or b - x.
 // Batched over right-hand sides: blockIdx.y selects the vector, stride vs.
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+__global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L0, const __grid_constant__ Tab<K, T> tb,
                                                   const T* __restrict__ x, const T* __restrict__ b,
-                                                  T* __restrict__ r, int zero_c, int64_t vs) {
+                                                  T* __restrict__ r, int zero_c, int64_t vs, const ProbStride ps) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= L.ndof) return;
+  if (g >= L0.ndof) return;
+  Lvl<D, K, T> L = L0;
+  L.c += ps.of(blockIdx.y) * ps.c;
   x += blockIdx.y * vs;
   b += blockIdx.y * vs;
   r += blockIdx.y * vs;
@@ -576,10 +578,10 @@ __device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* wi
 }
 
 template <int D, int K, typename T, typename TS, int NR>
-__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const ColourGeom cg, int64_t count,
+__global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count,
                                                      const TS* __restrict__ S, const unsigned char* __restrict__ tabs,
                                                      T* x, const T* __restrict__ b, int evict_first,
-                                                     int* __restrict__ err, int64_t vs) {
+                                                     int* __restrict__ err, int64_t vs, const ProbStride ps) {
   using P = PassShape<D, K, T, TS, NR>;
   using PL = typename P::PL;
   using PSum = typename P::PSum;
@@ -587,6 +589,11 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L, const
   constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>(), NSI = P::NSI;
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
+  // the problem of this block's right-hand sides: its coefficients and inverses
+  const int64_t prob = ps.of((int64_t)blockIdx.y * NR);
+  Lvl<D, K, T> L = L0;
+  L.c += prob * ps.c;
+  S = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(S) + prob * ps.s_bytes);
   extern __shared__ __align__(128) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane / LW, lp = lane - g * LW;

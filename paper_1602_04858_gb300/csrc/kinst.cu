@@ -52,6 +52,15 @@ template <> const Tab<K, float>& tab<float>() { return tabs().f; }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Problem strides of a level (colour < 0: no inverses involved).
+ProbStride pstride(const HostLevel& h, int colour) {
+  ProbStride p;
+  p.rhs = h.rhs_prob;
+  p.c = h.c_prob;
+  p.s_bytes = colour >= 0 ? h.s_prob[colour] : 0;
+  return p;
+}
+
 void apply(const HostLevel& h, int f32, const void* x, void* y, int nrhs, cudaStream_t s) {
   const dim3 grid(blocks(h.ndof, 256), nrhs);
   if (f32)
@@ -65,10 +74,10 @@ void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r
   const dim3 grid(blocks(h.ndof, 256), nrhs);
   if (f32)
     k_residual<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (const float*)b,
-                                                 (float*)r, zero_c, h.ndof);
+                                                 (float*)r, zero_c, h.ndof, pstride(h, -1));
   else
     k_residual<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x,
-                                                  (const double*)b, (double*)r, zero_c, h.ndof);
+                                                  (const double*)b, (double*)r, zero_c, h.ndof, pstride(h, -1));
 }
 
 void restrict_(const HostLevel& f, const HostLevel& c, int f32, const void* rf, void* bc, int nrhs, cudaStream_t s) {
@@ -141,7 +150,8 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour), h.count[colour],
-                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     pstride(h, colour));
 }
 
 // Byte offset of the block-per-patch tables inside a level's table blob.
@@ -167,7 +177,8 @@ void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, 
   cfg.numAttrs = 1;
   const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
   cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour),
-                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof);
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     pstride(h, colour));
 }
 
 // Right-hand sides in groups of four share each S_v load; the rest one by one.
@@ -175,7 +186,8 @@ template <typename T, typename TS>
 void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
                    cudaStream_t s) {
   if (h.count[colour] == 0) return;
-  const int g4 = nrhs / 4, rest = nrhs - 4 * g4;
+  // groups of four right-hand sides must not straddle two problems
+  const int g4 = (h.rhs_prob > 0 && h.rhs_prob % 4 != 0) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
   const size_t off = (size_t)4 * g4 * h.ndof;
   if (h.pass_cta) {
     if (g4 > 0) colour_pass_cta_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
@@ -285,13 +297,15 @@ void load_vector(const HostLevel& h, const double* f, const double* g, double* b
 __global__ void k_copy_constrained(const Lvl<D, K, double> L, const double* __restrict__ r, double* __restrict__ z) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= L.ndof) return;
+  r += blockIdx.y * L.ndof;   // vector blockIdx.y of nvec, ndof apart
+  z += blockIdx.y * L.ndof;
   int idx[D];
   const int comp = decode(L, g, idx);
   if (is_constrained(L, comp, idx)) z[g] = r[g];
 }
 
-void copy_constrained(const HostLevel& h, const double* r, double* z, cudaStream_t s) {
-  k_copy_constrained<<<blocks(h.ndof, 256), 256, 0, s>>>(mk<double>(h), r, z);
+void copy_constrained(const HostLevel& h, const double* r, double* z, int nvec, cudaStream_t s) {
+  k_copy_constrained<<<dim3(blocks(h.ndof, 256), nvec), 256, 0, s>>>(mk<double>(h), r, z);
 }
 
 DKOps make_ops() {

@@ -24,6 +24,12 @@ struct HostLevel {
   void* R0;              // colour-pass tables: gather segments, lane plans and row maps of the
                          // warp-per-patch pass, followed by those of the block-per-patch pass
   int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch
+  // problems of one shape stored one after another (grouped batches): rhs_prob
+  // vectors per problem (0: a single problem), coefficients c_prob cells
+  // apart, the inverses of colour col s_prob[col] bytes apart
+  int rhs_prob;
+  int64_t c_prob;
+  int64_t s_prob[27];
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   void* X;               // level vectors in the working precision
@@ -67,8 +73,8 @@ struct DKOps {
                            cudaStream_t);
   // load vector of cellwise-constant f (D x ncell) and g (ncell, may be null), FP64
   void (*load_vector)(const HostLevel&, const double* f, const double* g, double* b, cudaStream_t);
-  // z[g] = r[g] on the constrained dofs (FP64)
-  void (*copy_constrained)(const HostLevel&, const double* r, double* z, cudaStream_t);
+  // z[g] = r[g] on the constrained dofs (FP64), nvec vectors ndof apart
+  void (*copy_constrained)(const HostLevel&, const double* r, double* z, int nvec, cudaStream_t);
 };
 
 // Records msg as the text of mg_last_error() and returns s.
@@ -125,5 +131,9 @@ void launch_seg_scale(const double* a, const double* scale, double* out, const S
 constexpr int DENSE_CHUNKS = 64;
 void launch_dense_apply(int f32, const void* Bd, int64_t n, const void* b, void* z, void* partial, int nrhs,
                         cudaStream_t);
+// The same for nprob problems with rhs_prob vectors each: problem q uses the
+// matrix Bd + q bd_stride elements and partial + q 4 DENSE_CHUNKS n.
+void launch_dense_apply_grouped(int f32, const void* Bd, int64_t bd_stride, int64_t n, const void* b, void* z,
+                                void* partial, int nprob, int rhs_prob, cudaStream_t);
 
 }  // namespace mgd

@@ -311,9 +311,9 @@ int check_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& wh
 
 template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
-    k_colour_pass_cta(const Lvl<D, K, T> L, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
+    k_colour_pass_cta(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
-                      int* __restrict__ err, int64_t vs) {
+                      int* __restrict__ err, int64_t vs, const ProbStride ps) {
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
@@ -326,6 +326,11 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   const int64_t p = blockIdx.x;
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
+  // the problem of this block's right-hand sides: its coefficients and inverses
+  const int64_t prob = ps.of((int64_t)blockIdx.y * NR);
+  Lvl<D, K, T> L = L0;
+  L.c += prob * ps.c;
+  S = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(S) + prob * ps.s_bytes);
   int v[D];
   geom_vertex<D>(cg, (uint32_t)p, v);
   const int type = patch_type<D>(v, L.n);

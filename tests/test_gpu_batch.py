@@ -86,3 +86,57 @@ def test_batched_solve_converges_every_system(oracle_hierarchies):
             assert s.converged == 1
             res = np.linalg.norm(A @ xh[seg] - b[seg]) / np.linalg.norm(b[seg])
             assert res <= 1.01e-8, (p, rr, res)
+
+
+# Problems of one shape run as one group (storage one after another, one
+# launch per kernel for the whole group); two shapes, in contiguous or
+# interleaved order, with 1, 2 or 4 right-hand sides per problem.
+GROUP_SHAPES = {"a": (4, 3, 1, 0.01), "b": (2, 4, 0, 1.0)}   # (n_coarse, n_levels, degree, mu)
+
+
+def _group_problems(order, precision):
+    probs, hier = [], []
+    for i, key in enumerate(order):
+        n0, L, k, mu = GROUP_SHAPES[key]
+        n = n0 * 2 ** (L - 1)
+        c = inputs.lognormal_c(n, 2, 1.0 + 0.5 * i, n / 4, 40 + i)
+        probs.append(dict(dim=2, n_coarse=n0, n_levels=L, degree=k, mu=mu, c=torch.as_tensor(c, device="cuda"),
+                          precision=precision))
+        hier.append(mg.Hierarchy(2, n0, L, k, mu, c))
+    return probs, hier
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 4])
+@pytest.mark.parametrize("order", ["aaabb", "ababa"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_grouped_batch_matches_oracle(precision, tol, order, nrhs):
+    probs, hier = _group_problems(order, precision)
+    B = mgdarcy.Batch(probs, nrhs=nrhs)
+    total = B.total()
+    r = np.random.default_rng(6).standard_normal(total)
+    z = torch.zeros(total, dtype=torch.float64, device="cuda")
+    B.vcycle(torch.as_tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    zh = z.cpu().numpy()
+    for p, H in enumerate(hier):
+        nd, off, _ = B.layout(p)
+        for rr in range(nrhs):
+            seg = slice(off + rr * nd, off + (rr + 1) * nd)
+            zo = mg.vcycle(H, r[seg])
+            err = np.linalg.norm(zh[seg] - zo) / np.linalg.norm(zo)
+            assert err < tol, (p, rr, err)
+
+
+def test_group_launches_once_per_kernel():
+    """A V-cycle of three problems of one shape launches as many kernels as
+    one problem's."""
+    def per_vcycle(order):
+        probs, _ = _group_problems(order, "fp32")
+        B = mgdarcy.Batch(probs, nrhs=4)
+        r = torch.zeros(B.total(), dtype=torch.float64, device="cuda")
+        z = torch.zeros_like(r)
+        B.vcycle(r, z)
+        l0 = B.launches()
+        B.vcycle(r, z)
+        return B.launches() - l0
+    assert per_vcycle("aaa") == per_vcycle("a")
