@@ -254,11 +254,13 @@ def bench_batched(args):
     l0 = B.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler()
+    torch.cuda.nvtx.range_push("timed_vcycles")   # lets profilers select the timed region
     e0.record()
     for _ in range(args.steps):
         B.vcycle(r, z)
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     launches = B.launches() - l0
@@ -277,8 +279,11 @@ def bench_batched(args):
             uy = seg[(N + 1) * N:nu].reshape(N + 1, N)
             uy[0, :] = uy[-1, :] = 0.0
     x = torch.zeros_like(r)
-    stats, status = B.solve(torch.as_tensor(b, device="cuda"), x, tol=1e-8, maxit=400, restart=20, check=False)
-    its = [s.iterations for s in stats]
+    if args.no_companions:
+        stats, status = [], -1
+    else:
+        stats, status = B.solve(torch.as_tensor(b, device="cuda"), x, tol=1e-8, maxit=400, restart=20, check=False)
+    its = [s.iterations for s in stats] or [0]
     line = {"metric": METRIC, "value": total * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -287,7 +292,8 @@ def bench_batched(args):
                                    "4 right-hand sides each, one CUDA graph per batched V-cycle, FP32 smoother",
                        "dofs_times_rhs": total, "l2": "inputs larger than L2"},
             "gpu_launches": int(launches), "clocks": clocks, "setup_s": setup_s,
-            "time_to_1e-8": {"ms": stats[0].solve_ms, "converged": bool(status == 0), "systems": len(stats),
+            "time_to_1e-8": {"ms": stats[0].solve_ms if stats else None, "converged": bool(status == 0),
+                             "systems": len(stats),
                              "iterations_max": int(max(its)), "iterations_mean": float(np.mean(its)),
                              "restart": 20}}
     print(json.dumps(line), flush=True)

@@ -87,7 +87,9 @@ typedef struct {
                            (persistent), 2: one thread block per patch,
                            0: per level, the block kernel where the largest
                            colour holds at most 10,000 inverse entries
-                           (n_v^2 per patch) per SM, else the warp kernel,
+                           (n_v^2 per patch) per SM or four or more
+                           right-hand sides share the inverses (batches),
+                           else the warp kernel,
                            3: per level, the faster of the two in a timed
                            trial at setup.                                     */
 } mg_problem;

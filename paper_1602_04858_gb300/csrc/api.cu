@@ -201,7 +201,9 @@ int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - 
 // colour holds at most 10,000 inverse entries (n_v^2 per patch) per SM, warp
 // per patch elsewhere (the crossover measured on GB300: 2-D RT_1 colours of
 // 441 patches and 3-D RT_0 colours of 1,103 favour the block, 2-D RT_1
-// colours of 1,800 patches the warp); 3 times three symmetric smoothing steps of each on
+// colours of 1,800 patches the warp), and block per patch on every level
+// when four or more right-hand sides share the inverses (measured faster on
+// 2-D RT_1 levels of up to 512^2 cells); 3 times three symmetric smoothing steps of each on
 // the level's own vectors (after one untimed step) and keeps the faster, the
 // choice cached per level shape and device (timings taken under a profiler
 // that serialises kernels can flip it).
@@ -219,7 +221,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
         int64_t mx = 0;
         for (int col = 0; col < num_colours(h->d); ++col) mx = std::max(mx, L.count[col]);
         const int64_t nv = h->ops->nv;
-        L.pass_cta = (mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
+        L.pass_cta = (nrhs >= 4 || mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
       } else {
         L.pass_cta = (mode == 2) ? 1 : 0;
       }

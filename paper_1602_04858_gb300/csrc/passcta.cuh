@@ -57,6 +57,8 @@ struct PassShapeC {
   static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
   static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
   static constexpr int OFF_T = ((S_BYTES + SC_BYTES + 15) / 16) * 16;
+  // T data, right-hand sides fastest (entry w of right-hand side rr at w NR + rr):
+  // window, patch rows of b, residual, cells, BF16 row scales
   static constexpr int T_WIN = 0, T_B = NR * WIN, T_R = T_B + NR * NV, T_C = T_R + NR * NV, T_SC = T_C + NC;
   static constexpr int T_N = T_SC + NV;
   static constexpr int OFF_I = ((OFF_T + T_N * (int)sizeof(T) + 15) / 16) * 16;
@@ -309,6 +311,39 @@ int check_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& wh
 
 // --- the kernel -------------------------------------------------------------------
 
+// NR consecutive values (the right-hand sides of one entry) from shared memory.
+template <typename T, int NR>
+__device__ __forceinline__ void ld_rhs(const T* p, T (&o)[NR]) {
+  if constexpr (NR == 4 && sizeof(T) == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    o[0] = q.x;
+    o[1] = q.y;
+    o[2] = q.z;
+    o[3] = q.w;
+  } else if constexpr (NR == 4 && sizeof(T) == 8) {
+    const double2 q0 = *reinterpret_cast<const double2*>(p), q1 = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = q0.x;
+    o[1] = q0.y;
+    o[2] = q1.x;
+    o[3] = q1.y;
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) o[rr] = p[rr];
+  }
+}
+template <typename T, int NR>
+__device__ __forceinline__ void st_rhs(T* p, const T (&v)[NR]) {
+  if constexpr (NR == 4 && sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (NR == 4 && sizeof(T) == 8) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) p[rr] = v[rr];
+  }
+}
+
 template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     k_colour_pass_cta(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
@@ -398,12 +433,15 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   // (2) gather
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
+    T val[NR];
     if (kind[k] == 0) {
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) st[C::T_WIN + rr * WIN + dst[k]] = ok[k] ? x[src[k] + rr * vs] : T(0);
+      for (int rr = 0; rr < NR; ++rr) val[rr] = ok[k] ? x[src[k] + rr * vs] : T(0);
+      st_rhs<T, NR>(st + C::T_WIN + dst[k] * NR, val);
     } else if (kind[k] == 1) {
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) st[C::T_B + rr * NV + dst[k]] = b[src[k] + rr * vs];
+      for (int rr = 0; rr < NR; ++rr) val[rr] = b[src[k] + rr * vs];
+      st_rhs<T, NR>(st + C::T_B + dst[k] * NR, val);
       gidx[dst[k]] = (int)src[k];
       wcol[dst[k]] = aux[k];
     } else if (kind[k] == 2) {
@@ -419,14 +457,19 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   if (row < NV) {
     const T* win = st + C::T_WIN;
 #pragma unroll
-    for (int s = 0; s < ZW; ++s)
+    for (int s = 0; s < ZW; ++s) {
+      T wv[NR];
+      ld_rhs<T, NR>(win + pw[s] * NR, wv);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) acc[rr] += pc[s] * win[rr * WIN + pw[s]];
+      for (int rr = 0; rr < NR; ++rr) acc[rr] += pc[s] * wv[rr];
+    }
 #pragma unroll
     for (int s = 0; s < ZMW; ++s) {
       const T cc = mc[s] * st[C::T_C + mcell[s]];
+      T wv[NR];
+      ld_rhs<T, NR>(win + mw[s] * NR, wv);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * win[rr * WIN + mw[s]];
+      for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * wv[rr];
     }
   }
 #pragma unroll
@@ -450,8 +493,11 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
       srow = (T)sc[row];
       st[C::T_SC + row] = srow;
     }
+    T bv[NR], rv[NR];
+    ld_rhs<T, NR>(st + C::T_B + row * NR, bv);
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) st[C::T_R + rr * NV + row] = (st[C::T_B + rr * NV + row] - acc[rr]) * srow;
+    for (int rr = 0; rr < NR; ++rr) rv[rr] = (bv[rr] - acc[rr]) * srow;
+    st_rhs<T, NR>(st + C::T_R + row * NR, rv);
   }
   __syncthreads();
 
@@ -468,14 +514,13 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     for (int jj = 0; jj < C::JCH; ++jj) {
       const int j = sp + jj * SPL;
       if (j < NV) {
-        T sv[RG];
+        T sv[RG], rj[NR];
         load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
+        ld_rhs<T, NR>(st + C::T_R + j * NR, rj);
 #pragma unroll
-        for (int rr = 0; rr < NR; ++rr) {
-          const T rj = st[C::T_R + rr * NV + j];
+        for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-          for (int r = 0; r < RG; ++r) d[r][rr] += sv[r] * rj;
-        }
+          for (int r = 0; r < RG; ++r) d[r][rr] += sv[r] * rj[rr];
       }
     }
   }
@@ -493,13 +538,15 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
       const int g = gidx[l], wc = wcol[l];
       T scl = T(1);
       if constexpr (C::BF) scl = st[C::T_SC + l];
+      T wv[NR];
+      ld_rhs<T, NR>(st + C::T_WIN + wc * NR, wv);
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) {
         T dv = d[0][rr];
 #pragma unroll
         for (int r = 1; r < RG; ++r)
           if (sp == r) dv = d[r][rr];
-        x[g + rr * vs] = st[C::T_WIN + rr * WIN + wc] + dv * scl;
+        x[g + rr * vs] = wv[rr] + dv * scl;
       }
     }
   }
