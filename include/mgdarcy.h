@@ -85,12 +85,13 @@ typedef struct {
   int pass_kernel;      /* kernel of the colour passes of the smoother (same
                            update up to rounding): 1: one warp per patch
                            (persistent), 2: one thread block per patch,
+                           3: persistent thread blocks, one patch at a time,
                            0: per level, the block kernel where the largest
                            colour holds at most 10,000 inverse entries
                            (n_v^2 per patch) per SM or four or more
                            right-hand sides share the inverses (batches),
                            else the warp kernel,
-                           3: per level, the faster of the two in a timed
+                           4: per level, the fastest of the three in a timed
                            trial at setup.                                     */
 } mg_problem;
 
@@ -286,8 +287,8 @@ mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
 mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v);
 
 /* Colour-pass kernel chosen for `level` (1 <= level <= J) at setup, see
- * mg_problem.pass_kernel: *kernel = 1 (warp per patch) or 2 (block per
- * patch).  Host only. */
+ * mg_problem.pass_kernel: *kernel = 1 (warp per patch), 2 (block per patch)
+ * or 3 (persistent blocks).  Host only. */
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel);
 
 /* Number of kernels the library launched on this handle so far. */

@@ -192,21 +192,24 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, i
 
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
-// Sets the colour-pass kernel of every level.  Both compute the same update
-// up to rounding.  A warp per patch, persistent over the colour, keeps the
-// copies of the patch inverses streaming and suits levels whose passes fill
-// the GPU; a block per patch shortens the latency of one patch update, which
-// is what a pass costs on coarse levels.  Modes: 1 warp per patch, 2 block
-// per patch everywhere; 0 (default) block per patch on levels whose largest
-// colour holds at most 10,000 inverse entries (n_v^2 per patch) per SM, warp
-// per patch elsewhere (the crossover measured on GB300: 2-D RT_1 colours of
-// 441 patches and 3-D RT_0 colours of 1,103 favour the block, 2-D RT_1
-// colours of 1,800 patches the warp), and block per patch on every level
-// when four or more right-hand sides share the inverses (measured faster on
-// 2-D RT_1 levels of up to 512^2 cells); 3 times three symmetric smoothing steps of each on
-// the level's own vectors (after one untimed step) and keeps the faster, the
-// choice cached per level shape and device (timings taken under a profiler
-// that serialises kernels can flip it).
+// Sets the colour-pass kernel of every level (HostLevel::pass_cta: 0 warp
+// per patch, 1 block per patch, 2 persistent blocks).  All compute the same
+// update up to rounding.  A warp per patch, persistent over the colour, keeps
+// the copies of the patch inverses streaming and suits levels whose passes
+// fill the GPU; a block per patch shortens the latency of one patch update,
+// which is what a pass costs on coarse levels; persistent blocks load their
+// tables once and overlap the next patch's copies with the current one.
+// Modes: 1 warp, 2 block, 3 persistent blocks everywhere; 0 (default) block
+// per patch on levels whose largest colour holds at most 10,000 inverse
+// entries (n_v^2 per patch) per SM, warp per patch elsewhere (the crossover
+// measured on GB300: 2-D RT_1 colours of 441 patches and 3-D RT_0 colours of
+// 1,103 favour the block, 2-D RT_1 colours of 1,800 patches the warp), and
+// block per patch on every level when four or more right-hand sides share
+// the inverses (measured faster on 2-D RT_1 levels of up to 512^2 cells);
+// 4 times three symmetric smoothing steps of each kernel on the level's own
+// vectors (after one untimed step) and keeps the fastest, the choice cached
+// per level shape and device (timings taken under a profiler that serialises
+// kernels can change it).
 mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   static std::mutex mu;
   static std::map<std::vector<int>, int> cache;
@@ -214,7 +217,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   const int64_t l0 = h->launches;
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
-    if (mode != 3) {
+    if (mode != 4) {
       if (mode == 0) {
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
@@ -223,7 +226,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
         const int64_t nv = h->ops->nv;
         L.pass_cta = (nrhs >= 4 || mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
       } else {
-        L.pass_cta = (mode == 2) ? 1 : 0;
+        L.pass_cta = mode - 1;
       }
       continue;
     }
@@ -241,8 +244,8 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       CU(cudaEventCreate(&e1));
     }
     const size_t bytes = (size_t)L.ndof * nrhs * h->vbytes();
-    float ms[2] = {0.f, 0.f};
-    for (int var = 0; var < 2; ++var) {
+    float ms[3] = {0.f, 0.f, 0.f};
+    for (int var = 0; var < 3; ++var) {
       L.pass_cta = var;
       CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
       CU(cudaMemsetAsync(L.B, 0, bytes, h->stream));
@@ -253,7 +256,9 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       CU(cudaEventSynchronize(e1));
       CU(cudaEventElapsedTime(&ms[var], e0, e1));
     }
-    L.pass_cta = ms[1] < ms[0] ? 1 : 0;
+    L.pass_cta = 0;
+    for (int var = 1; var < 3; ++var)
+      if (ms[var] < ms[L.pass_cta]) L.pass_cta = var;
     CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
     std::lock_guard<std::mutex> g(mu);
     cache[key] = L.pass_cta;
@@ -432,7 +437,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
-  if (p->pass_kernel < 0 || p->pass_kernel > 3) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (p->pass_kernel < 0 || p->pass_kernel > 4) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -699,7 +704,7 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
 
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
   if (!h || level < 1 || level > h->J || !kernel) return fail(MG_ERR_INVALID_ARG, "bad level or argument");
-  *kernel = h->lv[level].pass_cta ? 2 : 1;
+  *kernel = h->lv[level].pass_cta + 1;
   return MG_OK;
 }
 

@@ -181,6 +181,39 @@ void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, 
                      pstride(h, colour));
 }
 
+// Persistent blocks: at most as many as are resident at once, each walking
+// its sequence of patches.
+template <typename T, typename TS, int NR>
+void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err,
+                         int groups, cudaStream_t s) {
+  using C = PassShapeC<D, K, T, TS, NR>;
+  static int cap = [] {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass_ctap<D, K, T, TS, NR>, C::NT, 0);
+    return (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
+  }();
+  // the blocks of all right-hand-side groups share the device
+  int64_t nb = (cap + groups - 1) / groups;
+  if (nb > h.count[colour]) nb = h.count[colour];
+  if (nb < 1) nb = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nb, groups);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
+  cudaLaunchKernelEx(&cfg, k_colour_pass_ctap<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour),
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     pstride(h, colour));
+}
+
 // Right-hand sides in groups of four share each S_v load; the rest one by one.
 template <typename T, typename TS>
 void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int nrhs,
@@ -189,6 +222,11 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
   // groups of four right-hand sides must not straddle two problems
   const int g4 = (h.rhs_prob > 0 && h.rhs_prob % 4 != 0) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
   const size_t off = (size_t)4 * g4 * h.ndof;
+  if (h.pass_cta == 2) {
+    if (g4 > 0) colour_pass_ctap_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+    if (rest > 0) colour_pass_ctap_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+    return;
+  }
   if (h.pass_cta) {
     if (g4 > 0) colour_pass_cta_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
     if (rest > 0) colour_pass_cta_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);

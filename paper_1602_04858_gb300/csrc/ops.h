@@ -23,7 +23,8 @@ struct HostLevel {
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
   void* R0;              // colour-pass tables: gather segments, lane plans and row maps of the
                          // warp-per-patch pass, followed by those of the block-per-patch pass
-  int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch
+  int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch,
+                         // 2 persistent blocks, one patch at a time
   // problems of one shape stored one after another (grouped batches): rhs_prob
   // vectors per problem (0: a single problem), coefficients c_prob cells
   // apart, the inverses of colour col s_prob[col] bytes apart

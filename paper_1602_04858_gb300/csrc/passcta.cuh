@@ -64,6 +64,12 @@ struct PassShapeC {
   static constexpr int OFF_I = ((OFF_T + T_N * (int)sizeof(T) + 15) / 16) * 16;
   static constexpr int OFF_BAR = ((OFF_I + 2 * NV * 4 + 15) / 16) * 16;
   static constexpr int SMEM = OFF_BAR + 16;
+  // persistent variant: two inverse buffers, then the same T data and ints
+  static constexpr int SBUF = ((S_BYTES + SC_BYTES + 15) / 16) * 16;
+  static constexpr int P_OFF_T = 2 * SBUF;
+  static constexpr int P_OFF_I = ((P_OFF_T + T_N * (int)sizeof(T) + 15) / 16) * 16;
+  static constexpr int P_OFF_BAR = ((P_OFF_I + 2 * NV * 4 + 15) / 16) * 16;
+  static constexpr int P_SMEM = P_OFF_BAR + 16;   // two mbarriers
   // per-level tables
   static constexpr int NTYPE = W::NTYPE;
   static constexpr size_t TB_ELEM = 0;
@@ -72,7 +78,7 @@ struct PassShapeC {
   static constexpr size_t TAB_BYTES = TB_MASS + W::al16((size_t)NTYPE * ZMW * NT * MASS_BYTES);
   static_assert(NT <= 1024 && NT % 32 == 0, "block of whole warps");
   static_assert(32 % SPL == 0 && LPP * SPL <= NT, "column parts of a row group lie in one warp");
-  static_assert(SMEM <= 48 * 1024, "static shared memory");
+  static_assert(SMEM <= 48 * 1024 && P_SMEM <= 48 * 1024, "static shared memory");
   static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(RG <= 32, "row group fits the shuffle");
 };
@@ -547,6 +553,254 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
         for (int r = 1; r < RG; ++r)
           if (sp == r) dv = d[r][rr];
         x[g + rr * vs] = wv[rr] + dv * scl;
+      }
+    }
+  }
+}
+
+// Persistent variant for levels with many more patches than resident blocks:
+// each block walks the patches blockIdx.x, + gridDim.x, ...; the plan entries
+// and gather descriptors are loaded once, the inverses of the next patch are
+// bulk-copied into the second buffer and its entries gathered into registers
+// while the current patch is computed (patches of one colour never write an
+// entry another one reads).
+template <int D, int K, typename T, typename TS, int NR>
+__global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
+    k_colour_pass_ctap(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
+                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
+                       int* __restrict__ err, int64_t vs, const ProbStride ps) {
+  using C = PassShapeC<D, K, T, TS, NR>;
+  constexpr int NT = C::NT, NV = C::NV, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
+  constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
+  __shared__ __align__(128) unsigned char sm[C::P_SMEM];
+  T* st = reinterpret_cast<T*>(sm + C::P_OFF_T);
+  int* gidx = reinterpret_cast<int*>(sm + C::P_OFF_I);
+  int* wcol = gidx + NV;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + C::P_OFF_BAR);
+  const int tid = threadIdx.x;
+  const int64_t G = gridDim.x;
+  x += (int64_t)blockIdx.y * NR * vs;
+  b += (int64_t)blockIdx.y * NR * vs;
+  const int64_t prob = ps.of((int64_t)blockIdx.y * NR);
+  Lvl<D, K, T> L = L0;
+  L.c += prob * ps.c;
+  S = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(S) + prob * ps.s_bytes);
+  const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
+  // (1) bulk copy of the inverses (and BF16 row scales) of patch q into buffer sb (thread 0)
+  auto issue_S = [&](int64_t q, int sb) {
+    unsigned char* dst = sm + sb * C::SBUF;
+    fence_proxy_async_smem();   // earlier reads of the buffer before the async writes
+    mbar_arrive_expect_tx(bars + sb, (uint32_t)(C::S_BYTES + C::SC_BYTES));
+    bulk_load(dst, S + q * C::SL::STRIDE, C::S_BYTES, bars + sb, pol);
+    if constexpr (C::BF)
+      bulk_load(dst + C::S_BYTES, reinterpret_cast<const float*>(S + count * C::SL::STRIDE) + q * NVP, C::SC_BYTES,
+                bars + sb, pol);
+  };
+  int64_t p = blockIdx.x;
+  if (tid == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    issue_S(p, 0);
+    if (p + G < count) issue_S(p + G, 1);
+  }
+  int v[D];
+  geom_vertex<D>(cg, (uint32_t)p, v);
+  int rtype = patch_type<D>(v, L.n);
+  const int row = tid / C::TPR;
+  T pc[ZW], mc[ZMW];
+  int pw[ZW], mw[ZMW], mcell[ZMW];
+  auto load_plan = [&](int type) {
+    const unsigned char* pp = tabs + C::TB_PLAIN + ((size_t)type * ZW * NT + tid) * PB;
+    const unsigned char* pm = tabs + C::TB_MASS + ((size_t)type * ZMW * NT + tid) * MASS_BYTES;
+#pragma unroll
+    for (int s = 0; s < ZW; ++s) PlainLd<T>::get(pp + (size_t)s * NT * PB, pc[s], pw[s]);
+#pragma unroll
+    for (int s = 0; s < ZMW; ++s) MassLd<T>::get(pm + (size_t)s * NT * MASS_BYTES, mc[s], mw[s], mcell[s]);
+  };
+  load_plan(rtype);
+  // gather descriptors of this thread's entries (the same for every patch)
+  int kind[EPT], dst[EPT], aux[EPT], base[EPT], stp[EPT][D], a0[EPT][D], hi[EPT][D], mm[EPT];
+  {
+    const int4* el = reinterpret_cast<const int4*>(tabs + C::TB_ELEM);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int q = tid + k * NT;
+      kind[k] = -1;
+      dst[k] = aux[k] = base[k] = mm[k] = 0;
+#pragma unroll
+      for (int f = 0; f < D; ++f) stp[k][f] = a0[k][f] = hi[k][f] = 0;
+      if (q < C::NE) {
+        const int4 e0 = __ldg(el + 3 * q), e1 = __ldg(el + 3 * q + 1), e2 = __ldg(el + 3 * q + 2);
+        const int st3[3] = {e0.z, e0.w, e1.x}, a3[3] = {e1.y, e1.z, e1.w}, hi3[3] = {e2.y, e2.z, e2.w};
+        kind[k] = e0.x & 3;
+        dst[k] = e0.x >> 2;
+        base[k] = e0.y;
+        mm[k] = e2.x;
+        aux[k] = e2.y;   // window column of a patch row
+#pragma unroll
+        for (int f = 0; f < D; ++f) {
+          stp[k][f] = st3[f];
+          a0[k][f] = a3[f];
+          hi[k][f] = hi3[f];
+        }
+      }
+    }
+  }
+  // (2) gather of patch q into registers (window entries outside the domain are zero)
+  T gv[EPT][NR];
+  int gsrc[EPT];
+  auto gather = [&](const int (&vq)[D]) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      int64_t sidx = base[k];
+      bool in = true;
+#pragma unroll
+      for (int f = 0; f < D; ++f) {
+        sidx += (int64_t)vq[f] * stp[k][f];
+        const int ix = mm[k] * vq[f] + a0[k][f];
+        in = in && ix >= 0 && ix <= hi[k][f];
+      }
+      gsrc[k] = (int)sidx;
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) {
+        T val = T(0);
+        if (kind[k] == 0 && in) val = x[sidx + rr * vs];
+        else if (kind[k] == 1) val = b[sidx + rr * vs];
+        else if (kind[k] == 2 && rr == 0) val = L.c[sidx];
+        gv[k][rr] = val;
+      }
+    }
+  };
+  __syncthreads();   // barriers initialised
+  pdl_launch_dependents();
+  pdl_wait();        // x and b come from the preceding kernels
+  gather(v);
+
+  for (int it = 0; p < count; ++it, p += G) {
+    const int sb = it & 1;
+    __syncthreads();   // the previous patch is done with its buffers
+    if (tid == 0 && it >= 1 && p + G < count) issue_S(p + G, sb ^ 1);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      if (kind[k] == 0) {
+        st_rhs<T, NR>(st + C::T_WIN + dst[k] * NR, gv[k]);
+      } else if (kind[k] == 1) {
+        st_rhs<T, NR>(st + C::T_B + dst[k] * NR, gv[k]);
+        gidx[dst[k]] = gsrc[k];
+        wcol[dst[k]] = aux[k];
+      } else if (kind[k] == 2) {
+        st[C::T_C + dst[k]] = gv[k][0];
+      }
+    }
+    __syncthreads();
+    const int type = patch_type<D>(v, L.n);
+    if (p + G < count) {   // the next patch's entries load while this one is computed
+      geom_vertex<D>(cg, (uint32_t)(p + G), v);
+      gather(v);
+    }
+    if (type != rtype) {
+      load_plan(type);
+      rtype = type;
+    }
+    // (3) local residual rows, four threads per row
+    T acc[NR];
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
+    if (row < NV) {
+      const T* win = st + C::T_WIN;
+#pragma unroll
+      for (int s = 0; s < ZW; ++s) {
+        T wv[NR];
+        ld_rhs<T, NR>(win + pw[s] * NR, wv);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[rr] += pc[s] * wv[rr];
+      }
+#pragma unroll
+      for (int s = 0; s < ZMW; ++s) {
+        const T cc = mc[s] * st[C::T_C + mcell[s]];
+        T wv[NR];
+        ld_rhs<T, NR>(win + mw[s] * NR, wv);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * wv[rr];
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) {
+      acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 1);
+      acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 2);
+    }
+    // the inverses of this patch (bounded wait; every thread reaches the block barrier)
+    const bool timed_out = !mbar_wait_bounded(bars + sb, (uint32_t)((it >> 1) & 1), 2000000000ull);
+    if (__syncthreads_or(timed_out)) {
+      if (tid == 0) {
+        atomicExch(err, 2);
+        // copies issued for this and the next patch may still land
+        mbar_wait_bounded(bars + sb, (uint32_t)((it >> 1) & 1), 100000000ull);
+        if (p + G < count) mbar_wait_bounded(bars + (sb ^ 1), (uint32_t)(((it + 1) >> 1) & 1), 100000000ull);
+      }
+      return;
+    }
+    const unsigned char* sbuf = sm + sb * C::SBUF;
+    const float* sc = reinterpret_cast<const float*>(sbuf + C::S_BYTES);
+    if (row < NV && (tid % C::TPR) == 0) {
+      T srow = T(1);
+      if constexpr (C::BF) {
+        srow = (T)sc[row];
+        st[C::T_SC + row] = srow;
+      }
+      T bv[NR], rv[NR];
+      ld_rhs<T, NR>(st + C::T_B + row * NR, bv);
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) rv[rr] = (bv[rr] - acc[rr]) * srow;
+      st_rhs<T, NR>(st + C::T_R + row * NR, rv);
+    }
+    __syncthreads();
+    // (4) delta = S_v r
+    const int grp = tid / SPL, sp = tid % SPL;
+    T d[RG][NR];
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+#pragma unroll
+      for (int rr = 0; rr < NR; ++rr) d[r][rr] = T(0);
+    if (grp < C::LPP) {
+      const TS* Sg = reinterpret_cast<const TS*>(sbuf) + grp * RG;
+#pragma unroll
+      for (int jj = 0; jj < C::JCH; ++jj) {
+        const int j = sp + jj * SPL;
+        if (j < NV) {
+          T sv[RG], rj[NR];
+          load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
+          ld_rhs<T, NR>(st + C::T_R + j * NR, rj);
+#pragma unroll
+          for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+            for (int r = 0; r < RG; ++r) d[r][rr] += sv[r] * rj[rr];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = SPL / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < RG; ++r)
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) d[r][rr] += __shfl_xor_sync(0xffffffffu, d[r][rr], o);
+    // (5) x|_v = window copy + delta; thread sp < RG of a group writes row grp RG + sp
+    if (grp < C::LPP && sp < RG) {
+      const int l = grp * RG + sp;
+      if (l < NV) {
+        const int g = gidx[l], wc = wcol[l];
+        T scl = T(1);
+        if constexpr (C::BF) scl = st[C::T_SC + l];
+        T wv[NR];
+        ld_rhs<T, NR>(st + C::T_WIN + wc * NR, wv);
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) {
+          T dv = d[0][rr];
+#pragma unroll
+          for (int r = 1; r < RG; ++r)
+            if (sp == r) dv = d[r][rr];
+          x[g + rr * vs] = wv[rr] + dv * scl;
+        }
       }
     }
   }

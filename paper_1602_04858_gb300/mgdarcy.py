@@ -240,7 +240,7 @@ class Multigrid:
         return cnt.value, nv.value
 
     def pass_kernel(self, level):
-        """Colour-pass kernel of a level: 1 warp per patch, 2 block per patch."""
+        """Colour-pass kernel of a level: 1 warp per patch, 2 block per patch, 3 persistent blocks."""
         k = ctypes.c_int()
         _check(load().mg_level_pass_kernel(self.h, level, ctypes.byref(k)))
         return k.value

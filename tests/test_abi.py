@@ -63,7 +63,7 @@ def _setup(lib, **kw):
     (dict(c=None), 1),
     (dict(dense_level=3), 1),
     (dict(dense_level=-2), 1),
-    (dict(pass_kernel=4), 1),
+    (dict(pass_kernel=5), 1),
     (dict(pass_kernel=-1), 1),
 ])
 def test_setup_rejects_bad_arguments(lib, kw, status):

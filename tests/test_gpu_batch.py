@@ -38,7 +38,7 @@ def oracle_hierarchies():
     return _problems("fp64")[1]
 
 
-@pytest.mark.parametrize("kernel", [0, 3, 1, 2], ids=["rule", "timed", "warp", "block"])
+@pytest.mark.parametrize("kernel", [0, 4, 1, 2, 3], ids=["rule", "timed", "warp", "block", "persistent"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_batched_vcycle_matches_oracle(precision, tol, kernel, oracle_hierarchies):
     probs, _ = _problems(precision, kernel)
@@ -140,3 +140,21 @@ def test_group_launches_once_per_kernel():
         B.vcycle(r, z)
         return B.launches() - l0
     assert per_vcycle("aaa") == per_vcycle("a")
+
+
+def test_persistent_blocks_in_a_large_group():
+    """Sixteen 32^2 RT_1 problems with four right-hand sides: the persistent
+    blocks of each right-hand-side group walk several patches; the FP64
+    batched V-cycle agrees with the warp kernel's to rounding."""
+    probs_w, probs_p = [], []
+    for i in range(16):
+        c = torch.as_tensor(inputs.lognormal_c(32, 2, 1.5, 4.0, 60 + i), device="cuda")
+        for lst, pk in ((probs_w, 1), (probs_p, 3)):
+            lst.append(dict(dim=2, n_coarse=4, n_levels=4, degree=1, mu=0.01, c=c, precision="fp64", pass_kernel=pk))
+    Bw, Bp = mgdarcy.Batch(probs_w, nrhs=4), mgdarcy.Batch(probs_p, nrhs=4)
+    r = torch.as_tensor(np.random.default_rng(8).standard_normal(Bw.total()), device="cuda")
+    zw, zp = torch.zeros_like(r), torch.zeros_like(r)
+    Bw.vcycle(r, zw)
+    Bp.vcycle(r, zp)
+    torch.cuda.synchronize()
+    assert (torch.linalg.norm(zp - zw) / torch.linalg.norm(zw)).item() < 1e-11

@@ -55,9 +55,10 @@ def physical_rhs(L, seed):
 _cache = {}
 
 
-# colour-pass kernels: 1 one warp per patch, 2 one thread block per patch
-KERNELS = [1, 2]
-KERNEL_IDS = ["warp", "block"]
+# colour-pass kernels: 1 one warp per patch, 2 one thread block per patch,
+# 3 persistent thread blocks
+KERNELS = [1, 2, 3]
+KERNEL_IDS = ["warp", "block", "persistent"]
 
 
 def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_kernel=0):
@@ -193,14 +194,15 @@ def test_smoothing_step_fp32_each_kernel(case, kernel):
         assert err < tol, f"level {j}: {err}"
 
 
+@pytest.mark.parametrize("other", [2, 3], ids=["block", "persistent"])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
-def test_colour_pass_kernels_agree(case, precision):
-    """Both kernels read the same stored inverses (BF16 ones included) and
+def test_colour_pass_kernels_agree(case, precision, other):
+    """The kernels read the same stored inverses (BF16 ones included) and
     differ only in FP32 summation order, so their smoothing steps agree within
     twice the FP32 bound FP32_VCYCLE_TOL."""
     _, Gw = build(case, precision=precision, pass_kernel=1)
-    _, Gb = build(case, precision=precision, pass_kernel=2)
+    _, Gb = build(case, precision=precision, pass_kernel=other)
     tol = 2.0 * FP32_VCYCLE_TOL.get(case[0], 1e-5)
     rng = np.random.default_rng(17)
     for j in range(1, case[4]):
@@ -275,7 +277,7 @@ def test_solve_fp64_matches_oracle(case):
     assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) < SOLVE_TOL.get(case[0], 1e-8)
 
 
-@pytest.mark.parametrize("kernel", [0, 3], ids=["rule", "timed"])
+@pytest.mark.parametrize("kernel", [0, 4], ids=["rule", "timed"])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
 def test_mixed_precision_solve_reaches_1e8(case, precision, kernel):
@@ -306,12 +308,32 @@ def test_vcycle_fp32_error(case, kernel):
     assert err < FP32_VCYCLE_TOL.get(case[0], 1e-5), err
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_persistent_blocks_walk_many_patches(precision, tol):
+    """On a 128^2 RT_1 level (1,800 patches per colour, more than the resident
+    blocks) each persistent block updates several patches in turn: its
+    smoothing step agrees with the warp kernel's to rounding."""
+    c = inputs.lognormal_c(128, 2, 2.0, 8.0, 21)
+    Gs = [mgdarcy.Multigrid(2, 4, 6, 1, 0.01, dev(c), precision=precision, dense_level=0, pass_kernel=pk)
+          for pk in (1, 3)]
+    rng = np.random.default_rng(22)
+    for j in (5, 4):
+        nd = Gs[0].ndof(j)
+        x0, b = rng.standard_normal(nd), rng.standard_normal(nd)
+        d = []
+        for G in Gs:
+            x = dev(x0)
+            G.smooth(j, x, dev(b), steps=1)
+            d.append(host(x) - x0)
+        assert np.linalg.norm(d[1] - d[0]) <= tol * np.linalg.norm(d[0]), j
+
+
 def test_pass_kernel_choice():
     """Explicit choices are kept; the default rule takes the block kernel
     where a level's largest colour holds at most 10,000 inverse entries per SM."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     case = CASES[1]
-    for pk, want in ((1, 1), (2, 2)):
+    for pk, want in ((1, 1), (2, 2), (3, 3)):
         _, G = build(case, pass_kernel=pk)
         assert all(G.pass_kernel(j) == want for j in range(1, case[4]))
     _, G = build(case)
