@@ -71,9 +71,11 @@ typedef struct {
   int precision;        /* mg_precision                                        */
   int m_fine;           /* smoothing steps on the finest level, m(J) >= 1      */
   int variable_cycle;   /* 1: m(j) = m(J) 2^(J-j) (Sec. 3.2); 0: m(j) = m(J)   */
-  int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1):
-                           0: harmonic mean of c (= arithmetic mean of the
-                           permeability 1/c), 1: arithmetic mean of c          */
+  int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1,
+                           "arithmetic averaging of permeabilities", where
+                           Sec. 4 calls c's counterpart kappa permeability):
+                           0: arithmetic mean of c, 1: harmonic mean of c
+                           (= arithmetic mean of 1/c)                          */
   int dense_level;      /* the V-cycle B_j of levels 0..j (Sec. 3.2) is a fixed
                            linear map; setup may store it as a dense matrix,
                            computed by running that sub-cycle on the unit

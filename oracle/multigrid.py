@@ -4,8 +4,12 @@
   n_j = n_0 2^j, each level re-discretised (eq. ML-problem) with its own
   penalty sigma_j = (k+1)(k+2)/h_j (Sec. 4.1) and its own coefficient.
 * Coarse coefficient (Sec. 4.1, "arithmetic averaging of permeabilities"):
-  permeability is 1/c, so the coarse c is the harmonic mean of the 2^d
-  children's c (the arithmetic mean of c is available as an option).
+  Sec. 4 calls the coefficient kappa of the zero-order term "permeability"
+  (kappa = 1 in the high-permeability regions), so the averaged quantity is
+  that coefficient: the coarse c is the arithmetic mean of the 2^d
+  children's c (the harmonic mean of c, i.e. the arithmetic mean of 1/c, is
+  available as an option).  With this reading the iteration counts stay flat
+  in h and in the contrast, as Tables 1 and 2 report.
 * Injection I_j (Sec. 3.1): a coarse function is evaluated at the fine nodes.
   Its L2-adjoint acting on residual vectors is the transpose P^T (eq. 3);
   constrained (boundary normal) rows of the restricted residual are zeroed.
@@ -35,7 +39,7 @@ from . import basis
 from .fem import Space, operator
 
 
-def coarsen_c(c: np.ndarray, d: int, mode: str = "harmonic") -> np.ndarray:
+def coarsen_c(c: np.ndarray, d: int, mode: str = "arithmetic") -> np.ndarray:
     """Coefficient of the parent cells from the 2^d children (Sec. 4.1)."""
     n = c.shape[0]
     m = n // 2
@@ -227,7 +231,7 @@ class Level:
 class Hierarchy:
     """Levels 0..J with transfers; ``c_fine`` is the finest-level coefficient."""
 
-    def __init__(self, d, n_coarse, n_levels, k, mu, c_fine, coarse_avg="harmonic"):
+    def __init__(self, d, n_coarse, n_levels, k, mu, c_fine, coarse_avg="arithmetic"):
         self.d, self.k, self.mu = d, k, mu
         cs = [np.asarray(c_fine, dtype=np.float64)]
         for _ in range(n_levels - 1):

@@ -9,8 +9,9 @@ namespace {
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Coarse coefficient from the 2^d children (Sec. 4.1): mode 0 harmonic mean
-// of c (arithmetic mean of the permeability 1/c), mode 1 arithmetic mean of c.
+// Coarse coefficient from the 2^d children (Sec. 4.1): mode 0 arithmetic mean
+// of c (the coefficient Sec. 4 calls permeability), mode 1 harmonic mean of c
+// (arithmetic mean of 1/c).
 __global__ void k_coarsen_c(int d, int nc, const double* __restrict__ cf, double* __restrict__ cc, int mode) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t tot = (int64_t)nc * nc * (d == 3 ? nc : 1);
@@ -23,10 +24,10 @@ __global__ void k_coarsen_c(int d, int nc, const double* __restrict__ cf, double
     for (int b = 0; b < 2; ++b)
       for (int a = 0; a < 2; ++a) {
         const int64_t f = (int64_t)(2 * i + a) + (int64_t)nf * ((2 * j + b) + (int64_t)nf * (2 * l + c));
-        s += (mode == 0) ? 1.0 / cf[f] : cf[f];
+        s += (mode == 1) ? 1.0 / cf[f] : cf[f];
       }
   const double m = (double)(d == 3 ? 8 : 4);
-  cc[g] = (mode == 0) ? m / s : s / m;
+  cc[g] = (mode == 1) ? m / s : s / m;
 }
 
 __global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {

@@ -75,6 +75,43 @@ def channel_c(n: int, count: int, seed: int, c_channel: float = 1.0,
     return np.where(m, c_channel, c_background).astype(np.float64)
 
 
+def inclusions_mask(n: int, seed: int, fraction: float = 0.15) -> np.ndarray:
+    """Isolated rectangular inclusions on an n x n grid (2-D, axis order (y, x)).
+
+    Rectangles with sides drawn from U{n/32 .. n/16} cells (at least 2) are
+    placed at uniform random positions and kept only if they stay one cell
+    clear of every earlier one, until `fraction` of the cells is covered
+    (or 20,000 draws).  Returns a bool array.
+    """
+    g = rng(seed)
+    mask = np.zeros((n, n), dtype=bool)
+    grow = np.zeros((n, n), dtype=bool)   # inclusions dilated by one cell
+    lo, hi = max(2, n // 32), max(3, n // 16)
+    for _ in range(20000):
+        if mask.mean() >= fraction:
+            break
+        w, h = int(g.integers(lo, hi + 1)), int(g.integers(lo, hi + 1))
+        x0, y0 = int(g.integers(0, n - w + 1)), int(g.integers(0, n - h + 1))
+        if grow[y0:y0 + h, x0:x0 + w].any():
+            continue
+        mask[y0:y0 + h, x0:x0 + w] = True
+        grow[max(0, y0 - 1):y0 + h + 1, max(0, x0 - 1):x0 + w + 1] = True
+    return mask
+
+
+def foam_mask(n: int, seed: int, level: float = 1.2) -> np.ndarray:
+    """Foam-like phase: the islands where a Gaussian random field (sigma = 1,
+    correlation length n/40 cells) exceeds `level`; mostly disconnected blobs
+    of irregular shape covering about 12 % of the cells.  2-D bool (y, x)."""
+    return grf(n, 2, 1.0, max(1.0, n / 40.0), seed) > level
+
+
+def refine_cells(a: np.ndarray, factor: int) -> np.ndarray:
+    """Each cell of a 2-D field split into factor x factor equal cells (the
+    same geometry on a finer mesh)."""
+    return np.ascontiguousarray(np.repeat(np.repeat(a, factor, axis=0), factor, axis=1))
+
+
 def normal(shape, seed: int) -> np.ndarray:
     """iid N(0,1) FP64 array."""
     return rng(seed).standard_normal(shape)

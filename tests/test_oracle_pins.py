@@ -220,10 +220,12 @@ def test_galerkin_identity(d, k, nc, mu):
     assert np.max(np.abs(G - Ac.toarray())) < 1e-12 * max(1.0, np.max(np.abs(G)))
 
 
-def test_coarsen_is_arithmetic_mean_of_permeability():
+def test_coarsen_is_arithmetic_mean_of_the_coefficient():
     c = np.array([[1.0, 1.0], [1.0, 1e6]])
-    assert np.isclose(mg.coarsen_c(c, 2)[0, 0], 4.0 / (3.0 + 1e-6), rtol=1e-15)
-    assert np.isclose(mg.coarsen_c(c, 2, "arithmetic")[0, 0], (3 + 1e6) / 4, rtol=1e-15)
+    assert np.isclose(mg.coarsen_c(c, 2)[0, 0], (3 + 1e6) / 4, rtol=1e-15)
+    assert np.isclose(mg.coarsen_c(c, 2, "harmonic")[0, 0], 4.0 / (3.0 + 1e-6), rtol=1e-15)
+    c3 = np.arange(1.0, 9.0).reshape(2, 2, 2)
+    assert np.isclose(mg.coarsen_c(c3, 3)[0, 0, 0], 4.5, rtol=1e-15)
 
 
 # --- smoother and V-cycle ---------------------------------------------------------
