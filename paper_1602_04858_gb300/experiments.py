@@ -21,6 +21,7 @@ u = u_g + u_0 where u_0 solves the same problem with homogeneous boundary
 values and body force -c g (cellwise constant).  The solves below compute u_0.
 
     python -m paper_1602_04858_gb300.experiments [--sizes 128,256,512] [--precision fp32]
+    python -m paper_1602_04858_gb300.experiments --table4
 
 Prints one JSON line per solve and a table of GMRES iterations.
 """
@@ -57,14 +58,15 @@ def coefficient(geometry: str, case: str, contrast: float, n: int, n0: int = 128
 
 def driven_solve(torch, c: np.ndarray, mu: float, degree: int = 0, g=(1.0, 0.0), tol: float = 1e-6,
                  maxit: int = 400, precision: str = "fp32", n_coarse: int = 4, coarse_avg: int = 0):
-    """u_0 of the driven problem (boundary velocity g, f = 0): GMRES statistics,
-    the solution vector (x of u_0, pressure with zero mean) and the handle."""
-    n = c.shape[0]
+    """u_0 of the driven problem (boundary velocity g, f = 0) on the 2-D or 3-D
+    mesh of c: GMRES statistics, the solution vector (x of u_0, pressure with
+    zero mean) and the handle."""
+    d, n = c.ndim, c.shape[0]
     levels = int(np.log2(n // n_coarse)) + 1
     cd = torch.as_tensor(c, device="cuda")
-    G = mgdarcy.Multigrid(2, n_coarse, levels, degree, mu, cd, precision=precision, coarse_avg=coarse_avg)
+    G = mgdarcy.Multigrid(d, n_coarse, levels, degree, mu, cd, precision=precision, coarse_avg=coarse_avg)
     nu, npr = G.sizes()
-    f = torch.stack([-float(g[0]) * cd.reshape(-1), -float(g[1]) * cd.reshape(-1)]).contiguous()
+    f = torch.stack([-float(g[e]) * cd.reshape(-1) for e in range(d)]).contiguous()
     b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
     G.load_vector(f, None, b)
     x = torch.zeros_like(b)
@@ -74,12 +76,41 @@ def driven_solve(torch, c: np.ndarray, mu: float, degree: int = 0, g=(1.0, 0.0),
 
 def add_lift(x: np.ndarray, n: int, degree: int = 0, g=(1.0, 0.0)) -> np.ndarray:
     """u = u_g + u_0: every velocity node of component i gets g_i added."""
+    d = len(g)
     N = n * (degree + 1)
-    nu1 = (N + 1) * N
+    nu1 = (N + 1) * N ** (d - 1)
     y = x.copy()
-    y[:nu1] += g[0]
-    y[nu1:2 * nu1] += g[1]
+    for e in range(d):
+        y[e * nu1:(e + 1) * nu1] += g[e]
     return y
+
+
+def table4(torch, sizes=(64, 128), precision="fp32", sigma=2.0, seed=7):
+    """Analogue of Table 4: 3-D Brinkman (mu = 0.01), RT_0, lognormal c =
+    exp(G) with G ~ GRF(sigma, 4 cells) on 64^3 cells refined to the finer
+    meshes (contrast max c / min c = 1.3e6 for sigma = 2, seed 7; SPE10 itself
+    is not available), boundary data BC1 g = (1, 0, 0) and BC2 g = (0, 1, 0),
+    GMRES to 1e-6, 1e-8, 1e-10."""
+    base = inputs.lognormal_c(64, 3, sigma, 4.0, seed)
+    rows = []
+    for n in sizes:
+        r = n // 64
+        c = np.ascontiguousarray(np.repeat(np.repeat(np.repeat(base, r, 0), r, 1), r, 2))
+        for name, g in (("BC1", (1.0, 0.0, 0.0)), ("BC2", (0.0, 1.0, 0.0))):
+            for tol in (1e-6, 1e-8, 1e-10):
+                st, _, G = driven_solve(torch, c, 0.01, g=g, tol=tol, precision=precision, n_coarse=2)
+                rows.append(dict(table=4, n=n, bc=name, tol=tol, iterations=st.iterations,
+                                 converged=bool(st.converged), rel_residual=st.rel_residual,
+                                 solve_ms=st.solve_ms, contrast=float(c.max() / c.min())))
+                print(json.dumps(rows[-1]), flush=True)
+                del G
+                torch.cuda.empty_cache()
+    print("\nTable 4 analogue: GMRES iterations (3-D Brinkman, lognormal c)")
+    print("| h | BC1 1e-6 | BC2 1e-6 | BC1 1e-8 | BC2 1e-8 | BC1 1e-10 | BC2 1e-10 |")
+    for n in sizes:
+        it = {(r_["bc"], r_["tol"]): r_["iterations"] for r_ in rows if r_["n"] == n}
+        print(f"| 1/{n} | " + " | ".join(str(it[(b, t)]) for t in (1e-6, 1e-8, 1e-10) for b in ("BC1", "BC2")) + " |")
+    return rows
 
 
 def main():
@@ -89,7 +120,11 @@ def main():
     ap.add_argument("--contrasts", default="1e4,1e5,1e6")
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--coarse-avg", type=int, default=0, help="coarse coefficient: 0 arithmetic, 1 harmonic mean of c")
+    ap.add_argument("--table4", action="store_true", help="the 3-D Brinkman analogue of Table 4 instead")
     args = ap.parse_args()
+    if args.table4:
+        table4(torch, precision=args.precision)
+        return
     sizes = [int(s) for s in args.sizes.split(",")]
     contrasts = [float(s) for s in args.contrasts.split(",")]
     table = {}

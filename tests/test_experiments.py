@@ -34,6 +34,17 @@ def small_field(n, seed):
     return np.where(m, 1.0e3, 1.0)
 
 
+def test_constant_lift_reproduces_the_driven_problem_3d():
+    n = 4
+    c = np.exp(np.random.default_rng(5).standard_normal((n, n, n)))
+    L = mg.Level(fem.Space(3, n, 0), 0.01, c, with_patches=False)
+    g = np.array([0.0, 1.0, 0.0])
+    x_drv = direct(L, fem.load_vector(L.S, 0.01, c, g=lambda X: np.tile(g, (X.shape[0], 1))))
+    x_0 = direct(L, fem.load_vector(L.S, 0.01, c, f=lambda X, cv: np.tile(-cv * g, (X.shape[0], 1))))
+    x = experiments.add_lift(x_0, n, 0, tuple(g))
+    assert np.max(np.abs(x - x_drv)) <= 1e-10 * np.max(np.abs(x_drv))
+
+
 @pytest.mark.parametrize("degree", [0, 1])
 @pytest.mark.parametrize("mu", [0.0, 0.01, 1.0])
 def test_constant_lift_reproduces_the_driven_problem(mu, degree):
