@@ -175,7 +175,10 @@ struct PassShape {
   static constexpr int RG = SL::RG;
   static constexpr int NVP = SL::NVP;
   static constexpr int LPP = NVP / RG;                    // row groups of the S_v product
-  static constexpr int GPW = (32 / (4 * LPP)) > 1 ? 32 / (4 * LPP) : 1;   // patches per warp
+  // patches per warp: as many as leave each patch at least 3 (3-D) or 4 (2-D)
+  // column splits of the S_v product, a power of two
+  static constexpr int GPW_RAW = 32 / ((D == 3 ? 3 : 4) * LPP);
+  static constexpr int GPW = GPW_RAW >= 4 ? 4 : (GPW_RAW >= 2 ? 2 : 1);
   static constexpr int LW = 32 / GPW;                     // lanes per patch
   static constexpr int SSPL = LW / LPP;                   // column splits of the S_v product
   static constexpr int JCH = (NV + SSPL - 1) / SSPL;      // columns per split
