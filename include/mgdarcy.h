@@ -95,6 +95,12 @@ typedef struct {
                            else the warp kernel,
                            4: per level, the fastest of the three in a timed
                            trial at setup.                                     */
+  double additive;      /* smoother: 0 the symmetric multiplicative vertex-patch
+                           Schwarz smoother of Sec. 3.3 (the paper's); in
+                           (0, 1]: additive vertex-patch Schwarz with this
+                           damping, all patches on the same residual (a
+                           variant for comparison, not in the paper; 0.25
+                           bounds the overlap of 2-D patches)                  */
 } mg_problem;
 
 typedef struct {

@@ -275,6 +275,21 @@ def smooth_step(L: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray:
     return x
 
 
+def additive_step(L: Level, x: np.ndarray, b: np.ndarray, omega: float) -> np.ndarray:
+    """x + omega sum_v Pi_v^T S_v (b - A_j x)|_v: one additive vertex-patch
+    Schwarz step, every patch on the same residual.  A variant for comparison
+    (the paper's smoother is the multiplicative one of smooth_step); it is
+    symmetric, and omega = 1/4 bounds the overlap of the 2-D patches."""
+    r = b - L.A @ x
+    d = np.zeros_like(x)
+    for entry in L.colours:
+        if entry is None:
+            continue
+        dofs, Sv, _ = entry
+        np.add.at(d, dofs, np.einsum("pij,pj->pi", Sv, r[dofs]))
+    return x + omega * d
+
+
 def smooth_step_sequential(L: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray:
     """The same step applied one patch at a time with a fresh global residual."""
     C = len(L.colours)
@@ -304,31 +319,38 @@ def smoothing_steps(H: Hierarchy, j: int, m_fine: int, variable: bool) -> int:
     return m_fine * (2 ** (H.J - j) if variable else 1)
 
 
-def vcycle_level(H: Hierarchy, j: int, b: np.ndarray, m_fine: int, variable: bool) -> np.ndarray:
-    """B_j b (Sec. 3.2) on the free dofs of level j (constrained entries of b ignored)."""
+def vcycle_level(H: Hierarchy, j: int, b: np.ndarray, m_fine: int, variable: bool,
+                 additive: float = 0.0) -> np.ndarray:
+    """B_j b (Sec. 3.2) on the free dofs of level j (constrained entries of b
+    ignored); additive > 0 smooths with additive_step(omega = additive)."""
     if j == 0:
         return coarse_solve(H, b)
     L = H.levels[j]
     m = smoothing_steps(H, j, m_fine, variable)
+
+    def smooth(x):
+        return additive_step(L, x, b, additive) if additive > 0 else smooth_step(L, x, b)
+
     x = np.zeros_like(b)
     for _ in range(m):
-        x = smooth_step(L, x, b)
+        x = smooth(x)
     r = b - L.A @ x
     r[L.cm] = 0.0
     bc = H.P[j].T @ r
     bc[H.levels[j - 1].cm] = 0.0
-    xc = vcycle_level(H, j - 1, bc, m_fine, variable)
+    xc = vcycle_level(H, j - 1, bc, m_fine, variable, additive)
     x = x + H.P[j] @ xc
     for _ in range(m):
-        x = smooth_step(L, x, b)
+        x = smooth(x)
     return x
 
 
-def vcycle(H: Hierarchy, r: np.ndarray, m_fine: int = 2, variable: bool = True) -> np.ndarray:
+def vcycle(H: Hierarchy, r: np.ndarray, m_fine: int = 2, variable: bool = True,
+           additive: float = 0.0) -> np.ndarray:
     """The preconditioner B_J applied to r; identity on the constrained dofs."""
     LJ = H.levels[-1]
     b = r.copy()
     b[LJ.cm] = 0.0
-    z = vcycle_level(H, H.J, b, m_fine, variable)
+    z = vcycle_level(H, H.J, b, m_fine, variable, additive)
     z[LJ.cm] = r[LJ.cm]
     return z

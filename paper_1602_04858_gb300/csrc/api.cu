@@ -89,6 +89,7 @@ struct mg_handle {
   // a group of grp_nprob problems of one shape run as one (batches): nrhs
   // counts the vectors of all of them, the dense operators are bd_stride
   // elements apart; the storage belongs to the batch
+  double additive = 0.0;   // > 0: additive Schwarz smoothing with this damping (a variant)
   int grp_nprob = 1;
   int64_t bd_stride = 0;
   int64_t launches = 0;
@@ -176,9 +177,27 @@ bool host_constrained(const HostLevel& L, int64_t g) {
   return false;
 }
 
-mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, int steps, int nrhs, cudaStream_t stream) {
+// `steps` smoothing steps on level j for nrhs vectors x, b (acc: a level
+// vector of scratch for the additive variant).  Multiplicative (the paper's,
+// Sec. 3.3): colours 0..C-1, C-2..0 per step.  Additive (h->additive = omega >
+// 0, a variant for comparison): every colour on the same x, then x += acc.
+mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, void* acc, int steps, int nrhs,
+                       cudaStream_t stream) {
   HostLevel& L = h->lv[j];
   const int C = num_colours(h->d);
+  if (h->additive > 0.0) {
+    CU(cudaMemsetAsync(acc, 0, (size_t)L.ndof * nrhs * h->vbytes(), stream));
+    for (int s = 0; s < steps; ++s) {
+      for (int col = 0; col < C; ++col) {
+        if (L.count[col] == 0) continue;
+        h->ops->additive_pass(L, col, L.sprec, L.S[col], x, b, acc, h->additive, h->d_fail, nrhs, stream);
+        ++h->launches;
+      }
+      launch_add_clear(h->f32(), x, acc, L.ndof * nrhs, stream);
+      ++h->launches;
+    }
+    return MG_OK;
+  }
   for (int s = 0; s < steps; ++s) {
     for (int t = 0; t < 2 * C - 1; ++t) {
       const int col = t < C ? t : 2 * C - 2 - t;
@@ -249,9 +268,9 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       L.pass_cta = var;
       CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
       CU(cudaMemsetAsync(L.B, 0, bytes, h->stream));
-      TRY(smooth_steps(h, j, L.X, L.B, 1, nrhs, h->stream));
+      TRY(smooth_steps(h, j, L.X, L.B, L.R, 1, nrhs, h->stream));
       CU(cudaEventRecord(e0, h->stream));
-      TRY(smooth_steps(h, j, L.X, L.B, 3, nrhs, h->stream));
+      TRY(smooth_steps(h, j, L.X, L.B, L.R, 3, nrhs, h->stream));
       CU(cudaEventRecord(e1, h->stream));
       CU(cudaEventSynchronize(e1));
       CU(cudaEventElapsedTime(&ms[var], e0, e1));
@@ -294,7 +313,7 @@ mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cu
   }
   CU(cudaMemsetAsync(vs.X[j], 0, L.ndof * nr * h->vbytes(), stream));
   const int m = m_of(h, j);
-  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], m, nr, stream));
+  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], vs.R[j], m, nr, stream));
   h->ops->residual(L, h->f32(), vs.X[j], vs.B[j], vs.R[j], 1, nr, stream);
   HostLevel& Lc = h->lv[j - 1];
   h->ops->restrict_(L, Lc, h->f32(), vs.R[j], vs.B[j - 1], nr, stream);
@@ -302,7 +321,7 @@ mg_status vcycle_level(mg_handle* h, int j, const VecSet& vs, bool use_dense, cu
   TRY(vcycle_level(h, j - 1, vs, use_dense, stream));
   h->ops->prolong_add(L, Lc, h->f32(), vs.X[j - 1], vs.X[j], nr, stream);
   ++h->launches;
-  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], m, nr, stream));
+  TRY(smooth_steps(h, j, vs.X[j], vs.B[j], vs.R[j], m, nr, stream));
   return MG_OK;
 }
 
@@ -438,6 +457,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
   if (p->pass_kernel < 0 || p->pass_kernel > 4) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -462,6 +482,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   h->m_fine = p->m_fine;
   h->variable = p->variable_cycle ? 1 : 0;
   h->coarse_avg = p->coarse_avg;
+  h->additive = p->additive;
   h->mu = p->mu;
   h->ops = (d == 2) ? (k == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
 
@@ -776,7 +797,7 @@ mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int ste
   if (!h || level < 1 || level > h->J || !x || !b || steps < 0) return fail(MG_ERR_INVALID_ARG, "bad argument");
   TRY(mg_level_load(h, level, x, b));
   HostLevel& L = h->lv[level];
-  TRY(smooth_steps(h, level, L.X, L.B, steps, 1, h->stream));
+  TRY(smooth_steps(h, level, L.X, L.B, L.R, steps, 1, h->stream));
   TRY(mg_level_store(h, level, x));
   return MG_OK;
 }
@@ -1130,6 +1151,7 @@ void release(mg_handle* h, void* p) {
 bool same_shape(const mg_handle* a, const mg_handle* b) {
   if (a->d != b->d || a->k != b->k || a->J != b->J || a->prec != b->prec || a->m_fine != b->m_fine ||
       a->variable != b->variable || a->mu != b->mu || a->Ls != b->Ls || a->nrhs != b->nrhs ||
+      a->additive != b->additive ||
       a->lv[0].n != b->lv[0].n)
     return false;
   for (int j = 0; j <= a->J; ++j)

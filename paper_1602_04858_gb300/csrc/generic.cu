@@ -338,6 +338,19 @@ void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cud
   const int64_t tot = (int64_t)nc * nc * (d == 3 ? nc : 1);
   k_coarsen_c<<<blocks(tot, 256), 256, 0, s>>>(d, nc, cf, cc, mode);
 }
+template <typename T>
+__global__ void k_add_clear(T* __restrict__ x, T* __restrict__ acc, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += acc[i];
+  acc[i] = T(0);
+}
+
+void launch_add_clear(int f32, void* x, void* acc, int64_t n, cudaStream_t s) {
+  if (f32) k_add_clear<float><<<blocks(n, 256), 256, 0, s>>>((float*)x, (float*)acc, n);
+  else k_add_clear<double><<<blocks(n, 256), 256, 0, s>>>((double*)x, (double*)acc, n);
+}
+
 void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t s) { k_d2f<<<blocks(n, 256), 256, 0, s>>>(a, b, n); }
 void launch_f2d(const float* a, double* b, int64_t n, cudaStream_t s) { k_f2d<<<blocks(n, 256), 256, 0, s>>>(a, b, n); }
 

@@ -176,9 +176,50 @@ void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, 
   cfg.attrs = at;
   cfg.numAttrs = 1;
   const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
-  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour),
+  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, false>, mk<T>(h), colour_geom(D, h.n, colour),
                      h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
-                     pstride(h, colour));
+                     pstride(h, colour), (T*)nullptr, T(0));
+}
+
+// Additive variant: acc += omega sum over the colour's patches of the patch
+// corrections on the residual of x (x is not modified).
+template <typename T, typename TS, int NR>
+void additive_pass_nr(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc,
+                      double omega, int* err, int groups, cudaStream_t s) {
+  using C = PassShapeC<D, K, T, TS, NR>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h.count[colour], groups);
+  cfg.blockDim = dim3(C::NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
+  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, true>, mk<T>(h), colour_geom(D, h.n, colour),
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     pstride(h, colour), (T*)acc, (T)omega);
+}
+
+template <typename T, typename TS>
+void additive_pass_t(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc,
+                     double omega, int* err, int nrhs, cudaStream_t s) {
+  if (h.count[colour] == 0) return;
+  const int g4 = (h.rhs_prob > 0 && h.rhs_prob % 4 != 0) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
+  const size_t off = (size_t)4 * g4 * h.ndof;
+  if (g4 > 0) additive_pass_nr<T, TS, 4>(h, colour, S, x, b, acc, omega, err, g4, s);
+  if (rest > 0)
+    additive_pass_nr<T, TS, 1>(h, colour, S, (const T*)x + off, (const T*)b + off, (T*)acc + off, omega, err, rest,
+                               s);
+}
+
+void additive_pass(const HostLevel& h, int colour, int prec, const void* S, const void* x, const void* b, void* acc,
+                   double omega, int* err, int nrhs, cudaStream_t s) {
+  if (prec == P64) additive_pass_t<double, double>(h, colour, S, x, b, acc, omega, err, nrhs, s);
+  else if (prec == P32) additive_pass_t<float, float>(h, colour, S, x, b, acc, omega, err, nrhs, s);
+  else additive_pass_t<float, __nv_bfloat16>(h, colour, S, x, b, acc, omega, err, nrhs, s);
 }
 
 // Persistent blocks: at most as many as are resident at once, each walking
@@ -362,6 +403,7 @@ DKOps make_ops() {
   o.prolong_add = prolong_add;
   o.patch_setup = patch_setup;
   o.colour_pass = colour_pass;
+  o.additive_pass = additive_pass;
   o.coarse_assemble = coarse_assemble;
   o.copy_constrained = copy_constrained;
   o.residual_norm = residual_norm;

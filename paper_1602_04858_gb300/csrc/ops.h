@@ -59,6 +59,10 @@ struct DKOps {
   // the patch inverses sets *err = 2
   void (*colour_pass)(const HostLevel&, int colour, int prec, const void* S, void* x, const void* b, int* err,
                       int nrhs, cudaStream_t);
+  // additive variant of a colour pass: acc += omega sum of the patch corrections
+  // on the residual of x (x unchanged; patches of all colours may share x)
+  void (*additive_pass)(const HostLevel&, int colour, int prec, const void* S, const void* x, const void* b,
+                        void* acc, double omega, int* err, int nrhs, cudaStream_t);
   // per-level colour-pass tables: bytes for storage precision sprec, and their
   // construction on the host (nonzero with a reason if the level is not supported)
   int64_t (*template_elems)(int sprec);
@@ -88,6 +92,8 @@ const DKOps* ops_3_0();
 // --- generic kernels (generic.cu) -------------------------------------------
 void launch_coarsen_c(int d, int nc, const double* cf, double* cc, int mode, cudaStream_t);
 void launch_d2f(const double* a, float* b, int64_t n, cudaStream_t);
+// x += acc; acc = 0 (n entries; f32: float vectors)
+void launch_add_clear(int f32, void* x, void* acc, int64_t n, cudaStream_t);
 void launch_f2d(const float* a, double* b, int64_t n, cudaStream_t);
 void launch_gauss_jordan(double* M, double* E, int n, int nrhs, int* fail, cudaStream_t);
 // x = 0 on level 0, then x[free[i]] = sum_j inv[i][j] b[free[j]]  (f32: float x, b)

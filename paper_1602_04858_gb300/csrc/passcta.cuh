@@ -350,11 +350,14 @@ __device__ __forceinline__ void st_rhs(T* p, const T (&v)[NR]) {
   }
 }
 
-template <int D, int K, typename T, typename TS, int NR>
+// ADD: additive variant (not the paper's smoother): x is only read, and
+// omega delta is added atomically to `sum` instead of updating x|_v, so that
+// the patches of every colour may run on the same x.
+template <int D, int K, typename T, typename TS, int NR, bool ADD = false>
 __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     k_colour_pass_cta(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
-                      int* __restrict__ err, int64_t vs, const ProbStride ps) {
+                      int* __restrict__ err, int64_t vs, const ProbStride ps, T* __restrict__ sum, T omega) {
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
@@ -367,6 +370,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   const int64_t p = blockIdx.x;
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
+  if constexpr (ADD) sum += (int64_t)blockIdx.y * NR * vs;
   // the problem of this block's right-hand sides: its coefficients and inverses
   const int64_t prob = ps.of((int64_t)blockIdx.y * NR);
   Lvl<D, K, T> L = L0;
@@ -552,7 +556,8 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
 #pragma unroll
         for (int r = 1; r < RG; ++r)
           if (sp == r) dv = d[r][rr];
-        x[g + rr * vs] = wv[rr] + dv * scl;
+        if constexpr (ADD) atomicAdd(sum + g + rr * vs, omega * (dv * scl));
+        else x[g + rr * vs] = wv[rr] + dv * scl;
       }
     }
   }

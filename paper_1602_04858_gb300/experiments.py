@@ -22,6 +22,7 @@ values and body force -c g (cellwise constant).  The solves below compute u_0.
 
     python -m paper_1602_04858_gb300.experiments [--sizes 128,256,512] [--precision fp32]
     python -m paper_1602_04858_gb300.experiments --table4
+    python -m paper_1602_04858_gb300.experiments --variants
 
 Prints one JSON line per solve and a table of GMRES iterations.
 """
@@ -113,6 +114,60 @@ def table4(torch, sizes=(64, 128), precision="fp32", sigma=2.0, seed=7):
     return rows
 
 
+def variants(torch, precision="fp32"):
+    """Smoother and cycle variants on two workloads: the paper's symmetric
+    multiplicative Schwarz smoother against additive Schwarz (omega = 1/4,
+    every patch on the same residual: one launch per colour and one update per
+    step instead of 2C - 1 dependent passes), each in the variable cycle
+    (m(J) = 2) and the standard V(2,2) cycle.  Reports GMRES iterations, the
+    V-cycle time and the solve time (CUDA events, GB300)."""
+    cases = []
+    w = inputs.workload("channels_256")
+    cases.append(("channels 256^2 RT_1, random load, 1e-8", w["c"], w["mu"], w["degree"], 1e-8, "random"))
+    cases.append(("inclusions 512^2 RT_0 Darcy, driven (a) 1e6, 1e-6",
+                  coefficient("inclusions", "a", 1e6, 512), 0.0, 0, 1e-6, "driven"))
+    rows = []
+    for name, c, mu, k, tol, kind in cases:
+        n = c.shape[0]
+        for smoother, omega in (("multiplicative", 0.0), ("additive", 0.25)):
+            for cycle, variable in (("variable", True), ("V(2,2)", False)):
+                levels = int(np.log2(n // 4)) + 1
+                cd = torch.as_tensor(c, device="cuda")
+                G = mgdarcy.Multigrid(2, 4, levels, k, mu, cd, precision=precision, variable_cycle=variable,
+                                      additive=omega)
+                nu, npr = G.sizes()
+                b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
+                if kind == "driven":
+                    f = torch.stack([-cd.reshape(-1), 0.0 * cd.reshape(-1)]).contiguous()
+                    G.load_vector(f, None, b)
+                else:
+                    b[:nu] = torch.as_tensor(np.random.default_rng(11).standard_normal(nu), device="cuda")
+                r = torch.as_tensor(np.random.default_rng(1).standard_normal(nu + npr), device="cuda")
+                z = torch.zeros_like(r)
+                for _ in range(3):
+                    G.vcycle(r, z)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    G.vcycle(r, z)
+                e1.record()
+                torch.cuda.synchronize()
+                x = torch.zeros_like(b)
+                st, _ = G.solve(b[:nu].contiguous(), b[nu:].contiguous(), x, tol=tol, maxit=400, check=False)
+                rows.append(dict(case=name, smoother=smoother, cycle=cycle, iterations=st.iterations,
+                                 converged=bool(st.converged), vcycle_ms=e0.elapsed_time(e1) / 10,
+                                 solve_ms=st.solve_ms))
+                print(json.dumps(rows[-1]), flush=True)
+                del G
+                torch.cuda.empty_cache()
+    print("\n| workload | smoother | cycle | iterations | V-cycle ms | solve ms |")
+    for r_ in rows:
+        print(f"| {r_['case']} | {r_['smoother']} | {r_['cycle']} | {r_['iterations']}"
+              f"{'' if r_['converged'] else ' (not converged)'} | {r_['vcycle_ms']:.2f} | {r_['solve_ms']:.1f} |")
+    return rows
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -121,9 +176,13 @@ def main():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--coarse-avg", type=int, default=0, help="coarse coefficient: 0 arithmetic, 1 harmonic mean of c")
     ap.add_argument("--table4", action="store_true", help="the 3-D Brinkman analogue of Table 4 instead")
+    ap.add_argument("--variants", action="store_true", help="smoother and cycle variants instead")
     args = ap.parse_args()
     if args.table4:
         table4(torch, precision=args.precision)
+        return
+    if args.variants:
+        variants(torch, precision=args.precision)
         return
     sizes = [int(s) for s in args.sizes.split(",")]
     contrasts = [float(s) for s in args.contrasts.split(",")]

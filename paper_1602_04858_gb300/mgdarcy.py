@@ -36,7 +36,8 @@ class mg_problem(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n_coarse", ctypes.c_int), ("n_levels", ctypes.c_int),
                 ("degree", ctypes.c_int), ("mu", ctypes.c_double), ("c", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("m_fine", ctypes.c_int), ("variable_cycle", ctypes.c_int),
-                ("coarse_avg", ctypes.c_int), ("dense_level", ctypes.c_int), ("pass_kernel", ctypes.c_int)]
+                ("coarse_avg", ctypes.c_int), ("dense_level", ctypes.c_int), ("pass_kernel", ctypes.c_int),
+                ("additive", ctypes.c_double)]
 
 
 class mg_stats(ctypes.Structure):
@@ -166,12 +167,13 @@ class Multigrid:
     """A level hierarchy on the current CUDA device (mg_setup)."""
 
     def __init__(self, dim, n_coarse, n_levels, degree, mu, c, precision="fp64", m_fine=2,
-                 variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, stream=None):
+                 variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, additive=0.0, stream=None):
         lib = load()
         self._keep = c if not isinstance(c, np.ndarray) else np.ascontiguousarray(c, dtype=np.float64)
         prob = mg_problem(dim, n_coarse, n_levels, degree, float(mu), _ptr(self._keep),
                           PREC[precision] if isinstance(precision, str) else int(precision), int(m_fine),
-                          1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel))
+                          1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel),
+                          float(additive))
         h = ctypes.c_void_p()
         _check(lib.mg_setup(ctypes.byref(prob), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
         self.h = h
@@ -263,7 +265,7 @@ class Batch:
     """Independent problems with nrhs right-hand sides each (mg_setup_batch).
 
     problems: list of dicts with keys dim, n_coarse, n_levels, degree, mu, c
-    (and optionally precision, m_fine, variable_cycle, coarse_avg, dense_level, pass_kernel).
+    (and optionally precision, m_fine, variable_cycle, coarse_avg, dense_level, pass_kernel, additive).
     """
 
     def __init__(self, problems, nrhs=4, stream=None):
@@ -277,7 +279,8 @@ class Batch:
             arr[k] = mg_problem(p["dim"], p["n_coarse"], p["n_levels"], p["degree"], float(p["mu"]), _ptr(c),
                                 PREC[prec] if isinstance(prec, str) else int(prec), int(p.get("m_fine", 2)),
                                 1 if p.get("variable_cycle", True) else 0, int(p.get("coarse_avg", 0)),
-                                int(p.get("dense_level", -1)), int(p.get("pass_kernel", 0)))
+                                int(p.get("dense_level", -1)), int(p.get("pass_kernel", 0)),
+                                float(p.get("additive", 0.0)))
         h = ctypes.c_void_p()
         _check(lib.mg_setup_batch(arr, len(problems), int(nrhs), ctypes.c_void_p(_stream_ptr(stream)),
                                   ctypes.byref(h)))

@@ -44,7 +44,7 @@ def _setup(lib, **kw):
     p = mgdarcy.mg_problem(kw.get("dim", 2), kw.get("n_coarse", 2), kw.get("n_levels", 3), kw.get("degree", 0),
                            kw.get("mu", 1.0), c.ctypes.data if c is not None else None, kw.get("precision", 0),
                            kw.get("m_fine", 2), 1, kw.get("coarse_avg", 0), kw.get("dense_level", 0),
-                           kw.get("pass_kernel", 0))
+                           kw.get("pass_kernel", 0), kw.get("additive", 0.0))
     h = ctypes.c_void_p()
     return lib.mg_setup(ctypes.byref(p), None, ctypes.byref(h))
 
@@ -65,6 +65,9 @@ def _setup(lib, **kw):
     (dict(dense_level=-2), 1),
     (dict(pass_kernel=5), 1),
     (dict(pass_kernel=-1), 1),
+    (dict(additive=-0.1), 1),
+    (dict(additive=1.5), 1),
+    (dict(additive=float("nan")), 1),
 ])
 def test_setup_rejects_bad_arguments(lib, kw, status):
     assert _setup(lib, **kw) == status

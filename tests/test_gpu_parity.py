@@ -61,7 +61,7 @@ KERNELS = [1, 2, 3]
 KERNEL_IDS = ["warp", "block", "persistent"]
 
 
-def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_kernel=0):
+def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_kernel=0, additive=0.0):
     name, d, k, n0, L, mu, cf = case
     nf = n0 * 2 ** (L - 1)
     c = cf(nf)
@@ -70,7 +70,7 @@ def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_
         _cache[key] = mg.Hierarchy(d, n0, L, k, mu, c)
     H = _cache[key]
     G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, m_fine=m_fine, variable_cycle=variable,
-                          dense_level=dense_level, pass_kernel=pass_kernel)
+                          dense_level=dense_level, pass_kernel=pass_kernel, additive=additive)
     return H, G
 
 
@@ -326,6 +326,31 @@ def test_persistent_blocks_walk_many_patches(precision, tol):
             G.smooth(j, x, dev(b), steps=1)
             d.append(host(x) - x0)
         assert np.linalg.norm(d[1] - d[0]) <= tol * np.linalg.norm(d[0]), j
+
+
+@pytest.mark.parametrize("dense_level", [0, -1], ids=["passes", "dense_auto"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_additive_vcycle_parity_fp64(case, dense_level):
+    """The additive Schwarz variant (omega = 0.25, not the paper's smoother):
+    one V-cycle against the oracle's."""
+    H, G = build(case, dense_level=dense_level, additive=0.25)
+    LJ = H.levels[-1]
+    r = np.random.default_rng(23).standard_normal(LJ.S.ndof)
+    z = torch.zeros_like(dev(r))
+    G.vcycle(dev(r), z)
+    assert rel_inf(host(z), mg.vcycle(H, r, additive=0.25)) < 1e-10
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_additive_solve_reaches_1e8(case):
+    H, G = build(case, precision="fp32", additive=0.25)
+    LJ = H.levels[-1]
+    S = LJ.S
+    b = physical_rhs(LJ, 24)
+    x = torch.zeros_like(dev(b))
+    st, _ = G.solve(dev(b[:S.n_u]), dev(b[S.n_u:]), x, tol=1e-8, maxit=400)
+    assert st.converged == 1
+    assert np.linalg.norm(LJ.A @ host(x) - b) <= 1.01e-8 * np.linalg.norm(b)
 
 
 def test_pass_kernel_choice():

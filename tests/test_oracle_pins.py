@@ -416,3 +416,67 @@ def test_h_independent_iterations(k, mu):
         its.append(it)
     assert max(its) - min(its) <= 3, its
     assert its[-1] <= its[0] + 2, its
+
+
+# --- additive vertex-patch Schwarz (a variant for comparison) -----------------------
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_additive_step_is_sum_of_ritz_corrections(d, k):
+    """The additive step against the patch corrections computed one by one as
+    Ritz projections with an explicit basis Z of the patch space (velocity dofs
+    and mean-zero patch pressures, Z = null(w_v^T)), without the stored S_v."""
+    from scipy.linalg import null_space
+    H = _hier(d, k, 2, 3 if d == 2 else 2, 0.2, seed=8)
+    L = H.levels[-1]
+    A = L.A.toarray()
+    rng = np.random.default_rng(9)
+    b = rng.standard_normal(L.S.ndof)
+    x0 = rng.standard_normal(L.S.ndof)
+    r = b - A @ x0
+    total = np.zeros_like(x0)
+    for entry in L.colours:
+        if entry is None:
+            continue
+        dofs, _, _ = entry
+        for p in range(dofs.shape[0]):
+            idx = dofs[p]
+            Z = null_space(L.w[idx][None, :])
+            Av = A[np.ix_(idx, idx)]
+            y = Z @ np.linalg.solve(Z.T @ Av @ Z, Z.T @ r[idx])
+            total[idx] += y
+    omega = 0.3
+    x1 = mg.additive_step(L, x0, b, omega)
+    assert np.max(np.abs(x1 - (x0 + omega * total))) < 1e-10 * np.max(np.abs(x1))
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_additive_step_on_single_patch_mesh_is_exact(d, k):
+    """One patch holds every free dof of a 2^d mesh: with omega = 1 one step solves A x = b."""
+    rng = np.random.default_rng(10)
+    S = fem.Space(d, 2, k)
+    L = mg.Level(S, 0.7, np.exp(rng.standard_normal((2,) * d)))
+    b = rng.standard_normal(S.ndof)
+    b[L.cm] = 0.0
+    b[S.n_u:] -= b[S.n_u:].mean()
+    x = mg.additive_step(L, np.zeros(S.ndof), b, 1.0)
+    assert np.max(np.abs((b - L.A @ x)[L.free])) < 1e-10 * np.max(np.abs(b))
+
+
+@pytest.mark.parametrize("d,k,L", [(2, 0, 3), (2, 1, 3), (3, 0, 2)])
+def test_additive_vcycle_is_symmetric_and_converges(d, k, L):
+    H = _hier(d, k, 2, L, 0.05)
+    LJ = H.levels[-1]
+    N = LJ.S.ndof
+    B = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        B[:, i] = mg.vcycle(H, e, 2, True, additive=0.25)
+    fr = LJ.free
+    Bf = B[np.ix_(fr, fr)]
+    assert np.max(np.abs(Bf - Bf.T)) < 1e-12 * np.max(np.abs(Bf))
+    b = np.random.default_rng(11).standard_normal(N)
+    b[LJ.cm] = 0.0
+    b[LJ.S.n_u:] = 0.0
+    x, its, _ = krylov.fgmres(lambda v: LJ.A @ v, lambda v: mg.vcycle(H, v, 2, True, additive=0.25), b, tol=1e-8)
+    assert np.linalg.norm(LJ.A @ x - b) <= 1.01e-8 * np.linalg.norm(b) and its < 60
