@@ -23,6 +23,7 @@ values and body force -c g (cellwise constant).  The solves below compute u_0.
     python -m paper_1602_04858_gb300.experiments [--sizes 128,256,512] [--precision fp32]
     python -m paper_1602_04858_gb300.experiments --table4
     python -m paper_1602_04858_gb300.experiments --variants
+    python -m paper_1602_04858_gb300.experiments --scale
 
 Prints one JSON line per solve and a table of GMRES iterations.
 """
@@ -168,6 +169,28 @@ def variants(torch, precision="fp32"):
     return rows
 
 
+def scale(torch, precision="fp32"):
+    """Larger meshes and contrast 1e8 (NEXT-4): the driven flow of Tables 1-2
+    on 2048^2 RT_0 cells (12.6 M dofs) and 512^2 RT_1 cells (3.1 M dofs),
+    structures refined from 128^2, GMRES to a 1e-6 reduction."""
+    rows = []
+    for geom, case, model, mu, n, k in (("inclusions", "a", "Darcy", 0.0, 2048, 0),
+                                        ("inclusions", "a", "Brinkman", 0.01, 2048, 0),
+                                        ("connected", "b", "Brinkman", 0.01, 2048, 0),
+                                        ("foam", "a", "Darcy", 0.0, 512, 1),
+                                        ("connected", "a", "Brinkman", 0.01, 512, 1)):
+        c = coefficient(geom, case, 1e8, n)
+        t0 = time.perf_counter()
+        st, x, G = driven_solve(torch, c, mu, degree=k, precision=precision)
+        rows.append(dict(n=n, degree=k, geometry=geom, case=case, model=model, contrast=1e8,
+                         dofs=int(x.numel()), iterations=st.iterations, converged=bool(st.converged),
+                         solve_ms=st.solve_ms, setup_and_solve_s=time.perf_counter() - t0))
+        print(json.dumps(rows[-1]), flush=True)
+        del G, x
+        torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     import torch
     ap = argparse.ArgumentParser()
@@ -177,7 +200,11 @@ def main():
     ap.add_argument("--coarse-avg", type=int, default=0, help="coarse coefficient: 0 arithmetic, 1 harmonic mean of c")
     ap.add_argument("--table4", action="store_true", help="the 3-D Brinkman analogue of Table 4 instead")
     ap.add_argument("--variants", action="store_true", help="smoother and cycle variants instead")
+    ap.add_argument("--scale", action="store_true", help="2048^2 RT_0 and 512^2 RT_1 at contrast 1e8 instead")
     args = ap.parse_args()
+    if args.scale:
+        scale(torch, precision=args.precision)
+        return
     if args.table4:
         table4(torch, precision=args.precision)
         return
