@@ -19,8 +19,9 @@ L2 cache, so every V-cycle streams them from HBM.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 With N > 1 (torchrun), each rank runs an independent replica on its own GPU
-(the single solve has no data-parallel split) and value sums
-the ranks' DoF x V-cycles over the slowest rank's time.
+(a single solve has no data-parallel split: it would need a halo exchange
+after every colour pass) and value sums the ranks' DoF x V-cycles over the
+slowest rank's time.
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ import argparse
 import json
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -72,7 +74,9 @@ class ClockSampler:
 
     def __init__(self, gpu_id=None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples (the summary goes into the JSON line); MG_CLOCKS_DIR picks the folder
+        self.path = os.path.join(os.environ.get("MG_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_bench_{os.getpid()}.csv")
         cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
         if gpu_id:
             cmd += ["-i", gpu_id]
