@@ -187,12 +187,24 @@ __global__ void __launch_bounds__(DENSE_THREADS) k_dense_partial(const T* __rest
   T acc[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) acc[q] = T(0);
-  if (i < n)
-    for (int64_t r = r0; r < r1; ++r) {
-      const T a = Bd[r * n + i];
+  if (i < n) {
+    // eight rows at a time: their loads are issued before the first use
+    int64_t r = r0;
+    for (; r + 8 <= r1; r += 8) {
+      T a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcs(Bd + (r + u) * n + i);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += a[u] * b[q * n + r + u];
+    }
+    for (; r < r1; ++r) {
+      const T a = __ldcs(Bd + r * n + i);
 #pragma unroll
       for (int q = 0; q < NR; ++q) acc[q] += a * b[q * n + r];
     }
+  }
   if (i < n)
 #pragma unroll
     for (int q = 0; q < NR; ++q) partial[((int64_t)q * gridDim.y + blockIdx.y) * n + i] = acc[q];
