@@ -512,52 +512,88 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   __syncthreads();
 
   // (4) delta = S_v r
-  const int grp = tid / SPL, sp = tid % SPL;
-  T d[RG][NR];
+  if constexpr (NR == 1) {
+    const int grp = tid / SPL, sp = tid % SPL;
+    T d[RG];
 #pragma unroll
-  for (int r = 0; r < RG; ++r)
+    for (int r = 0; r < RG; ++r) d[r] = T(0);
+    if (grp < C::LPP) {
+      const TS* Sg = reinterpret_cast<const TS*>(sm) + grp * RG;
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) d[r][rr] = T(0);
-  if (grp < C::LPP) {
-    const TS* Sg = reinterpret_cast<const TS*>(sm) + grp * RG;
+      for (int jj = 0; jj < C::JCH; ++jj) {
+        const int j = sp + jj * SPL;
+        if (j < NV) {
+          T sv[RG];
+          load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
+          const T rj = st[C::T_R + j];
 #pragma unroll
-    for (int jj = 0; jj < C::JCH; ++jj) {
-      const int j = sp + jj * SPL;
-      if (j < NV) {
-        T sv[RG], rj[NR];
-        load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
-        ld_rhs<T, NR>(st + C::T_R + j * NR, rj);
-#pragma unroll
-        for (int rr = 0; rr < NR; ++rr)
-#pragma unroll
-          for (int r = 0; r < RG; ++r) d[r][rr] += sv[r] * rj[rr];
+          for (int r = 0; r < RG; ++r) d[r] += sv[r] * rj;
+        }
       }
     }
-  }
 #pragma unroll
-  for (int o = SPL / 2; o > 0; o >>= 1)
+    for (int o = SPL / 2; o > 0; o >>= 1)
 #pragma unroll
-    for (int r = 0; r < RG; ++r)
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr) d[r][rr] += __shfl_xor_sync(0xffffffffu, d[r][rr], o);
-
-  // (5) x|_v = window copy + delta; thread sp < RG of a group writes row grp RG + sp
-  if (grp < C::LPP && sp < RG) {
-    const int l = grp * RG + sp;
-    if (l < NV) {
-      const int g = gidx[l], wc = wcol[l];
-      T scl = T(1);
-      if constexpr (C::BF) scl = st[C::T_SC + l];
-      T wv[NR];
-      ld_rhs<T, NR>(st + C::T_WIN + wc * NR, wv);
-#pragma unroll
-      for (int rr = 0; rr < NR; ++rr) {
-        T dv = d[0][rr];
+      for (int r = 0; r < RG; ++r) d[r] += __shfl_xor_sync(0xffffffffu, d[r], o);
+    // (5) x|_v = window copy + delta; thread sp < RG of a group writes row grp RG + sp
+    if (grp < C::LPP && sp < RG) {
+      const int l = grp * RG + sp;
+      if (l < NV) {
+        const int g = gidx[l];
+        T scl = T(1);
+        if constexpr (C::BF) scl = st[C::T_SC + l];
+        T dv = d[0];
 #pragma unroll
         for (int r = 1; r < RG; ++r)
-          if (sp == r) dv = d[r][rr];
-        if constexpr (ADD) atomicAdd(sum + g + rr * vs, omega * (dv * scl));
-        else x[g + rr * vs] = wv[rr] + dv * scl;
+          if (sp == r) dv = d[r];
+        if constexpr (ADD) atomicAdd(sum + g, omega * (dv * scl));
+        else x[g] = st[C::T_WIN + wcol[l]] + dv * scl;
+      }
+    }
+  } else {
+    // several right-hand sides: NT / NR threads per right-hand side, thread
+    // (rhs, g, s) owns row group g and the columns s, s + SPR, ... (SPR column
+    // parts, reduced by a short butterfly)
+    constexpr int TPR_RHS = NT / NR;
+    constexpr int SPR = C::pow2_floor(TPR_RHS / C::LPP);
+    constexpr int JCR = (NV + SPR - 1) / SPR;
+    static_assert(TPR_RHS % SPR == 0 && 32 % SPR == 0, "column parts of a row group lie in one warp");
+    const int rhs = tid / TPR_RHS, tr = tid - rhs * TPR_RHS;
+    const int grp = tr / SPR, sp = tr % SPR;
+    T d[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) d[r] = T(0);
+    if (rhs < NR && grp < C::LPP) {
+      const TS* Sg = reinterpret_cast<const TS*>(sm) + grp * RG;
+#pragma unroll
+      for (int jj = 0; jj < JCR; ++jj) {
+        const int j = sp + jj * SPR;
+        if (j < NV) {
+          T sv[RG];
+          load_rg_smem<TS, T>(Sg + (size_t)j * NVP, sv);
+          const T rj = st[C::T_R + j * NR + rhs];
+#pragma unroll
+          for (int r = 0; r < RG; ++r) d[r] += sv[r] * rj;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = SPR / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int r = 0; r < RG; ++r) d[r] += __shfl_xor_sync(0xffffffffu, d[r], o);
+    // (5) x|_v = window copy + delta; thread sp < RG of a group writes row grp RG + sp
+    if (rhs < NR && grp < C::LPP && sp < RG) {
+      const int l = grp * RG + sp;
+      if (l < NV) {
+        const int g = gidx[l];
+        T scl = T(1);
+        if constexpr (C::BF) scl = st[C::T_SC + l];
+        T dv = d[0];
+#pragma unroll
+        for (int r = 1; r < RG; ++r)
+          if (sp == r) dv = d[r];
+        if constexpr (ADD) atomicAdd(sum + g + rhs * vs, omega * (dv * scl));
+        else x[g + rhs * vs] = st[C::T_WIN + wcol[l] * NR + rhs] + dv * scl;
       }
     }
   }
