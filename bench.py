@@ -220,18 +220,20 @@ def end_to_end(args, make, rh, N, barrier, dist, dev, world):
     return e2e_value
 
 
-def batched_workload(per_size=16):
+def batched_workload(per_size=16, sizes=(64, 128, 256, 512), pass_kernel=0):
     """64 independent problems: per_size each of 64^2, 128^2, 256^2, 512^2 cells (coarsest 4^2), RT_1,
-    mu = 0.01, c = exp(G) with G ~ GRF(sigma_i, n/16), sigma_i ~ U[1, 3] (seed 4000 + i)."""
+    mu = 0.01, c = exp(G) with G ~ GRF(sigma_i, n/16), sigma_i ~ U[1, 3] (seed 4000 + i; i counts the
+    problems of all four sizes, so a subset of the sizes keeps the same problems)."""
     from paper_1602_04858_gb300 import inputs
     probs = []
     i = 0
     for n in (64, 128, 256, 512):
         for _ in range(per_size):
-            sig = float(inputs.rng(4000 + i).uniform(1.0, 3.0))
-            c = inputs.lognormal_c(n, 2, sig, n / 16.0, 4000 + i)
-            probs.append(dict(dim=2, n_coarse=4, n_levels=int(np.log2(n // 4)) + 1, degree=1, mu=0.01, c=c,
-                              precision="fp32"))
+            if n in sizes:
+                sig = float(inputs.rng(4000 + i).uniform(1.0, 3.0))
+                c = inputs.lognormal_c(n, 2, sig, n / 16.0, 4000 + i)
+                probs.append(dict(dim=2, n_coarse=4, n_levels=int(np.log2(n // 4)) + 1, degree=1, mu=0.01, c=c,
+                                  precision="fp32", pass_kernel=pass_kernel))
             i += 1
     return probs
 
@@ -241,7 +243,8 @@ def bench_batched(args):
     FP64 FGMRES(20) time to 1e-8; random load vectors (no divergence source, no-slip walls)."""
     import torch
     from paper_1602_04858_gb300 import mgdarcy
-    probs = batched_workload(args.batch_per_size)
+    sizes = tuple(int(v) for v in args.batch_sizes.split(","))
+    probs = batched_workload(args.batch_per_size, sizes, args.pass_kernel)
     for p in probs:
         p["c"] = torch.as_tensor(p["c"], device="cuda")
     t0 = time.perf_counter()
@@ -291,10 +294,11 @@ def bench_batched(args):
     line = {"metric": METRIC, "value": total * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of 64^2, "
-                                   "128^2, 256^2, 512^2 cells), RT_1, mu=0.01, lognormal c with sigma in [1,3], "
-                                   "4 right-hand sides each, one CUDA graph per batched V-cycle, FP32 smoother",
-                       "dofs_times_rhs": total, "l2": "inputs larger than L2"},
+            "config": {"workload": f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of "
+                                   + ", ".join(f"{n}^2" for n in sizes) + " cells), RT_1, mu=0.01, lognormal c "
+                                   "with sigma in [1,3], 4 right-hand sides each, one CUDA graph per batched "
+                                   "V-cycle, FP32 smoother",
+                       "dofs_times_rhs": total, "l2": "inputs larger than L2", "pass_kernel": args.pass_kernel},
             "gpu_launches": int(launches), "clocks": clocks, "setup_s": setup_s,
             "time_to_1e-8": {"ms": stats[0].solve_ms if stats else None, "converged": bool(status == 0),
                              "systems": len(stats),
@@ -313,6 +317,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="channels", choices=["channels", "batched"])
     ap.add_argument("--batch-per-size", type=int, default=16)
+    ap.add_argument("--batch-sizes", default="64,128,256,512", help="batched: the mesh sizes taken (one group each)")
+    ap.add_argument("--pass-kernel", type=int, default=0, help="mg_problem.pass_kernel of the batched problems")
     ap.add_argument("--no-companions", action="store_true",
                     help="skip the FP64/BF16 V-cycles, the solves and the end-to-end pass (profiling runs)")
     args = ap.parse_args()
