@@ -106,7 +106,7 @@ def _group_problems(order, precision):
     return probs, hier
 
 
-@pytest.mark.parametrize("nrhs", [1, 2, 4])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("order", ["aaabb", "ababa"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_grouped_batch_matches_oracle(precision, tol, order, nrhs):
