@@ -465,8 +465,11 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   int64_t ncell = 1;
   for (int e = 0; e < d; ++e) ncell *= nfine;
   // the finest level vector must be addressable with int node indices
-  if ((double)ncell * (k + 1) * (k + 1) * (d == 3 ? (k + 1) : 1) * (d + 1) > 4.0e9)
-    return fail(MG_ERR_INVALID_ARG, "mesh too large");
+  {   // the kernels index a level vector with 32-bit ints
+    const double N = (double)nfine * (k + 1);
+    const double ndof = d * (N + 1.0) * std::pow(N, d - 1) + std::pow(N, d);
+    if (ndof > 2147483647.0) return fail(MG_ERR_INVALID_ARG, "mesh too large: more than 2^31 - 1 dofs");
+  }
 
   mg_handle* h = new mg_handle();
   auto cleanup = [&](mg_status s) {
