@@ -311,7 +311,8 @@ const char* mg_last_error(void);
  * every row of every patch type is reproduced exactly by its lane plan, the
  * plan evaluated on a random window agrees with the row of the operator, and
  * every gather segment addresses the window column, patch row or cell it
- * stands for (zero outside the domain).  Returns 0 if all hold, 1 with a
+ * stands for (zero outside the domain); likewise the row plans and gather
+ * descriptors of the block-per-patch pass.  Returns 0 if all hold, 1 with a
  * reason in msg (msg_len bytes, may be null) otherwise, 2 for unsupported
  * arguments. */
 int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len);

@@ -13,7 +13,10 @@ mg_setup does and checks on the host that
   tables: 1e-5 of the sum of the magnitudes of the terms);
 * every segment entry gathers the window column, patch row or cell it stands
   for, zero outside the domain, and the patch-row segments name the window
-  column of each row.
+  column of each row;
+* the same for the tables of the block-per-patch pass: its four-thread row
+  plans reproduce the row visitor, and its per-entry gather descriptors
+  address every window column, patch row and cell exactly once.
 
 Levels with n = 2 (one patch touching every side), n = 3 (only boundary
 types) and n >= 4 (all types) are covered for every supported (d, k), every
