@@ -357,7 +357,8 @@ def main():
                                  precision=prec, m_fine=2, variable_cycle=variable, stream=stream.cuda_stream)
 
     G = make("fp32")
-    pass_kernels = {j: ("warp" if G.pass_kernel(j) == 1 else "block") for j in range(1, w["n_levels"])}
+    names = {1: "warp", 2: "block", 3: "persistent blocks"}
+    pass_kernels = {j: names[G.pass_kernel(j)] for j in range(1, w["n_levels"])}
     nu, npr = G.sizes()
     N = nu + npr
     rng = np.random.default_rng(11 + rank)
