@@ -384,11 +384,22 @@ def main():
     for _ in range(args.warmup):
         G.vcycle(r, z)
     barrier()
+    # The timed region lasts well under the 200 ms sampling interval of
+    # nvidia-smi, so the sampler runs from 0.6 s of untimed V-cycles (the same
+    # load) through the end of the timed region.
     sampler = ClockSampler(gpu_uuid(torch, dev))
+    t_load = time.perf_counter()
+    while time.perf_counter() - t_load < 0.6:
+        for _ in range(20):
+            G.vcycle(r, z)
+        torch.cuda.synchronize()
+    barrier()
     torch.cuda.nvtx.range_push("timed_vcycles")   # lets profilers select the timed region
     ms, launches = time_vcycles(G, args.steps, 0)
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
+    if clocks is not None:
+        clocks["window"] = "0.6 s of untimed V-cycles, then the timed region"
     value, ms_max = aggregate_throughput(N, args.steps, ms, dist, dev)
 
     # --- dominant kernel: finest-level colour pass ---------------------------------
