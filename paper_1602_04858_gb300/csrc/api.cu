@@ -179,7 +179,11 @@ bool host_constrained(const HostLevel& L, int64_t g) {
 
 // `steps` smoothing steps on level j for nrhs vectors x, b (acc: a level
 // vector of scratch for the additive variant).  Multiplicative (the paper's,
-// Sec. 3.3): colours 0..C-1, C-2..0 per step.  Additive (h->additive = omega >
+// Sec. 3.3): colours 0..C-1, C-2..0 per step.  A step ends and the next one
+// begins with colour 0; the patches of one colour do not couple, so their
+// joint update is an A-orthogonal projection and applying it twice in a row
+// changes nothing: the second is skipped (as the turn colour C-1 is within a
+// step), the same operator up to rounding.  Additive (h->additive = omega >
 // 0, a variant for comparison): every colour on the same x, then x += acc.
 mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, void* acc, int steps, int nrhs,
                        cudaStream_t stream) {
@@ -199,7 +203,7 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, void* acc, i
     return MG_OK;
   }
   for (int s = 0; s < steps; ++s) {
-    for (int t = 0; t < 2 * C - 1; ++t) {
+    for (int t = (s > 0 ? 1 : 0); t < 2 * C - 1; ++t) {
       const int col = t < C ? t : 2 * C - 2 - t;
       if (L.count[col] == 0) continue;
       h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, h->d_fail, nrhs, stream);
