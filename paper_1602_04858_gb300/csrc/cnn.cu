@@ -307,11 +307,10 @@ template <int CIN, int COUT, typename TIN>
 void conv_fwd(const mg_cnn* N, const TIN* x, int relu_in, const __nv_bfloat16* w, const float* bias, int batch,
               __nv_bfloat16* y, float* yf) {
   const size_t smem = sizeof(float) * ((size_t)CIN * (TILE + 2) * (TILE + 2) + (size_t)CIN * 9 * COUT);
-  static bool attr = [&] {
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [&] {
     cudaFuncSetAttribute(k_conv_fwd<CIN, COUT, TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return true;
-  }();
-  (void)attr;
+  });
   const dim3 grid(cdiv(N->n, TILE), cdiv(N->n, TILE), batch);
   k_conv_fwd<CIN, COUT, TIN><<<grid, TILE * TILE, smem, N->stream>>>(x, relu_in, w, bias, N->n, y, yf);
 }
@@ -319,11 +318,10 @@ void conv_fwd(const mg_cnn* N, const TIN* x, int relu_in, const __nv_bfloat16* w
 template <int CIN, int COUT>
 void conv_dgrad(const mg_cnn* N, const float* gz, const __nv_bfloat16* w, const __nv_bfloat16* zin, int batch, float* gx) {
   const size_t smem = sizeof(float) * ((size_t)COUT * (TILE + 2) * (TILE + 2) + (size_t)COUT * 9 * CIN);
-  static bool attr = [&] {
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [&] {
     cudaFuncSetAttribute(k_conv_dgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return true;
-  }();
-  (void)attr;
+  });
   const dim3 grid(cdiv(N->n, TILE), cdiv(N->n, TILE), batch);
   k_conv_dgrad<CIN, COUT><<<grid, TILE * TILE, smem, N->stream>>>(gz, w, zin, N->n, gx);
 }
@@ -331,11 +329,10 @@ void conv_dgrad(const mg_cnn* N, const float* gz, const __nv_bfloat16* w, const 
 template <int CIN, int COUT, typename TIN>
 void conv_wgrad(const mg_cnn* N, const float* gz, const TIN* x, int relu_in, int batch, float* gw) {
   const size_t smem = sizeof(float) * ((size_t)CIN * (TILE + 2) * (TILE + 2) + (size_t)COUT * TILE * TILE);
-  static bool attr = [&] {
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [&] {
     cudaFuncSetAttribute(k_conv_wgrad<CIN, COUT, TIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return true;
-  }();
-  (void)attr;
+  });
   const dim3 grid(cdiv(N->n, TILE), cdiv(N->n, TILE), batch);
   k_conv_wgrad<CIN, COUT, TIN><<<grid, TILE * TILE, smem, N->stream>>>(gz, x, relu_in, N->n, N->partial);
   const int64_t nblk = (int64_t)grid.x * grid.y * grid.z;

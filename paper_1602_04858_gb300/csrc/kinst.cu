@@ -122,11 +122,10 @@ template <typename T, typename TS, int NR>
 void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
                     cudaStream_t s) {
   using P = PassShape<D, K, T, TS, NR>;
-  static bool attr = [] {
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
     cudaFuncSetAttribute(k_colour_pass<D, K, T, TS, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
-    return true;
-  }();
-  (void)attr;
+  });
   // persistent: at most as many blocks as fit on the device at once; each
   // warp then walks a strided sequence of patch groups
   static int cap = [] {

@@ -1,5 +1,6 @@
 // ops.h -- host-side launchers of the per-(d, k) kernels, type-erased.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <string>
@@ -7,6 +8,18 @@
 #include "../../include/mgdarcy.h"
 
 namespace mgd {
+
+// Calls f() the first time it is reached with each device current (function
+// attributes such as the dynamic shared-memory limit are set per device).
+template <class F>
+void once_per_device(std::atomic<unsigned long long>& done, F&& f) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return;
+  f();
+  done.fetch_or(bit);
+}
 
 enum Prec { P64 = 0, P32 = 1, P32B = 2 };   // matches mg_precision
 
