@@ -481,11 +481,12 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 // Colour pass of the multiplicative Schwarz smoother (Sec. 3.3):
 // for every patch v of one colour, x|_v += S_v (b - A x)|_v.
 //
-// A warp owns GPW patches (one for n_v >= 20) and NR right-hand sides and walks
-// a strided sequence of patch groups; while it computes one group it stages the
-// next (two stages per warp):
-//  1. lane 0 bulk-copies the stored inverses S_v into shared memory; they do
-//     not depend on earlier passes, so the first copy precedes the wait for the
+// A warp owns GPW patches (one for 2-D RT_1, two for 3-D RT_0 in FP32, four
+// for 2-D RT_0) and NR right-hand sides and walks a strided sequence of patch
+// groups; while it computes one group it stages the next:
+//  1. lane 0 bulk-copies the stored inverses S_v into one of NSB shared-memory
+//     buffers (two unless they are FP64), NSB groups ahead; they do not depend
+//     on earlier passes, so the first copies precede the wait for the
 //     preceding kernel (programmatic dependent launch);
 //  2. the lanes gather the window of x, the patch rows of b and the 2^D cell
 //     coefficients by contiguous segments (cp.async, zero outside the domain);
