@@ -3,13 +3,14 @@
 * Levels: uniform refinement of the coarse mesh (Sec. 3, first paragraph),
   n_j = n_0 2^j, each level re-discretised (eq. ML-problem) with its own
   penalty sigma_j = (k+1)(k+2)/h_j (Sec. 4.1) and its own coefficient.
-* Coarse coefficient (Sec. 4.1, "arithmetic averaging of permeabilities"):
-  Sec. 4 calls the coefficient kappa of the zero-order term "permeability"
-  (kappa = 1 in the high-permeability regions), so the averaged quantity is
-  that coefficient: the coarse c is the arithmetic mean of the 2^d
-  children's c (the harmonic mean of c, i.e. the arithmetic mean of 1/c, is
-  available as an option).  With this reading the iteration counts stay flat
-  in h and in the contrast, as Tables 1 and 2 report.
+* Coarse coefficient (Sec. 4.1 forms the coarse-level coefficient by an
+  arithmetic mean over the children's permeability; Sec. 4 itself calls the
+  zero-order coefficient kappa the permeability, with kappa = 1 in the
+  high-permeability regions).  The paper adds that other averages could be
+  used, so this is a choice: the coarse c is the arithmetic mean of the 2^d
+  children's c, picked over the harmonic mean of c (the arithmetic mean of
+  1/c, kept as an option) because it gave the smaller iteration counts on the
+  synthetic binary fields and the benchmark field.
 * Injection I_j (Sec. 3.1): a coarse function is evaluated at the fine nodes.
   Its L2-adjoint acting on residual vectors is the transpose P^T (eq. 3);
   constrained (boundary normal) rows of the restricted residual are zeroed.
