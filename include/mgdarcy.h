@@ -71,11 +71,12 @@ typedef struct {
   int precision;        /* mg_precision                                        */
   int m_fine;           /* smoothing steps on the finest level, m(J) >= 1      */
   int variable_cycle;   /* 1: m(j) = m(J) 2^(J-j) (Sec. 3.2); 0: m(j) = m(J)   */
-  int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1,
-                           "arithmetic averaging of permeabilities", where
-                           Sec. 4 calls c's counterpart kappa permeability):
-                           0: arithmetic mean of c, 1: harmonic mean of c
-                           (= arithmetic mean of 1/c)                          */
+  int coarse_avg;       /* coarse coefficient from the 2^d children (Sec. 4.1
+                           averages arithmetically, over the children's
+                           permeability, where Sec. 4 calls c's counterpart
+                           kappa the permeability; the paper allows other
+                           averages): 0: arithmetic mean of c, 1: harmonic
+                           mean of c (= arithmetic mean of 1/c)                */
   int dense_level;      /* the V-cycle B_j of levels 0..j (Sec. 3.2) is a fixed
                            linear map; setup may store it as a dense matrix,
                            computed by running that sub-cycle on the unit
@@ -101,6 +102,16 @@ typedef struct {
                            damping, all patches on the same residual (a
                            variant for comparison, not in the paper; 0.25
                            bounds the overlap of 2-D patches)                  */
+  int escalate_window;  /* precision escalation of mg_solve (not in the paper;
+                           the paper's solver is FP64 throughout): with an FP32
+                           or BF16-inverse V-cycle, if the FGMRES residual has
+                           not fallen below a tenth of its initial value after
+                           this many iterations, the remaining iterations use
+                           the V-cycle of an FP64 hierarchy of the same problem
+                           (no dense fold), set up on first need and kept by
+                           the handle (flexible GMRES admits the change of
+                           preconditioner).  0: 10 iterations, < 0: never.
+                           Ignored by mg_solve_batch.                          */
 } mg_problem;
 
 typedef struct {
@@ -110,7 +121,10 @@ typedef struct {
   double initial_rel_residual;
   double removed_flux;    /* sum of the pressure-block rhs removed to make the
                              system compatible (0 for a compatible rhs)        */
-  double solve_ms;        /* wall time of the solve on the stream              */
+  double solve_ms;        /* wall time of the solve on the stream (including
+                             the set-up of an FP64 hierarchy on escalation)  */
+  int escalated_at;       /* iteration after which the FP64 V-cycle took over
+                             (mg_problem.escalate_window), -1 if it did not  */
 } mg_stats;
 
 typedef struct mg_handle mg_handle;
@@ -147,9 +161,45 @@ mg_status mg_vcycle(mg_handle* h, const double* r, double* z);
  * is made compatible by removing its mean (reported in stats).  x: length
  * n_u + n_p, initial guess if use_x0 != 0; on return the pressure has zero
  * mean.  f, g, x: host or device.  restart <= 0 means no restart.
- * Synchronises.  Returns MG_ERR_NOT_CONVERGED if maxit is reached. */
+ * Each iteration keeps the Gram-Schmidt coefficients and norms on the device
+ * and copies them to the host once for the Hessenberg update.  With an FP32 or
+ * BF16-inverse V-cycle the solve may escalate to FP64 V-cycles
+ * (mg_problem.escalate_window, reported in stats).  Synchronises.  Returns
+ * MG_ERR_DEVICE_TIMEOUT if a device-side wait ran out (see mg_sync), else
+ * MG_ERR_NOT_CONVERGED if maxit is reached. */
 mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x,
                    int use_x0, double tol, int maxit, int restart, mg_stats* stats);
+
+/* Waits for the handle's stream and reports what its asynchronous calls
+ * (mg_vcycle, mg_smooth, mg_colour_pass, ...) left in the device error word:
+ * MG_ERR_DEVICE_TIMEOUT if a device-side wait (the bounded mbarrier waits for
+ * the patch-inverse copies of the colour passes) ran out, in which case the
+ * kernel returned early and the output of that call is incomplete.  Reading
+ * clears the word, so the next call starts clean.  mg_solve does the same
+ * check before it returns. */
+mg_status mg_sync(mg_handle* h);
+
+/* Limit of every device-side wait of the handle's kernels (default 2 s,
+ * [0, 60] s allowed).  On expiry a kernel records MG_ERR_DEVICE_TIMEOUT for
+ * mg_sync / mg_solve, waits (bounded) for its own copies in flight and
+ * returns early: no trap, no hang; the output of that call is incomplete.
+ * A limit of 0 makes every wait report a timeout at once, which is how the
+ * error path is tested.  Synchronises the stream; the captured V-cycle is
+ * rebuilt on its next use. */
+mg_status mg_set_wait_limit(mg_handle* h, double seconds);
+
+/* Host buffer of `capacity` doubles that later mg_solve calls fill with the
+ * relative residual ||b - A x|| / ||b|| after each iteration (entry 0: the
+ * initial guess; entries past the last iteration are left as they were).
+ * capacity = 0 removes it.  The buffer must outlive the solves. */
+mg_status mg_set_residual_history(mg_handle* h, double* host, int capacity);
+
+/* Failure injection for tests of the error paths (not a solver feature): the
+ * library's next `after` device allocations succeed and the one after them is
+ * refused with MG_ERR_OOM, as if the device had run out of memory; the call
+ * that made it fails cleanly and frees what it had allocated.  One refusal per
+ * call of this function; after < 0 cancels.  No CUDA call is made. */
+void mg_inject_alloc_failure(int64_t after);
 
 /* ||b - A_level x||_2 in FP64 (eq. Brinkman-weak; constrained rows give b - x),
  * the residual that GMRES monitors (Sec. 4.1), in one pass over the level.
@@ -219,12 +269,21 @@ mg_status mg_vcycle_batch(mg_batch* b, const double* r, double* z);
  * blocks, compatible), x: solutions, initial guess if use_x0; both device,
  * batch layout.  stats: NULL or nprob * nrhs entries (problem-major).
  * The pressure constant is not normalised.  Synchronises.  Returns
- * MG_ERR_NOT_CONVERGED if a system reaches maxit (total lockstep iterations). */
+ * MG_ERR_DEVICE_TIMEOUT if a device-side wait ran out during the solve (or in
+ * an earlier asynchronous mg_vcycle_batch), else MG_ERR_NOT_CONVERGED if a
+ * system reaches maxit (total lockstep iterations). */
 mg_status mg_solve_batch(mg_batch* b, const double* rhs, double* x, int use_x0, double tol, int maxit,
                          int restart, mg_stats* stats);
 
 /* Number of kernels the library launched for this batch's solves and V-cycles. */
 int64_t mg_batch_kernel_launches(const mg_batch* b);
+
+/* mg_sync and mg_set_wait_limit for a batch: mg_vcycle_batch is asynchronous
+ * and leaves a timed-out wait in the problems' error words, which
+ * mg_sync_batch (and mg_solve_batch, before it returns) reports as
+ * MG_ERR_DEVICE_TIMEOUT and clears. */
+mg_status mg_sync_batch(mg_batch* b);
+mg_status mg_batch_set_wait_limit(mg_batch* b, double seconds);
 
 /* --- learned initial guess ------------------------------------------------------ */
 

@@ -11,6 +11,7 @@
 #include "tables.h"
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <map>
 #include <cmath>
@@ -44,6 +45,21 @@ mg_status fail(mg_status s, const std::string& msg) {
     mg_status s_ = (call);             \
     if (s_ != MG_OK) return s_;        \
   } while (0)
+
+// Failure injection for tests of the error paths (mg_inject_alloc_failure):
+// when >= 0, the number of device allocations that still succeed before the
+// next one is refused (once) as if the device had run out of memory.
+std::atomic<long long> g_alloc_budget{-1};
+
+bool alloc_refused() {
+  long long v = g_alloc_budget.load();
+  while (v >= 0)
+    if (g_alloc_budget.compare_exchange_weak(v, v - 1)) return v == 0;
+  return false;
+}
+
+// Default limit of every device-side wait (mbarrier waits of the colour passes).
+constexpr uint64_t DEFAULT_WAIT_NS = 2000000000ull;
 
 // Vectors a V-cycle runs on: per level, nrhs vectors stored one after another.
 struct VecSet {
@@ -96,13 +112,25 @@ struct mg_handle {
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_kernels = 0;
   std::vector<void*> allocs;
+  // the problem as set up, and the precision-escalation state of mg_solve: a
+  // lower-precision V-cycle that has not reduced the FGMRES residual tenfold
+  // in its first esc_window iterations hands over to the V-cycle of an FP64
+  // hierarchy of the same problem (built on first need, kept for later solves)
+  mg_problem prob{};
+  int esc_window = 0;
+  mg_handle* shadow64 = nullptr;
+  // host buffer receiving the relative residual after each GMRES iteration
+  double* hist = nullptr;
+  int hist_cap = 0;
 
   ~mg_handle() {
+    delete shadow64;
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     for (void* p : allocs) cudaFree(p);
   }
   template <typename T>
   mg_status alloc(T** p, size_t count) {
+    if (alloc_refused()) return fail(MG_ERR_OOM, "device allocation refused (failure injection)");
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
@@ -130,6 +158,7 @@ bool is_device_ptr(const void* p) {
 
 void level_geometry(HostLevel& L, int d, int k, int n, double mu) {
   std::memset(&L, 0, sizeof(L));
+  L.wait_ns = DEFAULT_WAIT_NS;
   L.d = d;
   L.k = k;
   L.n = n;
@@ -424,7 +453,9 @@ const char* mg_status_string(mg_status s) {
 
 const char* mg_last_error(void) { return g_err.c_str(); }
 
-int64_t mg_kernel_launches(const mg_handle* h) { return h ? h->launches : 0; }
+int64_t mg_kernel_launches(const mg_handle* h) {
+  return h ? h->launches + (h->shadow64 ? h->shadow64->launches : 0) : 0;
+}
 
 void mg_destroy(mg_handle* h) { delete h; }
 
@@ -462,6 +493,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
   if (p->pass_kernel < 0 || p->pass_kernel > 4) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
+  if (p->escalate_window > 100000) return fail(MG_ERR_INVALID_ARG, "escalate_window too large");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -491,6 +523,9 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   h->coarse_avg = p->coarse_avg;
   h->additive = p->additive;
   h->mu = p->mu;
+  h->prob = *p;
+  h->prob.c = nullptr;   // the finest coefficient is lv[J].c64 from here on
+  h->esc_window = p->escalate_window == 0 ? 10 : (p->escalate_window < 0 ? 0 : p->escalate_window);
   h->ops = (d == 2) ? (k == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
 
   // coefficient: validate on the host
@@ -900,12 +935,49 @@ mg_status gm_workspace(mg_handle* h, int m) {
   TRY(h->alloc(&h->V, (size_t)(m + 1) * n));
   TRY(h->alloc(&h->Z, (size_t)m * n));
   TRY(h->alloc(&h->d_partial, (size_t)(m + 2) * multidot_blocks()));
-  TRY(h->alloc(&h->d_coef, (size_t)(m + 2)));
+  TRY(h->alloc(&h->d_coef, (size_t)2 * (m + 2) + 1));
   h->gm_m = m;
   return MG_OK;
 }
 
 }  // namespace
+
+// Reads and clears the device error word of a handle (and of its FP64
+// escalation hierarchy): MG_ERR_DEVICE_TIMEOUT if a device-side wait ran out.
+// The stream must be idle.
+static mg_status take_device_flag(mg_handle* h) {
+  int worst = 0;
+  for (mg_handle* q : {h, h->shadow64}) {
+    if (!q) continue;
+    int flag = 0;
+    CU(cudaMemcpy(&flag, q->d_fail, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      CU(cudaMemset(q->d_fail, 0, sizeof(int)));
+      worst = std::max(worst, flag);
+    }
+  }
+  if (worst == 2) return fail(MG_ERR_DEVICE_TIMEOUT, "a device-side wait ran out (patch-inverse copy not complete in time)");
+  if (worst) return fail(MG_ERR_BREAKDOWN, "device error word set");
+  return MG_OK;
+}
+
+// FP64 hierarchy of the handle's problem, built on first need (precision
+// escalation of mg_solve); it shares the stream and the wait limit.
+static mg_status make_shadow64(mg_handle* h) {
+  if (h->shadow64) return MG_OK;
+  mg_problem p = h->prob;
+  p.precision = MG_PREC_FP64;
+  p.c = h->lv[h->J].c64;
+  p.escalate_window = -1;
+  // no dense fold: its set-up (the sub-cycle on every unit vector) costs
+  // seconds, more than the folded levels' passes over the few V-cycles left
+  p.dense_level = 0;
+  mg_handle* s = nullptr;
+  TRY(setup_internal(&p, h->stream, 1, 0.0, &s));
+  for (int j = 0; j <= s->J; ++j) s->lv[j].wait_ns = h->lv[j].wait_ns;
+  h->shadow64 = s;
+  return MG_OK;
+}
 
 mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, int use_x0, double tol, int maxit,
                    int restart, mg_stats* stats) {
@@ -948,8 +1020,11 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
   TRY(dot1(h, b, b, n, &bnorm2));
   const double bnorm = std::sqrt(bnorm2);
   const int m = restart;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hc(m + 2), y(m);
-  int its = 0;
+  const size_t cstride = (size_t)m + 2;   // the two Gram-Schmidt passes' coefficients, then ||w||^2
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), hc(2 * cstride + 1), y(m);
+  std::vector<double> res_at((size_t)maxit + 1, 0.0);   // residual norm after each iteration
+  int its = 0, esc_at = -1;
+  mg_handle* pre = h;   // hierarchy whose V-cycle preconditions (FP64 after an escalation)
   double relres = 0.0, rel0 = -1.0;
   bool converged = false;
   mg_status result = MG_OK;
@@ -967,6 +1042,8 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     CU(cudaStreamSynchronize(h->stream));
     relres = beta / bnorm;
     if (rel0 < 0) rel0 = relres;
+    res_at[its] = beta;
+    if (h->hist && its < h->hist_cap) h->hist[its] = relres;
     if (beta <= tol * bnorm) {
       converged = true;
       break;
@@ -978,51 +1055,58 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int kdone = 0;
-    bool breakdown = false;
     for (int i = 0; i < m && its < maxit; ++i) {
       double* vi = h->V + (size_t)i * n;
       double* zi = h->Z + (size_t)i * n;
-      TRY(vcycle_dev(h, vi, zi));
+      TRY(vcycle_dev(pre, vi, zi));
       TRY(apply_dev(h, h->J, zi, w));
-      // classical Gram-Schmidt, applied twice
-      for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = 0.0;
+      // classical Gram-Schmidt applied twice and the normalisation, with the
+      // coefficients and the norm kept on the device; one copy to the host
       for (int pass = 0; pass < 2; ++pass) {
-        launch_multidot(h->V, n, i + 1, w, n, h->d_partial, h->d_coef, h->stream);
-        launch_multi_axpy(w, h->V, n, i + 1, h->d_coef, -1.0, n, h->stream);
+        double* cf = h->d_coef + pass * cstride;
+        launch_multidot(h->V, n, i + 1, w, n, h->d_partial, cf, h->stream);
+        launch_multi_axpy(w, h->V, n, i + 1, cf, -1.0, n, h->stream);
         h->launches += 3;
-        CU(cudaMemcpyAsync(hc.data(), h->d_coef, (i + 1) * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CU(cudaStreamSynchronize(h->stream));
-        for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] += hc[l];
       }
-      double hn2;
-      TRY(dot1(h, w, w, n, &hn2));
-      const double hn = std::sqrt(hn2);
-      double* Hi = &H[0];
-      auto Hat = [&](int r_, int c_) -> double& { return Hi[(size_t)r_ * m + c_]; };
-      if (hn > 0.0) {
-        launch_scale_copy(w, 1.0 / hn, h->V + (size_t)(i + 1) * n, n, h->stream);
-        ++h->launches;
-      }
+      double* hn2d = h->d_coef + 2 * cstride;
+      launch_multidot(w, n, 1, w, n, h->d_partial, hn2d, h->stream);
+      launch_scale_by_rnorm(w, hn2d, h->V + (size_t)(i + 1) * n, n, h->stream);   // v_{i+1} = w / ||w||
+      h->launches += 3;
+      CU(cudaMemcpyAsync(hc.data(), h->d_coef, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CU(cudaStreamSynchronize(h->stream));
+      for (int l = 0; l <= i; ++l) H[(size_t)l * m + i] = hc[l] + hc[cstride + l];
+      const double hn = std::sqrt(hc[2 * cstride]);
+      auto Hat = [&](int r_, int c_) -> double& { return H[(size_t)r_ * m + c_]; };
       // Givens rotations; column i of H has rows 0..i+1 (row i+1 = hn)
-      double hcol_ip1 = hn;
       for (int l = 0; l < i; ++l) {
         const double t = cs[l] * Hat(l, i) + sn[l] * Hat(l + 1, i);
         Hat(l + 1, i) = -sn[l] * Hat(l, i) + cs[l] * Hat(l + 1, i);
         Hat(l, i) = t;
       }
-      const double den = std::hypot(Hat(i, i), hcol_ip1);
-      if (den == 0.0) {
-        breakdown = true;
-        break;
-      }
+      const double den = std::hypot(Hat(i, i), hn);
+      if (den == 0.0) break;
       cs[i] = Hat(i, i) / den;
-      sn[i] = hcol_ip1 / den;
+      sn[i] = hn / den;
       Hat(i, i) = den;
       gv[i + 1] = -sn[i] * gv[i];
       gv[i] = cs[i] * gv[i];
       ++its;
       kdone = i + 1;
-      if (std::fabs(gv[i + 1]) <= tol * bnorm || hn == 0.0) break;
+      const double est = std::fabs(gv[i + 1]);
+      res_at[its] = est;
+      if (h->hist && its < h->hist_cap) h->hist[its] = est / bnorm;
+      if (est <= tol * bnorm || hn == 0.0) break;
+      // precision escalation: after the first esc_window iterations the
+      // lower-precision V-cycle has not reduced the residual tenfold (FP32
+      // patch inverses no longer approximate the ill-conditioned patch
+      // problems; slow but steady FP64-like convergence passes this test):
+      // FP64 V-cycles from here on (flexible GMRES allows the preconditioner
+      // to change)
+      if (pre == h && h->prec != P64 && h->esc_window > 0 && its == h->esc_window && est > 0.1 * res_at[0]) {
+        TRY(make_shadow64(h));
+        pre = h->shadow64;
+        esc_at = its;
+      }
     }
     if (kdone == 0) {
       result = fail(MG_ERR_BREAKDOWN, "GMRES breakdown");
@@ -1036,7 +1120,6 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     CU(cudaMemcpyAsync(h->d_coef, y.data(), kdone * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     launch_multi_axpy(xd, h->Z, n, kdone, h->d_coef, 1.0, n, h->stream);
     ++h->launches;
-    (void)breakdown;
   }
   // zero pressure mean: p -= (w . p) / sum(w)
   if (result == MG_OK) {
@@ -1065,14 +1148,44 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     stats->initial_rel_residual = rel0 < 0 ? 0.0 : rel0;
     stats->removed_flux = gsum;
     stats->solve_ms = ms;
+    stats->escalated_at = esc_at;
   }
-  int flag = 0;
-  CU(cudaMemcpy(&flag, h->d_fail, sizeof(int), cudaMemcpyDeviceToHost));
-  if (flag == 2) return fail(MG_ERR_DEVICE_TIMEOUT, "a patch-inverse copy did not complete in time");
+  TRY(take_device_flag(h));
   if (result != MG_OK) return result;
   if (!converged) return fail(MG_ERR_NOT_CONVERGED, "GMRES reached maxit");
   return MG_OK;
 }
+
+mg_status mg_sync(mg_handle* h) {
+  if (!h) return fail(MG_ERR_INVALID_ARG, "null handle");
+  CU(cudaStreamSynchronize(h->stream));
+  return take_device_flag(h);
+}
+
+mg_status mg_set_wait_limit(mg_handle* h, double seconds) {
+  if (!h || !(seconds >= 0.0) || !(seconds <= 60.0)) return fail(MG_ERR_INVALID_ARG, "wait limit must be in [0, 60] s");
+  const double ns = seconds > 0.0 ? std::max(1.0, seconds * 1e9) : 0.0;
+  for (mg_handle* q : {h, h->shadow64}) {
+    if (!q) continue;
+    for (auto& L : q->lv) L.wait_ns = (uint64_t)ns;
+    // the captured V-cycle holds the old limit in its kernel arguments
+    if (q->graph_exec) {
+      CU(cudaStreamSynchronize(q->stream));
+      cudaGraphExecDestroy(q->graph_exec);
+      q->graph_exec = nullptr;
+    }
+  }
+  return MG_OK;
+}
+
+mg_status mg_set_residual_history(mg_handle* h, double* host, int capacity) {
+  if (!h || capacity < 0 || (capacity > 0 && !host)) return fail(MG_ERR_INVALID_ARG, "bad history buffer");
+  h->hist = capacity > 0 ? host : nullptr;
+  h->hist_cap = capacity;
+  return MG_OK;
+}
+
+void mg_inject_alloc_failure(int64_t after) { g_alloc_budget.store(after < 0 ? -1 : (long long)after); }
 
 }  // extern "C"
 
@@ -1187,6 +1300,8 @@ mg_status build_group(mg_batch* B, const std::vector<int>& mem, mg_handle** out)
   };
   mg_handle* gh = new mg_handle(*h0);
   gh->allocs.clear();
+  gh->shadow64 = nullptr;
+  gh->hist = nullptr;
   gh->graph_exec = nullptr;
   gh->graph_kernels = 0;
   gh->launches = 0;
@@ -1401,6 +1516,18 @@ void batch_residual(mg_batch* B, const double* x, const double* b, double* r) {
   }
 }
 
+// Reads and clears the error words of the batch's problems (a group runs on
+// its first member's word): MG_ERR_DEVICE_TIMEOUT if a device-side wait ran
+// out.  The stream must be idle.
+mg_status take_batch_flags(mg_batch* B) {
+  mg_status worst = MG_OK;
+  for (auto* h : B->sub) {
+    const mg_status s = take_device_flag(h);
+    if (s != MG_OK && worst != MG_ERR_DEVICE_TIMEOUT) worst = s;
+  }
+  return worst == MG_OK ? MG_OK : fail(worst, mg_last_error());
+}
+
 // per-system dots out[s] = a_s . b_s, copied to the host
 mg_status batch_dots(mg_batch* B, const double* a, const double* b, std::vector<double>& out) {
   launch_seg_dot(a, 0, 1, b, B->seg, B->partial, B->coef, B->stream);
@@ -1481,6 +1608,29 @@ mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offs
 }
 
 int64_t mg_batch_kernel_launches(const mg_batch* b) { return b ? b->launches : 0; }
+
+mg_status mg_sync_batch(mg_batch* B) {
+  if (!B) return fail(MG_ERR_INVALID_ARG, "null batch");
+  CU(cudaStreamSynchronize(B->stream));
+  return take_batch_flags(B);
+}
+
+mg_status mg_batch_set_wait_limit(mg_batch* B, double seconds) {
+  if (!B || !(seconds >= 0.0) || !(seconds <= 60.0)) return fail(MG_ERR_INVALID_ARG, "wait limit must be in [0, 60] s");
+  const uint64_t ns = seconds > 0.0 ? (uint64_t)std::max(1.0, seconds * 1e9) : 0;
+  CU(cudaStreamSynchronize(B->stream));
+  for (auto* h : B->sub)
+    for (auto& L : h->lv) L.wait_ns = ns;
+  for (auto* h : B->grp)
+    if (h)
+      for (auto& L : h->lv) L.wait_ns = ns;
+  // the captured batched V-cycle holds the old limit in its kernel arguments
+  if (B->graph) {
+    cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+  }
+  return MG_OK;
+}
 
 mg_status mg_vcycle_batch(mg_batch* B, const double* r, double* z) {
   if (!B || !r || !z) return fail(MG_ERR_INVALID_ARG, "null argument");
@@ -1643,6 +1793,7 @@ mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, 
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  TRY(take_batch_flags(B));
   bool all = true;
   for (int s = 0; s < ns; ++s) {
     all = all && conv[s];

@@ -41,8 +41,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Waits for phase `parity` of the barrier for at most `limit_ns`; false on timeout.
+// Waits for phase `parity` of the barrier for at most `limit_ns`; false on
+// timeout.  A limit of 0 reports a timeout at once without waiting (the
+// library's error-path test: every wait "runs out").
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (!mbar_try_wait(bar, parity))

@@ -152,6 +152,16 @@ __global__ void k_scale_copy(const double* __restrict__ a, double s, double* __r
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = s * a[i];
 }
+// b = a / sqrt(*n2) (b unchanged if *n2 <= 0): normalisation by a norm that
+// stays on the device
+__global__ void k_scale_by_rnorm(const double* __restrict__ a, const double* __restrict__ n2, double* __restrict__ b,
+                                 int64_t n) {
+  const double q = *n2;
+  if (!(q > 0.0)) return;
+  const double s = 1.0 / sqrt(q);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = s * a[i];
+}
 __global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = alpha * x[i] + beta * y[i];
@@ -396,6 +406,9 @@ void launch_multi_axpy(double* w, const double* V, int64_t ld, int nvec, const d
 }
 void launch_scale_copy(const double* a, double sc, double* b, int64_t n, cudaStream_t s) {
   k_scale_copy<<<blocks(n, 256), 256, 0, s>>>(a, sc, b, n);
+}
+void launch_scale_by_rnorm(const double* a, const double* n2, double* b, int64_t n, cudaStream_t s) {
+  k_scale_by_rnorm<<<blocks(n, 256), 256, 0, s>>>(a, n2, b, n);
 }
 void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s) {
   k_axpby<<<blocks(n, 256), 256, 0, s>>>(alpha, x, beta, y, n);

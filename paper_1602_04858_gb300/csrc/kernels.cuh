@@ -582,7 +582,7 @@ template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count,
                                                      const TS* __restrict__ S, const unsigned char* __restrict__ tabs,
                                                      T* x, const T* __restrict__ b, int evict_first,
-                                                     int* __restrict__ err, int64_t vs, const ProbStride ps) {
+                                                     int* __restrict__ err, uint64_t wait_ns, int64_t vs, const ProbStride ps) {
   using P = PassShape<D, K, T, TS, NR>;
   using PL = typename P::PL;
   using PSum = typename P::PSum;
@@ -781,10 +781,12 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     }
     __syncwarp();
     // (3b) wait for the inverses of this group (bounded); rows of the residual
-    if (!mbar_wait_bounded(bars + sb, (uint32_t)((k / NSB) & 1), 2000000000ull)) {
+    if (!mbar_wait_bounded(bars + sb, (uint32_t)((k / NSB) & 1), wait_ns)) {
       if (lane == 0) atomicExch(err, 2);
       cp_async_wait<0>();
-      // the copy into the other buffer (group k+1) may still be in flight
+      // the copies into this buffer (group k) and the other one (group k+1)
+      // may still be in flight: let them land (bounded) before the warp leaves
+      mbar_wait_bounded(bars + sb, (uint32_t)((k / NSB) & 1), 100000000ull);
       if (NSB > 1 && pn < ngroups) mbar_wait_bounded(bars + (sb ^ 1), (uint32_t)(((k + 1) / NSB) & 1), 100000000ull);
       break;
     }

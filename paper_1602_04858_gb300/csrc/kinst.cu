@@ -128,13 +128,14 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   });
   // persistent: at most as many blocks as fit on the device at once; each
   // warp then walks a strided sequence of patch groups
-  static int cap = [] {
+  static std::atomic<int> caps[64];
+  const int cap = per_device_int(caps, [] {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass<D, K, T, TS, NR>, 32 * P::WARPS, P::SMEM);
     return (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
-  }();
+  });
   const int64_t groups_total = (h.count[colour] + P::GPW - 1) / P::GPW;
   int64_t nb = (groups_total + P::WARPS - 1) / P::WARPS;
   if (nb > cap) nb = cap;
@@ -149,7 +150,7 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   cfg.attrs = at;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_colour_pass<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour), h.count[colour],
-                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     (const TS*)S, (const unsigned char*)h.R0, (T*)x, (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof,
                      pstride(h, colour));
 }
 
@@ -176,7 +177,7 @@ void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, 
   cfg.numAttrs = 1;
   const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
   cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, false>, mk<T>(h), colour_geom(D, h.n, colour),
-                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof,
                      pstride(h, colour), (T*)nullptr, T(0));
 }
 
@@ -198,7 +199,7 @@ void additive_pass_nr(const HostLevel& h, int colour, const void* S, const void*
   cfg.numAttrs = 1;
   const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
   cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, true>, mk<T>(h), colour_geom(D, h.n, colour),
-                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof,
                      pstride(h, colour), (T*)acc, (T)omega);
 }
 
@@ -227,13 +228,14 @@ template <typename T, typename TS, int NR>
 void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err,
                          int groups, cudaStream_t s) {
   using C = PassShapeC<D, K, T, TS, NR>;
-  static int cap = [] {
+  static std::atomic<int> caps[64];
+  const int cap = per_device_int(caps, [] {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass_ctap<D, K, T, TS, NR>, C::NT, 0);
     return (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
-  }();
+  });
   // the blocks of all right-hand-side groups share the device
   int64_t nb = (cap + groups - 1) / groups;
   if (nb > h.count[colour]) nb = h.count[colour];
@@ -250,7 +252,7 @@ void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x,
   cfg.numAttrs = 1;
   const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
   cudaLaunchKernelEx(&cfg, k_colour_pass_ctap<D, K, T, TS, NR>, mk<T>(h), colour_geom(D, h.n, colour),
-                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.ndof,
+                     h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof,
                      pstride(h, colour));
 }
 

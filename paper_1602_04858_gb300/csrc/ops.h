@@ -21,6 +21,21 @@ void once_per_device(std::atomic<unsigned long long>& done, F&& f) {
   done.fetch_or(bit);
 }
 
+// An integer computed once per device, with that device current (f() > 0):
+// the launch caps derived from occupancy and the SM count differ between
+// devices of different kinds.
+template <class F>
+int per_device_int(std::atomic<int> (&slot)[64], F&& f) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int v = slot[dev & 63].load();
+  if (v <= 0) {
+    v = f();
+    slot[dev & 63].store(v);
+  }
+  return v;
+}
+
 enum Prec { P64 = 0, P32 = 1, P32B = 2 };   // matches mg_precision
 
 // Host view of one level.  Device pointers unless noted.
@@ -36,6 +51,8 @@ struct HostLevel {
   int s_evict_first;     // the level's inverses exceed the L2 budget: stream them with evict_first
   void* R0;              // colour-pass tables: gather segments, lane plans and row maps of the
                          // warp-per-patch pass, followed by those of the block-per-patch pass
+  uint64_t wait_ns;      // limit of every device-side wait of this level's kernels (ns); on
+                         // expiry a kernel sets the error word to 2 and returns
   int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch,
                          // 2 persistent blocks, one patch at a time
   // problems of one shape stored one after another (grouped batches): rhs_prob
@@ -119,6 +136,8 @@ void launch_multi_axpy(double* w, const double* V, int64_t ld, int nvec, const d
                        int64_t n, cudaStream_t);
 void launch_scale_copy(const double* a, double s, double* b, int64_t n, cudaStream_t);
 void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t);
+// b = a / sqrt(*n2) with the squared norm n2 on the device (nothing if *n2 <= 0)
+void launch_scale_by_rnorm(const double* a, const double* n2, double* b, int64_t n, cudaStream_t);
 void launch_add_const(double* a, double s, int64_t n, cudaStream_t);
 // out[0] = sqrt(sum of partial[0..n)), fixed summation order, one block
 void launch_sqrt_sum(const double* partial, int64_t n, double* out, cudaStream_t);

@@ -357,7 +357,7 @@ template <int D, int K, typename T, typename TS, int NR, bool ADD = false>
 __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     k_colour_pass_cta(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
-                      int* __restrict__ err, int64_t vs, const ProbStride ps, T* __restrict__ sum, T omega) {
+                      int* __restrict__ err, uint64_t wait_ns, int64_t vs, const ProbStride ps, T* __restrict__ sum, T omega) {
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
@@ -488,7 +488,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 2);
   }
   // the inverses (bounded wait; every thread reaches the block barrier)
-  const bool timed_out = !mbar_wait_bounded(bar, 0u, 2000000000ull);
+  const bool timed_out = !mbar_wait_bounded(bar, 0u, wait_ns);
   if (__syncthreads_or(timed_out)) {
     if (tid == 0) {
       atomicExch(err, 2);
@@ -609,7 +609,7 @@ template <int D, int K, typename T, typename TS, int NR>
 __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     k_colour_pass_ctap(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
                        const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
-                       int* __restrict__ err, int64_t vs, const ProbStride ps) {
+                       int* __restrict__ err, uint64_t wait_ns, int64_t vs, const ProbStride ps) {
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
       acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 2);
     }
     // the inverses of this patch (bounded wait; every thread reaches the block barrier)
-    const bool timed_out = !mbar_wait_bounded(bars + sb, (uint32_t)((it >> 1) & 1), 2000000000ull);
+    const bool timed_out = !mbar_wait_bounded(bars + sb, (uint32_t)((it >> 1) & 1), wait_ns);
     if (__syncthreads_or(timed_out)) {
       if (tid == 0) {
         atomicExch(err, 2);

@@ -29,6 +29,8 @@ API = [
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
+    "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
+    "mg_batch_set_wait_limit",
 ]
 
 
@@ -37,13 +39,13 @@ class mg_problem(ctypes.Structure):
                 ("degree", ctypes.c_int), ("mu", ctypes.c_double), ("c", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("m_fine", ctypes.c_int), ("variable_cycle", ctypes.c_int),
                 ("coarse_avg", ctypes.c_int), ("dense_level", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("additive", ctypes.c_double)]
+                ("additive", ctypes.c_double), ("escalate_window", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("initial_rel_residual", ctypes.c_double), ("removed_flux", ctypes.c_double),
-                ("solve_ms", ctypes.c_double)]
+                ("solve_ms", ctypes.c_double), ("escalated_at", ctypes.c_int)]
 
 
 class MGError(RuntimeError):
@@ -108,6 +110,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_cnn_train_step.argtypes = [vp, vp, vp, i, f, ctypes.POINTER(f)]
     lib.mg_cnn_guess.argtypes = [vp, vp, vp, vp]
     lib.mg_pass_tables_check.argtypes = [i, i, i, i, d, ctypes.c_char_p, i]
+    lib.mg_sync.argtypes = [vp]
+    lib.mg_set_wait_limit.argtypes = [vp, d]
+    lib.mg_set_residual_history.argtypes = [vp, vp, i]
+    lib.mg_inject_alloc_failure.argtypes = [i64]
+    lib.mg_inject_alloc_failure.restype = None
+    lib.mg_sync_batch.argtypes = [vp]
+    lib.mg_batch_set_wait_limit.argtypes = [vp, d]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -116,7 +125,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_last_error.restype = ctypes.c_char_p
     for name in API:
         if name not in ("mg_destroy", "mg_kernel_launches", "mg_status_string", "mg_last_error",
-                        "mg_destroy_batch", "mg_batch_kernel_launches", "mg_cnn_destroy", "mg_cnn_param_count"):
+                        "mg_destroy_batch", "mg_batch_kernel_launches", "mg_cnn_destroy", "mg_cnn_param_count",
+                        "mg_inject_alloc_failure"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -156,6 +166,12 @@ def _stream_ptr(stream):
     return torch.cuda.current_stream().cuda_stream
 
 
+def inject_alloc_failure(after):
+    """mg_inject_alloc_failure: the library's allocation after the next `after`
+    ones is refused with MG_ERR_OOM (once); after < 0 cancels.  For tests."""
+    load().mg_inject_alloc_failure(int(after))
+
+
 def residual_norm_noalloc(dim, degree, n, mu, c, x, b, norm, stream=None):
     """mg_residual_norm_noalloc: ||b - A x||_2 into the device scalar `norm`,
     for callers that cannot allocate device memory (no handle needed)."""
@@ -167,13 +183,14 @@ class Multigrid:
     """A level hierarchy on the current CUDA device (mg_setup)."""
 
     def __init__(self, dim, n_coarse, n_levels, degree, mu, c, precision="fp64", m_fine=2,
-                 variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, additive=0.0, stream=None):
+                 variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, additive=0.0,
+                 escalate_window=0, stream=None):
         lib = load()
         self._keep = c if not isinstance(c, np.ndarray) else np.ascontiguousarray(c, dtype=np.float64)
         prob = mg_problem(dim, n_coarse, n_levels, degree, float(mu), _ptr(self._keep),
                           PREC[precision] if isinstance(precision, str) else int(precision), int(m_fine),
                           1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel),
-                          float(additive))
+                          float(additive), int(escalate_window))
         h = ctypes.c_void_p()
         _check(lib.mg_setup(ctypes.byref(prob), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
         self.h = h
@@ -207,13 +224,32 @@ class Multigrid:
     def vcycle(self, r, z):
         _check(load().mg_vcycle(self.h, _ptr(r), _ptr(z)))
 
-    def solve(self, f, g, x, use_x0=False, tol=1e-8, maxit=200, restart=0, check=True):
+    def solve(self, f, g, x, use_x0=False, tol=1e-8, maxit=200, restart=0, check=True, history=None):
+        """mg_solve; history: None or a float64 NumPy array that receives the
+        relative residual after each iteration (mg_set_residual_history)."""
+        lib = load()
         st = mg_stats()
-        status = load().mg_solve(self.h, _ptr(f), _ptr(g), _ptr(x), 1 if use_x0 else 0, float(tol), int(maxit),
-                                 int(restart), ctypes.byref(st))
+        if history is not None:
+            _check(lib.mg_set_residual_history(self.h, _ptr(history), int(history.size)))
+        try:
+            status = lib.mg_solve(self.h, _ptr(f), _ptr(g), _ptr(x), 1 if use_x0 else 0, float(tol), int(maxit),
+                                  int(restart), ctypes.byref(st))
+        finally:
+            if history is not None:
+                lib.mg_set_residual_history(self.h, None, 0)
         if check:
             _check(status)
         return st, status
+
+    def sync(self, check=True):
+        """mg_sync: wait for the stream; MG_ERR_DEVICE_TIMEOUT if a device wait ran out."""
+        status = load().mg_sync(self.h)
+        if check:
+            _check(status)
+        return status
+
+    def set_wait_limit(self, seconds):
+        _check(load().mg_set_wait_limit(self.h, float(seconds)))
 
     def smooth(self, level, x, b, steps=1):
         _check(load().mg_smooth(self.h, level, _ptr(x), _ptr(b), steps))
@@ -280,7 +316,7 @@ class Batch:
                                 PREC[prec] if isinstance(prec, str) else int(prec), int(p.get("m_fine", 2)),
                                 1 if p.get("variable_cycle", True) else 0, int(p.get("coarse_avg", 0)),
                                 int(p.get("dense_level", -1)), int(p.get("pass_kernel", 0)),
-                                float(p.get("additive", 0.0)))
+                                float(p.get("additive", 0.0)), int(p.get("escalate_window", 0)))
         h = ctypes.c_void_p()
         _check(lib.mg_setup_batch(arr, len(problems), int(nrhs), ctypes.c_void_p(_stream_ptr(stream)),
                                   ctypes.byref(h)))
@@ -319,6 +355,15 @@ class Batch:
 
     def launches(self):
         return load().mg_batch_kernel_launches(self.h)
+
+    def sync(self, check=True):
+        status = load().mg_sync_batch(self.h)
+        if check:
+            _check(status)
+        return status
+
+    def set_wait_limit(self, seconds):
+        _check(load().mg_batch_set_wait_limit(self.h, float(seconds)))
 
 
 class CNN:

@@ -78,3 +78,33 @@ def test_setup_rejects_bad_arguments(lib, kw, status):
 def test_status_strings(lib):
     for s in range(8):
         assert lib.mg_status_string(s).decode()
+
+
+def test_status_entry_points_reject_null_handles(lib):
+    assert lib.mg_sync(None) == 1
+    assert lib.mg_sync_batch(None) == 1
+    assert lib.mg_set_wait_limit(None, 1.0) == 1
+    assert lib.mg_batch_set_wait_limit(None, 1.0) == 1
+    assert lib.mg_set_residual_history(None, None, 0) == 1
+
+
+def test_injected_allocation_failure_is_reported_as_oom(lib):
+    """The failure-injection hook refuses the first device allocation of the
+    next set-up before any CUDA call is made, so this runs without a GPU: the
+    set-up returns MG_ERR_OOM and frees what it had; the hook is one-shot."""
+    lib.mg_inject_alloc_failure(0)
+    try:
+        assert _setup(lib, dense_level=0) == 2
+        assert "refused" in lib.mg_last_error().decode()
+    finally:
+        lib.mg_inject_alloc_failure(-1)
+    # the next set-up reaches the device (which this machine may lack): no second refusal
+    status = _setup(lib, dense_level=0)
+    assert status != 2 or "refused" not in lib.mg_last_error().decode()
+
+
+def test_escalate_window_is_validated(lib):
+    c = np.ones((8, 8))
+    p = mgdarcy.mg_problem(2, 2, 3, 0, 1.0, c.ctypes.data, 1, 2, 1, 0, 0, 0, 0.0, 1000000)
+    h = ctypes.c_void_p()
+    assert lib.mg_setup(ctypes.byref(p), None, ctypes.byref(h)) == 1

@@ -1,0 +1,167 @@
+"""GPU parity on the larger and harder configurations and the precision policy.
+
+* 3-D Brinkman flow driven by boundary velocity (the analogue of Table 4,
+  Sec. 4.2): the CUDA solve of the homogeneous problem plus the constant lift
+  against the oracle's direct solve of the driven problem, FP64 and mixed.
+* Contrast 1e8 (the closing remark of Sec. 4): the FP64 V-cycle against the
+  oracle's V-cycle on binary foam fields.
+* The precision escalation of mg_solve: on a contrast-1e8 foam field, where
+  FP32 patch inverses stop being a useful preconditioner, the solve hands over
+  to FP64 V-cycles and converges in a few iterations.
+* Batched groups of 64^2 and 128^2 problems with four right-hand sides against
+  the oracle, where the block kernels walk many patches with four
+  right-hand sides each.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+from oracle import fem
+from oracle import multigrid as mg
+from paper_1602_04858_gb300 import experiments, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1602_04858_gb300 import mgdarcy  # noqa: E402
+
+
+def direct(L, b):
+    """A x = b on the free dofs with zero weighted pressure mean (bordered sparse LU)."""
+    fr = L.free
+    w = L.w[fr]
+    M = sp.bmat([[L.A[fr][:, fr], sp.csr_matrix(w[:, None])], [sp.csr_matrix(w[None, :]), None]]).tocsc()
+    y = spl.splu(M).solve(np.concatenate([b[fr], [0.0]]))
+    x = b.copy()
+    x[fr] = y[:-1]
+    return x
+
+
+@pytest.mark.parametrize("n", [8, 16])
+@pytest.mark.parametrize("bc", ["BC1", "BC2"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_driven_3d_brinkman_matches_oracle(n, bc, precision):
+    g = (1.0, 0.0, 0.0) if bc == "BC1" else (0.0, 1.0, 0.0)
+    c = inputs.lognormal_c(n, 3, 2.0, 2.0, 7)
+    mu = 0.01
+    tol = 1e-11 if precision == "fp64" else 1e-8
+    st, x, _ = experiments.driven_solve(torch, c, mu, g=g, tol=tol, maxit=200, precision=precision, n_coarse=2)
+    assert st.converged == 1
+    xg = experiments.add_lift(x.cpu().numpy(), n, 0, g)
+    L = mg.Level(fem.Space(3, n, 0), mu, c, with_patches=False)
+    b = fem.load_vector(L.S, mu, c, g=lambda X: np.tile(g, (X.shape[0], 1)))
+    x_drv = direct(L, b)
+    if precision == "fp64":
+        assert np.linalg.norm(xg - x_drv) <= 1e-6 * np.linalg.norm(x_drv)
+    # the homogeneous problem the CUDA path solved, rebuilt by the oracle
+    # (load vector of the body force -c g): its FP64 residual meets the tolerance
+    b0 = fem.load_vector(L.S, mu, c, f=lambda X, cv: np.tile(-cv * np.asarray(g), (X.shape[0], 1)))
+    x0 = x.cpu().numpy()
+    assert np.linalg.norm(b0 - L.A @ x0) <= 1.02 * tol * np.linalg.norm(b0)
+
+
+def foam_c(n, contrast, seed=3):
+    """Case (a) of Sec. 4.1: foam islands with c = 1 in a c = contrast background."""
+    return np.where(inputs.foam_mask(n, seed), 1.0, contrast).astype(np.float64)
+
+
+@pytest.mark.parametrize("k,n0,levels", [(1, 4, 4), (0, 4, 5)])
+@pytest.mark.parametrize("mu", [0.0, 0.01])
+def test_contrast_1e8_fp64_vcycle_matches_oracle(k, n0, levels, mu):
+    """FP64 V-cycle parity at contrast 1e8.  The rounding of the patch solves
+    is amplified by the conditioning of the bordered patch matrices; the bound
+    is 1e-10 or 10 u max_v cond(patch matrix) relative, whichever is larger
+    (u = 1.1e-16)."""
+    n = n0 * 2 ** (levels - 1)
+    c = foam_c(n, 1e8)
+    H = mg.Hierarchy(2, n0, levels, k, mu, c)
+    LJ = H.levels[-1]
+    cond = 0.0
+    for entry in LJ.colours:
+        if entry is None:
+            continue
+        dofs = entry[0]
+        Av = mg.submatrices(LJ.A, dofs)
+        P, nv = dofs.shape
+        Bv = np.zeros((P, nv + 1, nv + 1))
+        Bv[:, :nv, :nv] = Av
+        Bv[:, :nv, nv] = LJ.w[dofs]
+        Bv[:, nv, :nv] = LJ.w[dofs]
+        cond = max(cond, float(np.max(np.linalg.cond(Bv))))
+    tol = max(1e-10, 10 * 1.1e-16 * cond)
+    G = mgdarcy.Multigrid(2, n0, levels, k, mu, torch.as_tensor(c, device="cuda"), precision="fp64")
+    r = np.random.default_rng(9).standard_normal(LJ.S.ndof)
+    z = torch.zeros(LJ.S.ndof, dtype=torch.float64, device="cuda")
+    G.vcycle(torch.as_tensor(r, device="cuda"), z)
+    zo = mg.vcycle(H, r)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err <= tol, (err, cond)
+
+
+def test_escalation_converges_where_fp32_stalls():
+    """256^2 RT_1 Darcy flow through foam islands at contrast 1e8 (case (a)):
+    with FP32 patch inverses the residual falls by less than a tenth in ten
+    iterations; the solve then continues with FP64 V-cycles and converges,
+    in fewer iterations than FP32 alone needs."""
+    c = experiments.coefficient("foam", "a", 1e8, 256)
+    st_esc, x, _ = experiments.driven_solve(torch, c, 0.0, degree=1, tol=1e-6, maxit=400, precision="fp32")
+    assert st_esc.converged == 1 and st_esc.escalated_at == 10
+    assert st_esc.iterations <= 30
+    # without the policy the FP32 V-cycle needs many more iterations
+    cd = torch.as_tensor(c, device="cuda")
+    G = mgdarcy.Multigrid(2, 4, 7, 1, 0.0, cd, precision="fp32", escalate_window=-1)
+    nu, npr = G.sizes()
+    f = torch.stack([-cd.reshape(-1), torch.zeros_like(cd.reshape(-1))]).contiguous()
+    b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
+    G.load_vector(f, None, b)
+    x2 = torch.zeros_like(b)
+    st32, _ = G.solve(b[:nu].contiguous(), b[nu:].contiguous(), x2, tol=1e-6, maxit=400, check=False)
+    assert st32.escalated_at == -1 and st32.iterations > 2 * st_esc.iterations
+    # both solutions satisfy the same FP64 residual criterion
+    r = torch.zeros_like(b)
+    for xx in (x, x2):
+        assert G.residual_norm(xx, b, r) <= 1.01e-6 * torch.linalg.norm(b).item()
+
+
+# Two problems of 64^2 and two of 128^2 cells (RT_1, mu = 0.01, lognormal c),
+# four right-hand sides each: groups whose block kernels walk many patches.
+BIG = [(5, 2.0, 21), (5, 2.5, 22), (6, 2.0, 23), (6, 3.0, 24)]
+
+
+@pytest.fixture(scope="module")
+def big_oracle():
+    hier, cs = [], []
+    for L, sig, seed in BIG:
+        n = 4 * 2 ** (L - 1)
+        c = inputs.lognormal_c(n, 2, sig, n / 16, seed)
+        cs.append(c)
+        hier.append(mg.Hierarchy(2, 4, L, 1, 0.01, c))
+    sizes = [H.levels[-1].S.ndof * 4 for H in hier]
+    r = np.random.default_rng(31).standard_normal(sum(sizes))
+    zo, off = [], 0
+    for H, s in zip(hier, sizes):
+        nd = s // 4
+        zo.append([mg.vcycle(H, r[off + rr * nd: off + (rr + 1) * nd]) for rr in range(4)])
+        off += s
+    return cs, r, zo
+
+
+@pytest.mark.parametrize("kernel", [0, 3], ids=["rule", "persistent"])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_large_groups_match_oracle(precision, tol, kernel, big_oracle):
+    cs, r, zo = big_oracle
+    probs = [dict(dim=2, n_coarse=4, n_levels=L, degree=1, mu=0.01, c=torch.as_tensor(c, device="cuda"),
+                  precision=precision, pass_kernel=kernel) for (L, _, _), c in zip(BIG, cs)]
+    B = mgdarcy.Batch(probs, nrhs=4)
+    assert B.total() == r.size
+    z = torch.zeros(r.size, dtype=torch.float64, device="cuda")
+    B.vcycle(torch.as_tensor(r, device="cuda"), z)
+    torch.cuda.synchronize()
+    zh = z.cpu().numpy()
+    for p in range(len(BIG)):
+        nd, off, _ = B.layout(p)
+        for rr in range(4):
+            seg = slice(off + rr * nd, off + (rr + 1) * nd)
+            err = np.linalg.norm(zh[seg] - zo[p][rr]) / np.linalg.norm(zo[p][rr])
+            assert err < tol, (p, rr, err)
