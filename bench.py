@@ -124,8 +124,9 @@ def gpu_uuid(torch, dev):
         return None
 
 
-def run_cpu_baseline(seconds=15.0):
-    """The FP64 oracle (plain NumPy/SciPy) on one host core: V-cycles of the same workload."""
+def _oracle_worker(seconds, seed, barrier, queue):
+    """One oracle replica (single-threaded NumPy/SciPy): set-up, then FP64
+    V-cycles of the full workload for `seconds` once every replica is set up."""
     from oracle import multigrid as mg
     from paper_1602_04858_gb300 import inputs
     w = inputs.workload(WORKLOAD)
@@ -133,7 +134,8 @@ def run_cpu_baseline(seconds=15.0):
     H = mg.Hierarchy(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"], w["c"])
     setup_s = time.perf_counter() - t0
     LJ = H.levels[-1]
-    r = np.random.default_rng(7).standard_normal(LJ.S.ndof)
+    r = np.random.default_rng(seed).standard_normal(LJ.S.ndof)
+    barrier.wait()
     n = 0
     t0 = time.perf_counter()
     while True:
@@ -142,9 +144,56 @@ def run_cpu_baseline(seconds=15.0):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": LJ.S.ndof * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} FP64 V-cycles of the full workload after a {setup_s:.0f} s oracle setup "
-                      f"(single thread: NumPy/SciPy with BLAS threads = 1)"}
+    queue.put((n, el, setup_s, LJ.S.ndof))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def available_memory_bytes():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def run_cpu_baseline(seconds=15.0, workers=None):
+    """The FP64 oracle as it stands (plain NumPy/SciPy, single-threaded) on all
+    host cores: one independent replica per core (each ~3.3 GB), the same
+    replicas-only split as the GPU side, processes started with spawn.  value =
+    the DoF x V-cycles of all replicas over the slowest replica's time."""
+    import multiprocessing as mp
+    cores = host_cores()
+    if workers is None:
+        workers = cores
+        mem = available_memory_bytes()
+        if mem is not None:
+            workers = max(1, min(workers, int(mem // (4.5 * 2 ** 30))))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(seconds, 7 + i, barrier, queue)) for i in range(workers)]
+    for pr in procs:
+        pr.start()
+    res = [queue.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    ndof = res[0][3]
+    total = sum(n for n, _, _, _ in res)
+    span = max(el for _, el, _, _ in res)
+    per = [ndof * n / el for n, el, _, _ in res]
+    return {"value": ndof * total / span, "unit": UNIT, "cores": workers, "host_cores": cores, "kind": "oracle",
+            "per_core_value": float(np.mean(per)),
+            "sample": f"{workers} single-threaded oracle replicas (one per core, NumPy/SciPy with BLAS threads = 1), "
+                      f"{total} FP64 V-cycles of the full workload in {span:.1f} s after a "
+                      f"{max(s for _, _, s, _ in res):.0f} s oracle set-up"}
 
 
 def reference_arm(args, rank):
@@ -193,6 +242,32 @@ def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
 FINEST_PASS_DRAM_BYTES = 51.024e6 + 0.044e6
 
 
+def vcycle_model(levels, d, prec, l2_bytes, m_fine=2, variable=True):
+    """Algorithmic bytes and smoother FLOPs of one V-cycle (the hot path's
+    per-V-cycle roofline): per level j >= 1 with N_j dofs and P_j patches of
+    n_v dofs (nnz_j operator entries in a patch's rows),
+        bytes_j = S_j + 2 m(j) (2C - 1)/C (3 N_j s_v) + 6 N_j s_v,
+        S_j = P_j n_v^2 s_inv, counted once per V-cycle if it fits the L2
+              cache, else 2 m(j) (2C - 1)/C times (one sweep per smoothing
+              step and direction, C = 3^d colours),
+        flops_j = 2 m(j) (2C - 1)/C P_j (2 n_v^2 + 2 nnz_j).
+    s_v: bytes per vector entry (4, FP64: 8); s_inv: bytes per stored inverse
+    entry (4, FP64: 8, BF16 inverses on the finest level: 2).
+    levels: list of (N_j, P_j, n_v, nnz_j) for j = 1..J."""
+    C = 3 ** d
+    J = len(levels)
+    total_b = total_f = 0.0
+    for j, (N, P, nv, nnz) in enumerate(levels, start=1):
+        s_v = 8 if prec == "fp64" else 4
+        s_inv = 8 if prec == "fp64" else (2 if (prec == "fp32_bf16inv" and j == J) else 4)
+        m = m_fine * (2 ** (J - j) if variable else 1)
+        sweeps = 2 * m * (2 * C - 1) / C
+        inv = P * nv * nv * s_inv
+        total_b += (inv if inv <= l2_bytes else sweeps * inv) + sweeps * 3 * N * s_v + 6 * N * s_v
+        total_f += sweeps * P * (2 * nv * nv + 2 * nnz)
+    return total_b, total_f
+
+
 def colour_pass_bytes(count, nv, s_inv, s_v):
     """Algorithmic bytes of one colour pass: each patch streams its n_v x n_v
     inverse once and reads b_v, x_v and writes x_v (3 n_v vector entries)."""
@@ -238,9 +313,10 @@ def batched_workload(per_size=16, sizes=(64, 128, 256, 512), pass_kernel=0):
     return probs
 
 
-def bench_batched(args):
-    """DoF x V-cycles/s of the batched V-cycle (all problems, 4 right-hand sides) and the batched
-    FP64 FGMRES(20) time to 1e-8; random load vectors (no divergence source, no-slip walls)."""
+def batched_figures(args, steps, warmup, solve=True):
+    """Batched V-cycle (all problems, 4 right-hand sides) with CUDA events, and
+    the batched FP64 FGMRES(20) time to 1e-8 on random load vectors (no
+    divergence source, no-slip walls)."""
     import torch
     from paper_1602_04858_gb300 import mgdarcy
     sizes = tuple(int(v) for v in args.batch_sizes.split(","))
@@ -255,7 +331,7 @@ def bench_batched(args):
     rng = np.random.default_rng(17)
     r = torch.as_tensor(rng.standard_normal(total), device="cuda")
     z = torch.zeros_like(r)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         B.vcycle(r, z)
     torch.cuda.synchronize()
     l0 = B.launches()
@@ -263,7 +339,7 @@ def bench_batched(args):
     sampler = ClockSampler()
     torch.cuda.nvtx.range_push("timed_vcycles")   # lets profilers select the timed region
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         B.vcycle(r, z)
     e1.record()
     torch.cuda.synchronize()
@@ -271,39 +347,47 @@ def bench_batched(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     launches = B.launches() - l0
-    # right-hand sides: random loads in the free velocity rows
-    b = rng.standard_normal(total)
-    for p in range(len(probs)):
-        nd, off, _ = B.layout(p)
-        n = probs[p]["c"].shape[0]
-        N = 2 * n
-        nu = 2 * (N + 1) * N
-        for rr in range(4):
-            seg = b[off + rr * nd: off + (rr + 1) * nd]
-            seg[nu:] = 0.0
-            ux = seg[:(N + 1) * N].reshape(N, N + 1)
-            ux[:, 0] = ux[:, -1] = 0.0
-            uy = seg[(N + 1) * N:nu].reshape(N + 1, N)
-            uy[0, :] = uy[-1, :] = 0.0
-    x = torch.zeros_like(r)
-    if args.no_companions:
-        stats, status = [], -1
-    else:
+    status = B.sync(check=False)
+    stats = []
+    if solve:
+        # right-hand sides: random loads in the free velocity rows
+        b = rng.standard_normal(total)
+        for p in range(len(probs)):
+            nd, off, _ = B.layout(p)
+            n = probs[p]["c"].shape[0]
+            N = 2 * n
+            nu = 2 * (N + 1) * N
+            for rr in range(4):
+                seg = b[off + rr * nd: off + (rr + 1) * nd]
+                seg[nu:] = 0.0
+                ux = seg[:(N + 1) * N].reshape(N, N + 1)
+                ux[:, 0] = ux[:, -1] = 0.0
+                uy = seg[(N + 1) * N:nu].reshape(N + 1, N)
+                uy[0, :] = uy[-1, :] = 0.0
+        x = torch.zeros_like(r)
         stats, status = B.solve(torch.as_tensor(b, device="cuda"), x, tol=1e-8, maxit=400, restart=20, check=False)
-    its = [s.iterations for s in stats] or [0]
-    line = {"metric": METRIC, "value": total * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of "
-                                   + ", ".join(f"{n}^2" for n in sizes) + " cells), RT_1, mu=0.01, lognormal c "
-                                   "with sigma in [1,3], 4 right-hand sides each, one CUDA graph per batched "
-                                   "V-cycle, FP32 smoother",
-                       "dofs_times_rhs": total, "l2": "inputs larger than L2", "pass_kernel": args.pass_kernel},
-            "gpu_launches": int(launches), "clocks": clocks, "setup_s": setup_s,
+    its = [s_.iterations for s_ in stats] or [0]
+    desc = (f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of "
+            + ", ".join(f"{n}^2" for n in sizes) + " cells), RT_1, mu=0.01, lognormal c with sigma in [1,3], "
+            "4 right-hand sides each, one CUDA graph per batched V-cycle, FP32 smoother")
+    return {"workload": desc, "dofs_times_rhs": total, "vcycle_ms": ms / steps,
+            "value": total * steps / (ms / 1e3), "unit": "DoF x rhs x V-cycles/s", "gpu_launches_per_vcycle":
+                int(launches // max(1, steps)), "setup_s": setup_s, "clocks": clocks,
             "time_to_1e-8": {"ms": stats[0].solve_ms if stats else None, "converged": bool(status == 0),
-                             "systems": len(stats),
-                             "iterations_max": int(max(its)), "iterations_mean": float(np.mean(its)),
-                             "restart": 20}}
+                             "systems": len(stats), "iterations_max": int(max(its)),
+                             "iterations_mean": float(np.mean(its)), "restart": 20} if solve else None}
+
+
+def bench_batched(args):
+    """The batched workload as the timed step (--workload batched)."""
+    f = batched_figures(args, args.steps, args.warmup, solve=not args.no_companions)
+    line = {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["vcycle_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f["workload"], "dofs_times_rhs": f["dofs_times_rhs"], "l2": "inputs larger than L2",
+                       "pass_kernel": args.pass_kernel},
+            "gpu_launches": f["gpu_launches_per_vcycle"] * args.steps, "clocks": f["clocks"], "setup_s": f["setup_s"],
+            "time_to_1e-8": f["time_to_1e-8"]}
     print(json.dumps(line), flush=True)
 
 
@@ -321,6 +405,7 @@ def main():
     ap.add_argument("--pass-kernel", type=int, default=0, help="mg_problem.pass_kernel of the batched problems")
     ap.add_argument("--no-companions", action="store_true",
                     help="skip the FP64/BF16 V-cycles, the solves and the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched companion figures")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,11 +441,22 @@ def main():
         return mgdarcy.Multigrid(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"], cdev,
                                  precision=prec, m_fine=2, variable_cycle=variable, stream=stream.cuda_stream)
 
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     G = make("fp32")
+    setup_s = time.perf_counter() - t_setup
     names = {1: "warp", 2: "block", 3: "persistent blocks"}
     pass_kernels = {j: names[G.pass_kernel(j)] for j in range(1, w["n_levels"])}
     nu, npr = G.sizes()
     N = nu + npr
+    # per level j >= 1: (dofs, patches, n_v, nonzeros of a patch's rows) for the V-cycle model
+    J = w["n_levels"] - 1
+    C = 3 ** w["d"]
+    level_info = []
+    for j in range(1, J + 1):
+        cnts = [G.patch_info(j, col) for col in range(C)]
+        level_info.append((sum(G.sizes(j)), sum(cn for cn, _ in cnts), cnts[0][1], G.patch_nnz(j)))
+    l2_bytes = torch.cuda.get_device_properties(dev).L2_cache_size
     rng = np.random.default_rng(11 + rank)
     rh = rng.standard_normal(N)
     r = torch.as_tensor(rh, device=dev)
@@ -443,6 +539,7 @@ def main():
 
     # --- companions: FP64 and BF16-inverse V-cycles, time to 1e-8 ----------------
     extra = {}
+    vc_ms = {"fp32": ms_max / args.steps}
     solves = {}
     e2e_value = None
     bsol = rng.standard_normal(N)
@@ -466,6 +563,7 @@ def main():
         ksteps = max(3, args.steps // 2)
         ms_p, _ = time_vcycles(Gh, ksteps, 2)
         extra[key] = N * ksteps / (ms_p / 1e3)
+        vc_ms[key] = ms_p / ksteps
         x = torch.zeros_like(r)
         st, status = Gh.solve(f, g, x, tol=1e-8, maxit=400, check=False)
         solves[key] = {"ms": st.solve_ms, "iterations": st.iterations, "rel_residual": st.rel_residual,
@@ -477,12 +575,38 @@ def main():
     if not args.no_companions:
         e2e_value = end_to_end(args, make, rh, N, barrier, dist, dev, world)
 
+    # --- per-V-cycle roofline of every mode; ALU roofline of the FP64 mode -----------
+    peaks_alu = {}
+    if not args.no_companions:
+        for kind in ("fp64", "fp32", "fp32x2"):
+            try:
+                peaks_alu[kind + "_tflops"] = mgdarcy.measure_fma_peak(kind)
+            except Exception as ex:  # reported, not required
+                peaks_alu[kind + "_tflops"] = None
+                peaks_alu["error"] = str(ex)
+    rv = {}
+    for key, t in vc_ms.items():
+        prec = key.split("_V(")[0]
+        nbytes, flops = vcycle_model(level_info, w["d"], prec, l2_bytes, 2, "V(2,2)" not in key)
+        ent = {"bytes": nbytes, "ms": t, "achieved_gbs": nbytes / (t / 1e3) / 1e9,
+               "frac": nbytes / (t / 1e3) / 1e9 / hbm, "flops": flops,
+               "achieved_tflops": flops / (t / 1e3) / 1e12}
+        if prec == "fp64" and peaks_alu.get("fp64_tflops"):
+            ent["alu_frac"] = ent["achieved_tflops"] / peaks_alu["fp64_tflops"]
+        rv[key] = ent
+    batched = None
+    if not args.no_companions and not args.no_batched and world == 1:
+        try:
+            batched = batched_figures(args, 3, 1, solve=True)
+        except Exception as ex:  # reported, not required
+            batched = {"error": str(ex)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             cpu = run_cpu_baseline(args.cpu_seconds)
         except Exception as ex:  # the baseline is reported, not required
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+            cpu = {"value": None, "unit": UNIT, "cores": host_cores(), "kind": "oracle", "sample": f"failed: {ex}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -501,6 +625,15 @@ def main():
                              "timing": "CUDA events around back-to-back symmetric steps (17 passes) on the "
                                        "launching stream, as the passes run inside the V-cycle"},
                 "clocks": clocks,
+                "roofline_vcycle": {"model": "algorithmic bytes of one V-cycle: per level the patch inverses once "
+                                             "if the level's set fits the L2 cache, else once per sweep, plus the "
+                                             "vector traffic of the sweeps, residual and transfers; achieved = bytes "
+                                             "/ CUDA-event time of a V-cycle; frac against the measured HBM copy "
+                                             "bandwidth (peak above); FP64 also against the measured FP64 FMA peak",
+                                    "l2_bytes": l2_bytes, "modes": rv},
+                "alu_peaks": peaks_alu or None,
+                "setup_s": setup_s,
+                "batched": batched,
                 "cpu_baseline": cpu,
                 "dofs": N,
                 "fp64_value": extra.get("fp64"), "bf16inv_value": extra.get("fp32_bf16inv"),

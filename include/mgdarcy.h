@@ -353,6 +353,20 @@ mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
 /* Patch counts: number of patches of `colour` on `level` and their size n_v. */
 mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v);
 
+/* Nonzeros of the rows of A_level (eq. Brinkman-weak) restricted to the dofs
+ * of one vertex patch (Sec. 3.3), for an interior patch (level >= 1): the
+ * local residual (b - A x)|_v of a colour pass costs two FLOPs per nonzero,
+ * the product S_v r another 2 n_v^2.  Host only. */
+mg_status mg_patch_nnz(const mg_handle* h, int level, int64_t* nnz);
+
+/* Measured CUDA-core FMA throughput of the current device in TFLOP/s (two
+ * FLOPs per FMA): kind 0 FP64, 1 FP32, 2 FP32 packed pairs.  The paper has
+ * no counterpart: this is the denominator of the roofline of the colour passes
+ * that their arithmetic, not their bytes, bounds (the FP64 mode).  Runs
+ * independent FMA chains on every SM for a few milliseconds; allocates and
+ * frees a small device buffer; synchronises the stream. */
+mg_status mg_measure_fma_peak(int kind, double* tflops, void* cuda_stream);
+
 /* Colour-pass kernel chosen for `level` (1 <= level <= J) at setup, see
  * mg_problem.pass_kernel: *kernel = 1 (warp per patch), 2 (block per patch)
  * or 3 (persistent blocks).  Host only. */

@@ -30,6 +30,7 @@ UNITS = [
     ("generic.cu", "generic.o", []),
     ("api.cu", "api.o", []),
     ("noalloc.cu", "noalloc.o", []),
+    ("peaks.cu", "peaks.o", []),
     ("cnn.cu", "cnn.o", []),
     ("tables.cpp", "tables.o", ["-x", "cu"]),
 ]

@@ -765,6 +765,12 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
   return MG_OK;
 }
 
+mg_status mg_patch_nnz(const mg_handle* h, int level, int64_t* nnz) {
+  if (!h || level < 1 || level > h->J || !nnz) return fail(MG_ERR_INVALID_ARG, "bad level or argument");
+  *nnz = h->ops->patch_nnz(h->lv[level]);
+  return MG_OK;
+}
+
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
   if (!h || level < 1 || level > h->J || !kernel) return fail(MG_ERR_INVALID_ARG, "bad level or argument");
   *kernel = h->lv[level].pass_cta + 1;

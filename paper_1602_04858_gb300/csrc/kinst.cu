@@ -358,6 +358,20 @@ int plan_selftest(int sprec, int n, double mu, std::string* why) {
   return r;
 }
 
+// Nonzeros of the operator rows of one patch (its local residual costs two
+// FLOPs per nonzero): the interior patch type where the level has one, else
+// the first present type.
+int64_t patch_nnz(const HostLevel& h) {
+  const Lvl<D, K, double> L = mk<double>(h);
+  int v[D];
+  for (int e = 0; e < D; ++e) v[e] = h.n >= 4 ? 2 : 1;
+  std::vector<PlanRow<double>> rows;
+  plan_rows(L, tab<double>(), v, rows);
+  int64_t nnz = 0;
+  for (const auto& r : rows) nnz += (int64_t)(r.pl.size() + r.ms.size());
+  return nnz;
+}
+
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
                      cudaStream_t s) {
   k_coarse_assemble<D, K><<<1, 512, 0, s>>>(mk<double>(h), tab<double>(), free_list, g2l, nf, M, E);
@@ -412,6 +426,7 @@ DKOps make_ops() {
   o.template_elems = template_elems;
   o.build_template = build_template;
   o.plan_selftest = plan_selftest;
+  o.patch_nnz = patch_nnz;
   return o;
 }
 

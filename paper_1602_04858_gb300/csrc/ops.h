@@ -99,6 +99,8 @@ struct DKOps {
   int (*build_template)(const HostLevel&, int sprec, void* R0, cudaStream_t, std::string* why);
   // host check of the tables of an n^d level (no GPU); nonzero with a reason on failure
   int (*plan_selftest)(int sprec, int n, double mu, std::string* why);
+  // nonzeros of the operator rows of one (interior) patch of a level
+  int64_t (*patch_nnz)(const HostLevel&);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);

@@ -30,7 +30,7 @@ API = [
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
     "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
-    "mg_batch_set_wait_limit",
+    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak",
 ]
 
 
@@ -117,6 +117,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_inject_alloc_failure.restype = None
     lib.mg_sync_batch.argtypes = [vp]
     lib.mg_batch_set_wait_limit.argtypes = [vp, d]
+    lib.mg_patch_nnz.argtypes = [vp, i, ctypes.POINTER(i64)]
+    lib.mg_measure_fma_peak.argtypes = [i, ctypes.POINTER(d), vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -170,6 +172,14 @@ def inject_alloc_failure(after):
     """mg_inject_alloc_failure: the library's allocation after the next `after`
     ones is refused with MG_ERR_OOM (once); after < 0 cancels.  For tests."""
     load().mg_inject_alloc_failure(int(after))
+
+
+def measure_fma_peak(kind, stream=None):
+    """mg_measure_fma_peak: measured FMA throughput in TFLOP/s; kind "fp64", "fp32" or "fp32x2"."""
+    k = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
+    out = ctypes.c_double()
+    _check(load().mg_measure_fma_peak(k, ctypes.byref(out), ctypes.c_void_p(_stream_ptr(stream))))
+    return out.value
 
 
 def residual_norm_noalloc(dim, degree, n, mu, c, x, b, norm, stream=None):
@@ -276,6 +286,12 @@ class Multigrid:
         cnt, nv = ctypes.c_int64(), ctypes.c_int()
         _check(load().mg_patch_info(self.h, level, colour, ctypes.byref(cnt), ctypes.byref(nv)))
         return cnt.value, nv.value
+
+    def patch_nnz(self, level):
+        """Nonzeros of the operator rows of one interior patch of a level (mg_patch_nnz)."""
+        v = ctypes.c_int64()
+        _check(load().mg_patch_nnz(self.h, level, ctypes.byref(v)))
+        return v.value
 
     def pass_kernel(self, level):
         """Colour-pass kernel of a level: 1 warp per patch, 2 block per patch, 3 persistent blocks."""

@@ -14,9 +14,27 @@ def test_colour_pass_bytes_of_the_finest_pass():
     assert bench.colour_pass_bytes(7225, 40, 4, 4) == 7225 * (1600 * 4 + 3 * 40 * 4) == 49_708_000
 
 
-def test_traffic_figure_is_close_to_the_algorithmic_bytes():
-    algo = bench.colour_pass_bytes(7225, 40, 4, 4)
-    assert algo <= bench.FINEST_PASS_DRAM_BYTES <= 1.05 * algo
+def test_vcycle_model_by_hand():
+    """Two levels (J = 2), variable cycle with m(J) = 2: m(2) = 2, m(1) = 4;
+    2-D, C = 9 colours, so a sweep count of 2 m (2C - 1)/C = 68/9 on the finest
+    level and 136/9 on level 1."""
+    lv = [(50, 1, 8, 30), (200, 9, 8, 40)]   # (dofs, patches, n_v, nnz)
+    big = 1 << 40
+    b, f = bench.vcycle_model(lv, 2, "fp32", big)
+    s1, s2 = 136 / 9, 68 / 9
+    expect_b = (1 * 64 * 4 + s1 * 3 * 50 * 4 + 6 * 50 * 4) + (9 * 64 * 4 + s2 * 3 * 200 * 4 + 6 * 200 * 4)
+    expect_f = s1 * 1 * (2 * 64 + 60) + s2 * 9 * (2 * 64 + 80)
+    assert abs(b - expect_b) < 1e-9 * expect_b and abs(f - expect_f) < 1e-9 * expect_f
+    # an L2 smaller than the finest inverses: those are streamed once per sweep
+    b_small, _ = bench.vcycle_model(lv, 2, "fp32", 1000)
+    assert abs(b_small - (expect_b + (s2 - 1) * 9 * 64 * 4)) < 1e-9 * b_small
+    # FP64 doubles every byte; BF16 inverses halve the finest level's inverse bytes only
+    assert abs(bench.vcycle_model(lv, 2, "fp64", big)[0] - 2 * expect_b) < 1e-9 * expect_b
+    b_bf, _ = bench.vcycle_model(lv, 2, "fp32_bf16inv", big)
+    assert abs(b_bf - (expect_b - 9 * 64 * 2)) < 1e-9 * expect_b
+    # the standard cycle: m = 2 on both levels
+    b_std, _ = bench.vcycle_model(lv, 2, "fp32", big, variable=False)
+    assert abs(b_std - (expect_b - (s1 - s2) * 3 * 50 * 4)) < 1e-9 * expect_b
 
 
 def test_batched_workload_recipe():
