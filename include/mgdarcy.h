@@ -89,13 +89,14 @@ typedef struct {
                            update up to rounding): 1: one warp per patch
                            (persistent), 2: one thread block per patch,
                            3: persistent thread blocks, one patch at a time,
-                           0: per level, the block kernel where the largest
-                           colour holds at most 10,000 inverse entries
-                           (n_v^2 per patch) per SM or four or more
-                           right-hand sides share the inverses (batches),
-                           else the warp kernel,
-                           4: per level, the fastest of the three in a timed
-                           trial at setup.                                     */
+                           0 (default) or 4: per level, the fastest of the
+                           three, timed at setup on the level itself (two
+                           symmetric smoothing steps as a CUDA graph, see
+                           mg_time_passes; cached per level shape, precision,
+                           right-hand sides and device), 5: a fixed rule
+                           (block kernel where the largest colour holds at
+                           most 10,000 inverse entries per SM or four or more
+                           right-hand sides share the inverses, else warp).    */
   double additive;      /* smoother: 0 the symmetric multiplicative vertex-patch
                            Schwarz smoother of Sec. 3.3 (the paper's); in
                            (0, 1]: additive vertex-patch Schwarz with this
@@ -358,6 +359,16 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
  * local residual (b - A x)|_v of a colour pass costs two FLOPs per nonzero,
  * the product S_v r another 2 n_v^2.  Host only. */
 mg_status mg_patch_nnz(const mg_handle* h, int level, int64_t* nnz);
+
+/* Average time in microseconds of one colour pass (Sec. 3.3) of `level`
+ * (>= 1) with colour-pass kernel `kernel` (1 warp per patch, 2 block per
+ * patch, 3 persistent blocks; 0: the level's own, see mg_level_pass_kernel):
+ * two symmetric smoothing steps captured as a CUDA graph, replayed five times
+ * between CUDA events after one untimed replay, so that the passes run back
+ * to back as inside the V-cycle.  Overwrites the handle's level vectors of
+ * that level (mg_level_load reloads them).  For measurement and the kernel
+ * choice at setup; synchronises the stream. */
+mg_status mg_time_passes(mg_handle* h, int level, int kernel, double* us_per_pass);
 
 /* Measured CUDA-core FMA throughput of the current device in TFLOP/s (two
  * FLOPs per FMA): kind 0 FP64, 1 FP32, 2 FP32 packed pairs.  The paper has

@@ -251,26 +251,75 @@ int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - 
 // fill the GPU; a block per patch shortens the latency of one patch update,
 // which is what a pass costs on coarse levels; persistent blocks load their
 // tables once and overlap the next patch's copies with the current one.
-// Modes: 1 warp, 2 block, 3 persistent blocks everywhere; 0 (default) block
-// per patch on levels whose largest colour holds at most 10,000 inverse
+// Modes: 1 warp, 2 block, 3 persistent blocks everywhere; 5 a fixed rule:
+// block per patch on levels whose largest colour holds at most 10,000 inverse
 // entries (n_v^2 per patch) per SM, warp per patch elsewhere (the crossover
-// measured on GB300: 2-D RT_1 colours of 441 patches and 3-D RT_0 colours of
-// 1,103 favour the block, 2-D RT_1 colours of 1,800 patches the warp), and
-// block per patch on every level when four or more right-hand sides share
-// the inverses (measured faster on 2-D RT_1 levels of up to 512^2 cells);
-// 4 times three symmetric smoothing steps of each kernel on the level's own
-// vectors (after one untimed step) and keeps the fastest, the choice cached
-// per level shape and device (timings taken under a profiler that serialises
-// kernels can change it).
+// measured on GB300 for FP32: 2-D RT_1 colours of 441 patches and 3-D RT_0
+// colours of 1,103 favour the block, 2-D RT_1 colours of 1,800 patches the
+// warp), and block per patch on every level when four or more right-hand
+// sides share the inverses; 0 (default) and 4 time each kernel on the level's own vectors (two symmetric smoothing
+// steps captured as a CUDA graph and replayed three times, as the passes run
+// back to back inside the V-cycle graph) and keeps the fastest, the choice
+// cached per level shape and device (timings taken under a profiler that
+// serialises kernels can change it).
+// Time of `steps` smoothing steps of level j on the level's own vectors (their
+// contents are overwritten), captured once as a CUDA graph and replayed `reps`
+// times between CUDA events after one untimed replay, so that the launches run
+// back to back as they do inside the V-cycle graph.  *ms: per replay;
+// *npass: colour-pass launches per replay.
+mg_status time_smoothing(mg_handle* h, int j, int nrhs, int steps, int reps, float* ms, int64_t* npass) {
+  HostLevel& L = h->lv[j];
+  const size_t bytes = (size_t)L.ndof * nrhs * h->vbytes();
+  CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
+  CU(cudaMemsetAsync(L.B, 0, bytes, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  cudaStream_t cap;
+  CU(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  const int64_t l0 = h->launches;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return fail(MG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+  }
+  const mg_status st = smooth_steps(h, j, L.X, L.B, L.R, steps, nrhs, cap);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(cap, &g);
+  if (npass) *npass = h->launches - l0;
+  h->launches = l0;
+  cudaGraphExec_t ge = nullptr;
+  if (st == MG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == MG_OK && e == cudaSuccess) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    e = cudaGraphLaunch(ge, cap);
+    cudaEventRecord(e0, cap);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, cap);
+    cudaEventRecord(e1, cap);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / (reps > 0 ? reps : 1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaStreamDestroy(cap);
+  if (st != MG_OK) return st;
+  if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("timed smoothing: ") + cudaGetErrorString(e));
+  CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
+  return MG_OK;
+}
+
 mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   static std::mutex mu;
   static std::map<std::vector<int>, int> cache;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int64_t l0 = h->launches;
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
-    if (mode != 4) {
-      if (mode == 0) {
+    if (mode != 4 && mode != 0) {
+      if (mode == 5) {
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
         int64_t mx = 0;
@@ -291,32 +340,17 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
         continue;
       }
     }
-    if (!e0) {
-      CU(cudaEventCreate(&e0));
-      CU(cudaEventCreate(&e1));
-    }
-    const size_t bytes = (size_t)L.ndof * nrhs * h->vbytes();
     float ms[3] = {0.f, 0.f, 0.f};
     for (int var = 0; var < 3; ++var) {
       L.pass_cta = var;
-      CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
-      CU(cudaMemsetAsync(L.B, 0, bytes, h->stream));
-      TRY(smooth_steps(h, j, L.X, L.B, L.R, 1, nrhs, h->stream));
-      CU(cudaEventRecord(e0, h->stream));
-      TRY(smooth_steps(h, j, L.X, L.B, L.R, 3, nrhs, h->stream));
-      CU(cudaEventRecord(e1, h->stream));
-      CU(cudaEventSynchronize(e1));
-      CU(cudaEventElapsedTime(&ms[var], e0, e1));
+      TRY(time_smoothing(h, j, nrhs, 2, 3, &ms[var], nullptr));
     }
     L.pass_cta = 0;
     for (int var = 1; var < 3; ++var)
       if (ms[var] < ms[L.pass_cta]) L.pass_cta = var;
-    CU(cudaMemsetAsync(L.X, 0, bytes, h->stream));
     std::lock_guard<std::mutex> g(mu);
     cache[key] = L.pass_cta;
   }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
   h->launches = l0;
   CU(cudaGetLastError());
   return MG_OK;
@@ -491,7 +525,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
-  if (p->pass_kernel < 0 || p->pass_kernel > 4) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (p->pass_kernel < 0 || p->pass_kernel > 5) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
   if (p->escalate_window > 100000) return fail(MG_ERR_INVALID_ARG, "escalate_window too large");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
@@ -762,6 +796,21 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
     return fail(MG_ERR_INVALID_ARG, "bad level or colour");
   if (count) *count = h->lv[level].count[colour];
   if (n_v) *n_v = h->ops->nv;
+  return MG_OK;
+}
+
+mg_status mg_time_passes(mg_handle* h, int level, int kernel, double* us_per_pass) {
+  if (!h || level < 1 || level > h->J || kernel < 0 || kernel > 3 || !us_per_pass)
+    return fail(MG_ERR_INVALID_ARG, "bad level, kernel or argument");
+  HostLevel& L = h->lv[level];
+  const int keep = L.pass_cta;
+  if (kernel > 0) L.pass_cta = kernel - 1;
+  float ms = 0.f;
+  int64_t np = 0;
+  const mg_status st = time_smoothing(h, level, h->nrhs, 2, 5, &ms, &np);
+  L.pass_cta = keep;
+  if (st != MG_OK) return st;
+  *us_per_pass = np > 0 ? 1e3 * ms / (double)np : 0.0;
   return MG_OK;
 }
 

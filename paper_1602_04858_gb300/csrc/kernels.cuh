@@ -556,25 +556,35 @@ struct PlanRegs {
 // Lane pieces of the local residual: piece PI accumulates its plain slots
 // (coefficient x window column) and mass slots (coefficient x cell
 // coefficient x window column) into one partial sum.
+// With one right-hand side the slots of a piece feed NA independent partial
+// sums (slot s into sum s mod NA), added at the end: the chain of dependent
+// FMAs, not the FMA count, sets the latency of a warp's residual.
 template <int PI, class P, typename T, int NR>
 __device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* win, const T* cw, T* part, int lp) {
   using PL = typename P::PL;
   using PSum = typename P::PSum;
-  T acc[NR];
+  constexpr int NA = NR == 1 ? 4 : 1;
+  T acc[NA][NR];
 #pragma unroll
-  for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc[a][rr] = T(0);
 #pragma unroll
   for (int s = PSum::zoff(PI); s < PSum::zoff(PI) + PL::z(PI); ++s)
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) acc[rr] += R.pc[s] * win[rr * P::WIN + R.pw[s]];
+    for (int rr = 0; rr < NR; ++rr) acc[s % NA][rr] += R.pc[s] * win[rr * P::WIN + R.pw[s]];
 #pragma unroll
   for (int s = PSum::zmoff(PI); s < PSum::zmoff(PI) + PL::zm(PI); ++s) {
     const T cc = R.mc[s] * cw[R.mcell[s]];
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * win[rr * P::WIN + R.mw[s]];
+    for (int rr = 0; rr < NR; ++rr) acc[(s + 1) % NA][rr] += cc * win[rr * P::WIN + R.mw[s]];
   }
 #pragma unroll
-  for (int rr = 0; rr < NR; ++rr) part[rr * P::PARTS + PI * P::LW + lp] = acc[rr];
+  for (int rr = 0; rr < NR; ++rr) {
+    T t = acc[0][rr];
+    if constexpr (NA == 4) t = (acc[0][rr] + acc[1][rr]) + (acc[2][rr] + acc[3][rr]);
+    part[rr * P::PARTS + PI * P::LW + lp] = t;
+  }
   if constexpr (PI + 1 < PL::NP) plan_pieces<PI + 1, P, T, NR>(R, win, cw, part, lp);
 }
 
@@ -822,12 +832,17 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
       const int q = lp % LPP, sp = lp / LPP;
       if (actc && sp < SSPL) {
         const TS* Sg = reinterpret_cast<const TS*>(sbase + (size_t)g * P::S_BYTES) + q * RG;
+        // with one right-hand side, columns jj feed NA independent partial
+        // sums (jj mod NA), added at the end (shorter dependent FMA chains)
+        constexpr int NA = NR == 1 ? 2 : 1;
         if constexpr (P::F2) {
-          float2 acc[RG / 2][NR];
+          float2 acc[NA][RG / 2][NR];
 #pragma unroll
-          for (int h = 0; h < RG / 2; ++h)
+          for (int a = 0; a < NA; ++a)
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr) acc[h][rr] = make_float2(0.f, 0.f);
+            for (int h = 0; h < RG / 2; ++h)
+#pragma unroll
+              for (int rr = 0; rr < NR; ++rr) acc[a][h][rr] = make_float2(0.f, 0.f);
           const float2* rv = reinterpret_cast<const float2*>(pb + P::OFF_R);
 #pragma unroll
           for (int jj = 0; jj < P::JCH; ++jj) {
@@ -840,21 +855,27 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
                 const float2 rj = rv[rr * NV + j];
 #pragma unroll
                 for (int h = 0; h < RG / 2; ++h)
-                  acc[h][rr] = __ffma2_rn(make_float2(sv[2 * h], sv[2 * h + 1]), rj, acc[h][rr]);
+                  acc[jj % NA][h][rr] = __ffma2_rn(make_float2(sv[2 * h], sv[2 * h + 1]), rj, acc[jj % NA][h][rr]);
               }
             }
           }
 #pragma unroll
           for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-            for (int h = 0; h < RG / 2; ++h)
-              *reinterpret_cast<float2*>(part + rr * PARTS + sp * NVP + q * RG + 2 * h) = acc[h][rr];
+            for (int h = 0; h < RG / 2; ++h) {
+              float2 t = acc[0][h][rr];
+              if constexpr (NA == 2) t = make_float2(acc[0][h][rr].x + acc[1][h][rr].x, acc[0][h][rr].y + acc[1][h][rr].y);
+              *reinterpret_cast<float2*>(part + rr * PARTS + sp * NVP + q * RG + 2 * h) = t;
+            }
         } else {
-          T acc[RG][NR];
+          constexpr int NAD = 1;   // FP64: more partial sums cost registers and occupancy
+          T acc[NAD][RG][NR];
 #pragma unroll
-          for (int r = 0; r < RG; ++r)
+          for (int a = 0; a < NAD; ++a)
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr) acc[r][rr] = T(0);
+            for (int r = 0; r < RG; ++r)
+#pragma unroll
+              for (int rr = 0; rr < NR; ++rr) acc[a][r][rr] = T(0);
           const T* rv = pb + P::OFF_R;
 #pragma unroll
           for (int jj = 0; jj < P::JCH; ++jj) {
@@ -866,14 +887,18 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
               for (int rr = 0; rr < NR; ++rr) {
                 const T rj = rv[rr * NV + j];
 #pragma unroll
-                for (int r = 0; r < RG; ++r) acc[r][rr] += sv[r] * rj;
+                for (int r = 0; r < RG; ++r) acc[jj % NAD][r][rr] += sv[r] * rj;
               }
             }
           }
 #pragma unroll
           for (int rr = 0; rr < NR; ++rr)
 #pragma unroll
-            for (int r = 0; r < RG; ++r) part[rr * PARTS + sp * NVP + q * RG + r] = acc[r][rr];
+            for (int r = 0; r < RG; ++r) {
+              T t = acc[0][r][rr];
+              if constexpr (NAD == 4) t = (acc[0][r][rr] + acc[1][r][rr]) + (acc[2][r][rr] + acc[3][r][rr]);
+              part[rr * PARTS + sp * NVP + q * RG + r] = t;
+            }
         }
       }
     }

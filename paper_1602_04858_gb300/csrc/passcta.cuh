@@ -460,10 +460,14 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   }
   __syncthreads();
 
-  // (3) local residual rows, four threads per row
-  T acc[NR];
+  // (3) local residual rows, four threads per row (one right-hand side: two
+  // independent partial sums per thread, shorter FMA chains)
+  constexpr int NA = NR == 1 ? 2 : 1;
+  T acc[NR], acc2[NA][NR];
 #pragma unroll
-  for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
+  for (int a = 0; a < NA; ++a)
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc2[a][rr] = T(0);
   if (row < NV) {
     const T* win = st + C::T_WIN;
 #pragma unroll
@@ -471,7 +475,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
       T wv[NR];
       ld_rhs<T, NR>(win + pw[s] * NR, wv);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) acc[rr] += pc[s] * wv[rr];
+      for (int rr = 0; rr < NR; ++rr) acc2[s % NA][rr] += pc[s] * wv[rr];
     }
 #pragma unroll
     for (int s = 0; s < ZMW; ++s) {
@@ -479,9 +483,11 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
       T wv[NR];
       ld_rhs<T, NR>(win + mw[s] * NR, wv);
 #pragma unroll
-      for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * wv[rr];
+      for (int rr = 0; rr < NR; ++rr) acc2[(s + 1) % NA][rr] += cc * wv[rr];
     }
   }
+#pragma unroll
+  for (int rr = 0; rr < NR; ++rr) acc[rr] = NA == 2 ? acc2[0][rr] + acc2[NA - 1][rr] : acc2[0][rr];
 #pragma unroll
   for (int rr = 0; rr < NR; ++rr) {
     acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 1);

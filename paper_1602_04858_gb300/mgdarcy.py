@@ -30,7 +30,7 @@ API = [
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
     "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
-    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak",
+    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_time_passes",
 ]
 
 
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_sync_batch.argtypes = [vp]
     lib.mg_batch_set_wait_limit.argtypes = [vp, d]
     lib.mg_patch_nnz.argtypes = [vp, i, ctypes.POINTER(i64)]
+    lib.mg_time_passes.argtypes = [vp, i, i, ctypes.POINTER(d)]
     lib.mg_measure_fma_peak.argtypes = [i, ctypes.POINTER(d), vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
@@ -291,6 +292,12 @@ class Multigrid:
         """Nonzeros of the operator rows of one interior patch of a level (mg_patch_nnz)."""
         v = ctypes.c_int64()
         _check(load().mg_patch_nnz(self.h, level, ctypes.byref(v)))
+        return v.value
+
+    def time_passes(self, level, kernel=0):
+        """Microseconds per colour pass of a level (mg_time_passes); kernel 0: the level's own."""
+        v = ctypes.c_double()
+        _check(load().mg_time_passes(self.h, level, int(kernel), ctypes.byref(v)))
         return v.value
 
     def pass_kernel(self, level):

@@ -38,7 +38,7 @@ def oracle_hierarchies():
     return _problems("fp64")[1]
 
 
-@pytest.mark.parametrize("kernel", [0, 4, 1, 2, 3], ids=["rule", "timed", "warp", "block", "persistent"])
+@pytest.mark.parametrize("kernel", [0, 5, 1, 2, 3], ids=["timed", "rule", "warp", "block", "persistent"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_batched_vcycle_matches_oracle(precision, tol, kernel, oracle_hierarchies):
     probs, _ = _problems(precision, kernel)
