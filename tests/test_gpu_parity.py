@@ -354,17 +354,25 @@ def test_additive_solve_reaches_1e8(case):
 
 
 def test_pass_kernel_choice():
-    """Explicit choices are kept; the default rule takes the block kernel
-    where a level's largest colour holds at most 10,000 inverse entries per SM."""
+    """Explicit choices are kept; the fixed rule (pass_kernel 5) takes the
+    block kernel where a level's largest colour holds at most 10,000 inverse
+    entries per SM; the default timed trial picks, per level, a kernel whose
+    measured pass time is within the timing noise of the fastest."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     case = CASES[1]
     for pk, want in ((1, 1), (2, 2), (3, 3)):
         _, G = build(case, pass_kernel=pk)
         assert all(G.pass_kernel(j) == want for j in range(1, case[4]))
-    _, G = build(case)
+    _, G = build(case, pass_kernel=5)
     for j in range(1, case[4]):
         mx, nv = max(G.patch_info(j, c) for c in range(9))
         assert G.pass_kernel(j) == (2 if mx * nv * nv <= 10000 * nsm else 1)
+    for precision in ("fp32", "fp64"):
+        _, G = build(case, precision=precision)
+        for j in range(1, case[4]):
+            t = [G.time_passes(j, k) for k in (1, 2, 3)]
+            assert G.pass_kernel(j) in (1, 2, 3)
+            assert t[G.pass_kernel(j) - 1] <= 1.25 * min(t) + 0.3, (precision, j, t, G.pass_kernel(j))
     with pytest.raises(mgdarcy.MGError):
         G.pass_kernel(0)
 
