@@ -25,10 +25,17 @@ def workload():
     return w, H
 
 
-def _gpu(w, prec):
+@pytest.fixture(scope="module")
+def oracle_vcycle(workload):
+    w, H = workload
+    r = np.random.default_rng(2).standard_normal(H.levels[-1].S.ndof)
+    return r, mg.vcycle(H, r, m_fine=2, variable=True)
+
+
+def _gpu(w, prec, pass_kernel=0):
     return mgdarcy.Multigrid(w["d"], w["n_coarse"], w["n_levels"], w["degree"], w["mu"],
                              torch.as_tensor(w["c"], device="cuda"), precision=prec, m_fine=2,
-                             variable_cycle=True)
+                             variable_cycle=True, pass_kernel=pass_kernel)
 
 
 def test_fullsize_apply(workload):
@@ -43,15 +50,15 @@ def test_fullsize_apply(workload):
     assert np.all(np.abs(y.cpu().numpy() - yo) <= bound)
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3], ids=["timed", "warp", "block", "persistent"])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-3)])
-def test_fullsize_vcycle(workload, prec, tol):
+def test_fullsize_vcycle(workload, oracle_vcycle, prec, tol, kernel):
+    """Every colour-pass kernel on every level of the benchmark."""
     w, H = workload
-    LJ = H.levels[-1]
-    G = _gpu(w, prec)
-    r = np.random.default_rng(2).standard_normal(LJ.S.ndof)
-    z = torch.zeros(LJ.S.ndof, dtype=torch.float64, device="cuda")
+    r, zo = oracle_vcycle
+    G = _gpu(w, prec, kernel)
+    z = torch.zeros(r.size, dtype=torch.float64, device="cuda")
     G.vcycle(torch.as_tensor(r, device="cuda"), z)
-    zo = mg.vcycle(H, r, m_fine=2, variable=True)
     err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
     assert err < tol, err
 
