@@ -54,22 +54,29 @@ def conv3x3_backward(x, w, gy):
     return gxp[:, 1:-1, 1:-1], gw, gy.sum(axis=(1, 2))
 
 
-def forward(params, x):
-    """Returns the output and the per-layer inputs/pre-activations for backward."""
+def forward(params, x, store=None):
+    """Returns the output and the per-layer inputs/pre-activations for backward.
+
+    store: None, or a function applied to every hidden pre-activation as it is
+    kept (a network that stores its hidden activations in a narrower format
+    is the same definition with store = that rounding); the output layer is
+    not rounded."""
     acts = [x]
     pre = []
     h = x
     for li, (w, b) in enumerate(params):
         z = conv3x3(h, w, b)
+        if store is not None and li < len(params) - 1:
+            z = store(z)
         pre.append(z)
         h = np.maximum(z, 0.0) if li < len(params) - 1 else z
         acts.append(h)
     return h, (acts, pre)
 
 
-def loss_and_grads(params, x, target):
+def loss_and_grads(params, x, target, store=None):
     """MSE loss mean((y - target)^2) and its gradients with respect to every parameter."""
-    y, (acts, pre) = forward(params, x)
+    y, (acts, pre) = forward(params, x, store)
     diff = y - target
     loss = float(np.mean(diff * diff))
     g = 2.0 * diff / diff.size

@@ -169,6 +169,250 @@ __global__ void __launch_bounds__(TILE* TILE) k_conv_wgrad(const float* __restri
   }
 }
 
+// --- tensor-core convolutions ------------------------------------------------
+// The 32-channel layers are contractions over K = 9 taps x 32 channels per
+// output pixel: implicit GEMMs on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation).  An FP32 operand (the backward signal) enters
+// as two BF16 parts, hi = bf16(v) and lo = bf16(v - hi), each multiplied and
+// accumulated in FP32, so that it keeps 16 significant bits.
+constexpr int MT_CP = 40;                  // channel pitch of a pixel in shared memory (bank-conflict-free rows)
+constexpr int MT_HALO = TILE + 2;          // 18 x 18 input pixels per 16 x 16 output tile
+constexpr int MT_KP = 9 * 32 + 8;          // weight row pitch (K = 288 plus padding)
+constexpr int MT_WARPS = 8;                // warp w computes output rows 2w, 2w + 1 of the tile
+
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// Shared memory of k_conv_mma: NPART input parts [18][18][MT_CP] then the
+// weights [NOUTP][MT_KP], all BF16.
+template <int NPART, int NOUTP>
+constexpr size_t conv_mma_smem() {
+  return sizeof(__nv_bfloat16) * ((size_t)NPART * MT_HALO * MT_HALO * MT_CP + (size_t)NOUTP * MT_KP);
+}
+
+// One 3x3 convolution from 32 input channels to NOUT output channels as an
+// implicit GEMM per 16 x 16 output tile: M = 256 pixels, N = NOUT (padded to
+// NOUTP, a multiple of 8), K = 288 ordered (tap, channel).
+//  forward (DGRAD false): in = the BF16 pre-activation of the previous layer,
+//    ReLU applied on load; y = conv + bias in BF16 (and yf in FP32 if given);
+//  input gradient (DGRAD true): in = the FP32 gradient of the layer output
+//    (two BF16 parts), the flipped kernel with input and output channels
+//    swapped; gx = result times the ReLU mask of zin (the pre-activation that
+//    fed this layer), FP32.
+template <int NOUT, bool DGRAD>
+__global__ void __launch_bounds__(MT_WARPS * 32) k_conv_mma(const void* __restrict__ in_, const __nv_bfloat16* __restrict__ w,
+                                                          const float* __restrict__ bias,
+                                                          const __nv_bfloat16* __restrict__ zin, int n,
+                                                          __nv_bfloat16* __restrict__ y, float* __restrict__ yf) {
+  constexpr int NPART = DGRAD ? 2 : 1;
+  constexpr int NOUTP = (NOUT + 7) / 8 * 8;
+  constexpr int NT = NOUTP / 8;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(smraw);       // [NPART][18][18][MT_CP]
+  __nv_bfloat16* ws = xs + (size_t)NPART * MT_HALO * MT_HALO * MT_CP;  // [NOUTP][MT_KP]
+  const int b = blockIdx.z, tx0 = blockIdx.x * TILE, ty0 = blockIdx.y * TILE;
+  const int tid = threadIdx.x;
+  const int64_t plane = (int64_t)n * n;
+  // input tile with a one-pixel halo (zero outside the image), channels fastest
+  for (int q = tid; q < 32 * MT_HALO * MT_HALO; q += MT_WARPS * 32) {
+    const int c = q / (MT_HALO * MT_HALO), r = q - c * MT_HALO * MT_HALO;
+    const int yy = r / MT_HALO, xx = r - yy * MT_HALO;
+    const int gy = ty0 + yy - 1, gx = tx0 + xx - 1;
+    const bool inside = gy >= 0 && gy < n && gx >= 0 && gx < n;
+    const int64_t gi = ((int64_t)b * 32 + c) * plane + (int64_t)gy * n + gx;
+    __nv_bfloat16* dst = xs + ((size_t)yy * MT_HALO + xx) * MT_CP + c;
+    if constexpr (DGRAD) {
+      const float v = inside ? reinterpret_cast<const float*>(in_)[gi] : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16(v);
+      dst[0] = hi;
+      dst[(size_t)MT_HALO * MT_HALO * MT_CP] = __float2bfloat16(v - __bfloat162float(hi));
+    } else {
+      float v = inside ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(in_)[gi]) : 0.f;
+      dst[0] = __float2bfloat16(fmaxf(v, 0.f));   // ReLU of a BF16 value is exact
+    }
+  }
+  // weights as B[k = tap * 32 + input channel][output channel], one row per output channel
+  for (int q = tid; q < NOUTP * 288; q += MT_WARPS * 32) {
+    const int o = q / 288, k = q - o * 288, t = k >> 5, c = k & 31;
+    __nv_bfloat16 v = __float2bfloat16(0.f);
+    if (o < NOUT) {
+      if constexpr (DGRAD) v = w[((int64_t)c * 32 + o) * 9 + (8 - t)];   // layer weight [c][o][tap], flipped
+      else v = w[((int64_t)o * 32 + c) * 9 + t];
+    }
+    ws[(size_t)o * MT_KP + k] = v;
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[m][j][i] = 0.f;
+#pragma unroll 2
+  for (int kt = 0; kt < 18; ++kt) {
+    const int t = kt >> 1, c0 = (kt & 1) * 16, dy = t / 3, dx = t - 3 * dy;
+    uint32_t bfr[NT][2];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const __nv_bfloat16* wr = ws + (size_t)(j * 8 + g) * MT_KP + kt * 16 + 2 * tq;
+      bfr[j][0] = ld_u32(wr);
+      bfr[j][1] = ld_u32(wr + 8);
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int py = 2 * warp + m;
+#pragma unroll
+      for (int part = 0; part < NPART; ++part) {
+        const __nv_bfloat16* xr = xs + (size_t)part * MT_HALO * MT_HALO * MT_CP +
+                                  ((size_t)(py + dy) * MT_HALO + dx) * MT_CP + c0 + 2 * tq;
+        uint32_t a[4];
+        a[0] = ld_u32(xr + (size_t)g * MT_CP);
+        a[1] = ld_u32(xr + (size_t)(g + 8) * MT_CP);
+        a[2] = ld_u32(xr + (size_t)g * MT_CP + 8);
+        a[3] = ld_u32(xr + (size_t)(g + 8) * MT_CP + 8);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) mma_16816(acc[m][j], a, bfr[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int oy = ty0 + 2 * warp + m;
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int o = j * 8 + 2 * tq + (i & 1), ox = tx0 + g + (i >= 2 ? 8 : 0);
+        if (o >= NOUT || ox >= n || oy >= n) continue;
+        const int64_t oi = ((int64_t)b * NOUT + o) * plane + (int64_t)oy * n + ox;
+        if constexpr (DGRAD) {
+          float v = acc[m][j][i];
+          if (zin && __bfloat162float(zin[oi]) <= 0.f) v = 0.f;
+          yf[oi] = v;
+        } else {
+          const float v = acc[m][j][i] + bias[o];
+          y[oi] = __float2bfloat16(v);
+          if (yf) yf[oi] = v;
+        }
+      }
+  }
+}
+
+// Weight and bias gradients of a 32 -> 32 layer per 16 x 16 tile of one image
+// as a GEMM on the tensor cores: C[o][tap * 32 + c] = sum over the tile's
+// pixels of gz[o][p] act(x)[c][p + tap offset], M = 32, N = 288, K = 256
+// pixels (one k-step per tile row).  gz (FP32) enters as two BF16 parts; the
+// activations are BF16 values with the ReLU applied, exact.  Shared memory:
+// gz parts [2][32][WG_PITCH], then act(x) shifted by dx = 0, 1, 2 so that pixel
+// pairs start on 4-byte boundaries: [3][32][18][WX_PITCH].
+constexpr int WG_PITCH = TILE * TILE + 8;
+constexpr int WX_PITCH = 20;
+constexpr size_t wgrad_mma_smem() {
+  return sizeof(__nv_bfloat16) * ((size_t)2 * 32 * WG_PITCH + (size_t)3 * 32 * MT_HALO * WX_PITCH);
+}
+
+__global__ void __launch_bounds__(MT_WARPS * 32) k_wgrad_mma(const float* __restrict__ gz,
+                                                           const __nv_bfloat16* __restrict__ x, int n,
+                                                           float* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __nv_bfloat16* gs = reinterpret_cast<__nv_bfloat16*>(smraw);   // [2][32][WG_PITCH]
+  __nv_bfloat16* xs = gs + (size_t)2 * 32 * WG_PITCH;             // [3][32][18][WX_PITCH]
+  const int b = blockIdx.z, tx0 = blockIdx.x * TILE, ty0 = blockIdx.y * TILE;
+  const int tid = threadIdx.x;
+  const int64_t plane = (int64_t)n * n;
+  for (int q = tid; q < 32 * TILE * TILE; q += MT_WARPS * 32) {
+    const int o = q / (TILE * TILE), p = q - o * TILE * TILE;
+    const int yy = ty0 + p / TILE, xx = tx0 + p % TILE;
+    const float v = (yy < n && xx < n) ? gz[((int64_t)b * 32 + o) * plane + (int64_t)yy * n + xx] : 0.f;
+    const __nv_bfloat16 hi = __float2bfloat16(v);
+    gs[(size_t)o * WG_PITCH + p] = hi;
+    gs[(size_t)(32 + o) * WG_PITCH + p] = __float2bfloat16(v - __bfloat162float(hi));
+  }
+  for (int q = tid; q < 3 * 32 * MT_HALO * TILE; q += MT_WARPS * 32) {
+    const int dx = q / (32 * MT_HALO * TILE), r0 = q - dx * 32 * MT_HALO * TILE;
+    const int c = r0 / (MT_HALO * TILE), r = r0 - c * MT_HALO * TILE;
+    const int yy = r / TILE, xs_ = r - yy * TILE;
+    const int gy = ty0 + yy - 1, gx = tx0 + xs_ + dx - 1;
+    float v = 0.f;
+    if (gy >= 0 && gy < n && gx >= 0 && gx < n)
+      v = fmaxf(__bfloat162float(x[((int64_t)b * 32 + c) * plane + (int64_t)gy * n + gx]), 0.f);
+    xs[(((size_t)dx * 32 + c) * MT_HALO + yy) * WX_PITCH + xs_] = __float2bfloat16(v);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+  constexpr int NTW = 5;   // n-tiles per warp: w, w + 8, ..., up to 36 tiles
+  float acc[2][NTW][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NTW; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[m][j][i] = 0.f;
+  for (int kt = 0; kt < TILE; ++kt) {   // pixel row kt of the tile
+    uint32_t bfr[NTW][2];
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+      const int nt = warp + 8 * j;
+      if (nt < 36) {
+        const int nn = nt * 8 + g, t = nn >> 5, c = nn & 31, dy = t / 3, dx = t - 3 * dy;
+        const __nv_bfloat16* xr = xs + (((size_t)dx * 32 + c) * MT_HALO + kt + dy) * WX_PITCH + 2 * tq;
+        bfr[j][0] = ld_u32(xr);
+        bfr[j][1] = ld_u32(xr + 8);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const __nv_bfloat16* gr = gs + ((size_t)part * 32 + m * 16 + g) * WG_PITCH + kt * TILE + 2 * tq;
+        uint32_t a[4];
+        a[0] = ld_u32(gr);
+        a[1] = ld_u32(gr + (size_t)8 * WG_PITCH);
+        a[2] = ld_u32(gr + 8);
+        a[3] = ld_u32(gr + (size_t)8 * WG_PITCH + 8);
+#pragma unroll
+        for (int j = 0; j < NTW; ++j)
+          if (warp + 8 * j < 36) mma_16816(acc[m][j], a, bfr[j]);
+      }
+  }
+  constexpr int NW = 32 * 32 * 9;
+  const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  float* pb = partial + blk * (NW + 32);
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int j = 0; j < NTW; ++j) {
+      const int nt = warp + 8 * j;
+      if (nt >= 36) continue;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int o = m * 16 + g + (i >= 2 ? 8 : 0), nn = nt * 8 + 2 * tq + (i & 1);
+        const int t = nn >> 5, c = nn & 31;
+        pb[((size_t)o * 32 + c) * 9 + t] = acc[m][j][i];
+      }
+    }
+  // bias gradient: the tile's sum of gz per output channel (FP32)
+  for (int o = warp; o < 32; o += MT_WARPS) {
+    float s = 0.f;
+    for (int p = lane; p < TILE * TILE; p += 32) {
+      const int yy = ty0 + p / TILE, xx = tx0 + p % TILE;
+      if (yy < n && xx < n) s += gz[((int64_t)b * 32 + o) * plane + (int64_t)yy * n + xx];
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) s += __shfl_xor_sync(0xffffffffu, s, sh);
+    if (lane == 0) pb[NW + o] = s;
+  }
+}
+
 __global__ void k_sum_partials(const float* __restrict__ partial, int64_t nblk, int m, float* __restrict__ out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
@@ -340,12 +584,41 @@ void conv_wgrad(const mg_cnn* N, const float* gz, const TIN* x, int relu_in, int
   k_sum_partials<<<cdiv(mw, 256), 256, 0, N->stream>>>(N->partial, nblk, mw, gw);
 }
 
-// forward of the whole network on `batch` inputs (FP32, B x 3 x n x n)
+// 32-input-channel convolution on the tensor cores (k_conv_mma).
+template <int NOUT, bool DGRAD>
+void conv_mma(const mg_cnn* N, const void* in, const __nv_bfloat16* w, const float* bias, const __nv_bfloat16* zin,
+              int batch, __nv_bfloat16* y, float* yf) {
+  constexpr size_t smem = conv_mma_smem<DGRAD ? 2 : 1, (NOUT + 7) / 8 * 8>();
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_conv_mma<NOUT, DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  const dim3 grid(cdiv(N->n, TILE), cdiv(N->n, TILE), batch);
+  k_conv_mma<NOUT, DGRAD><<<grid, MT_WARPS * 32, smem, N->stream>>>(in, w, bias, zin, N->n, y, yf);
+}
+
+// weight and bias gradients of a 32 -> 32 layer on the tensor cores
+void wgrad_mma(const mg_cnn* N, const float* gz, const __nv_bfloat16* x, int batch, float* gw) {
+  constexpr size_t smem = wgrad_mma_smem();
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_wgrad_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  const dim3 grid(cdiv(N->n, TILE), cdiv(N->n, TILE), batch);
+  k_wgrad_mma<<<grid, MT_WARPS * 32, smem, N->stream>>>(gz, x, N->n, N->partial);
+  const int64_t nblk = (int64_t)grid.x * grid.y * grid.z;
+  const int mw = 32 * 32 * 9 + 32;
+  k_sum_partials<<<cdiv(mw, 256), 256, 0, N->stream>>>(N->partial, nblk, mw, gw);
+}
+
+// forward of the whole network on `batch` inputs (FP32, B x 3 x n x n): the
+// first layer (3 input channels, K = 27) on the CUDA cores, the three layers
+// with 32 input channels on the tensor cores
 void forward(mg_cnn* N, const float* in, int batch) {
   conv_fwd<3, 32, float>(N, in, 0, N->wbf + N->woff[0], N->master + N->boff[0], batch, N->z[0], nullptr);
-  conv_fwd<32, 32, __nv_bfloat16>(N, N->z[0], 1, N->wbf + N->woff[1], N->master + N->boff[1], batch, N->z[1], nullptr);
-  conv_fwd<32, 32, __nv_bfloat16>(N, N->z[1], 1, N->wbf + N->woff[2], N->master + N->boff[2], batch, N->z[2], nullptr);
-  conv_fwd<32, 3, __nv_bfloat16>(N, N->z[2], 1, N->wbf + N->woff[3], N->master + N->boff[3], batch, N->z[3], N->outf);
+  conv_mma<32, false>(N, N->z[0], N->wbf + N->woff[1], N->master + N->boff[1], nullptr, batch, N->z[1], nullptr);
+  conv_mma<32, false>(N, N->z[1], N->wbf + N->woff[2], N->master + N->boff[2], nullptr, batch, N->z[2], nullptr);
+  conv_mma<3, false>(N, N->z[2], N->wbf + N->woff[3], N->master + N->boff[3], nullptr, batch, N->z[3], N->outf);
 }
 
 // gradients of the mean squared error into N->grad; returns the loss
@@ -356,10 +629,10 @@ mg_status backward(mg_cnn* N, const float* in, const float* target, int batch, f
   // layer 3 (32 -> 3), input z[2] through ReLU
   conv_wgrad<32, 3, __nv_bfloat16>(N, g3, N->z[2], 1, batch, N->grad + N->woff[3]);
   conv_dgrad<32, 3>(N, g3, N->wbf + N->woff[3], N->z[2], batch, N->gbuf[1]);
-  conv_wgrad<32, 32, __nv_bfloat16>(N, N->gbuf[1], N->z[1], 1, batch, N->grad + N->woff[2]);
-  conv_dgrad<32, 32>(N, N->gbuf[1], N->wbf + N->woff[2], N->z[1], batch, N->gbuf[0]);
-  conv_wgrad<32, 32, __nv_bfloat16>(N, N->gbuf[0], N->z[0], 1, batch, N->grad + N->woff[1]);
-  conv_dgrad<32, 32>(N, N->gbuf[0], N->wbf + N->woff[1], N->z[0], batch, N->gbuf[1]);
+  wgrad_mma(N, N->gbuf[1], N->z[1], batch, N->grad + N->woff[2]);
+  conv_mma<32, true>(N, N->gbuf[1], N->wbf + N->woff[2], nullptr, N->z[1], batch, nullptr, N->gbuf[0]);
+  wgrad_mma(N, N->gbuf[0], N->z[0], batch, N->grad + N->woff[1]);
+  conv_mma<32, true>(N, N->gbuf[0], N->wbf + N->woff[1], nullptr, N->z[0], batch, nullptr, N->gbuf[1]);
   conv_wgrad<3, 32, float>(N, N->gbuf[1], in, 0, batch, N->grad + N->woff[0]);
   std::vector<float> lp(cdiv(cnt, 256));
   mg_status st = cnn_cuda(cudaMemcpyAsync(lp.data(), N->lpart, lp.size() * sizeof(float), cudaMemcpyDeviceToHost,
