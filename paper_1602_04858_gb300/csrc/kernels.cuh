@@ -622,15 +622,6 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   auto st_T = [&](int bi) {
     return reinterpret_cast<T*>(wbase + NSB * P::STAGE_S + (size_t)bi * P::STAGE_T) + g * P::T_PER_PATCH;
   };
-  auto st_Bb = [&](int bi) {   // patch-row segment bases
-    return reinterpret_cast<int64_t*>(wbase + NSB * P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B) +
-           g * P::NSEGB;
-  };
-  auto st_Bi = [&](int bi) {   // patch-row segment (length, first row, window column)
-    return reinterpret_cast<int4*>(wbase + NSB * P::STAGE_S + 2 * P::STAGE_T + (size_t)bi * P::STAGE_B +
-                                   P::STAGE_BI) +
-           g * P::NSEGB;
-  };
   auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
 
   // (1) bulk copies of the inverses of patch group pg into buffer sb (lane 0)
@@ -659,68 +650,51 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     for (int e = 0; e < D; ++e) v[e] = 2;
     return false;
   };
-  // this lane's gather segments (the same for every patch), kept in registers
-  int4 sd0[NSI], sd1[NSI], sd2[NSI], sd3[NSI];
+  // this lane's gather elements (element lp + LW i of every patch) and patch
+  // rows (lp + LW it), the same for every patch, kept in registers
+  const int2* elw = reinterpret_cast<const int2*>(tabs + P::TB_ELW);
+  const int2* rowd = reinterpret_cast<const int2*>(tabs + P::TB_ROWD);
+  const uint32_t* valp = reinterpret_cast<const uint32_t*>(tabs + P::TB_VAL);
+  int2 el[P::EPL];
 #pragma unroll
-  for (int i = 0; i < NSI; ++i) {
-    const int s = lp + i * LW;
-    if (s < P::NSEG) {
-      sd0[i] = __ldg(segs + 4 * s);
-      sd1[i] = __ldg(segs + 4 * s + 1);
-      sd2[i] = __ldg(segs + 4 * s + 2);
-      sd3[i] = __ldg(segs + 4 * s + 3);
-    } else {
-      sd0[i] = make_int4(-1, 0, 0, 0);
-      sd1[i] = sd2[i] = sd3[i] = make_int4(0, 0, 0, 0);
-    }
-  }
-  // (2) asynchronous gather of the window, the patch rows of b and the cells;
-  //     window entries outside the domain are zero
-  auto issue_gather = [&](int bi, const int (&v)[D], bool act) {
+  for (int i = 0; i < P::EPL; ++i) el[i] = __ldg(elw + i * LW + lp);
+  int2 rd[P::NROWIT];
+#pragma unroll
+  for (int it = 0; it < P::NROWIT; ++it) rd[it] = __ldg(rowd + it * LW + lp);
+  // array offsets of the patch at vertex v for each component (elements and rows add their own)
+  auto offsets = [&](const int (&v)[D], int (&Pv)[D + 2]) {
+#pragma unroll
+    for (int c = 0; c < D + 2; ++c) Pv[c] = (int)vertex_offset<D, K>(L.N, L.n, c, v);
+  };
+  auto pick = [](const int (&Pv)[D + 2], int c) {
+    int r = Pv[0];
+#pragma unroll
+    for (int q = 1; q < D + 2; ++q) r = (c == q) ? Pv[q] : r;
+    return r;
+  };
+  // (2) asynchronous gather of the window, the patch rows of b and the cells:
+  //     one entry per element, consecutive lanes to consecutive shared-memory
+  //     words; window entries outside the domain (vmask bit clear) are zero
+  auto issue_gather = [&](int bi, const int (&v)[D], bool act, uint32_t vmask) {
     T* tw = st_T(bi);
-    int64_t* bb = st_Bb(bi);
-    int4* binf = st_Bi(bi);
     if (act) {
+      int Pv[D + 2];
+      offsets(v, Pv);
 #pragma unroll
-      for (int si = 0; si < NSI; ++si) {
-        const int4 d0 = sd0[si], d1 = sd1[si], d2 = sd2[si], d3 = sd3[si];
-        const int kind = d0.x, len = d0.y, dst = d0.z;
-        if (kind < 0) continue;
-        int64_t src = (int64_t)d0.w + (int64_t)v[0] * d1.x + (int64_t)v[1] * d1.y;
-        if constexpr (D == 3) src += (int64_t)v[2] * d1.z;
-        const int m = d1.w;
-        bool okr;
-        {
-          const int ix = m * v[1] + d2.y;
-          okr = ix >= 0 && ix <= d3.x;
-        }
-        if constexpr (D == 3) {
-          const int ix = m * v[2] + d2.z;
-          okr = okr && ix >= 0 && ix <= d3.y;
-        }
-        const int i0 = m * v[0] + d2.x, hi0 = d2.w;
-        // entries [ilo, ihi) of the segment lie in the domain
-        const int ilo = okr ? (i0 < 0 ? -i0 : 0) : len;
-        const int ihi = (hi0 - i0 + 1 < len) ? hi0 - i0 + 1 : len;
+      for (int i = 0; i < P::EPL; ++i) {
+        const int pk = el[i].y, kind = elem_kind(pk);
+        if (kind == 3) continue;
+        const int gi = el[i].x + pick(Pv, elem_comp(pk));
+        const int dst = elem_dst(pk);
         if (kind == 2) {
-#pragma unroll
-          for (int i = 0; i < 2; ++i) cp_async_t(tw + P::OFF_C + dst + i, L.c + (src + i), true);
+          cp_async_t(tw + P::OFF_C + dst, L.c + gi, true);
         } else {
+          const bool ok = (vmask >> i) & 1u;
           const T* base = (kind == 0) ? x : b;
           T* dd = tw + ((kind == 0) ? P::OFF_W : P::OFF_B) + dst;
           const int rs = (kind == 0) ? WIN : NV;
-          if (kind == 1) {
-            bb[d3.w] = src;
-            binf[d3.w] = make_int4(len, dst, d3.z, 0);
-          }
 #pragma unroll
-          for (int rr = 0; rr < NR; ++rr)
-#pragma unroll
-            for (int i = 0; i < P::LMAX; ++i)
-              if (i < len) {
-                if (i >= ilo && i < ihi) cp_async_t(dd + rr * rs + i, base + (src + rr * vs + i), true);
-                else dd[rr * rs + i] = T(0);
-              }
+          for (int rr = 0; rr < NR; ++rr) cp_async_t(dd + rr * rs, ok ? base + (gi + rr * vs) : base, ok);
         }
       }
     }
@@ -734,6 +708,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   // preceding kernel (the tables do not depend on it)
   PlanRegs<P, T> R;
   int rtype = patch_type<D>(vc, L.n);
+  uint32_t vmc = __ldg(valp + rtype * LW + lp);
   R.load(plan_p + (size_t)rtype * PSum::ZP * LW * PB, plan_m + (size_t)rtype * PSum::ZM * LW * MASS_BYTES);
   // row maps of this lane's patch rows, for the current group; those of the
   // next group are loaded while the current one is computed
@@ -757,7 +732,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncwarp();
-  if (pg < ngroups) issue_gather(0, vc, actc);
+  if (pg < ngroups) issue_gather(0, vc, actc, vmc);
   for (int k = 0; pg < ngroups; ++k, pg += W) {
     const int bi = k & 1;
     const int sb = (NSB == 1) ? 0 : (k % NSB);
@@ -765,9 +740,10 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     int vn[D];
     const bool actn = vertex(pn, vn);
     uint32_t rpn[P::NROWIT];
-    load_rowmap(patch_type<D>(vn, L.n), rpn);
+    const int tn = patch_type<D>(vn, L.n);
+    load_rowmap(tn, rpn);
     if (pn < ngroups) {   // gather the next group while this one is computed
-      issue_gather(bi ^ 1, vn, actn);
+      issue_gather(bi ^ 1, vn, actn, __ldg(valp + tn * LW + lp));
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -905,28 +881,23 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     __syncwarp();
     // the inverses are consumed: copy those of the group NSB iterations ahead
     if (lane == 0 && pg + NSB * W < ngroups) issue_S(pg + NSB * W, sb);
-    // (5) x|_v = window copy of x|_v + delta, by patch-row segments
+    // (5) x|_v = window copy of x|_v + delta, one patch row per lane and step
     if (actc) {
-      const int64_t* bb = st_Bb(bi);
-      const int4* binf = st_Bi(bi);
-      for (int s = lp; s < P::NSEGB; s += LW) {
-        const int4 inf = binf[s];
-        const int len = inf.x, l0 = inf.y, wst = inf.z;
-        T* xs = x + bb[s];
-        const T* ws = win + wst;
-        const T* ps = part + l0;
+      int Pv[D + 2];
+      offsets(vc, Pv);
 #pragma unroll
-        for (int i = 0; i < P::LMAXB; ++i)
-          if (i < len) {
+      for (int it = 0; it < P::NROWIT; ++it) {
+        const int rp = rd[it].y;
+        if (!row_valid(rp)) continue;
+        const int l = lp + LW * it, gi = rd[it].x + pick(Pv, row_comp(rp)), wc = row_wcol(rp);
 #pragma unroll
-            for (int rr = 0; rr < NR; ++rr) {
-              T a = ps[rr * PARTS + i];
+        for (int rr = 0; rr < NR; ++rr) {
+          T a = part[rr * PARTS + l];
 #pragma unroll
-              for (int s2 = 1; s2 < SSPL; ++s2) a += ps[rr * PARTS + s2 * NVP + i];
-              if constexpr (P::BF) a *= pb[P::OFF_SC + l0 + i];
-              xs[rr * vs + i] = ws[rr * WIN + i] + a;
-            }
-          }
+          for (int s2 = 1; s2 < SSPL; ++s2) a += part[rr * PARTS + s2 * NVP + l];
+          if constexpr (P::BF) a *= pb[P::OFF_SC + l];
+          x[gi + rr * vs] = win[rr * WIN + wc] + a;
+        }
       }
     }
     __syncwarp();

@@ -229,7 +229,11 @@ struct PassShape {
   static constexpr size_t STAGE_BI = (((size_t)GPW * NSEGB * sizeof(int64_t) + 15) / 16) * 16;
   static constexpr size_t STAGE_B = STAGE_BI + (size_t)GPW * NSEGB * 16;
   static constexpr int NSI = (NSEG + LW - 1) / LW;         // gather segments per lane
-  static constexpr size_t WARP_BYTES = NSB * STAGE_S + 2 * (STAGE_T + STAGE_B);
+  // gather elements: every window column, patch row of b and cell of one
+  // patch, element e taken by lane e mod LW (EPL per lane)
+  static constexpr int NE = WIN + NV + NC;
+  static constexpr int EPL = (NE + LW - 1) / LW;
+  static constexpr size_t WARP_BYTES = NSB * STAGE_S + 2 * STAGE_T;
   static constexpr size_t SMEM = (size_t)WARPS * WARP_BYTES + (size_t)WARPS * NSB * sizeof(uint64_t) + 16;
   // per-level tables
   static constexpr int NTYPE = (D == 2) ? 16 : 64;
@@ -238,7 +242,16 @@ struct PassShape {
   static constexpr size_t TB_PLAIN = al16((size_t)NSEG * SEG_INTS * 4);
   static constexpr size_t TB_MASS = TB_PLAIN + al16((size_t)NTYPE * PSum::ZP * LW * plain_bytes<T>());
   static constexpr size_t TB_ROWP = TB_MASS + al16((size_t)NTYPE * PSum::ZM * LW * MASS_BYTES);
-  static constexpr size_t TAB_BYTES = TB_ROWP + al16((size_t)NTYPE * NV * 4);
+  // element descriptors [i][lane] (int2: array index at v = 0, packed kind |
+  // component | destination), row descriptors [it][lane] (int2: array index at
+  // v = 0, packed component | window column | valid), in-domain masks
+  // [type][lane] (bit i: element lane + LW i lies in the domain)
+  static constexpr size_t TB_ELW = TB_ROWP + al16((size_t)NTYPE * NV * 4);
+  static constexpr size_t TB_ROWD = TB_ELW + al16((size_t)EPL * LW * 8);
+  static constexpr size_t TB_VAL = TB_ROWD + al16((size_t)NROWIT * LW * 8);
+  static constexpr size_t TAB_BYTES = TB_VAL + al16((size_t)NTYPE * LW * 4);
+  static_assert(EPL <= 32, "in-domain mask holds 32 elements per lane");
+  static_assert(NR * WIN < 2048 && NR * NV < 2048, "element destinations fit 11 bits");
   static_assert(PL::MAXP <= 4, "row map holds four pieces");
   static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(STAGE_S % 16 == 0 && STAGE_T % 16 == 0 && STAGE_B % 16 == 0 && WARP_BYTES % 16 == 0,
@@ -566,6 +579,117 @@ void make_segments(const Lvl<D, K, T>& L, int* out) {
   }
 }
 
+// Packed element and row descriptors of the warp-per-patch pass.
+//   element: bits 0-1 kind (0 window of x, 1 patch row of b, 2 cell, 3 none),
+//            bits 2-4 component (0 .. D nodes of u_0 .. u_{D-1}, p; D+1 cells),
+//            bits 5-15 destination inside its block (window column, patch row, cell bit)
+//   row:     bits 0-2 component, bits 3-13 window column, bit 14 valid
+__host__ __device__ __forceinline__ int elem_pack(int kind, int comp, int dst) { return kind | (comp << 2) | (dst << 5); }
+__host__ __device__ __forceinline__ int elem_kind(int p) { return p & 3; }
+__host__ __device__ __forceinline__ int elem_comp(int p) { return (p >> 2) & 7; }
+__host__ __device__ __forceinline__ int elem_dst(int p) { return (p >> 5) & 2047; }
+__host__ __device__ __forceinline__ int row_pack(int comp, int wcol) { return comp | (wcol << 3) | (1 << 14); }
+__host__ __device__ __forceinline__ int row_comp(int p) { return p & 7; }
+__host__ __device__ __forceinline__ int row_wcol(int p) { return (p >> 3) & 2047; }
+__host__ __device__ __forceinline__ bool row_valid(int p) { return (p >> 14) & 1; }
+
+// Offset of the array index of a patch at vertex v from its index at v = 0,
+// for component comp (0 .. D: nodes of u_0 .. u_{D-1}, p; D + 1: cells):
+// sum_e v_e step_e, the node step K1 (strides of the component's array) or the
+// cell step.
+template <int D, int K>
+__host__ __device__ __forceinline__ int64_t vertex_offset(int N, int n, int comp, const int (&v)[D]) {
+  constexpr int K1 = K + 1;
+  int64_t off = 0, st = 1;
+#pragma unroll
+  for (int e = 0; e < D; ++e) {
+    if (comp <= D) {
+      off += (int64_t)K1 * v[e] * st;
+      st *= (comp < D && e == comp) ? (N + 1) : N;
+    } else {
+      off += (int64_t)v[e] * st;
+      st *= n;
+    }
+  }
+  return off;
+}
+
+// The warp pass's element, row and in-domain tables from the segment
+// descriptors (expanded entry by entry).
+template <int D, int K, typename T, typename TS>
+void make_warp_elements(const Lvl<D, K, T>& L, const int* seg, int2* elw, int2* rowd, uint32_t* val) {
+  using P = PassShape<D, K, T, TS, 1>;
+  constexpr int LW = P::LW;
+  struct E { int kind, comp, dst; int64_t base; int m; int a[D], hi[D]; int wcol; };
+  std::vector<E> el;
+  for (int s = 0; s < P::NSEG; ++s) {
+    const int* d = seg + (size_t)s * SEG_INTS;
+    int comp = -1;
+    if (d[0] == 2) comp = D + 1;
+    else {   // the component whose array the segment addresses: base = off[c] + sum_e a_e stride_e(c)
+      for (int c = D; c >= 0; --c) {
+        int64_t b0 = d[3];
+        for (int e = 0; e < D; ++e) {
+          int64_t stride = 1;
+          for (int f = 0; f < e; ++f) stride *= (c < D && f == c) ? (L.N + 1) : L.N;
+          b0 -= (int64_t)d[8 + e] * stride;
+        }
+        if (b0 == L.off[c]) { comp = c; break; }
+      }
+    }
+    if (comp < 0) continue;   // not reached: check_pass_tables compares every element with its row
+    for (int i = 0; i < d[1]; ++i) {
+      E e;
+      e.kind = d[0];
+      e.comp = comp;
+      e.dst = d[2] + i;
+      e.base = (int64_t)d[3] + i;
+      e.m = d[7];
+      for (int f = 0; f < D; ++f) {
+        e.a[f] = d[8 + f] + (f == 0 ? i : 0);
+        e.hi[f] = d[11 + f];
+      }
+      e.wcol = d[0] == 1 ? d[14] + i : 0;
+      el.push_back(e);
+    }
+  }
+  for (int i = 0; i < P::EPL; ++i)
+    for (int lp = 0; lp < LW; ++lp) {
+      const int q = lp + LW * i;
+      int2 v2 = make_int2(0, elem_pack(3, 0, 0));
+      if (q < (int)el.size()) v2 = make_int2((int)el[q].base, elem_pack(el[q].kind, el[q].comp, el[q].dst));
+      elw[i * LW + lp] = v2;
+    }
+  for (int it = 0; it < P::NROWIT; ++it)
+    for (int lp = 0; lp < LW; ++lp) {
+      const int l = lp + LW * it;
+      int2 r = make_int2(0, 0);
+      for (const E& e : el)
+        if (e.kind == 1 && e.dst == l) r = make_int2((int)e.base, row_pack(e.comp, e.wcol));
+      rowd[it * LW + lp] = r;
+    }
+  for (int t = 0; t < P::NTYPE; ++t)
+    for (int lp = 0; lp < LW; ++lp) {
+      uint32_t mask = 0;
+      if (type_present<D>(t, L.n)) {
+        int v[D];
+        type_vertex<D>(t, L.n, v);
+        for (int i = 0; i < P::EPL; ++i) {
+          const int q = lp + LW * i;
+          if (q >= (int)el.size()) continue;
+          bool in = true;
+          if (el[q].kind == 0)
+            for (int f = 0; f < D; ++f) {
+              const int ix = el[q].m * v[f] + el[q].a[f];
+              in = in && ix >= 0 && ix <= el[q].hi[f];
+            }
+          if (in) mask |= 1u << i;
+        }
+      }
+      val[t * LW + lp] = mask;
+    }
+}
+
 // Builds the colour-pass tables of one level into blob (P::TAB_BYTES bytes).
 template <int D, int K, typename T, typename TS>
 bool build_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<unsigned char>& blob,
@@ -574,6 +698,10 @@ bool build_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<u
   using PSum = typename P::PSum;
   blob.assign(P::TAB_BYTES, 0);
   make_segments<D, K, T, TS>(L, reinterpret_cast<int*>(blob.data() + P::TB_SEG));
+  make_warp_elements<D, K, T, TS>(L, reinterpret_cast<const int*>(blob.data() + P::TB_SEG),
+                                  reinterpret_cast<int2*>(blob.data() + P::TB_ELW),
+                                  reinterpret_cast<int2*>(blob.data() + P::TB_ROWD),
+                                  reinterpret_cast<uint32_t*>(blob.data() + P::TB_VAL));
   uint32_t* rowp = reinterpret_cast<uint32_t*>(blob.data() + P::TB_ROWP);
   for (int t = 0; t < P::NTYPE; ++t) {
     if (!type_present<D>(t, L.n)) continue;
@@ -792,6 +920,92 @@ int check_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& w
         if (d[14] + i != win_index<D, K>(v, comp, idx)) { why = "row segment window column wrong"; return 1; }
       }
       if (d[15] != s - P::NSEGX) { why = "row segment numbering wrong"; return 1; }
+    }
+  }
+  // warp pass elements: emulate its gather (in-domain masks, zero outside) and
+  // its update addressing for one vertex of each type on x[g] = g + 1
+  {
+    const int2* elw = reinterpret_cast<const int2*>(blob.data() + P::TB_ELW);
+    const int2* rowd = reinterpret_cast<const int2*>(blob.data() + P::TB_ROWD);
+    const uint32_t* val = reinterpret_cast<const uint32_t*>(blob.data() + P::TB_VAL);
+    for (int t = 0; t < P::NTYPE; ++t) {
+      if (!type_present<D>(t, L.n)) continue;
+      int v[D];
+      type_vertex<D>(t, L.n, v);
+      std::vector<double> win(P::WIN, -1.0), brow(P::NV, -1.0), cells(P::NC, -1.0);
+      std::vector<int> seen(P::NE, 0);
+      for (int i = 0; i < P::EPL; ++i)
+        for (int lp = 0; lp < LW; ++lp) {
+          const int2 e2 = elw[i * LW + lp];
+          const int kind = elem_kind(e2.y), comp = elem_comp(e2.y), dst = elem_dst(e2.y);
+          if (kind == 3) continue;
+          const int64_t g = (int64_t)e2.x + vertex_offset<D, K>(L.N, L.n, comp, v);
+          const bool valid = (val[t * LW + lp] >> i) & 1u;
+          if (kind == 0) {
+            if (dst >= P::WIN) { why = "warp element past the window"; return 1; }
+            win[dst] = valid ? (double)(g + 1) : 0.0;
+            ++seen[dst];
+          } else if (kind == 1) {
+            if (dst >= P::NV || !valid) { why = "warp element: bad patch row"; return 1; }
+            brow[dst] = (double)(g + 1);
+            ++seen[P::WIN + dst];
+          } else {
+            if (dst >= P::NC || !valid) { why = "warp element: bad cell"; return 1; }
+            cells[dst] = (double)g;
+            ++seen[P::WIN + P::NV + dst];
+          }
+        }
+      for (int q = 0; q < P::NE; ++q)
+        if (seen[q] != 1) { why = "warp element " + std::to_string(q) + " not gathered exactly once"; return 1; }
+      for (int c = 0; c <= D; ++c) {
+        int ext[D], tot = 1;
+        for (int e = 0; e < D; ++e) {
+          ext[e] = win_extent<D, K>(c, e);
+          tot *= ext[e];
+        }
+        for (int q = 0; q < tot; ++q) {
+          int idx[D], rr = q;
+          bool in = true;
+          for (int e = 0; e < D; ++e) {
+            idx[e] = win_origin<D, K>(v, c, e) + rr % ext[e];
+            rr /= ext[e];
+            const int hi = (c < D && e == c) ? L.N : L.N - 1;
+            in = in && idx[e] >= 0 && idx[e] <= hi;
+          }
+          const double expect = in ? (double)(flat_index(L, c, idx) + 1) : 0.0;
+          if (win[win_index<D, K>(v, c, idx)] != expect) {
+            why = "type " + std::to_string(t) + ": warp element for window column " +
+                  std::to_string(win_index<D, K>(v, c, idx)) + " gathers the wrong entry";
+            return 1;
+          }
+        }
+      }
+      for (int l = 0; l < P::NV; ++l) {
+        int idx[D];
+        const int comp = patch_local_decode<D, K>(v, l, idx);
+        if (brow[l] != (double)(flat_index(L, comp, idx) + 1)) { why = "warp element: patch row wrong"; return 1; }
+      }
+      for (int cb = 0; cb < P::NC; ++cb) {
+        int cell[D];
+        for (int e = 0; e < D; ++e) cell[e] = v[e] - 1 + ((cb >> e) & 1);
+        if (cells[cb] != (double)cell_linear(L, cell)) { why = "warp element: cell wrong"; return 1; }
+      }
+      for (int it = 0; it < P::NROWIT; ++it)
+        for (int lp = 0; lp < LW; ++lp) {
+          const int l = lp + LW * it;
+          const int2 r = rowd[it * LW + lp];
+          if (l >= P::NV) {
+            if (row_valid(r.y)) { why = "row descriptor past the patch marked valid"; return 1; }
+            continue;
+          }
+          int idx[D];
+          const int comp = patch_local_decode<D, K>(v, l, idx);
+          const int64_t g = (int64_t)r.x + vertex_offset<D, K>(L.N, L.n, row_comp(r.y), v);
+          if (!row_valid(r.y) || g != flat_index(L, comp, idx) || row_wcol(r.y) != win_index<D, K>(v, comp, idx)) {
+            why = "type " + std::to_string(t) + ": row descriptor of patch row " + std::to_string(l) + " wrong";
+            return 1;
+          }
+        }
     }
   }
   // patch vertices by multiply-shift division agree with plain division
