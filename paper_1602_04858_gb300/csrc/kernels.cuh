@@ -661,10 +661,24 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   int2 rd[P::NROWIT];
 #pragma unroll
   for (int it = 0; it < P::NROWIT; ++it) rd[it] = __ldg(rowd + it * LW + lp);
-  // array offsets of the patch at vertex v for each component (elements and rows add their own)
+  // array offsets of the patch at vertex v for each component (elements and
+  // rows add their own index at v = 0), in 32 bits: a level has fewer than
+  // 2^31 dofs
   auto offsets = [&](const int (&v)[D], int (&Pv)[D + 2]) {
-#pragma unroll
-    for (int c = 0; c < D + 2; ++c) Pv[c] = (int)vertex_offset<D, K>(L.N, L.n, c, v);
+    constexpr int K1 = K + 1;
+    const int N = L.N, n = L.n;
+    if constexpr (D == 2) {
+      Pv[0] = K1 * (v[0] + v[1] * (N + 1));
+      Pv[1] = K1 * (v[0] + v[1] * N);
+      Pv[2] = Pv[1];
+      Pv[3] = v[0] + v[1] * n;
+    } else {
+      Pv[0] = K1 * (v[0] + (N + 1) * (v[1] + v[2] * N));
+      Pv[1] = K1 * (v[0] + N * (v[1] + v[2] * (N + 1)));
+      Pv[2] = K1 * (v[0] + N * (v[1] + v[2] * N));
+      Pv[3] = Pv[2];
+      Pv[4] = v[0] + n * (v[1] + v[2] * n);
+    }
   };
   auto pick = [](const int (&Pv)[D + 2], int c) {
     int r = Pv[0];
@@ -675,11 +689,10 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   // (2) asynchronous gather of the window, the patch rows of b and the cells:
   //     one entry per element, consecutive lanes to consecutive shared-memory
   //     words; window entries outside the domain (vmask bit clear) are zero
-  auto issue_gather = [&](int bi, const int (&v)[D], bool act, uint32_t vmask) {
+  auto issue_gather = [&](int bi, const int (&v)[D], bool act, uint32_t vmask, int (&Pv)[D + 2]) {
     T* tw = st_T(bi);
+    offsets(v, Pv);
     if (act) {
-      int Pv[D + 2];
-      offsets(v, Pv);
 #pragma unroll
       for (int i = 0; i < P::EPL; ++i) {
         const int pk = el[i].y, kind = elem_kind(pk);
@@ -710,8 +723,8 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   int rtype = patch_type<D>(vc, L.n);
   uint32_t vmc = __ldg(valp + rtype * LW + lp);
   R.load(plan_p + (size_t)rtype * PSum::ZP * LW * PB, plan_m + (size_t)rtype * PSum::ZM * LW * MASS_BYTES);
-  // row maps of this lane's patch rows, for the current group; those of the
-  // next group are loaded while the current one is computed
+  // row maps of this lane's patch rows for the patch type rtype, reloaded with
+  // the plan when the type changes (most patches are interior)
   uint32_t rps[P::NROWIT];
   auto load_rowmap = [&](int type, uint32_t (&o)[P::NROWIT]) {
 #pragma unroll
@@ -732,18 +745,23 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   pdl_launch_dependents();
   pdl_wait();   // x and b come from the preceding kernels
   __syncwarp();
-  if (pg < ngroups) issue_gather(0, vc, actc, vmc);
+  int Pc[D + 2], Pn[D + 2];   // offsets of the current and the next group's patch
+  offsets(vc, Pc);
+  if (pg < ngroups) issue_gather(0, vc, actc, vmc, Pc);
+  int mtype = rtype;   // type of the in-domain mask held in vmc
   for (int k = 0; pg < ngroups; ++k, pg += W) {
     const int bi = k & 1;
     const int sb = (NSB == 1) ? 0 : (k % NSB);
     const int64_t pn = pg + W;
     int vn[D];
     const bool actn = vertex(pn, vn);
-    uint32_t rpn[P::NROWIT];
-    const int tn = patch_type<D>(vn, L.n);
-    load_rowmap(tn, rpn);
     if (pn < ngroups) {   // gather the next group while this one is computed
-      issue_gather(bi ^ 1, vn, actn, __ldg(valp + tn * LW + lp));
+      const int tn = patch_type<D>(vn, L.n);
+      if (tn != mtype) {
+        vmc = __ldg(valp + tn * LW + lp);
+        mtype = tn;
+      }
+      issue_gather(bi ^ 1, vn, actn, vmc, Pn);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -751,6 +769,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     const int type = patch_type<D>(vc, L.n);
     if (type != rtype) {
       R.load(plan_p + (size_t)type * PSum::ZP * LW * PB, plan_m + (size_t)type * PSum::ZM * LW * MASS_BYTES);
+      load_rowmap(type, rps);
       rtype = type;
     }
     __syncwarp();
@@ -883,13 +902,11 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     if (lane == 0 && pg + NSB * W < ngroups) issue_S(pg + NSB * W, sb);
     // (5) x|_v = window copy of x|_v + delta, one patch row per lane and step
     if (actc) {
-      int Pv[D + 2];
-      offsets(vc, Pv);
 #pragma unroll
       for (int it = 0; it < P::NROWIT; ++it) {
         const int rp = rd[it].y;
         if (!row_valid(rp)) continue;
-        const int l = lp + LW * it, gi = rd[it].x + pick(Pv, row_comp(rp)), wc = row_wcol(rp);
+        const int l = lp + LW * it, gi = rd[it].x + pick(Pc, row_comp(rp)), wc = row_wcol(rp);
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) {
           T a = part[rr * PARTS + l];
@@ -904,7 +921,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
 #pragma unroll
     for (int e = 0; e < D; ++e) vc[e] = vn[e];
 #pragma unroll
-    for (int it = 0; it < P::NROWIT; ++it) rps[it] = rpn[it];
+    for (int c = 0; c < D + 2; ++c) Pc[c] = Pn[c];
     actc = actn;
   }
 }
