@@ -17,6 +17,8 @@
 * Vertex patches (Sec. 3.3): for every interior vertex the 2^d cells sharing
   it; the patch space holds the free dofs whose basis functions are supported
   inside the patch, plus all pressure dofs of its cells with zero patch mean.
+  Sec. 3.3 takes a patch for every vertex; the patches of the boundary
+  vertices (cells clipped to the domain) are an option (boundary_patches).
   The Ritz projection is a bordered local solve; S_v is the velocity/pressure
   block of the inverse of the bordered patch matrix.
 * Patch order (not fixed by the paper): colour-major with the 3^d colouring
@@ -171,6 +173,61 @@ def patches(S: Space):
     return colours
 
 
+def boundary_patches_of(S: Space):
+    """Vertex patches of the boundary vertices (Sec. 3.3 defines a patch for
+    every vertex of the mesh; patches() takes the interior ones): the cells
+    that share the vertex, clipped to the domain (2^(d-1) on a face, fewer at
+    an edge or corner), with the free dofs whose support lies in those cells
+    and all pressure dofs of the cells.  Patches without a velocity dof (RT_0
+    corners: a single pressure dof, zero under the mean-zero constraint) are
+    left out.
+
+    Returns, per colour (v_e mod 3, as for the interior patches), a list of
+    groups of equal size: (vertices (P, d), dofs (P, n_v) sorted), sizes
+    ascending.
+    """
+    d, n = S.d, S.n
+    lo, hi = support_ranges(S)
+    free = ~S.constrained()
+    cand = np.nonzero(free)[0]
+    pairs_v, pairs_dof = [], []
+    for choice in np.ndindex(*([2] * d)):
+        ok = np.ones(cand.size, dtype=bool)
+        vv = np.empty((cand.size, d), dtype=np.int64)
+        for e in range(d):
+            v = hi[cand, e] + choice[e]
+            ok &= v <= lo[cand, e] + 1
+            vv[:, e] = v
+        pairs_v.append(vv[ok])
+        pairs_dof.append(cand[ok])
+    V = np.concatenate(pairs_v)
+    Dd = np.concatenate(pairs_dof)
+    onb = np.any((V == 0) | (V == n), axis=1)
+    V, Dd = V[onb], Dd[onb]
+    vid = np.zeros(V.shape[0], dtype=np.int64)
+    stride = 1
+    for e in range(d):
+        vid += V[:, e] * stride
+        stride *= n + 1
+    order = np.lexsort((Dd, vid))
+    vid, Dd, V = vid[order], Dd[order], V[order]
+    starts = np.flatnonzero(np.r_[True, vid[1:] != vid[:-1]])
+    ends = np.r_[starts[1:], vid.size]
+    groups = [dict() for _ in range(3 ** d)]
+    for a, b in zip(starts, ends):
+        dofs = Dd[a:b]
+        if not np.any(dofs < S.n_u):
+            continue
+        v = V[a]
+        col = int(sum((int(v[e]) % 3) * 3 ** e for e in range(d)))
+        groups[col].setdefault(dofs.size, []).append((v, dofs))
+    out = []
+    for col in range(3 ** d):
+        out.append([(np.array([v for v, _ in g]), np.array([dd for _, dd in g]))
+                    for _, g in sorted(groups[col].items())])
+    return out
+
+
 def submatrices(A: sp.csr_matrix, dofs: np.ndarray) -> np.ndarray:
     """Dense A[dofs_p][:, dofs_p] for every patch p: (P, n_v, n_v)."""
     P, nv = dofs.shape
@@ -210,7 +267,13 @@ def patch_inverses(A: sp.csr_matrix, dofs: np.ndarray, w: np.ndarray) -> np.ndar
 
 
 class Level:
-    def __init__(self, S: Space, mu: float, c: np.ndarray, with_patches: bool = True):
+    """One level: operator, and per colour the patch data (dofs, S_v, rows of
+    A) of the interior-vertex patches (colours) and, with boundary_patches, of
+    the boundary-vertex patches (bcolours: per colour a list of such groups,
+    one per patch size)."""
+
+    def __init__(self, S: Space, mu: float, c: np.ndarray, with_patches: bool = True,
+                 boundary_patches: bool = False):
         self.S = S
         self.mu = mu
         self.c = c
@@ -219,6 +282,7 @@ class Level:
         self.free = ~self.cm
         self.w = S.pressure_weights()
         self.colours = []
+        self.bcolours = [[] for _ in range(3 ** S.d)]
         if with_patches and S.n >= 2:
             for verts, dofs in patches(S):
                 if dofs.shape[0] == 0:
@@ -227,12 +291,22 @@ class Level:
                 Sv = patch_inverses(self.A, dofs, self.w)
                 Arows = self.A[dofs.ravel()]
                 self.colours.append((dofs, Sv, Arows))
+            if boundary_patches:
+                for col, groups in enumerate(boundary_patches_of(S)):
+                    for _, dofs in groups:
+                        self.bcolours[col].append((dofs, patch_inverses(self.A, dofs, self.w),
+                                                   self.A[dofs.ravel()]))
+
+    def colour_groups(self, col):
+        """Patch groups (dofs, S_v, rows of A) of one colour: interior, then boundary."""
+        out = [] if self.colours[col] is None else [self.colours[col]]
+        return out + list(self.bcolours[col])
 
 
 class Hierarchy:
     """Levels 0..J with transfers; ``c_fine`` is the finest-level coefficient."""
 
-    def __init__(self, d, n_coarse, n_levels, k, mu, c_fine, coarse_avg="arithmetic"):
+    def __init__(self, d, n_coarse, n_levels, k, mu, c_fine, coarse_avg="arithmetic", boundary_patches=False):
         self.d, self.k, self.mu = d, k, mu
         cs = [np.asarray(c_fine, dtype=np.float64)]
         for _ in range(n_levels - 1):
@@ -241,7 +315,7 @@ class Hierarchy:
         self.levels = []
         for j in range(n_levels):
             S = Space(d, n_coarse * 2 ** j, k)
-            self.levels.append(Level(S, mu, cs[j], with_patches=(j > 0)))
+            self.levels.append(Level(S, mu, cs[j], with_patches=(j > 0), boundary_patches=boundary_patches))
         self.P = [None] + [prolongation(self.levels[j - 1].S, self.levels[j].S)
                            for j in range(1, n_levels)]
         L0 = self.levels[0]
@@ -266,13 +340,13 @@ def smooth_step(L: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray:
     order = list(range(C)) + list(range(C - 2, -1, -1))
     x = x.copy()
     for col in order:
-        entry = L.colours[col]
-        if entry is None:
-            continue
-        dofs, Sv, Arows = entry
-        r = (b[dofs.ravel()] - Arows @ x).reshape(dofs.shape)
-        delta = np.einsum("pij,pj->pi", Sv, r)
-        x[dofs] += delta
+        # the patches of one colour (interior and boundary) do not couple: one update
+        upd = []
+        for dofs, Sv, Arows in L.colour_groups(col):
+            r = (b[dofs.ravel()] - Arows @ x).reshape(dofs.shape)
+            upd.append((dofs, np.einsum("pij,pj->pi", Sv, r)))
+        for dofs, delta in upd:
+            x[dofs] += delta
     return x
 
 
@@ -283,11 +357,9 @@ def additive_step(L: Level, x: np.ndarray, b: np.ndarray, omega: float) -> np.nd
     symmetric, and omega = 1/4 bounds the overlap of the 2-D patches."""
     r = b - L.A @ x
     d = np.zeros_like(x)
-    for entry in L.colours:
-        if entry is None:
-            continue
-        dofs, Sv, _ = entry
-        np.add.at(d, dofs, np.einsum("pij,pj->pi", Sv, r[dofs]))
+    for col in range(len(L.colours)):
+        for dofs, Sv, _ in L.colour_groups(col):
+            np.add.at(d, dofs, np.einsum("pij,pj->pi", Sv, r[dofs]))
     return x + omega * d
 
 
@@ -297,13 +369,10 @@ def smooth_step_sequential(L: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray
     order = list(range(C)) + list(range(C - 2, -1, -1))
     x = x.copy()
     for col in order:
-        entry = L.colours[col]
-        if entry is None:
-            continue
-        dofs, Sv, _ = entry
-        for p in range(dofs.shape[0]):
-            r = (b - L.A @ x)[dofs[p]]
-            x[dofs[p]] += Sv[p] @ r
+        for dofs, Sv, _ in L.colour_groups(col):
+            for p in range(dofs.shape[0]):
+                r = (b - L.A @ x)[dofs[p]]
+                x[dofs[p]] += Sv[p] @ r
     return x
 
 

@@ -397,6 +397,41 @@ def test_two_grid_against_dense_ritz_construction(d, k):
     assert np.max(np.abs(z - x)) < 1e-11 * np.max(np.abs(x))
 
 
+@pytest.mark.parametrize("d,k,n,expect", [
+    (2, 0, 4, {3: 12}),            # edge: the face between the two cells, two pressures; corners empty
+    (2, 1, 4, {8: 4, 18: 12}),     # corner: 2 + 2 interior velocity nodes, 4 pressures; edge: 6 + 4 + 8
+    (3, 0, 3, {3: 24, 8: 24}),     # cube edge: one face and two pressures; cube face: 2 + 2 faces, 4 pressures
+])
+def test_boundary_patch_sizes_by_hand(d, k, n, expect):
+    """Patches of the boundary vertices (Sec. 3.3, every vertex): sizes and
+    numbers counted by hand from the supports of the nodal RT_k x Q_k basis."""
+    S = fem.Space(d, n, k)
+    got = {}
+    for groups in mg.boundary_patches_of(S):
+        for verts, dofs in groups:
+            got[dofs.shape[1]] = got.get(dofs.shape[1], 0) + dofs.shape[0]
+            assert np.all(np.any((verts == 0) | (verts == n), axis=1))
+    assert got == expect
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_boundary_patches_of_one_colour_do_not_couple(d, k):
+    """All patches of a colour, interior and boundary, have disjoint dofs and
+    no coupling through A, so one colour is one joint update."""
+    n = 6 if d == 2 else 5
+    S = fem.Space(d, n, k)
+    A = fem.operator(S, 0.5, np.ones((n,) * d))
+    inner = mg.patches(S)
+    for col, groups in enumerate(mg.boundary_patches_of(S)):
+        lists = [list(p) for p in inner[col][1]]
+        for _, dofs in groups:
+            lists += [list(p) for p in dofs]
+        for a in range(len(lists)):
+            for b in range(a + 1, len(lists)):
+                assert not set(lists[a]) & set(lists[b])
+                assert abs(A[lists[a]][:, lists[b]]).max() == 0.0
+
+
 def _dense_ritz_vcycle(H, counts, b):
     """Brute-force V-cycle of Sec. 3.2 with the smoothing steps of each level
     given explicitly (counts[j] pre- and post-smoothing steps on level j): dense
@@ -417,11 +452,10 @@ def _dense_ritz_vcycle(H, counts, b):
         C = len(L.colours)
         plist = []
         for col in list(range(C)) + list(range(C - 2, -1, -1)):
-            if L.colours[col] is None:
-                continue
-            for dofs in L.colours[col][0]:
-                Z = null_space(L.w[dofs][None, :])
-                plist.append((dofs, Z, Z.T @ A[np.ix_(dofs, dofs)] @ Z))
+            for group in L.colour_groups(col):
+                for dofs in group[0]:
+                    Z = null_space(L.w[dofs][None, :])
+                    plist.append((dofs, Z, Z.T @ A[np.ix_(dofs, dofs)] @ Z))
 
         def step(x):
             for dofs, Z, Azz in plist:
@@ -443,6 +477,36 @@ def _dense_ritz_vcycle(H, counts, b):
         return x
 
     return level(H.J, b)
+
+
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+def test_boundary_patch_vcycle_against_dense_construction(d, k):
+    """V-cycle with the patches of every vertex (Sec. 3.3): the brute-force
+    construction patch by patch (explicit mean-zero patch bases, the boundary
+    patches of a colour after its interior ones) against the oracle's vcycle,
+    which applies each colour's patches jointly; symmetric as well."""
+    L = 3 if d == 2 else 2
+    H = _hier(d, k, 2, L, 0.3, seed=17, sigma_c=1.5)
+    Hb = mg.Hierarchy(d, 2, L, k, 0.3, H.levels[-1].c, boundary_patches=True)
+    assert sum(len(g) for g in Hb.levels[-1].bcolours) > 0
+    LJ = Hb.levels[-1]
+    b = np.random.default_rng(18).standard_normal(LJ.S.ndof)
+    b[LJ.cm] = 0.0
+    counts = {j: 1 for j in range(1, L)}
+    x = _dense_ritz_vcycle(Hb, counts, b)
+    z = mg.vcycle(Hb, b, m_fine=1, variable=False)
+    assert np.max(np.abs(z - x)) < 1e-10 * np.max(np.abs(x))
+    # the boundary patches change the cycle
+    assert np.max(np.abs(mg.vcycle(H, b, m_fine=1, variable=False) - z)) > 1e-6 * np.max(np.abs(z))
+    N = LJ.S.ndof
+    B = np.zeros((N, N))
+    for i in range(N):
+        e = np.zeros(N)
+        e[i] = 1.0
+        B[:, i] = mg.vcycle(Hb, e, 1, True)
+    fr = LJ.free
+    Bf = B[np.ix_(fr, fr)]
+    assert np.max(np.abs(Bf - Bf.T)) < 1e-12 * np.max(np.abs(Bf))
 
 
 @pytest.mark.parametrize("d,k", [(2, 0), (2, 1)])
