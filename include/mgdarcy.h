@@ -113,6 +113,13 @@ typedef struct {
                            the handle (flexible GMRES admits the change of
                            preconditioner).  0: 10 iterations, < 0: never.
                            Ignored by mg_solve_batch.                          */
+  int boundary_patches; /* 1: the smoother also takes the patches of the
+                           boundary vertices (Sec. 3.3 defines a patch for every
+                           vertex: the cells sharing it, clipped to the domain,
+                           with the free dofs supported in them); 0 (default):
+                           interior vertices only, which already cover every
+                           free dof.  Not with additive smoothing or batches
+                           (MG_ERR_UNSUPPORTED).                               */
 } mg_problem;
 
 typedef struct {
@@ -353,6 +360,11 @@ mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
 
 /* Patch counts: number of patches of `colour` on `level` and their size n_v. */
 mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* n_v);
+
+/* Patches of the boundary vertices (mg_problem.boundary_patches) of `colour`
+ * on `level` >= 1: their number and the largest patch size of the level
+ * (0 and 0 without the option).  Host only. */
+mg_status mg_boundary_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* max_nv);
 
 /* Nonzeros of the rows of A_level (eq. Brinkman-weak) restricted to the dofs
  * of one vertex patch (Sec. 3.3), for an interior patch (level >= 1): the

@@ -234,9 +234,14 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, void* acc, i
   for (int s = 0; s < steps; ++s) {
     for (int t = (s > 0 ? 1 : 0); t < 2 * C - 1; ++t) {
       const int col = t < C ? t : 2 * C - 2 - t;
-      if (L.count[col] == 0) continue;
-      h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, h->d_fail, nrhs, stream);
-      ++h->launches;
+      if (L.count[col] > 0) {
+        h->ops->colour_pass(L, col, L.sprec, L.S[col], x, b, h->d_fail, nrhs, stream);
+        ++h->launches;
+      }
+      if (L.bcount[col] > 0) {   // the colour's boundary-vertex patches (option), independent of its others
+        h->ops->bpatch_pass(L, col, h->f32(), x, b, nrhs, stream);
+        ++h->launches;
+      }
     }
   }
   return MG_OK;
@@ -528,6 +533,9 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->pass_kernel < 0 || p->pass_kernel > 5) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
   if (p->escalate_window > 100000) return fail(MG_ERR_INVALID_ARG, "escalate_window too large");
+  if (p->boundary_patches < 0 || p->boundary_patches > 1) return fail(MG_ERR_INVALID_ARG, "bad boundary_patches");
+  if (p->boundary_patches && p->additive > 0.0)
+    return fail(MG_ERR_UNSUPPORTED, "boundary-vertex patches with the additive smoother are not supported");
   if (!p->c) return fail(MG_ERR_INVALID_ARG, "c is null");
   const int d = p->dim, k = p->degree, J = p->n_levels - 1;
   const int64_t nfine = (int64_t)p->n_coarse << J;
@@ -632,6 +640,28 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
       L.S[col] = q;
       h->ops->patch_setup(L, col, L.sprec, q, h->d_fail, h->stream);
       ++h->launches;
+    }
+    if (p->boundary_patches) {   // patches of the boundary vertices (Sec. 3.3 takes every vertex)
+      std::vector<int> lists[27];
+      L.bnv = h->ops->bpatch_lists(L, lists);
+      if (L.bnv > 40) return cleanup(fail(MG_ERR_UNSUPPORTED, "boundary patches larger than 40 dofs"));
+      const int f64 = L.sprec == P64 ? 1 : 0;
+      for (int col = 0; col < C && L.bnv > 0; ++col) {
+        if (lists[col].empty()) continue;
+        L.bcount[col] = (int64_t)lists[col].size() / L.bnv;
+        int* dd = nullptr;
+        if ((st = h->alloc(&dd, lists[col].size())) != MG_OK) return cleanup(st);
+        if (cudaMemcpyAsync(dd, lists[col].data(), lists[col].size() * sizeof(int), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+          return cleanup(fail(MG_ERR_CUDA, "upload of the boundary patch lists failed"));
+        L.bdofs[col] = dd;
+        if ((st = h->alloc((char**)&q, (size_t)L.bcount[col] * L.bnv * L.bnv * (f64 ? 8 : 4))) != MG_OK)
+          return cleanup(st);
+        L.bS[col] = q;
+        h->ops->bpatch_setup(L, col, f64, q, h->d_fail, h->stream);
+        ++h->launches;
+      }
     }
   }
   if ((st = tune_passes(h, p->pass_kernel, nrhs)) != MG_OK) return cleanup(st);
@@ -796,6 +826,14 @@ mg_status mg_patch_info(const mg_handle* h, int level, int colour, int64_t* coun
     return fail(MG_ERR_INVALID_ARG, "bad level or colour");
   if (count) *count = h->lv[level].count[colour];
   if (n_v) *n_v = h->ops->nv;
+  return MG_OK;
+}
+
+mg_status mg_boundary_patch_info(const mg_handle* h, int level, int colour, int64_t* count, int* max_nv) {
+  if (!h || level < 1 || level > h->J || colour < 0 || colour >= num_colours(h->d))
+    return fail(MG_ERR_INVALID_ARG, "bad level or colour");
+  if (count) *count = h->lv[level].bcount[colour];
+  if (max_nv) *max_nv = h->lv[level].bnv;
   return MG_OK;
 }
 
@@ -1601,6 +1639,9 @@ void mg_destroy_batch(mg_batch* b) { delete b; }
 
 mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* cuda_stream, mg_batch** out) {
   if (!problems || !out || nprob < 1 || nrhs < 1) return fail(MG_ERR_INVALID_ARG, "bad batch arguments");
+  for (int p = 0; p < nprob; ++p)
+    if (problems[p].boundary_patches)
+      return fail(MG_ERR_UNSUPPORTED, "boundary-vertex patches are not supported in batches");
   *out = nullptr;
   mg_batch* B = new mg_batch();
   B->nrhs = nrhs;

@@ -926,6 +926,119 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   }
 }
 
+// ---------------------------------------------------------------------------
+// Patches of the boundary vertices (an option: Sec. 3.3 takes a patch for
+// every vertex; the interior ones above cover every free dof for n >= 2).
+// Each is an explicit list of at most BNV free dofs (sorted, -1 padded) with
+// a dense S_v, column-major with column length BNV.  There are O(n^(D-1)) of
+// them, so a plain block per patch suffices.
+// ---------------------------------------------------------------------------
+
+// Collects the patch matrix row of one dof into row[], columns found in the
+// patch's sorted dof list.
+template <int D, int K>
+struct BPatchRowVisitor {
+  const Lvl<D, K, double>& L;
+  const int* dofs;
+  int nv;
+  double* row;
+  __device__ BPatchRowVisitor(const Lvl<D, K, double>& l, const int* d, int n, double* r) : L(l), dofs(d), nv(n), row(r) {}
+  __device__ __forceinline__ void operator()(int comp, const int (&j)[D], double coef) {
+    const int g = (int)flat_index(L, comp, j);
+    int lo = 0, hi = nv - 1;
+    while (lo <= hi) {
+      const int m = (lo + hi) >> 1, dm = dofs[m];
+      if (dm == g) {
+        row[m] += coef;
+        return;
+      }
+      if (dm < g) lo = m + 1;
+      else hi = m - 1;
+    }
+  }
+  __device__ __forceinline__ double cell_c(const int (&cell)[D]) const { return L.c[cell_linear(L, cell)]; }
+};
+
+// S_v of every boundary patch of one colour: the patch rows of A_j bordered
+// by the pressure-mean functional, inverted in FP64 (Sec. 3.3), stored as TS.
+template <int D, int K, typename TS>
+__global__ void __launch_bounds__(128) k_bpatch_setup(const Lvl<D, K, double> L, const __grid_constant__ Tab<K, double> tb,
+                                                      int64_t count, const int* __restrict__ dofs, int bnv,
+                                                      TS* __restrict__ S, int* __restrict__ fail) {
+  constexpr int K1 = K + 1;
+  extern __shared__ double sm[];
+  for (int64_t p = blockIdx.x; p < count; p += gridDim.x) {
+    const int* pd = dofs + p * bnv;
+    int nv = 0;
+    for (int i = 0; i < bnv; ++i)
+      if (pd[i] >= 0) nv = i + 1;
+    const int nb = nv + 1;
+    double* M = sm;                 // nb x nb
+    double* E = M + nb * nb;        // nb x nv
+    double* fac = E + nb * nv;      // nb
+    double* red_v = fac + nb;       // blockDim
+    int* red_i = reinterpret_cast<int*>(red_v + blockDim.x);
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) M[q] = 0.0;
+    for (int q = threadIdx.x; q < nb * nv; q += blockDim.x) E[q] = (q / nv == q % nv) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) {
+      int idx[D];
+      const int comp = decode(L, pd[l], idx);
+      BPatchRowVisitor<D, K> vis(L, pd, nv, M + l * nb);
+      visit_row(L, tb, comp, idx, vis);
+      if (comp == D) {
+        double w = L.s_c;
+#pragma unroll
+        for (int e = 0; e < D; ++e) w *= tb.wg[idx[e] % K1];
+        M[l * nb + nv] = w;
+        M[nv * nb + l] = w;
+      }
+    }
+    __syncthreads();
+    const int bad = gauss_jordan(M, nb, E, nv, nb, nv, fac, red_v, red_i);
+    if (bad && threadIdx.x == 0) atomicExch(fail, 1);
+    TS* Sp = S + p * bnv * bnv;
+    for (int q = threadIdx.x; q < bnv * bnv; q += blockDim.x) {
+      const int col = q / bnv, row = q - col * bnv;
+      Sp[q] = (TS)((row < nv && col < nv) ? E[row * nv + col] : 0.0);
+    }
+    __syncthreads();
+  }
+}
+
+// The boundary patches of one colour: x|_v += S_v (b - A x)|_v, one block per
+// patch and right-hand side (blockIdx.y, vectors vs apart), thread i owning
+// patch row i.  Every row's residual is formed before any x is written.
+constexpr int BPATCH_THREADS = 64;
+template <int D, int K, typename T, typename TS>
+__global__ void __launch_bounds__(BPATCH_THREADS) k_bpatch_pass(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                                                const int* __restrict__ dofs, int bnv,
+                                                                const TS* __restrict__ S, T* x, const T* __restrict__ b,
+                                                                int64_t vs) {
+  __shared__ T r[BPATCH_THREADS];
+  const int64_t p = blockIdx.x;
+  x += (int64_t)blockIdx.y * vs;
+  b += (int64_t)blockIdx.y * vs;
+  const int i = threadIdx.x;
+  const int g = (i < bnv) ? __ldg(dofs + p * bnv + i) : -1;
+  pdl_launch_dependents();
+  pdl_wait();   // x and b come from the preceding kernels
+  T ri = T(0);
+  if (g >= 0) {
+    int idx[D];
+    const int comp = decode(L, (int64_t)g, idx);
+    ri = b[g] - apply_row(L, tb, comp, idx, x);
+  }
+  r[i] = ri;
+  __syncthreads();
+  if (g >= 0) {
+    const TS* Sp = S + p * bnv * bnv;
+    T d = T(0);
+    for (int j = 0; j < bnv; ++j) d += (T)Sp[(int64_t)j * bnv + i] * r[j];
+    x[g] += d;
+  }
+}
+
 }  // namespace mgd
 
 #include "passcta.cuh"

@@ -3,6 +3,7 @@
 #include "kernels.cuh"
 #include "tables.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -372,6 +373,119 @@ int64_t patch_nnz(const HostLevel& h) {
   return nnz;
 }
 
+// Patches of the boundary vertices v (some v_e = 0 or n): the free dofs whose
+// support lies in the cells v_e - 1, v_e (clipped to the domain) and the
+// pressure dofs of those cells; patches without a velocity dof are left out.
+int bpatch_lists(const HostLevel& h, std::vector<int> (&lists)[27]) {
+  constexpr int K1 = K + 1;
+  const int n = h.n, N = h.N;
+  std::vector<std::vector<std::vector<int>>> per(27);
+  int bnv = 0;
+  int64_t nvert = 1;
+  for (int e = 0; e < D; ++e) nvert *= (n + 1);
+  for (int64_t q = 0; q < nvert; ++q) {
+    int v[D];
+    int64_t r = q;
+    bool onb = false;
+    for (int e = 0; e < D; ++e) {
+      v[e] = (int)(r % (n + 1));
+      r /= (n + 1);
+      onb = onb || v[e] == 0 || v[e] == n;
+    }
+    if (!onb) continue;
+    std::vector<int> dofs;
+    bool has_u = false;
+    for (int c = 0; c <= D; ++c) {
+      int lo[D], hi[D];
+      for (int e = 0; e < D; ++e) {
+        const bool own = c < D && e == c;
+        lo[e] = std::max(0, K1 * (v[e] - 1));
+        hi[e] = std::min(own ? N : N - 1, own ? K1 * (v[e] + 1) : K1 * (v[e] + 1) - 1);
+      }
+      int64_t tot = 1;
+      for (int e = 0; e < D; ++e) tot *= (hi[e] >= lo[e] ? hi[e] - lo[e] + 1 : 0);
+      for (int64_t t = 0; t < tot; ++t) {
+        int idx[D];
+        int64_t rr = t;
+        bool in = true;
+        for (int e = 0; e < D; ++e) {
+          const int ext = hi[e] - lo[e] + 1;
+          idx[e] = lo[e] + (int)(rr % ext);
+          rr /= ext;
+          const bool own = c < D && e == c;
+          int slo = idx[e] / K1, shi = idx[e] / K1;
+          if (own) {
+            if (idx[e] % K1 == 0) slo = idx[e] / K1 - 1;
+            slo = std::max(slo, 0);
+            shi = std::min(shi, n - 1);
+          }
+          in = in && slo >= v[e] - 1 && shi <= v[e];
+        }
+        if (!in) continue;
+        if (c < D && (idx[c] == 0 || idx[c] == N)) continue;   // constrained
+        int64_t g = h.off[c], st = 1;
+        for (int e = 0; e < D; ++e) {
+          g += (int64_t)idx[e] * st;
+          st *= (c < D && e == c) ? (N + 1) : N;
+        }
+        dofs.push_back((int)g);
+        has_u = has_u || c < D;
+      }
+    }
+    if (!has_u) continue;
+    std::sort(dofs.begin(), dofs.end());
+    int col = 0, p3 = 1;
+    for (int e = 0; e < D; ++e) {
+      col += (v[e] % 3) * p3;
+      p3 *= 3;
+    }
+    bnv = std::max(bnv, (int)dofs.size());
+    per[col].push_back(dofs);
+  }
+  for (int col = 0; col < 27; ++col) {
+    lists[col].clear();
+    for (const auto& d : per[col]) {
+      for (int i = 0; i < bnv; ++i) lists[col].push_back(i < (int)d.size() ? d[i] : -1);
+    }
+  }
+  return bnv;
+}
+
+void bpatch_setup(const HostLevel& h, int colour, int f64, void* S, int* fail, cudaStream_t s) {
+  const int64_t cnt = h.bcount[colour];
+  if (cnt == 0) return;
+  const int threads = 128, nb = h.bnv + 1;
+  const size_t smem = sizeof(double) * ((size_t)nb * nb + (size_t)nb * h.bnv + nb + threads) + sizeof(int) * threads;
+  const unsigned grid = (unsigned)(cnt < 152 * 8 ? cnt : 152 * 8);
+  if (f64)
+    k_bpatch_setup<D, K, double><<<grid, threads, smem, s>>>(mk<double>(h), tab<double>(), cnt, h.bdofs[colour], h.bnv,
+                                                              (double*)S, fail);
+  else
+    k_bpatch_setup<D, K, float><<<grid, threads, smem, s>>>(mk<double>(h), tab<double>(), cnt, h.bdofs[colour], h.bnv,
+                                                             (float*)S, fail);
+}
+
+template <typename T, typename TS>
+void bpatch_pass_t(const HostLevel& h, int colour, void* x, const void* b, int nrhs, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)h.bcount[colour], (unsigned)nrhs);
+  cfg.blockDim = dim3(BPATCH_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_bpatch_pass<D, K, T, TS>, mk<T>(h), tab<T>(), (const int*)h.bdofs[colour], h.bnv,
+                     (const TS*)h.bS[colour], (T*)x, (const T*)b, h.ndof);
+}
+
+void bpatch_pass(const HostLevel& h, int colour, int f32, void* x, const void* b, int nrhs, cudaStream_t s) {
+  if (h.bcount[colour] == 0) return;
+  if (f32) bpatch_pass_t<float, float>(h, colour, x, b, nrhs, s);
+  else bpatch_pass_t<double, double>(h, colour, x, b, nrhs, s);
+}
+
 void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2l, int nf, double* M, double* E,
                      cudaStream_t s) {
   k_coarse_assemble<D, K><<<1, 512, 0, s>>>(mk<double>(h), tab<double>(), free_list, g2l, nf, M, E);
@@ -427,6 +541,9 @@ DKOps make_ops() {
   o.build_template = build_template;
   o.plan_selftest = plan_selftest;
   o.patch_nnz = patch_nnz;
+  o.bpatch_lists = bpatch_lists;
+  o.bpatch_setup = bpatch_setup;
+  o.bpatch_pass = bpatch_pass;
   return o;
 }
 

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <string>
+#include <vector>
 
 #include "../../include/mgdarcy.h"
 
@@ -63,6 +64,13 @@ struct HostLevel {
   int64_t s_prob[27];
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
+  // patches of the boundary vertices (option): per colour their number, dof
+  // lists (bnv ints each, sorted, -1 padded) and S_v (bnv x bnv, column-major,
+  // FP64 for FP64 storage, else FP32)
+  int bnv;
+  int64_t bcount[27];
+  int* bdofs[27];
+  void* bS[27];
   void* X;               // level vectors in the working precision
   void* B;
   void* R;
@@ -101,6 +109,13 @@ struct DKOps {
   int (*plan_selftest)(int sprec, int n, double mu, std::string* why);
   // nonzeros of the operator rows of one (interior) patch of a level
   int64_t (*patch_nnz)(const HostLevel&);
+  // boundary-vertex patches of a level: per colour the concatenated sorted dof
+  // lists (bnv entries each, -1 padded); returns bnv (0: none)
+  int (*bpatch_lists)(const HostLevel&, std::vector<int> (&lists)[27]);
+  // their S_v for one colour (FP64 factorisation, stored as FP64 if f64 else FP32)
+  void (*bpatch_setup)(const HostLevel&, int colour, int f64, void* S, int* fail, cudaStream_t);
+  // x|_v += S_v (b - A x)|_v over the boundary patches of one colour (f32: FP32 vectors)
+  void (*bpatch_pass)(const HostLevel&, int colour, int f32, void* x, const void* b, int nrhs, cudaStream_t);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);

@@ -117,7 +117,8 @@ def table4(torch, sizes=(64, 128), precision="fp32", sigma=2.0, seed=7):
 
 def variants(torch, precision="fp32"):
     """Smoother and cycle variants on two workloads: the paper's symmetric
-    multiplicative Schwarz smoother against additive Schwarz (omega = 1/4,
+    multiplicative Schwarz smoother (interior-vertex patches, and with the
+    patches of the boundary vertices as well, Sec. 3.3) against additive Schwarz (omega = 1/4,
     every patch on the same residual: one launch per colour and one update per
     step instead of 2C - 1 dependent passes), each in the variable cycle
     (m(J) = 2) and the standard V(2,2) cycle.  Reports GMRES iterations, the
@@ -130,12 +131,13 @@ def variants(torch, precision="fp32"):
     rows = []
     for name, c, mu, k, tol, kind in cases:
         n = c.shape[0]
-        for smoother, omega in (("multiplicative", 0.0), ("additive", 0.25)):
+        for smoother, omega, bnd in (("multiplicative", 0.0, False), ("multiplicative, all vertices", 0.0, True),
+                                     ("additive", 0.25, False)):
             for cycle, variable in (("variable", True), ("V(2,2)", False)):
                 levels = int(np.log2(n // 4)) + 1
                 cd = torch.as_tensor(c, device="cuda")
                 G = mgdarcy.Multigrid(2, 4, levels, k, mu, cd, precision=precision, variable_cycle=variable,
-                                      additive=omega)
+                                      additive=omega, boundary_patches=bnd)
                 nu, npr = G.sizes()
                 b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
                 if kind == "driven":

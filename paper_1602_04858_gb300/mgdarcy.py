@@ -30,7 +30,7 @@ API = [
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
     "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
-    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_time_passes",
+    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_time_passes", "mg_boundary_patch_info",
 ]
 
 
@@ -39,7 +39,7 @@ class mg_problem(ctypes.Structure):
                 ("degree", ctypes.c_int), ("mu", ctypes.c_double), ("c", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("m_fine", ctypes.c_int), ("variable_cycle", ctypes.c_int),
                 ("coarse_avg", ctypes.c_int), ("dense_level", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("additive", ctypes.c_double), ("escalate_window", ctypes.c_int)]
+                ("additive", ctypes.c_double), ("escalate_window", ctypes.c_int), ("boundary_patches", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_batch_set_wait_limit.argtypes = [vp, d]
     lib.mg_patch_nnz.argtypes = [vp, i, ctypes.POINTER(i64)]
     lib.mg_time_passes.argtypes = [vp, i, i, ctypes.POINTER(d)]
+    lib.mg_boundary_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_measure_fma_peak.argtypes = [i, ctypes.POINTER(d), vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
@@ -195,13 +196,13 @@ class Multigrid:
 
     def __init__(self, dim, n_coarse, n_levels, degree, mu, c, precision="fp64", m_fine=2,
                  variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, additive=0.0,
-                 escalate_window=0, stream=None):
+                 escalate_window=0, boundary_patches=False, stream=None):
         lib = load()
         self._keep = c if not isinstance(c, np.ndarray) else np.ascontiguousarray(c, dtype=np.float64)
         prob = mg_problem(dim, n_coarse, n_levels, degree, float(mu), _ptr(self._keep),
                           PREC[precision] if isinstance(precision, str) else int(precision), int(m_fine),
                           1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel),
-                          float(additive), int(escalate_window))
+                          float(additive), int(escalate_window), 1 if boundary_patches else 0)
         h = ctypes.c_void_p()
         _check(lib.mg_setup(ctypes.byref(prob), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
         self.h = h
@@ -294,6 +295,12 @@ class Multigrid:
         _check(load().mg_patch_nnz(self.h, level, ctypes.byref(v)))
         return v.value
 
+    def boundary_patch_info(self, level, colour):
+        """(count, largest size) of the boundary-vertex patches of a colour (mg_boundary_patch_info)."""
+        cnt, nv = ctypes.c_int64(), ctypes.c_int()
+        _check(load().mg_boundary_patch_info(self.h, level, colour, ctypes.byref(cnt), ctypes.byref(nv)))
+        return cnt.value, nv.value
+
     def time_passes(self, level, kernel=0):
         """Microseconds per colour pass of a level (mg_time_passes); kernel 0: the level's own."""
         v = ctypes.c_double()
@@ -339,7 +346,8 @@ class Batch:
                                 PREC[prec] if isinstance(prec, str) else int(prec), int(p.get("m_fine", 2)),
                                 1 if p.get("variable_cycle", True) else 0, int(p.get("coarse_avg", 0)),
                                 int(p.get("dense_level", -1)), int(p.get("pass_kernel", 0)),
-                                float(p.get("additive", 0.0)), int(p.get("escalate_window", 0)))
+                                float(p.get("additive", 0.0)), int(p.get("escalate_window", 0)),
+                                1 if p.get("boundary_patches", False) else 0)
         h = ctypes.c_void_p()
         _check(lib.mg_setup_batch(arr, len(problems), int(nrhs), ctypes.c_void_p(_stream_ptr(stream)),
                                   ctypes.byref(h)))
