@@ -100,6 +100,16 @@ def _manufactured(d, k, mu):
         p = lambda X: X[:, 0] * X[:, 1] - 0.25
         f = lambda X, c: np.stack([-4 * mu * X[:, 1] + 2 * c * X[:, 0] ** 2 * X[:, 1] + X[:, 1],
                                    4 * mu * X[:, 0] - 2 * c * X[:, 0] * X[:, 1] ** 2 + X[:, 0]], 1)
+    elif d == 2 and k == 2:
+        # u = curl(x^3 y^3) = (3 x^3 y^2, -3 x^2 y^3) in Q_{3,2} x Q_{2,3}, p = x^2 y^2 - 1/9 in Q_2
+        # (zero mean); f = -mu Lap u + c u + grad p, derived by hand
+        u = lambda X: np.stack([3 * X[:, 0] ** 3 * X[:, 1] ** 2, -3 * X[:, 0] ** 2 * X[:, 1] ** 3], 1)
+        p = lambda X: X[:, 0] ** 2 * X[:, 1] ** 2 - 1.0 / 9.0
+        f = lambda X, c: np.stack([
+            -mu * (18 * X[:, 0] * X[:, 1] ** 2 + 6 * X[:, 0] ** 3) + 3 * c * X[:, 0] ** 3 * X[:, 1] ** 2
+            + 2 * X[:, 0] * X[:, 1] ** 2,
+            mu * (6 * X[:, 1] ** 3 + 18 * X[:, 0] ** 2 * X[:, 1]) - 3 * c * X[:, 0] ** 2 * X[:, 1] ** 3
+            + 2 * X[:, 0] ** 2 * X[:, 1]], 1)
     else:
         u = lambda X: np.stack([X[:, 0], X[:, 1], -2 * X[:, 2]], 1)
         p = lambda X: 0.0 * X[:, 0]
@@ -107,7 +117,7 @@ def _manufactured(d, k, mu):
     return u, p, f
 
 
-@pytest.mark.parametrize("d,k,n", [(2, 0, 4), (2, 1, 4), (3, 0, 2)])
+@pytest.mark.parametrize("d,k,n", [(2, 0, 4), (2, 1, 4), (2, 2, 3), (3, 0, 2)])
 @pytest.mark.parametrize("mu", [0.0, 0.01, 1.0])
 def test_polynomial_reproduction(d, k, n, mu):
     """A consistent method reproduces a solution lying in RT_k x Q_k exactly (eq. Brinkman-weak, BCh)."""
@@ -122,7 +132,7 @@ def test_polynomial_reproduction(d, k, n, mu):
     assert np.max(np.abs(x - xe)) <= 1e-11 * max(1.0, np.max(np.abs(xe)))
 
 
-@pytest.mark.parametrize("d,k,n", [(2, 0, 5), (2, 1, 4), (3, 0, 3)])
+@pytest.mark.parametrize("d,k,n", [(2, 0, 5), (2, 1, 4), (2, 2, 3), (3, 0, 3)])
 def test_symmetry_and_velocity_spd(d, k, n):
     rng = np.random.default_rng(2)
     S = fem.Space(d, n, k)
@@ -267,13 +277,14 @@ def _hier(d, k, n0, L, mu, seed=3, sigma_c=1.0):
     return mg.Hierarchy(d, n0, L, k, mu, c)
 
 
-@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (3, 0)])
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (2, 2), (3, 0)])
 def test_patch_count_and_colours(d, k):
     S = fem.Space(d, 6, k)
     cols = mg.patches(S)
     total = sum(v.shape[0] for v, _ in cols)
     assert total == 5 ** d
-    nv = {2: {0: 8, 1: 40}, 3: {0: 20}}[d][k]
+    # d (2k+1)(2k+2)^(d-1) velocity dofs inside the 2^d block + (2k+2)^d pressures
+    nv = {2: {0: 8, 1: 40, 2: 96}, 3: {0: 20}}[d][k]
     for v, dofs in cols:
         if dofs.shape[0]:
             assert dofs.shape[1] == nv
@@ -327,7 +338,7 @@ def test_colour_pass_equals_patch_by_patch(d, k):
     assert np.max(np.abs(x1 - x2)) < 1e-12 * np.max(np.abs(x1))
 
 
-@pytest.mark.parametrize("d,k,L", [(2, 0, 3), (2, 1, 3), (3, 0, 2)])
+@pytest.mark.parametrize("d,k,L", [(2, 0, 3), (2, 1, 3), (2, 2, 2), (3, 0, 2)])
 @pytest.mark.parametrize("variable", [False, True])
 def test_vcycle_is_symmetric(d, k, L, variable):
     H = _hier(d, k, 2, L, 0.05)
@@ -343,7 +354,7 @@ def test_vcycle_is_symmetric(d, k, L, variable):
     assert np.max(np.abs(Bf - Bf.T)) < 1e-12 * np.max(np.abs(Bf))
 
 
-@pytest.mark.parametrize("d,k", [(2, 0), (2, 1)])
+@pytest.mark.parametrize("d,k", [(2, 0), (2, 1), (2, 2)])
 def test_two_grid_against_dense_ritz_construction(d, k):
     """V-cycle on 4x4 (levels 2x2 -> 4x4) against a dense brute-force two-grid.
 
