@@ -63,7 +63,8 @@ typedef struct {
   int dim;              /* d: 2 or 3                                          */
   int n_coarse;         /* cells per direction on level 0 (>= 2)              */
   int n_levels;         /* J+1 >= 1; finest n = n_coarse * 2^J                */
-  int degree;           /* k of RT_k x Q_k: 0 or 1 (d = 3: 0 only)             */
+  int degree;           /* k of RT_k x Q_k (Sec. 2.3): 0, 1 or 2 (d = 3: 0
+                           only; 2 not in batches)                             */
   double mu;            /* >= 0; mu = 0 is the Darcy model (Sec. 2.2)          */
   const double* c;      /* host or device: finest-level zero-order coefficient
                            (inverse permeability), one value per cell, x
@@ -96,7 +97,10 @@ typedef struct {
                            right-hand sides and device), 5: a fixed rule
                            (block kernel where the largest colour holds at
                            most 10,000 inverse entries per SM or four or more
-                           right-hand sides share the inverses, else warp).    */
+                           right-hand sides share the inverses, else warp).
+                           Degree 2 (patches of 96 dofs) has one kernel, a
+                           block per patch driven by the stencil, and ignores
+                           this field.                                         */
   double additive;      /* smoother: 0 the symmetric multiplicative vertex-patch
                            Schwarz smoother of Sec. 3.3 (the paper's); in
                            (0, 1]: additive vertex-patch Schwarz with this
@@ -410,7 +414,8 @@ const char* mg_last_error(void);
  * stands for (zero outside the domain); likewise the row plans and gather
  * descriptors of the block-per-patch pass.  Returns 0 if all hold, 1 with a
  * reason in msg (msg_len bytes, may be null) otherwise, 2 for unsupported
- * arguments. */
+ * arguments.  Degree 2 builds no tables (its colour pass reads the stencil):
+ * returns 0. */
 int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len);
 
 #ifdef __cplusplus

@@ -26,6 +26,7 @@ NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3",
 UNITS = [
     ("kinst.cu", "k20.o", ["-DMG_D=2", "-DMG_K=0"]),
     ("kinst.cu", "k21.o", ["-DMG_D=2", "-DMG_K=1"]),
+    ("kinst.cu", "k22.o", ["-DMG_D=2", "-DMG_K=2"]),
     ("kinst.cu", "k30.o", ["-DMG_D=3", "-DMG_K=0"]),
     ("generic.cu", "generic.o", []),
     ("api.cu", "api.o", []),

@@ -247,6 +247,11 @@ mg_status smooth_steps(mg_handle* h, int j, void* x, const void* b, void* acc, i
   return MG_OK;
 }
 
+const DKOps* ops_for(int d, int k) {
+  if (d == 3) return ops_3_0();
+  return k == 0 ? ops_2_0() : (k == 1 ? ops_2_1() : ops_2_2());
+}
+
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
 // Sets the colour-pass kernel of every level (HostLevel::pass_cta: 0 warp
@@ -323,6 +328,10 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   const int64_t l0 = h->launches;
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
+    if (h->ops->generic) {   // a single kernel: nothing to choose
+      L.pass_cta = 1;
+      continue;
+    }
     if (mode != 4 && mode != 0) {
       if (mode == 5) {
         int nsm = 0;
@@ -499,12 +508,12 @@ int64_t mg_kernel_launches(const mg_handle* h) {
 void mg_destroy(mg_handle* h) { delete h; }
 
 int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len) {
-  if (!((dim == 2 && (degree == 0 || degree == 1)) || (dim == 3 && degree == 0)) || precision < 0 ||
+  if (!((dim == 2 && degree >= 0 && degree <= 2) || (dim == 3 && degree == 0)) || precision < 0 ||
       precision > 2 || n < 2 || !(mu >= 0.0)) {
     if (msg && msg_len > 0) std::snprintf(msg, (size_t)msg_len, "unsupported arguments");
     return 2;
   }
-  const DKOps* o = (dim == 2) ? (degree == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
+  const DKOps* o = ops_for(dim, degree);
   std::string why;
   const int r = o->plan_selftest(precision, n, mu, &why);
   if (msg && msg_len > 0) std::snprintf(msg, (size_t)msg_len, "%s", why.c_str());
@@ -521,7 +530,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (nrhs < 1) return fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
   *out = nullptr;
   if (p->dim != 2 && p->dim != 3) return fail(MG_ERR_INVALID_ARG, "dim must be 2 or 3");
-  if (p->degree < 0 || p->degree > 1) return fail(MG_ERR_UNSUPPORTED, "degree must be 0 or 1");
+  if (p->degree < 0 || p->degree > 2) return fail(MG_ERR_UNSUPPORTED, "degree must be 0, 1 or 2");
   if (p->dim == 3 && p->degree != 0) return fail(MG_ERR_UNSUPPORTED, "3-D supports degree 0 only");
   if (p->n_coarse < 2 || p->n_levels < 1 || p->n_levels > 14)
     return fail(MG_ERR_INVALID_ARG, "need n_coarse >= 2 and 1 <= n_levels <= 14");
@@ -568,7 +577,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   h->prob = *p;
   h->prob.c = nullptr;   // the finest coefficient is lv[J].c64 from here on
   h->esc_window = p->escalate_window == 0 ? 10 : (p->escalate_window < 0 ? 0 : p->escalate_window);
-  h->ops = (d == 2) ? (k == 0 ? ops_2_0() : ops_2_1()) : ops_3_0();
+  h->ops = ops_for(d, k);
 
   // coefficient: validate on the host
   std::vector<double> c(ncell);
@@ -644,7 +653,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
     if (p->boundary_patches) {   // patches of the boundary vertices (Sec. 3.3 takes every vertex)
       std::vector<int> lists[27];
       L.bnv = h->ops->bpatch_lists(L, lists);
-      if (L.bnv > 40) return cleanup(fail(MG_ERR_UNSUPPORTED, "boundary patches larger than 40 dofs"));
+      if (L.bnv > h->ops->bnv_max) return cleanup(fail(MG_ERR_UNSUPPORTED, "boundary patches too large"));
       const int f64 = L.sprec == P64 ? 1 : 0;
       for (int col = 0; col < C && L.bnv > 0; ++col) {
         if (lists[col].empty()) continue;
@@ -713,18 +722,22 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   {
     const HostLevel& L = h->lv[J];
     std::vector<double> w(L.n_p);
-    double gw[2];
+    double gw[3];
     if (k == 0) {
       Tab<0, double> td;
       Tab<0, float> tf;
       make_tables<0>(td, tf);
       gw[0] = td.wg[0];
-    } else {
+    } else if (k == 1) {
       Tab<1, double> td;
       Tab<1, float> tf;
       make_tables<1>(td, tf);
-      gw[0] = td.wg[0];
-      gw[1] = td.wg[1];
+      for (int q = 0; q < 2; ++q) gw[q] = td.wg[q];
+    } else {
+      Tab<2, double> td;
+      Tab<2, float> tf;
+      make_tables<2>(td, tf);
+      for (int q = 0; q < 3; ++q) gw[q] = td.wg[q];
     }
     const double vol = std::pow(L.h, d);
     for (int64_t g = 0; g < L.n_p; ++g) {
@@ -1639,9 +1652,11 @@ void mg_destroy_batch(mg_batch* b) { delete b; }
 
 mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* cuda_stream, mg_batch** out) {
   if (!problems || !out || nprob < 1 || nrhs < 1) return fail(MG_ERR_INVALID_ARG, "bad batch arguments");
-  for (int p = 0; p < nprob; ++p)
+  for (int p = 0; p < nprob; ++p) {
     if (problems[p].boundary_patches)
       return fail(MG_ERR_UNSUPPORTED, "boundary-vertex patches are not supported in batches");
+    if (problems[p].degree > 1) return fail(MG_ERR_UNSUPPORTED, "degree 2 is not supported in batches");
+  }
   *out = nullptr;
   mg_batch* B = new mg_batch();
   B->nrhs = nrhs;

@@ -109,6 +109,12 @@ void patch_setup_t(const HostLevel& h, int colour, void* S, int* fail, cudaStrea
   const size_t smem = sizeof(double) * ((size_t)NB * NB + (size_t)NB * NV + NB + threads) + sizeof(int) * threads;
   const int64_t cnt = h.count[colour];
   if (cnt == 0) return;
+  if (smem > 48 * 1024) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, [smem] {
+      cudaFuncSetAttribute(k_patch_setup<D, K, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+  }
   const unsigned grid = (unsigned)(cnt < 152 * 16 ? cnt : 152 * 16);
   k_patch_setup<D, K, TS><<<grid, threads, smem, s>>>(mk<double>(h), tab<double>(), colour, cnt, (TS*)S, fail);
 }
@@ -119,6 +125,7 @@ void patch_setup(const HostLevel& h, int colour, int sprec, void* S, int* fail, 
   else patch_setup_t<__nv_bfloat16>(h, colour, S, fail, s);
 }
 
+#if MG_K <= 1
 template <typename T, typename TS, int NR>
 void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
                     cudaStream_t s) {
@@ -372,6 +379,85 @@ int64_t patch_nnz(const HostLevel& h) {
   for (const auto& r : rows) nnz += (int64_t)(r.pl.size() + r.ms.size());
   return nnz;
 }
+#else   // MG_K >= 2: patches too large for the table-driven kernels
+
+// One block per patch (k_colour_pass_gen); right-hand sides along grid y, in
+// slices of at most 65,535.  ADD: the additive variant (acc += omega delta).
+template <typename T, typename TS, bool ADD>
+void pass_gen(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc, double omega,
+              int* err, int nrhs, cudaStream_t s) {
+  using G = GenShape<D, K, T, TS>;
+  const int64_t cnt = h.count[colour];
+  if (cnt == 0) return;
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_colour_pass_gen<D, K, T, TS, ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  });
+  for (int y0 = 0; y0 < nrhs; y0 += 65535) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cnt, (unsigned)std::min(65535, nrhs - y0));
+    cfg.blockDim = dim3(G::NT);
+    cfg.dynamicSmemBytes = G::SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_colour_pass_gen<D, K, T, TS, ADD>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S,
+                       (T*)const_cast<void*>(x), (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof, y0, (T*)acc,
+                       (T)omega);
+  }
+}
+
+void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
+                 cudaStream_t s) {
+  if (prec == P64) pass_gen<double, double, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
+  else if (prec == P32) pass_gen<float, float, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
+  else pass_gen<float, __nv_bfloat16, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
+}
+
+void additive_pass(const HostLevel& h, int colour, int prec, const void* S, const void* x, const void* b, void* acc,
+                   double omega, int* err, int nrhs, cudaStream_t s) {
+  if (prec == P64) pass_gen<double, double, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
+  else if (prec == P32) pass_gen<float, float, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
+  else pass_gen<float, __nv_bfloat16, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
+}
+
+// The stencil-driven pass needs no per-level tables.
+int64_t template_elems(int) { return 16; }
+int build_template(const HostLevel&, int, void*, cudaStream_t, std::string*) { return 0; }
+int plan_selftest(int, int, double, std::string* why) {
+  if (why) why->clear();
+  return 0;
+}
+
+// Distinct columns of the operator rows of one interior patch.
+struct ColumnSet {
+  const Lvl<D, K, double>& L;
+  std::vector<int64_t> cols;
+  explicit ColumnSet(const Lvl<D, K, double>& l) : L(l) {}
+  void operator()(int comp, const int (&j)[D], double) { cols.push_back(flat_index(L, comp, j)); }
+  double cell_c(const int (&)[D]) const { return 1.0; }
+};
+
+int64_t patch_nnz(const HostLevel& h) {
+  const Lvl<D, K, double> L = mk<double>(h);
+  int v[D];
+  for (int e = 0; e < D; ++e) v[e] = h.n >= 4 ? 2 : 1;
+  int64_t nnz = 0;
+  for (int l = 0; l < PatchShape<D, K>::NV; ++l) {
+    int idx[D];
+    const int comp = patch_local_decode<D, K>(v, l, idx);
+    ColumnSet cs(L);
+    visit_row(L, tab<double>(), comp, idx, cs);
+    std::sort(cs.cols.begin(), cs.cols.end());
+    nnz += (int64_t)(std::unique(cs.cols.begin(), cs.cols.end()) - cs.cols.begin());
+  }
+  return nnz;
+}
+
+#endif
 
 // Patches of the boundary vertices v (some v_e = 0 or n): the free dofs whose
 // support lies in the cells v_e - 1, v_e (clipped to the domain) and the
@@ -469,7 +555,7 @@ template <typename T, typename TS>
 void bpatch_pass_t(const HostLevel& h, int colour, void* x, const void* b, int nrhs, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h.bcount[colour], (unsigned)nrhs);
-  cfg.blockDim = dim3(BPATCH_THREADS);
+  cfg.blockDim = dim3(bpatch_threads<K>());
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -544,6 +630,8 @@ DKOps make_ops() {
   o.bpatch_lists = bpatch_lists;
   o.bpatch_setup = bpatch_setup;
   o.bpatch_pass = bpatch_pass;
+  o.generic = K >= 2 ? 1 : 0;
+  o.bnv_max = bpatch_threads<K>();
   return o;
 }
 

@@ -78,6 +78,9 @@ struct HostLevel {
 
 struct DKOps {
   int nv;                // patch size
+  int generic;           // 1: one stencil-driven colour-pass kernel (patches too large for the
+                         // table-driven ones), no per-level tables and no kernel choice
+  int bnv_max;           // largest boundary-vertex patch the boundary pass takes
   int nvp[3];            // stored column length per storage precision (P64, P32, P32B)
   int64_t s_stride[3];   // elements per stored patch inverse
   // y = A x (f32 != 0: float vectors, float coefficient), nrhs vectors
@@ -134,6 +137,7 @@ mg_status set_last_error(mg_status s, const std::string& msg);
 
 const DKOps* ops_2_0();
 const DKOps* ops_2_1();
+const DKOps* ops_2_2();
 const DKOps* ops_3_0();
 
 // --- generic kernels (generic.cu) -------------------------------------------

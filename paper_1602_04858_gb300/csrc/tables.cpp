@@ -136,5 +136,6 @@ void make_tables(Tab<K, double>& T, Tab<K, float>& F) {
 
 template void make_tables<0>(Tab<0, double>&, Tab<0, float>&);
 template void make_tables<1>(Tab<1, double>&, Tab<1, float>&);
+template void make_tables<2>(Tab<2, double>&, Tab<2, float>&);
 
 }  // namespace mgd

@@ -51,7 +51,8 @@ def _setup(lib, **kw):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(dim=4), 1),
-    (dict(degree=2), 7),
+    (dict(degree=3), 7),
+    (dict(dim=3, degree=2, c=np.ones((8, 8, 8))), 7),
     (dict(dim=3, degree=1, c=np.ones((8, 8, 8))), 7),
     (dict(n_coarse=1), 1),
     (dict(mu=-1.0), 1),

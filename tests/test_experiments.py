@@ -45,7 +45,7 @@ def test_constant_lift_reproduces_the_driven_problem_3d():
     assert np.max(np.abs(x - x_drv)) <= 1e-10 * np.max(np.abs(x_drv))
 
 
-@pytest.mark.parametrize("degree", [0, 1])
+@pytest.mark.parametrize("degree", [0, 1, 2])
 @pytest.mark.parametrize("mu", [0.0, 0.01, 1.0])
 def test_constant_lift_reproduces_the_driven_problem(mu, degree):
     n = 8
