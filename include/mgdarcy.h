@@ -98,9 +98,9 @@ typedef struct {
                            (block kernel where the largest colour holds at
                            most 10,000 inverse entries per SM or four or more
                            right-hand sides share the inverses, else warp).
-                           Degree 2 (patches of 96 dofs) has one kernel, a
-                           block per patch driven by the stencil, and ignores
-                           this field.                                         */
+                           Degree 2 (patches of 96 dofs) has no warp kernel:
+                           1 runs as 2, the rule takes 2, the timed choice
+                           picks between 2 and 3.                              */
   double additive;      /* smoother: 0 the symmetric multiplicative vertex-patch
                            Schwarz smoother of Sec. 3.3 (the paper's); in
                            (0, 1]: additive vertex-patch Schwarz with this
@@ -414,8 +414,7 @@ const char* mg_last_error(void);
  * stands for (zero outside the domain); likewise the row plans and gather
  * descriptors of the block-per-patch pass.  Returns 0 if all hold, 1 with a
  * reason in msg (msg_len bytes, may be null) otherwise, 2 for unsupported
- * arguments.  Degree 2 builds no tables (its colour pass reads the stencil):
- * returns 0. */
+ * arguments.  Degree 2 has block-per-patch tables only. */
 int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len);
 
 #ifdef __cplusplus

@@ -328,10 +328,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   const int64_t l0 = h->launches;
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
-    if (h->ops->generic) {   // a single kernel: nothing to choose
-      L.pass_cta = 1;
-      continue;
-    }
+    const int first = h->ops->warp_pass ? 0 : 1;   // RT_2: block kernels only
     if (mode != 4 && mode != 0) {
       if (mode == 5) {
         int nsm = 0;
@@ -343,6 +340,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       } else {
         L.pass_cta = mode - 1;
       }
+      L.pass_cta = std::max(L.pass_cta, first);
       continue;
     }
     const std::vector<int> key = {h->device, h->d, h->k, L.n, L.sprec, h->prec, nrhs, L.mu == 0.0 ? 1 : 0};
@@ -355,12 +353,12 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       }
     }
     float ms[3] = {0.f, 0.f, 0.f};
-    for (int var = 0; var < 3; ++var) {
+    for (int var = first; var < 3; ++var) {
       L.pass_cta = var;
       TRY(time_smoothing(h, j, nrhs, 2, 3, &ms[var], nullptr));
     }
-    L.pass_cta = 0;
-    for (int var = 1; var < 3; ++var)
+    L.pass_cta = first;
+    for (int var = first + 1; var < 3; ++var)
       if (ms[var] < ms[L.pass_cta]) L.pass_cta = var;
     std::lock_guard<std::mutex> g(mu);
     cache[key] = L.pass_cta;
@@ -855,7 +853,7 @@ mg_status mg_time_passes(mg_handle* h, int level, int kernel, double* us_per_pas
     return fail(MG_ERR_INVALID_ARG, "bad level, kernel or argument");
   HostLevel& L = h->lv[level];
   const int keep = L.pass_cta;
-  if (kernel > 0) L.pass_cta = kernel - 1;
+  if (kernel > 0) L.pass_cta = std::max(kernel - 1, h->ops->warp_pass ? 0 : 1);
   float ms = 0.f;
   int64_t np = 0;
   const mg_status st = time_smoothing(h, level, h->nrhs, 2, 5, &ms, &np);

@@ -1040,101 +1040,6 @@ __global__ void __launch_bounds__(NTH) k_bpatch_pass(const Lvl<D, K, T> L, const
   }
 }
 
-// ---------------------------------------------------------------------------
-// Colour pass for patches too large for the table-driven kernels (RT_2 x Q_2:
-// n_v = 96).  One block per patch and right-hand side, thread l owning patch
-// row l; the rows and their operator entries come from the stencil
-// (visit_row) rather than from per-level tables:
-//   1. thread 0 bulk-copies S_v (and the BF16 row scales) into shared memory
-//      before waiting for the preceding kernel;
-//   2. r_l = b_l - (A x)_l for the patch rows (an interior patch holds no
-//      constrained dof);
-//   3. delta_l = sum_m S_v(l, m) r_m from the staged S_v (column-major, so the
-//      threads of a warp read consecutive rows of one column);
-//   4. x_l += delta_l, or (ADD) acc_l += omega delta_l with x unchanged.
-// ---------------------------------------------------------------------------
-template <int D, int K, typename T, typename TS>
-struct GenShape {
-  using PS = PatchShape<D, K>;
-  using SL = SLayout<PS::NV, TS>;
-  static constexpr int NV = PS::NV, NVP = SL::NVP;
-  static constexpr int NT = ((NV + 31) / 32) * 32;
-  static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
-  static constexpr int S_BYTES = (int)(SL::STRIDE * sizeof(TS));
-  static constexpr int SC_BYTES = BF ? NVP * 4 : 0;
-  static constexpr int OFF_R = ((S_BYTES + SC_BYTES + 15) / 16) * 16;
-  static constexpr int OFF_BAR = ((OFF_R + NV * (int)sizeof(T) + 15) / 16) * 16;
-  static constexpr int SMEM = OFF_BAR + 16;
-  static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
-};
-
-template <int D, int K, typename T, typename TS, bool ADD>
-__global__ void __launch_bounds__(GenShape<D, K, T, TS>::NT)
-    k_colour_pass_gen(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb, int colour, int64_t count,
-                      const TS* __restrict__ S, T* x, const T* __restrict__ b, int evict_first, int* __restrict__ err,
-                      uint64_t wait_ns, int64_t vs, int y0, T* __restrict__ acc, T omega) {
-  using G = GenShape<D, K, T, TS>;
-  constexpr int NV = G::NV, NVP = G::NVP;
-  extern __shared__ __align__(128) unsigned char smem[];
-  const TS* sS = reinterpret_cast<const TS*>(smem);
-  const float* sSc = reinterpret_cast<const float*>(smem + G::S_BYTES);
-  T* sr = reinterpret_cast<T*>(smem + G::OFF_R);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::OFF_BAR);
-  const int l = threadIdx.x;
-  const int64_t p = blockIdx.x;
-  const int64_t rhs = (int64_t)blockIdx.y + y0;
-  x += rhs * vs;
-  b += rhs * vs;
-  if constexpr (ADD) acc += rhs * vs;
-  if (l == 0) {
-    mbar_init(bar, 1);
-    const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
-    mbar_arrive_expect_tx(bar, (uint32_t)(G::S_BYTES + G::SC_BYTES));
-    bulk_load(smem, S + p * G::SL::STRIDE, G::S_BYTES, bar, pol);
-    if constexpr (G::BF)
-      bulk_load(smem + G::S_BYTES, reinterpret_cast<const float*>(S + count * G::SL::STRIDE) + p * NVP, G::SC_BYTES,
-                bar, pol);
-  }
-  int v[D];
-  patch_vertex<D>(L.n, colour, p, v);
-  int idx[D];
-  int comp = 0;
-  int64_t g = -1;
-  if (l < NV) {
-    comp = patch_local_decode<D, K>(v, l, idx);
-    g = flat_index(L, comp, idx);
-  }
-  __syncthreads();   // the barrier is initialised before anyone waits on it
-  pdl_launch_dependents();
-  pdl_wait();        // x and b come from the preceding kernels
-  T rl = T(0);
-  if (l < NV) rl = b[g] - apply_row(L, tb, comp, idx, x);
-  const bool timed_out = !mbar_wait_bounded(bar, 0u, wait_ns);
-  if (__syncthreads_or(timed_out)) {
-    if (l == 0) {
-      atomicExch(err, 2);
-      mbar_wait_bounded(bar, 0u, 100000000ull);   // let a late copy land before the block exits
-    }
-    return;
-  }
-  T sl = T(1);
-  if constexpr (G::BF) sl = (l < NV) ? (T)sSc[l] : T(1);
-  if (l < NV) sr[l] = rl * sl;
-  __syncthreads();
-  if (l < NV) {
-    T d0 = T(0), d1 = T(0);
-#pragma unroll 8
-    for (int m = 0; m + 1 < NV; m += 2) {
-      d0 += (T)sS[m * NVP + l] * sr[m];
-      d1 += (T)sS[(m + 1) * NVP + l] * sr[m + 1];
-    }
-    if (NV % 2) d0 += (T)sS[(NV - 1) * NVP + l] * sr[NV - 1];
-    const T d = (d0 + d1) * sl;
-    if constexpr (ADD) acc[g] += omega * d;
-    else x[g] += d;
-  }
-}
-
 }  // namespace mgd
 
 #include "passcta.cuh"

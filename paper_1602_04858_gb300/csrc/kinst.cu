@@ -125,7 +125,6 @@ void patch_setup(const HostLevel& h, int colour, int sprec, void* S, int* fail, 
   else patch_setup_t<__nv_bfloat16>(h, colour, S, fail, s);
 }
 
-#if MG_K <= 1
 template <typename T, typename TS, int NR>
 void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
                     cudaStream_t s) {
@@ -162,10 +161,14 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
                      pstride(h, colour));
 }
 
+// The warp-per-patch pass takes RT_0 and RT_1 (RT_2: two 37 KB inverse
+// buffers per warp do not fit; its levels run the block kernels).
+constexpr bool WARP_PASS = K <= 1;
+
 // Byte offset of the block-per-patch tables inside a level's table blob.
 template <typename T, typename TS>
 constexpr size_t cta_tables_offset() {
-  return (PassShape<D, K, T, TS, 1>::TAB_BYTES + 255) / 256 * 256;
+  return WARP_PASS ? (PassShape<D, K, T, TS, 1>::TAB_BYTES + 255) / 256 * 256 : 0;
 }
 
 // One block per patch: grid = patches of the colour x right-hand-side groups.
@@ -173,10 +176,15 @@ template <typename T, typename TS, int NR>
 void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
                         cudaStream_t s) {
   using C = PassShapeC<D, K, T, TS, NR>;
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_colour_pass_cta<D, K, T, TS, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::SMEM);
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h.count[colour], groups);
   cfg.blockDim = dim3(C::NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -195,10 +203,15 @@ template <typename T, typename TS, int NR>
 void additive_pass_nr(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc,
                       double omega, int* err, int groups, cudaStream_t s) {
   using C = PassShapeC<D, K, T, TS, NR>;
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_colour_pass_cta<D, K, T, TS, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         C::SMEM);
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)h.count[colour], groups);
   cfg.blockDim = dim3(C::NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = C::SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -236,12 +249,16 @@ template <typename T, typename TS, int NR>
 void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err,
                          int groups, cudaStream_t s) {
   using C = PassShapeC<D, K, T, TS, NR>;
+  static std::atomic<unsigned long long> attr{0};
+  once_per_device(attr, [] {
+    cudaFuncSetAttribute(k_colour_pass_ctap<D, K, T, TS, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::P_SMEM);
+  });
   static std::atomic<int> caps[64];
   const int cap = per_device_int(caps, [] {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass_ctap<D, K, T, TS, NR>, C::NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_colour_pass_ctap<D, K, T, TS, NR>, C::NT, C::P_SMEM);
     return (per > 0 ? per : 1) * (nsm > 0 ? nsm : 1);
   });
   // the blocks of all right-hand-side groups share the device
@@ -251,7 +268,7 @@ void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x,
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nb, groups);
   cfg.blockDim = dim3(C::NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = C::P_SMEM;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -282,8 +299,13 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
     if (rest > 0) colour_pass_cta_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
     return;
   }
-  if (g4 > 0) colour_pass_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
-  if (rest > 0) colour_pass_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+  if constexpr (WARP_PASS) {
+    if (g4 > 0) colour_pass_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+    if (rest > 0) colour_pass_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+  } else {
+    if (g4 > 0) colour_pass_cta_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
+    if (rest > 0) colour_pass_cta_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+  }
 }
 
 void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
@@ -312,8 +334,9 @@ template <typename T, typename TS>
 int build_template_t(const HostLevel& h, void* tabs, cudaStream_t s, std::string* why) {
   std::vector<unsigned char> blob, blob_c;
   std::string msg;
-  if (!build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg) ||
-      !build_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob_c, msg)) {
+  bool ok = true;
+  if constexpr (WARP_PASS) ok = build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg);
+  if (!ok || !build_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob_c, msg)) {
     if (why) *why = "colour-pass tables of the " + std::to_string(h.n) + "^" + std::to_string(D) + " level: " + msg;
     return 1;
   }
@@ -351,8 +374,10 @@ int plan_selftest_t(int n, double mu, std::string& why) {
   h.ndof = o;
   h.h = 1.0 / n;
   h.mu = mu;
-  const int r = check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
-  if (r != 0) return r;
+  if constexpr (WARP_PASS) {
+    const int r = check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+    if (r != 0) return r;
+  }
   return check_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
 }
 
@@ -379,85 +404,6 @@ int64_t patch_nnz(const HostLevel& h) {
   for (const auto& r : rows) nnz += (int64_t)(r.pl.size() + r.ms.size());
   return nnz;
 }
-#else   // MG_K >= 2: patches too large for the table-driven kernels
-
-// One block per patch (k_colour_pass_gen); right-hand sides along grid y, in
-// slices of at most 65,535.  ADD: the additive variant (acc += omega delta).
-template <typename T, typename TS, bool ADD>
-void pass_gen(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc, double omega,
-              int* err, int nrhs, cudaStream_t s) {
-  using G = GenShape<D, K, T, TS>;
-  const int64_t cnt = h.count[colour];
-  if (cnt == 0) return;
-  static std::atomic<unsigned long long> attr{0};
-  once_per_device(attr, [] {
-    cudaFuncSetAttribute(k_colour_pass_gen<D, K, T, TS, ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-  });
-  for (int y0 = 0; y0 < nrhs; y0 += 65535) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cnt, (unsigned)std::min(65535, nrhs - y0));
-    cfg.blockDim = dim3(G::NT);
-    cfg.dynamicSmemBytes = G::SMEM;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_colour_pass_gen<D, K, T, TS, ADD>, mk<T>(h), tab<T>(), colour, cnt, (const TS*)S,
-                       (T*)const_cast<void*>(x), (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof, y0, (T*)acc,
-                       (T)omega);
-  }
-}
-
-void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* x, const void* b, int* err, int nrhs,
-                 cudaStream_t s) {
-  if (prec == P64) pass_gen<double, double, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
-  else if (prec == P32) pass_gen<float, float, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
-  else pass_gen<float, __nv_bfloat16, false>(h, colour, S, x, b, nullptr, 0.0, err, nrhs, s);
-}
-
-void additive_pass(const HostLevel& h, int colour, int prec, const void* S, const void* x, const void* b, void* acc,
-                   double omega, int* err, int nrhs, cudaStream_t s) {
-  if (prec == P64) pass_gen<double, double, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
-  else if (prec == P32) pass_gen<float, float, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
-  else pass_gen<float, __nv_bfloat16, true>(h, colour, S, x, b, acc, omega, err, nrhs, s);
-}
-
-// The stencil-driven pass needs no per-level tables.
-int64_t template_elems(int) { return 16; }
-int build_template(const HostLevel&, int, void*, cudaStream_t, std::string*) { return 0; }
-int plan_selftest(int, int, double, std::string* why) {
-  if (why) why->clear();
-  return 0;
-}
-
-// Distinct columns of the operator rows of one interior patch.
-struct ColumnSet {
-  const Lvl<D, K, double>& L;
-  std::vector<int64_t> cols;
-  explicit ColumnSet(const Lvl<D, K, double>& l) : L(l) {}
-  void operator()(int comp, const int (&j)[D], double) { cols.push_back(flat_index(L, comp, j)); }
-  double cell_c(const int (&)[D]) const { return 1.0; }
-};
-
-int64_t patch_nnz(const HostLevel& h) {
-  const Lvl<D, K, double> L = mk<double>(h);
-  int v[D];
-  for (int e = 0; e < D; ++e) v[e] = h.n >= 4 ? 2 : 1;
-  int64_t nnz = 0;
-  for (int l = 0; l < PatchShape<D, K>::NV; ++l) {
-    int idx[D];
-    const int comp = patch_local_decode<D, K>(v, l, idx);
-    ColumnSet cs(L);
-    visit_row(L, tab<double>(), comp, idx, cs);
-    std::sort(cs.cols.begin(), cs.cols.end());
-    nnz += (int64_t)(std::unique(cs.cols.begin(), cs.cols.end()) - cs.cols.begin());
-  }
-  return nnz;
-}
-
-#endif
 
 // Patches of the boundary vertices v (some v_e = 0 or n): the free dofs whose
 // support lies in the cells v_e - 1, v_e (clipped to the domain) and the
@@ -630,7 +576,7 @@ DKOps make_ops() {
   o.bpatch_lists = bpatch_lists;
   o.bpatch_setup = bpatch_setup;
   o.bpatch_pass = bpatch_pass;
-  o.generic = K >= 2 ? 1 : 0;
+  o.warp_pass = WARP_PASS ? 1 : 0;
   o.bnv_max = bpatch_threads<K>();
   return o;
 }

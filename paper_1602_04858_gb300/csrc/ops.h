@@ -78,8 +78,7 @@ struct HostLevel {
 
 struct DKOps {
   int nv;                // patch size
-  int generic;           // 1: one stencil-driven colour-pass kernel (patches too large for the
-                         // table-driven ones), no per-level tables and no kernel choice
+  int warp_pass;         // 1: the warp-per-patch colour pass exists (RT_0, RT_1); 0: block kernels only
   int bnv_max;           // largest boundary-vertex patch the boundary pass takes
   int nvp[3];            // stored column length per storage precision (P64, P32, P32B)
   int64_t s_stride[3];   // elements per stored patch inverse

@@ -32,6 +32,7 @@ template <int D, int K> struct PlanShapeC;
 template <> struct PlanShapeC<2, 1> { static constexpr int ZW = 9, ZMW = 2; };   // rows <= 34 + 6 entries
 template <> struct PlanShapeC<2, 0> { static constexpr int ZW = 3, ZMW = 1; };   // rows <= 11 + 4
 template <> struct PlanShapeC<3, 0> { static constexpr int ZW = 5, ZMW = 1; };   // rows <= 17 + 4
+template <> struct PlanShapeC<2, 2> { static constexpr int ZW = 18, ZMW = 2; };  // rows <= 7 x 9 + 6 + 8
 
 constexpr int ELEM_INTS = 12;   // gather descriptor: three int4
 
@@ -78,7 +79,7 @@ struct PassShapeC {
   static constexpr size_t TAB_BYTES = TB_MASS + W::al16((size_t)NTYPE * ZMW * NT * MASS_BYTES);
   static_assert(NT <= 1024 && NT % 32 == 0, "block of whole warps");
   static_assert(32 % SPL == 0 && LPP * SPL <= NT, "column parts of a row group lie in one warp");
-  static_assert(SMEM <= 48 * 1024 && P_SMEM <= 48 * 1024, "static shared memory");
+  static_assert(SMEM <= 227 * 1024 && P_SMEM <= 227 * 1024, "shared memory of one block");
   static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(RG <= 32, "row group fits the shuffle");
 };
@@ -361,7 +362,8 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
-  __shared__ __align__(128) unsigned char sm[C::SMEM];
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* const sm = smem;   // C::SMEM bytes
   T* st = reinterpret_cast<T*>(sm + C::OFF_T);
   int* gidx = reinterpret_cast<int*>(sm + C::OFF_I);
   int* wcol = gidx + NV;
@@ -619,7 +621,8 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
   using C = PassShapeC<D, K, T, TS, NR>;
   constexpr int NT = C::NT, NV = C::NV, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
-  __shared__ __align__(128) unsigned char sm[C::P_SMEM];
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* const sm = smem;   // C::P_SMEM bytes
   T* st = reinterpret_cast<T*>(sm + C::P_OFF_T);
   int* gidx = reinterpret_cast<int*>(sm + C::P_OFF_I);
   int* wcol = gidx + NV;

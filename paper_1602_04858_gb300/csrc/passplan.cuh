@@ -144,6 +144,13 @@ template <> struct PlanShape<3, 0, 32> {
   static constexpr int z(int) { return 9; }
   static constexpr int zm(int) { return 4; }
 };
+// RT_2 has no warp-per-patch pass (two 37 KB inverse buffers per warp do not
+// fit); this shape only completes the window geometry the block pass shares.
+template <> struct PlanShape<2, 2, 32> {
+  static constexpr int NP = 1, MAXP = 1;
+  static constexpr int z(int) { return 1; }
+  static constexpr int zm(int) { return 1; }
+};
 template <> struct PlanShape<3, 0, 16> {
   static constexpr int NP = 2, MAXP = 2;
   static constexpr int z(int) { return 9; }

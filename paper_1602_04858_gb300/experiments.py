@@ -24,6 +24,7 @@ values and body force -c g (cellwise constant).  The solves below compute u_0.
     python -m paper_1602_04858_gb300.experiments --table4
     python -m paper_1602_04858_gb300.experiments --variants
     python -m paper_1602_04858_gb300.experiments --scale
+    python -m paper_1602_04858_gb300.experiments --degrees
 
 Prints one JSON line per solve and a table of GMRES iterations.
 """
@@ -171,6 +172,52 @@ def variants(torch, precision="fp32"):
     return rows
 
 
+def degrees(torch, precision="fp32", sizes=(128, 256)):
+    """Polynomial degree (Sec. 2.3 defines RT_k x Q_k for every k): RT_0, RT_1
+    and RT_2 on the same meshes and coefficient (20 channels two cells wide,
+    contrast 1e6, mu = 0.01, the recipe of the 256^2 benchmark), random load
+    in the velocity rows, FGMRES to 1e-8, variable V-cycle with m(J) = 2.
+    Reports iterations, V-cycle and solve times (CUDA events) and the V-cycle
+    rate in dofs x V-cycles per second."""
+    rows = []
+    for n in sizes:
+        c = inputs.channel_c(n, 20, 2)
+        levels = int(np.log2(n // 4)) + 1
+        for k in (0, 1, 2):
+            cd = torch.as_tensor(c, device="cuda")
+            t0 = time.perf_counter()
+            G = mgdarcy.Multigrid(2, 4, levels, k, 0.01, cd, precision=precision)
+            setup_s = time.perf_counter() - t0
+            nu, npr = G.sizes()
+            b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
+            b[:nu] = torch.as_tensor(np.random.default_rng(11).standard_normal(nu), device="cuda")
+            r = torch.as_tensor(np.random.default_rng(1).standard_normal(nu + npr), device="cuda")
+            z = torch.zeros_like(r)
+            for _ in range(3):
+                G.vcycle(r, z)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                G.vcycle(r, z)
+            e1.record()
+            torch.cuda.synchronize()
+            vms = e0.elapsed_time(e1) / 10
+            x = torch.zeros_like(b)
+            st, _ = G.solve(b[:nu].contiguous(), b[nu:].contiguous(), x, tol=1e-8, maxit=400, check=False)
+            rows.append(dict(n=n, degree=k, dofs=nu + npr, iterations=st.iterations, converged=bool(st.converged),
+                             vcycle_ms=vms, dof_vcycles_per_s=(nu + npr) / (vms * 1e-3), solve_ms=st.solve_ms,
+                             setup_s=setup_s))
+            print(json.dumps(rows[-1]), flush=True)
+            del G
+            torch.cuda.empty_cache()
+    print("\n| n | RT_k | dofs | iterations | V-cycle ms | DoF*V/s | solve ms |")
+    for r_ in rows:
+        print(f"| {r_['n']}^2 | RT_{r_['degree']} | {r_['dofs']:,} | {r_['iterations']} | {r_['vcycle_ms']:.2f} | "
+              f"{r_['dof_vcycles_per_s']:.3g} | {r_['solve_ms']:.1f} |")
+    return rows
+
+
 def scale(torch, precision="fp32"):
     """Larger meshes and contrast 1e8 (NEXT-4): the driven flow of Tables 1-2
     on 2048^2 RT_0 cells (12.6 M dofs) and 512^2 RT_1 cells (3.1 M dofs),
@@ -203,7 +250,11 @@ def main():
     ap.add_argument("--table4", action="store_true", help="the 3-D Brinkman analogue of Table 4 instead")
     ap.add_argument("--variants", action="store_true", help="smoother and cycle variants instead")
     ap.add_argument("--scale", action="store_true", help="2048^2 RT_0 and 512^2 RT_1 at contrast 1e8 instead")
+    ap.add_argument("--degrees", action="store_true", help="RT_0, RT_1 and RT_2 on the same meshes instead")
     args = ap.parse_args()
+    if args.degrees:
+        degrees(torch, precision=args.precision)
+        return
     if args.scale:
         scale(torch, precision=args.precision)
         return

@@ -1,8 +1,9 @@
 """RT_2 x Q_2 (Sec. 2.3 defines RT_k x Q_k for every k) on the GPU against the
 FP64 oracle.
 
-Patches of RT_2 hold 96 dofs in 2-D; their colour pass is one block per patch
-whose rows and operator entries come from the stencil (no per-level tables).
+Patches of RT_2 hold 96 dofs in 2-D; their colour passes run the block
+kernels (one block per patch, or persistent blocks walking the patches), with
+the inverses staged in dynamic shared memory (37 KB FP32, 74 KB FP64).
 The bounds are those of the RT_0/RT_1 parity tests: FP64 operator 1e-13 of
 |A||x| per entry, transfers 1e-14, coarse solve 1e-11, single smoothing steps
 and V-cycles 1e-10 relative; FP32 V-cycles 1e-5 relative on lognormal fields
@@ -124,9 +125,14 @@ def test_transfer_and_coarse_parity(case):
     assert rel_inf(host(x), mg.coarse_solve(H, b)) < 1e-11
 
 
+KERNELS = [2, 3]
+KERNEL_IDS = ["block", "persistent"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_smoothing_step_parity_fp64(case):
-    H, G = build(case)
+def test_smoothing_step_parity_fp64(case, kernel):
+    H, G = build(case, pass_kernel=kernel)
     rng = np.random.default_rng(4)
     for j in range(1, len(H.levels)):
         L = H.levels[j]
@@ -148,9 +154,10 @@ def test_vcycle_parity_fp64(case, variable, dense_level):
     assert rel_inf(host(z), zo) < 1e-10
 
 
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
 @pytest.mark.parametrize("case", CASES[:2], ids=IDS[:2])
-def test_vcycle_fp32_error(case):
-    H, G = build(case, precision="fp32")
+def test_vcycle_fp32_error(case, kernel):
+    H, G = build(case, precision="fp32", pass_kernel=kernel)
     r = np.random.default_rng(9).standard_normal(H.levels[-1].S.ndof)
     z = torch.zeros_like(dev(r))
     G.vcycle(dev(r), z)
@@ -231,11 +238,13 @@ def big():
     return c, H, r, mg.vcycle(H, r)
 
 
+@pytest.mark.parametrize("kernel", [0, 2, 3], ids=["timed", "block", "persistent"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
-def test_vcycle_64(big, precision, tol):
-    """FP64 at the parity bound, FP32 at the FP32 bound of the small cases."""
+def test_vcycle_64(big, precision, tol, kernel):
+    """FP64 at the parity bound, FP32 at the FP32 bound of the small cases;
+    the persistent blocks walk several patches each on the finest level."""
     c, H, r, zo = big
-    G = mgdarcy.Multigrid(2, 4, 5, 2, 0.01, dev(c), precision=precision)
+    G = mgdarcy.Multigrid(2, 4, 5, 2, 0.01, dev(c), precision=precision, pass_kernel=kernel)
     z = torch.zeros_like(dev(r))
     G.vcycle(dev(r), z)
     err = np.linalg.norm(host(z) - zo) / np.linalg.norm(zo)
