@@ -588,6 +588,20 @@ def main():
             except Exception as ex:  # reported, not required
                 peaks_alu[kind + "_tflops"] = None
                 peaks_alu["error"] = str(ex)
+    # --- cost of one ordering point between colour passes: grid barrier vs dependent launch ---
+    sync_costs = None
+    if not args.no_companions:
+        sync_costs = {"unit": "us per ordering point", "grid_barrier": {}, "dependent_launch": {},
+                      "note": "grid barrier: one cooperative launch, blocks of 160 threads; dependent launch: "
+                              "a graph of launches with programmatic dependent launch, as the V-cycle runs"}
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        try:
+            for nb in (nsm, 2 * nsm, 4 * nsm):
+                sync_costs["grid_barrier"][str(nb)] = mgdarcy.measure_sync_cost("grid_barrier", nb)
+            for nb in (nsm, 441, 1800):
+                sync_costs["dependent_launch"][str(nb)] = mgdarcy.measure_sync_cost("dependent_launch", nb)
+        except Exception as ex:  # reported, not required
+            sync_costs["error"] = str(ex)
     rv = {}
     for key, t in vc_ms.items():
         prec = key.split("_V(")[0]
@@ -636,6 +650,7 @@ def main():
                                              "bandwidth (peak above); FP64 also against the measured FP64 FMA peak",
                                     "l2_bytes": l2_bytes, "modes": rv},
                 "alu_peaks": peaks_alu or None,
+                "sync_costs": sync_costs,
                 "setup_s": setup_s,
                 "batched": batched,
                 "cpu_baseline": cpu,

@@ -97,7 +97,10 @@ typedef struct {
                            right-hand sides and device), 5: a fixed rule
                            (block kernel where the largest colour holds at
                            most 10,000 inverse entries per SM or four or more
-                           right-hand sides share the inverses, else warp).
+                           right-hand sides share the inverses, else warp);
+                           6, 7, 8: as 1, 2, 3 with every right-hand side on
+                           its own (no sharing of the inverse loads; the timed
+                           choice tries this grouping too, mg_level_rhs_group).
                            Degree 2 (patches of 96 dofs) has no warp kernel:
                            1 runs as 2, the rule takes 2, the timed choice
                            picks between 2 and 3.                              */
@@ -270,6 +273,11 @@ void mg_destroy_batch(mg_batch* b);
  * layout, and the total batch-vector length (any pointer may be NULL). */
 mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offset, int64_t* total);
 
+/* Colour-pass choice of problem p on `level` (1 <= level <= J): the kernel as
+ * in mg_level_pass_kernel and the right-hand-side grouping as in
+ * mg_level_rhs_group (either output may be null).  Host only. */
+mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group);
+
 /* z = B_J r for every problem and right-hand side (Sec. 3.2): one CUDA graph
  * whose branches are the problems' V-cycles, the right-hand sides of a problem
  * sharing each patch-inverse load.  r, z: device, FP64, batch layout. */
@@ -394,10 +402,30 @@ mg_status mg_time_passes(mg_handle* h, int level, int kernel, double* us_per_pas
  * frees a small device buffer; synchronises the stream. */
 mg_status mg_measure_fma_peak(int kind, double* tflops, void* cuda_stream);
 
+/* Measured cost in microseconds of one grid-wide ordering point between two
+ * dependent steps on `blocks` blocks of 160 threads, each step reading a
+ * neighbour block's values written by the previous one (the dependence of
+ * consecutive colour passes of Sec. 3.3 in miniature): kind 0 a software grid
+ * barrier inside one cooperative launch (blocks must fit the device at once,
+ * else MG_ERR_INVALID_ARG; every wait bounded at 0.2 s, MG_ERR_DEVICE_TIMEOUT
+ * on expiry), kind 1 a chain of dependent launches with programmatic dependent
+ * launch in a CUDA graph, as the V-cycle runs its passes.  The paper has no
+ * counterpart: this is the evidence for how the passes are ordered.  Allocates
+ * and frees a small device buffer; synchronises the stream. */
+mg_status mg_measure_sync_cost(int kind, int blocks, double* us_per_step, void* cuda_stream);
+
 /* Colour-pass kernel chosen for `level` (1 <= level <= J) at setup, see
  * mg_problem.pass_kernel: *kernel = 1 (warp per patch), 2 (block per patch)
  * or 3 (persistent blocks).  Host only. */
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel);
+
+/* Right-hand sides sharing each patch-inverse load in the colour passes of
+ * `level` (1 <= level <= J): 4 (groups of four where the handle holds four or
+ * more right-hand sides) or 1 (each on its own, four times the blocks).  With
+ * four or more right-hand sides the timed choice (mg_problem.pass_kernel 0 or
+ * 4) tries both with every kernel and keeps the fastest pair; the other modes
+ * keep 4.  Host only. */
+mg_status mg_level_rhs_group(const mg_handle* h, int level, int* group);
 
 /* Number of kernels the library launched on this handle so far. */
 int64_t mg_kernel_launches(const mg_handle* h);
@@ -412,7 +440,9 @@ const char* mg_last_error(void);
  * plan evaluated on a random window agrees with the row of the operator, and
  * every gather segment addresses the window column, patch row or cell it
  * stands for (zero outside the domain); likewise the row plans and gather
- * descriptors of the block-per-patch pass.  Returns 0 if all hold, 1 with a
+ * descriptors of the block-per-patch pass, and the operator row plans of the
+ * apply and residual kernels (every free row against the stencil, 1e-13 of
+ * its sum of |terms|).  Returns 0 if all hold, 1 with a
  * reason in msg (msg_len bytes, may be null) otherwise, 2 for unsupported
  * arguments.  Degree 2 has block-per-patch tables only. */
 int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, char* msg, int msg_len);

@@ -159,6 +159,7 @@ bool is_device_ptr(const void* p) {
 void level_geometry(HostLevel& L, int d, int k, int n, double mu) {
   std::memset(&L, 0, sizeof(L));
   L.wait_ns = DEFAULT_WAIT_NS;
+  L.rhs_group = 4;
   L.d = d;
   L.k = k;
   L.n = n;
@@ -337,8 +338,11 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
         for (int col = 0; col < num_colours(h->d); ++col) mx = std::max(mx, L.count[col]);
         const int64_t nv = h->ops->nv;
         L.pass_cta = (nrhs >= 4 || mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
-      } else {
+      } else if (mode <= 3) {
         L.pass_cta = mode - 1;
+      } else {   // 6, 7, 8: forced kernel, every right-hand side on its own
+        L.pass_cta = mode - 6;
+        L.rhs_group = 1;
       }
       L.pass_cta = std::max(L.pass_cta, first);
       continue;
@@ -348,20 +352,33 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       std::lock_guard<std::mutex> g(mu);
       auto it = cache.find(key);
       if (it != cache.end()) {
-        L.pass_cta = it->second;
+        L.pass_cta = it->second % 3;
+        L.rhs_group = it->second >= 3 ? 1 : 4;
         continue;
       }
     }
-    float ms[3] = {0.f, 0.f, 0.f};
-    for (int var = first; var < 3; ++var) {
-      L.pass_cta = var;
-      TRY(time_smoothing(h, j, nrhs, 2, 3, &ms[var], nullptr));
+    // kernels x right-hand-side grouping (with four or more right-hand sides:
+    // four sharing each S_v load, or each on its own with four times the blocks)
+    const int ngroup = nrhs >= 4 ? 2 : 1;
+    float best = 0.f;
+    int best_var = first, best_grp = 4;
+    for (int gi = 0; gi < ngroup; ++gi) {
+      L.rhs_group = gi == 0 ? 4 : 1;
+      for (int var = first; var < 3; ++var) {
+        L.pass_cta = var;
+        float ms = 0.f;
+        TRY(time_smoothing(h, j, nrhs, 2, 3, &ms, nullptr));
+        if ((gi == 0 && var == first) || ms < best) {
+          best = ms;
+          best_var = var;
+          best_grp = L.rhs_group;
+        }
+      }
     }
-    L.pass_cta = first;
-    for (int var = first + 1; var < 3; ++var)
-      if (ms[var] < ms[L.pass_cta]) L.pass_cta = var;
+    L.pass_cta = best_var;
+    L.rhs_group = best_grp;
     std::lock_guard<std::mutex> g(mu);
-    cache[key] = L.pass_cta;
+    cache[key] = best_var + 3 * (best_grp == 1 ? 1 : 0);
   }
   h->launches = l0;
   CU(cudaGetLastError());
@@ -537,7 +554,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
-  if (p->pass_kernel < 0 || p->pass_kernel > 5) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (p->pass_kernel < 0 || p->pass_kernel > 8) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
   if (p->escalate_window > 100000) return fail(MG_ERR_INVALID_ARG, "escalate_window too large");
   if (p->boundary_patches < 0 || p->boundary_patches > 1) return fail(MG_ERR_INVALID_ARG, "bad boundary_patches");
@@ -608,6 +625,26 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
     }
     launch_d2f(L.c64, L.c32, nc, h->stream);
     ++h->launches;
+  }
+  // operator row plans of every level (apply, residuals)
+  for (int j = 0; j <= J; ++j) {
+    HostLevel& L = h->lv[j];
+    RowPlanBlob blob;
+    h->ops->row_plans(L, blob);
+    unsigned char* q = nullptr;
+    if ((st = h->alloc(&q, blob.bytes.size())) != MG_OK) return cleanup(st);
+    if (cudaMemcpyAsync(q, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return cleanup(fail(MG_ERR_CUDA, "upload of the operator row plans failed"));
+    L.rp.cls = reinterpret_cast<const int*>(q + blob.cls);
+    L.rp.ptr = reinterpret_cast<const int*>(q + blob.ptr);
+    L.rp.mptr = reinterpret_cast<const int*>(q + blob.mptr);
+    L.rp.pe = reinterpret_cast<const int2*>(q + blob.pe);
+    L.rp.me = reinterpret_cast<const int4*>(q + blob.me);
+    L.rp.pcf64 = reinterpret_cast<const double*>(q + blob.pcf64);
+    L.rp.mcf64 = reinterpret_cast<const double*>(q + blob.mcf64);
+    L.rp.pcf32 = reinterpret_cast<const float*>(q + blob.pcf32);
+    L.rp.mcf32 = reinterpret_cast<const float*>(q + blob.mcf32);
   }
   if ((st = h->alloc(&h->d_fail, 1)) != MG_OK) return cleanup(st);
   cudaMemsetAsync(h->d_fail, 0, sizeof(int), h->stream);
@@ -872,6 +909,12 @@ mg_status mg_patch_nnz(const mg_handle* h, int level, int64_t* nnz) {
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
   if (!h || level < 1 || level > h->J || !kernel) return fail(MG_ERR_INVALID_ARG, "bad level or argument");
   *kernel = h->lv[level].pass_cta + 1;
+  return MG_OK;
+}
+
+mg_status mg_level_rhs_group(const mg_handle* h, int level, int* group) {
+  if (!h || !group || level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  *group = h->lv[level].rhs_group;
   return MG_OK;
 }
 
@@ -1379,7 +1422,9 @@ bool same_shape(const mg_handle* a, const mg_handle* b) {
       a->lv[0].n != b->lv[0].n)
     return false;
   for (int j = 0; j <= a->J; ++j)
-    if (a->lv[j].pass_cta != b->lv[j].pass_cta || a->lv[j].sprec != b->lv[j].sprec) return false;
+    if (a->lv[j].pass_cta != b->lv[j].pass_cta || a->lv[j].rhs_group != b->lv[j].rhs_group ||
+        a->lv[j].sprec != b->lv[j].sprec)
+      return false;
   return true;
 }
 
@@ -1717,6 +1762,15 @@ mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offs
 }
 
 int64_t mg_batch_kernel_launches(const mg_batch* b) { return b ? b->launches : 0; }
+
+mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group) {
+  if (!b || p < 0 || p >= (int)b->sub.size()) return fail(MG_ERR_INVALID_ARG, "bad problem index");
+  const mg_handle* h = b->sub[p];
+  if (level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  if (kernel) *kernel = h->lv[level].pass_cta + 1;
+  if (rhs_group) *rhs_group = h->lv[level].rhs_group;
+  return MG_OK;
+}
 
 mg_status mg_sync_batch(mg_batch* B) {
   if (!B) return fail(MG_ERR_INVALID_ARG, "null batch");

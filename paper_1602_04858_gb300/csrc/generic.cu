@@ -154,13 +154,20 @@ __global__ void k_scale_copy(const double* __restrict__ a, double s, double* __r
 }
 // b = a / sqrt(*n2) (b unchanged if *n2 <= 0): normalisation by a norm that
 // stays on the device
+// The FP64 square root and division are slow on this part: one thread per
+// block forms the scale, and the block then walks the vector grid-stride.
 __global__ void k_scale_by_rnorm(const double* __restrict__ a, const double* __restrict__ n2, double* __restrict__ b,
                                  int64_t n) {
-  const double q = *n2;
-  if (!(q > 0.0)) return;
-  const double s = 1.0 / sqrt(q);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = s * a[i];
+  __shared__ double s_scale;
+  if (threadIdx.x == 0) {
+    const double q = *n2;
+    s_scale = q > 0.0 ? 1.0 / sqrt(q) : 0.0;
+  }
+  __syncthreads();
+  const double s = s_scale;
+  if (!(s > 0.0)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = s * a[i];
 }
 __global__ void k_axpby(double alpha, const double* __restrict__ x, double beta, double* __restrict__ y, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,7 +415,8 @@ void launch_scale_copy(const double* a, double sc, double* b, int64_t n, cudaStr
   k_scale_copy<<<blocks(n, 256), 256, 0, s>>>(a, sc, b, n);
 }
 void launch_scale_by_rnorm(const double* a, const double* n2, double* b, int64_t n, cudaStream_t s) {
-  k_scale_by_rnorm<<<blocks(n, 256), 256, 0, s>>>(a, n2, b, n);
+  const unsigned g = blocks(n, 256);
+  k_scale_by_rnorm<<<g < 152 * 8 ? g : 152 * 8, 256, 0, s>>>(a, n2, b, n);
 }
 void launch_axpby(double alpha, const double* x, double beta, double* y, int64_t n, cudaStream_t s) {
   k_axpby<<<blocks(n, 256), 256, 0, s>>>(alpha, x, beta, y, n);

@@ -9,31 +9,33 @@
 #include "device.cuh"
 #include "ops.h"
 #include "passplan.cuh"
+#include "rowplan.cuh"
 
 namespace mgd {
 
 // ---------------------------------------------------------------------------
 // Operator apply and residual (eq. Brinkman-weak), one thread per row.
 // ---------------------------------------------------------------------------
+// y = A x (rows from the level's row plans); constrained rows: y = x.
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
-                                               const T* __restrict__ x, T* __restrict__ y, int64_t vs) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_apply(const Lvl<D, K, T> L, const RowPlans<T> P, const T* __restrict__ x,
+                                               T* __restrict__ y, int64_t vs) {
+  const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (g >= L.ndof) return;
   x += blockIdx.y * vs;
   y += blockIdx.y * vs;
   int idx[D];
-  const int comp = decode(L, g, idx);
-  y[g] = apply_row(L, tb, comp, idx, x);
+  const int comp = decode32(L, g, idx);
+  y[g] = is_constrained(L, comp, idx) ? x[g] : plan_row(L, P, comp, idx, x);
 }
 
 // r = b - A x on free rows; constrained rows: r = 0 (zero_c) or b - x.
 // Batched over right-hand sides: blockIdx.y selects the vector, stride vs.
 template <int D, int K, typename T>
-__global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L0, const __grid_constant__ Tab<K, T> tb,
+__global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L0, const RowPlans<T> P,
                                                   const T* __restrict__ x, const T* __restrict__ b,
                                                   T* __restrict__ r, int zero_c, int64_t vs, const ProbStride ps) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (g >= L0.ndof) return;
   Lvl<D, K, T> L = L0;
   L.c += ps.of(blockIdx.y) * ps.c;
@@ -41,28 +43,30 @@ __global__ void __launch_bounds__(256) k_residual(const Lvl<D, K, T> L0, const _
   b += blockIdx.y * vs;
   r += blockIdx.y * vs;
   int idx[D];
-  const int comp = decode(L, g, idx);
+  const int comp = decode32(L, g, idx);
   if (is_constrained(L, comp, idx)) {
     r[g] = zero_c ? T(0) : b[g] - x[g];
     return;
   }
-  r[g] = b[g] - apply_row(L, tb, comp, idx, x);
+  r[g] = b[g] - plan_row(L, P, comp, idx, x);
 }
 
 // r = b - A x (stored if r != nullptr; constrained rows: b - x) and one
 // partial sum of |r|^2 per block, reduced in a fixed order afterwards.
+// Rows by `row` (the stencil visit without tables for the allocation-free
+// entry point, the row plans otherwise).
 constexpr int RN_THREADS = 256;
-template <int D, int K, typename T>
-__global__ void __launch_bounds__(RN_THREADS) k_residual_norm(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
-                                                              const T* __restrict__ x, const T* __restrict__ b,
-                                                              T* __restrict__ r, double* __restrict__ partial) {
+template <int D, int K, typename T, class Row>
+__device__ __forceinline__ void residual_norm_block(const Lvl<D, K, T>& L, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ r,
+                                                    double* __restrict__ partial, Row row) {
   __shared__ double red[RN_THREADS / 32];
   const int64_t g = (int64_t)blockIdx.x * RN_THREADS + threadIdx.x;
   double sq = 0.0;
   if (g < L.ndof) {
     int idx[D];
-    const int comp = decode(L, g, idx);
-    const T rv = is_constrained(L, comp, idx) ? b[g] - x[g] : b[g] - apply_row(L, tb, comp, idx, x);
+    const int comp = decode32(L, (int)g, idx);
+    const T rv = is_constrained(L, comp, idx) ? b[g] - x[g] : b[g] - row(comp, idx);
     if (r) r[g] = rv;
     sq = (double)rv * (double)rv;
   }
@@ -76,6 +80,22 @@ __global__ void __launch_bounds__(RN_THREADS) k_residual_norm(const Lvl<D, K, T>
     for (int w = 0; w < RN_THREADS / 32; ++w) s += red[w];
     partial[blockIdx.x] = s;
   }
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(RN_THREADS) k_residual_norm(const Lvl<D, K, T> L, const __grid_constant__ Tab<K, T> tb,
+                                                              const T* __restrict__ x, const T* __restrict__ b,
+                                                              T* __restrict__ r, double* __restrict__ partial) {
+  residual_norm_block(L, x, b, r, partial,
+                      [&](int comp, const int (&idx)[D]) { return apply_row(L, tb, comp, idx, x); });
+}
+
+template <int D, int K, typename T>
+__global__ void __launch_bounds__(RN_THREADS) k_residual_norm_rp(const Lvl<D, K, T> L, const RowPlans<T> P,
+                                                                 const T* __restrict__ x, const T* __restrict__ b,
+                                                                 T* __restrict__ r, double* __restrict__ partial) {
+  residual_norm_block(L, x, b, r, partial,
+                      [&](int comp, const int (&idx)[D]) { return plan_row(L, P, comp, idx, x); });
 }
 
 // Load vector of cellwise-constant data (the first term of F in eq. (BCh)

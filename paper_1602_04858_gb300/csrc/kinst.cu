@@ -62,22 +62,183 @@ ProbStride pstride(const HostLevel& h, int colour) {
   return p;
 }
 
+// --- operator row plans (rowplan.cuh) -----------------------------------------
+
+// Records every visit of one row: column, coefficient and the cell whose
+// coefficient the visit asked for last (the mass term of that cell).
+struct RowRecorder {
+  double cv;
+  int cur[D];
+  struct Visit {
+    int cc;
+    int j[D];
+    int cell[D];
+    double coef;
+  };
+  std::vector<Visit> v;
+  explicit RowRecorder(double c) : cv(c) {
+    for (int e = 0; e < D; ++e) cur[e] = 0;
+  }
+  void operator()(int comp, const int (&j)[D], double coef) {
+    Visit a;
+    a.cc = comp;
+    for (int e = 0; e < D; ++e) {
+      a.j[e] = j[e];
+      a.cell[e] = cur[e];
+    }
+    a.coef = coef;
+    v.push_back(a);
+  }
+  double cell_c(const int (&cell)[D]) {
+    for (int e = 0; e < D; ++e) cur[e] = cell[e];
+    return cv;
+  }
+};
+
+// One plan per class of free rows (see rowplan.cuh).  The coefficients come
+// from the same stencil visit as every other operator evaluation: a visit
+// with unit cell coefficient scaled by 2^30 minus one with cell coefficient 0
+// separates the mass part (times c of its cell) from the rest exactly up to
+// rounding of the separated parts.
+void row_plans(const HostLevel& h, RowPlanBlob& out) {
+  constexpr int K1 = K + 1, KEYS = row_keys<D, K>();
+  Lvl<D, K, double> L = mk<double>(h);
+  L.c = nullptr;   // the recorder supplies the cell coefficient
+  const Tab<K, double>& tb = tab<double>();
+  const int n = h.n, N = h.N;
+  std::vector<int> cls((size_t)(D + 1) * KEYS, -1);
+  std::vector<int> ptr(1, 0), mptr(1, 0);
+  std::vector<int2> pe;
+  std::vector<int4> me;
+  std::vector<double> pcf, mcf;
+  const double CV = 1073741824.0;   // 2^30
+  for (int comp = 0; comp <= D; ++comp) {
+    // candidate node indices per direction: those of the first and last three cells
+    std::vector<int> cand[D];
+    for (int e = 0; e < D; ++e) {
+      const bool own = comp < D && e == comp;
+      for (int t = own ? 1 : 0; t <= N - 1; ++t)
+        if (t <= 3 * K1 || t >= N - 3 * K1 - 1) cand[e].push_back(t);
+    }
+    int64_t total = 1;
+    for (int e = 0; e < D; ++e) total *= (int64_t)cand[e].size();
+    for (int64_t q = 0; q < total; ++q) {
+      int idx[D];
+      int64_t r = q;
+      for (int e = 0; e < D; ++e) {
+        idx[e] = cand[e][(size_t)(r % (int64_t)cand[e].size())];
+        r /= (int64_t)cand[e].size();
+      }
+      const int key = row_key<D, K>(n, comp, idx);
+      int& slot = cls[(size_t)comp * KEYS + key];
+      if (slot >= 0) continue;
+      slot = (int)ptr.size() - 1;
+      RowRecorder r0(0.0), r1(CV);
+      visit_row(L, tb, comp, idx, r0);
+      visit_row(L, tb, comp, idx, r1);
+      // merge the visits by column (plain) and by column and cell (mass)
+      std::vector<std::pair<std::vector<int>, double>> plain, mass;
+      auto add = [](std::vector<std::pair<std::vector<int>, double>>& list, const std::vector<int>& k, double c) {
+        for (auto& pr : list)
+          if (pr.first == k) {
+            pr.second += c;
+            return;
+          }
+        list.push_back({k, c});
+      };
+      for (size_t i = 0; i < r0.v.size(); ++i) {
+        const auto& a = r0.v[i];
+        const auto& b = r1.v[i];
+        std::vector<int> k(1 + D);
+        k[0] = a.cc;
+        for (int e = 0; e < D; ++e) k[1 + e] = a.j[e] - idx[e];
+        if (a.coef != 0.0) add(plain, k, a.coef);
+        const double m = (b.coef - a.coef) / CV;
+        if (m != 0.0) {
+          std::vector<int> km = k;
+          for (int e = 0; e < D; ++e) km.push_back(b.cell[e] - idx[e] / K1);
+          add(mass, km, m);
+        }
+      }
+      for (const auto& pr : plain) {
+        int k = (int)h.off[pr.first[0]];
+        for (int e = 0; e < D; ++e) k += pr.first[1 + e] * comp_stride<D>(N, pr.first[0], e);
+        pe.push_back(make_int2(pr.first[0], k));
+        pcf.push_back(pr.second);
+      }
+      for (const auto& pr : mass) {
+        int k = (int)h.off[pr.first[0]], cell = 0, cs = 1;
+        for (int e = 0; e < D; ++e) {
+          k += pr.first[1 + e] * comp_stride<D>(N, pr.first[0], e);
+          cell += pr.first[1 + D + e] * cs;
+          cs *= n;
+        }
+        me.push_back(make_int4(pr.first[0], k, cell, 0));
+        mcf.push_back(pr.second);
+      }
+      ptr.push_back((int)pe.size());
+      mptr.push_back((int)me.size());
+    }
+  }
+  auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+  size_t o = 0;
+  out.cls = o;
+  o = al(o + cls.size() * sizeof(int));
+  out.ptr = o;
+  o = al(o + ptr.size() * sizeof(int));
+  out.mptr = o;
+  o = al(o + mptr.size() * sizeof(int));
+  out.pe = o;
+  o = al(o + pe.size() * sizeof(int2));
+  out.me = o;
+  o = al(o + me.size() * sizeof(int4));
+  out.pcf64 = o;
+  o = al(o + pcf.size() * sizeof(double));
+  out.mcf64 = o;
+  o = al(o + mcf.size() * sizeof(double));
+  out.pcf32 = o;
+  o = al(o + pcf.size() * sizeof(float));
+  out.mcf32 = o;
+  o = al(o + mcf.size() * sizeof(float));
+  out.bytes.assign(o + 16, 0);
+  out.classes = (int)ptr.size() - 1;
+  unsigned char* B = out.bytes.data();
+  std::memcpy(B + out.cls, cls.data(), cls.size() * sizeof(int));
+  std::memcpy(B + out.ptr, ptr.data(), ptr.size() * sizeof(int));
+  std::memcpy(B + out.mptr, mptr.data(), mptr.size() * sizeof(int));
+  if (!pe.empty()) std::memcpy(B + out.pe, pe.data(), pe.size() * sizeof(int2));
+  if (!me.empty()) std::memcpy(B + out.me, me.data(), me.size() * sizeof(int4));
+  if (!pcf.empty()) std::memcpy(B + out.pcf64, pcf.data(), pcf.size() * sizeof(double));
+  if (!mcf.empty()) std::memcpy(B + out.mcf64, mcf.data(), mcf.size() * sizeof(double));
+  for (size_t i = 0; i < pcf.size(); ++i) reinterpret_cast<float*>(B + out.pcf32)[i] = (float)pcf[i];
+  for (size_t i = 0; i < mcf.size(); ++i) reinterpret_cast<float*>(B + out.mcf32)[i] = (float)mcf[i];
+}
+
+template <typename T> RowPlans<T> plans(const HostLevel& h);
+template <> RowPlans<double> plans<double>(const HostLevel& h) {
+  return RowPlans<double>{h.rp.cls, h.rp.ptr, h.rp.mptr, h.rp.pe, h.rp.pcf64, h.rp.me, h.rp.mcf64};
+}
+template <> RowPlans<float> plans<float>(const HostLevel& h) {
+  return RowPlans<float>{h.rp.cls, h.rp.ptr, h.rp.mptr, h.rp.pe, h.rp.pcf32, h.rp.me, h.rp.mcf32};
+}
+
 void apply(const HostLevel& h, int f32, const void* x, void* y, int nrhs, cudaStream_t s) {
   const dim3 grid(blocks(h.ndof, 256), nrhs);
   if (f32)
-    k_apply<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (float*)y, h.ndof);
+    k_apply<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), plans<float>(h), (const float*)x, (float*)y, h.ndof);
   else
-    k_apply<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x, (double*)y, h.ndof);
+    k_apply<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), plans<double>(h), (const double*)x, (double*)y,
+                                               h.ndof);
 }
 
 void residual(const HostLevel& h, int f32, const void* x, const void* b, void* r, int zero_c, int nrhs,
               cudaStream_t s) {
   const dim3 grid(blocks(h.ndof, 256), nrhs);
   if (f32)
-    k_residual<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), tab<float>(), (const float*)x, (const float*)b,
+    k_residual<D, K, float><<<grid, 256, 0, s>>>(mk<float>(h), plans<float>(h), (const float*)x, (const float*)b,
                                                  (float*)r, zero_c, h.ndof, pstride(h, -1));
   else
-    k_residual<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), tab<double>(), (const double*)x,
+    k_residual<D, K, double><<<grid, 256, 0, s>>>(mk<double>(h), plans<double>(h), (const double*)x,
                                                   (const double*)b, (double*)r, zero_c, h.ndof, pstride(h, -1));
 }
 
@@ -228,7 +389,7 @@ template <typename T, typename TS>
 void additive_pass_t(const HostLevel& h, int colour, const void* S, const void* x, const void* b, void* acc,
                      double omega, int* err, int nrhs, cudaStream_t s) {
   if (h.count[colour] == 0) return;
-  const int g4 = (h.rhs_prob > 0 && h.rhs_prob % 4 != 0) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
+  const int g4 = (h.rhs_group < 4 || (h.rhs_prob > 0 && h.rhs_prob % 4 != 0)) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
   const size_t off = (size_t)4 * g4 * h.ndof;
   if (g4 > 0) additive_pass_nr<T, TS, 4>(h, colour, S, x, b, acc, omega, err, g4, s);
   if (rest > 0)
@@ -287,7 +448,7 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
                    cudaStream_t s) {
   if (h.count[colour] == 0) return;
   // groups of four right-hand sides must not straddle two problems
-  const int g4 = (h.rhs_prob > 0 && h.rhs_prob % 4 != 0) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
+  const int g4 = (h.rhs_group < 4 || (h.rhs_prob > 0 && h.rhs_prob % 4 != 0)) ? 0 : nrhs / 4, rest = nrhs - 4 * g4;
   const size_t off = (size_t)4 * g4 * h.ndof;
   if (h.pass_cta == 2) {
     if (g4 > 0) colour_pass_ctap_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
@@ -358,6 +519,98 @@ int build_template(const HostLevel& h, int sprec, void* tabs, cudaStream_t s, st
   return build_template_t<float, __nv_bfloat16>(h, tabs, s, why);
 }
 
+// Accumulates coef * x[column] on the host (the stencil visit, reference of
+// the row-plan check); cell coefficients from cw.
+struct HostDot {
+  const Lvl<D, K, double>& L;
+  const double* x;
+  const double* cw;
+  double acc = 0.0, mag = 0.0;
+  HostDot(const Lvl<D, K, double>& l, const double* xx, const double* c) : L(l), x(xx), cw(c) {}
+  void operator()(int comp, const int (&j)[D], double coef) {
+    const double t = coef * x[flat_index(L, comp, j)];
+    acc += t;
+    mag += std::fabs(t);
+  }
+  double cell_c(const int (&cell)[D]) const { return cw[cell_linear(L, cell)]; }
+};
+
+// Every free row of an n^D level evaluated from its row plan (as the kernels
+// do: column B_cc + k, mass entries times c of the home cell plus the offset)
+// against the stencil visit, on random x and c; 0 if all agree to 1e-13 of
+// the row's sum of |terms|.
+int check_row_plans(const HostLevel& h, std::string& why) {
+  constexpr int K1 = K + 1, KEYS = row_keys<D, K>();
+  RowPlanBlob blob;
+  row_plans(h, blob);
+  const unsigned char* B = blob.bytes.data();
+  const int* cls = reinterpret_cast<const int*>(B + blob.cls);
+  const int* ptr = reinterpret_cast<const int*>(B + blob.ptr);
+  const int* mptr = reinterpret_cast<const int*>(B + blob.mptr);
+  const int2* pe = reinterpret_cast<const int2*>(B + blob.pe);
+  const int4* me = reinterpret_cast<const int4*>(B + blob.me);
+  const double* pcf = reinterpret_cast<const double*>(B + blob.pcf64);
+  const double* mcf = reinterpret_cast<const double*>(B + blob.mcf64);
+  int64_t ncell = 1;
+  for (int e = 0; e < D; ++e) ncell *= h.n;
+  uint64_t rng = 0x9E3779B97F4A7C15ull;
+  auto urand = [&]() {
+    rng ^= rng << 13;
+    rng ^= rng >> 7;
+    rng ^= rng << 17;
+    return (double)(rng >> 11) * (1.0 / 9007199254740992.0);
+  };
+  std::vector<double> x((size_t)h.ndof), cw((size_t)ncell);
+  for (auto& v : x) v = 2.0 * urand() - 1.0;
+  for (auto& v : cw) v = std::exp(12.0 * urand() - 6.0);
+  Lvl<D, K, double> L = mk<double>(h);
+  L.c = cw.data();
+  for (int64_t g = 0; g < h.ndof; ++g) {
+    int idx[D];
+    const int comp = decode(L, g, idx);
+    if (is_constrained(L, comp, idx)) continue;
+    HostDot ref(L, x.data(), cw.data());
+    visit_row(L, tab<double>(), comp, idx, ref);
+    const int q = cls[(size_t)comp * KEYS + row_key<D, K>(h.n, comp, idx)];
+    if (q < 0) {
+      why = "row " + std::to_string(g) + " has no row plan";
+      return 1;
+    }
+    int base[D + 1];
+    for (int cc = 0; cc <= D; ++cc) {
+      base[cc] = 0;
+      for (int e = 0; e < D; ++e) base[cc] += idx[e] * comp_stride<D>(h.N, cc, e);
+    }
+    int cell = 0, cs = 1;
+    for (int e = 0; e < D; ++e) {
+      cell += (idx[e] / K1) * cs;
+      cs *= h.n;
+    }
+    double acc = 0.0;
+    for (int i = ptr[q]; i < ptr[q + 1]; ++i) {
+      const int col = base[pe[i].x] + pe[i].y;
+      if (col < 0 || col >= h.ndof) {
+        why = "row " + std::to_string(g) + ": plain entry outside the level vector";
+        return 1;
+      }
+      acc += pcf[i] * x[(size_t)col];
+    }
+    for (int i = mptr[q]; i < mptr[q + 1]; ++i) {
+      const int col = base[me[i].x] + me[i].y, c = cell + me[i].z;
+      if (col < 0 || col >= h.ndof || c < 0 || c >= ncell) {
+        why = "row " + std::to_string(g) + ": mass entry outside the level";
+        return 1;
+      }
+      acc += mcf[i] * cw[(size_t)c] * x[(size_t)col];
+    }
+    if (std::fabs(acc - ref.acc) > 1e-13 * ref.mag + 1e-300) {
+      why = "row " + std::to_string(g) + ": row plan " + std::to_string(acc) + " vs stencil " + std::to_string(ref.acc);
+      return 1;
+    }
+  }
+  return 0;
+}
+
 // Host check of the colour-pass tables of an n^D level (no GPU needed).
 template <typename T, typename TS>
 int plan_selftest_t(int n, double mu, std::string& why) {
@@ -378,7 +631,9 @@ int plan_selftest_t(int n, double mu, std::string& why) {
     const int r = check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
     if (r != 0) return r;
   }
-  return check_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+  const int r = check_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+  if (r != 0) return r;
+  return check_row_plans(h, why);
 }
 
 int plan_selftest(int sprec, int n, double mu, std::string* why) {
@@ -526,7 +781,8 @@ void coarse_assemble(const HostLevel& h, const int64_t* free_list, const int* g2
 int64_t residual_norm(const HostLevel& h, const double* x, const double* b, double* r, double* partial,
                       cudaStream_t s) {
   const int64_t nb = residual_norm_blocks(h.ndof);
-  k_residual_norm<D, K, double><<<(unsigned)nb, RN_THREADS, 0, s>>>(mk<double>(h), tab<double>(), x, b, r, partial);
+  k_residual_norm_rp<D, K, double><<<(unsigned)nb, RN_THREADS, 0, s>>>(mk<double>(h), plans<double>(h), x, b, r,
+                                                                       partial);
   return nb;
 }
 
@@ -576,6 +832,7 @@ DKOps make_ops() {
   o.bpatch_lists = bpatch_lists;
   o.bpatch_setup = bpatch_setup;
   o.bpatch_pass = bpatch_pass;
+  o.row_plans = row_plans;
   o.warp_pass = WARP_PASS ? 1 : 0;
   o.bnv_max = bpatch_threads<K>();
   return o;

@@ -39,6 +39,27 @@ int per_device_int(std::atomic<int> (&slot)[64], F&& f) {
 
 enum Prec { P64 = 0, P32 = 1, P32B = 2 };   // matches mg_precision
 
+// Operator row plans of one level on the device (rowplan.cuh): class ids per
+// row key, the plain and mass entries of each class, coefficients in FP64 and
+// FP32.  One allocation, laid out by RowPlanBlob.
+struct RowPlanDev {
+  const int* cls = nullptr;
+  const int* ptr = nullptr;
+  const int* mptr = nullptr;
+  const int2* pe = nullptr;
+  const int4* me = nullptr;
+  const double* pcf64 = nullptr;
+  const double* mcf64 = nullptr;
+  const float* pcf32 = nullptr;
+  const float* mcf32 = nullptr;
+};
+// The same built on the host: the bytes and the offset of each section.
+struct RowPlanBlob {
+  std::vector<unsigned char> bytes;
+  size_t cls = 0, ptr = 0, mptr = 0, pe = 0, me = 0, pcf64 = 0, mcf64 = 0, pcf32 = 0, mcf32 = 0;
+  int classes = 0;
+};
+
 // Host view of one level.  Device pointers unless noted.
 struct HostLevel {
   int d, k;
@@ -56,12 +77,15 @@ struct HostLevel {
                          // expiry a kernel sets the error word to 2 and returns
   int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch,
                          // 2 persistent blocks, one patch at a time
+  int rhs_group;         // right-hand sides sharing each S_v load in the colour passes: 4 (groups
+                         // of four where the count allows) or 1 (every right-hand side on its own)
   // problems of one shape stored one after another (grouped batches): rhs_prob
   // vectors per problem (0: a single problem), coefficients c_prob cells
   // apart, the inverses of colour col s_prob[col] bytes apart
   int rhs_prob;
   int64_t c_prob;
   int64_t s_prob[27];
+  RowPlanDev rp;         // operator row plans (apply, residual, residual norm)
   void* S[27];           // patch inverses per colour (BF16: followed by FP32 row scales)
   int64_t count[27];     // patches per colour
   // patches of the boundary vertices (option): per colour their number, dof
@@ -118,6 +142,8 @@ struct DKOps {
   void (*bpatch_setup)(const HostLevel&, int colour, int f64, void* S, int* fail, cudaStream_t);
   // x|_v += S_v (b - A x)|_v over the boundary patches of one colour (f32: FP32 vectors)
   void (*bpatch_pass)(const HostLevel&, int colour, int f32, void* x, const void* b, int nrhs, cudaStream_t);
+  // operator row plans of a level, built on the host
+  void (*row_plans)(const HostLevel&, RowPlanBlob&);
   // bordered dense matrix of the coarsest level
   void (*coarse_assemble)(const HostLevel&, const int64_t* free_list, const int* g2l, int nf, double* M,
                           double* E, cudaStream_t);

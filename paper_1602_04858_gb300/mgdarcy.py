@@ -23,14 +23,14 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_level_pass_kernel", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
+    "mg_level_pass_kernel", "mg_level_rhs_group", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
     "mg_setup_batch", "mg_destroy_batch", "mg_batch_layout", "mg_vcycle_batch", "mg_solve_batch",
-    "mg_batch_kernel_launches", "mg_load_vector",
+    "mg_batch_kernel_launches", "mg_batch_level_choice", "mg_load_vector",
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
     "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
-    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_time_passes", "mg_boundary_patch_info",
+    "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_measure_sync_cost", "mg_time_passes", "mg_boundary_patch_info",
 ]
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_coarse_solve.argtypes = [vp, vp, vp]
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_level_pass_kernel.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.mg_level_rhs_group.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
     lib.mg_setup_batch.argtypes = [ctypes.POINTER(mg_problem), i, i, vp, ctypes.POINTER(vp)]
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_vcycle_batch.argtypes = [vp, vp, vp]
     lib.mg_solve_batch.argtypes = [vp, vp, vp, i, d, i, i, ctypes.POINTER(mg_stats)]
     lib.mg_batch_kernel_launches.argtypes = [vp]
+    lib.mg_batch_level_choice.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.mg_batch_kernel_launches.restype = i64
     lib.mg_load_vector.argtypes = [vp, i, vp, vp, vp]
     f = ctypes.c_float
@@ -121,6 +123,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_time_passes.argtypes = [vp, i, i, ctypes.POINTER(d)]
     lib.mg_boundary_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_measure_fma_peak.argtypes = [i, ctypes.POINTER(d), vp]
+    lib.mg_measure_sync_cost.argtypes = [i, i, ctypes.POINTER(d), vp]
     lib.mg_kernel_launches.argtypes = [vp]
     lib.mg_kernel_launches.restype = i64
     lib.mg_status_string.argtypes = [i]
@@ -181,6 +184,15 @@ def measure_fma_peak(kind, stream=None):
     k = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
     out = ctypes.c_double()
     _check(load().mg_measure_fma_peak(k, ctypes.byref(out), ctypes.c_void_p(_stream_ptr(stream))))
+    return out.value
+
+
+def measure_sync_cost(kind, blocks, stream=None):
+    """mg_measure_sync_cost: microseconds per grid-wide ordering point on `blocks`
+    blocks; kind "grid_barrier" (one cooperative launch) or "dependent_launch"."""
+    k = {"grid_barrier": 0, "dependent_launch": 1}[kind]
+    out = ctypes.c_double()
+    _check(load().mg_measure_sync_cost(k, int(blocks), ctypes.byref(out), ctypes.c_void_p(_stream_ptr(stream))))
     return out.value
 
 
@@ -313,6 +325,12 @@ class Multigrid:
         _check(load().mg_level_pass_kernel(self.h, level, ctypes.byref(k)))
         return k.value
 
+    def rhs_group(self, level):
+        """Right-hand sides sharing each patch-inverse load on a level (mg_level_rhs_group): 4 or 1."""
+        g = ctypes.c_int()
+        _check(load().mg_level_rhs_group(self.h, level, ctypes.byref(g)))
+        return g.value
+
     def residual_norm(self, x, b, r=None, level=-1):
         """||b - A x||_2 (FP64) of device tensors; also stores r = b - A x if given."""
         out = ctypes.c_double()
@@ -372,6 +390,12 @@ class Batch:
 
     def total(self):
         return self.layout(0)[2]
+
+    def level_choice(self, p, level):
+        """(kernel, right-hand-side grouping) of problem p's colour passes on a level (mg_batch_level_choice)."""
+        k, g = ctypes.c_int(), ctypes.c_int()
+        _check(load().mg_batch_level_choice(self.h, p, level, ctypes.byref(k), ctypes.byref(g)))
+        return k.value, g.value
 
     def vcycle(self, r, z):
         _check(load().mg_vcycle_batch(self.h, _ptr(r), _ptr(z)))

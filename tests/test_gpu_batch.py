@@ -38,7 +38,9 @@ def oracle_hierarchies():
     return _problems("fp64")[1]
 
 
-@pytest.mark.parametrize("kernel", [0, 5, 1, 2, 3], ids=["timed", "rule", "warp", "block", "persistent"])
+@pytest.mark.parametrize("kernel", [0, 5, 1, 2, 3, 6, 7, 8],
+                         ids=["timed", "rule", "warp", "block", "persistent", "warp_rhs1", "block_rhs1",
+                              "persistent_rhs1"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
 def test_batched_vcycle_matches_oracle(precision, tol, kernel, oracle_hierarchies):
     probs, _ = _problems(precision, kernel)
@@ -158,3 +160,21 @@ def test_persistent_blocks_in_a_large_group():
     Bp.vcycle(r, zp)
     torch.cuda.synchronize()
     assert (torch.linalg.norm(zp - zw) / torch.linalg.norm(zw)).item() < 1e-11
+
+
+def test_timed_choice_covers_rhs_grouping():
+    """With four right-hand sides the timed choice picks, per level, a kernel
+    and a grouping (four sharing each inverse load, or one each); forced modes
+    report what they force."""
+    probs, _ = _problems("fp32", 0)
+    B = mgdarcy.Batch(probs, nrhs=NRHS)
+    for p, (n0, L, *_rest) in enumerate(SPECS):
+        for j in range(1, L):
+            k, g = B.level_choice(p, j)
+            assert k in (1, 2, 3) and g in (1, 4)
+    probs, _ = _problems("fp32", 7)
+    B = mgdarcy.Batch(probs, nrhs=NRHS)
+    assert all(B.level_choice(p, j) == (2, 1) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))
+    probs, _ = _problems("fp32", 2)
+    B = mgdarcy.Batch(probs, nrhs=NRHS)
+    assert all(B.level_choice(p, j) == (2, 4) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))

@@ -16,10 +16,16 @@ mg_setup does and checks on the host that
   column of each row;
 * the same for the tables of the block-per-patch pass: its four-thread row
   plans reproduce the row visitor, and its per-entry gather descriptors
-  address every window column, patch row and cell exactly once.
+  address every window column, patch row and cell exactly once;
+* the operator row plans (one per class of rows, used by the apply and the
+  residual kernels) evaluated for every free row of the level, as the kernels
+  evaluate them, agree with the row visitor to 1e-13 of the row's sum of
+  |terms| on random x and cell coefficients spanning e^-6 .. e^6, and address
+  only entries and cells of the level.
 
 Levels with n = 2 (one patch touching every side), n = 3 (only boundary
-types) and n >= 4 (all types) are covered for every supported (d, k), every
+types) and n >= 4 (all types) are covered for every supported (d, k) (RT_2:
+block-pass tables only; it has no warp pass), every
 storage precision of the inverses and mu = 0 (Darcy) and mu > 0 (Brinkman).
 """
 import pytest
@@ -34,7 +40,7 @@ def lib():
     return mgdarcy.load()
 
 
-@pytest.mark.parametrize("dim,degree", [(2, 0), (2, 1), (3, 0)])
+@pytest.mark.parametrize("dim,degree", [(2, 0), (2, 1), (2, 2), (3, 0)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("n", [2, 3, 4, 7, 16])
 @pytest.mark.parametrize("mu", [0.0, 0.01, 1.0])
