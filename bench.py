@@ -367,12 +367,22 @@ def batched_figures(args, steps, warmup, solve=True):
         x = torch.zeros_like(r)
         stats, status = B.solve(torch.as_tensor(b, device="cuda"), x, tol=1e-8, maxit=400, restart=20, check=False)
     its = [s_.iterations for s_ in stats] or [0]
+    # colour-pass choice per level of the first problem of each size: (kernel, right-hand sides per S_v load)
+    names = {1: "warp", 2: "block", 3: "persistent blocks"}
+    choice, seen = {}, set()
+    for p_, pr in enumerate(probs):
+        n = pr["c"].shape[0]
+        if n in seen:
+            continue
+        seen.add(n)
+        choice[f"{n}^2"] = {str(j): "%s x%d" % ((lambda kg: (names[kg[0]], kg[1]))(B.level_choice(p_, j)))
+                            for j in range(1, pr["n_levels"])}
     desc = (f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of "
             + ", ".join(f"{n}^2" for n in sizes) + " cells), RT_1, mu=0.01, lognormal c with sigma in [1,3], "
             "4 right-hand sides each, one CUDA graph per batched V-cycle, FP32 smoother")
     return {"workload": desc, "dofs_times_rhs": total, "vcycle_ms": ms / steps,
             "value": total * steps / (ms / 1e3), "unit": "DoF x rhs x V-cycles/s", "gpu_launches_per_vcycle":
-                int(launches // max(1, steps)), "setup_s": setup_s, "clocks": clocks,
+                int(launches // max(1, steps)), "setup_s": setup_s, "clocks": clocks, "pass_choice": choice,
             "time_to_1e-8": {"ms": stats[0].solve_ms if stats else None, "converged": bool(status == 0),
                              "systems": len(stats), "iterations_max": int(max(its)),
                              "iterations_mean": float(np.mean(its)), "restart": 20} if solve else None}
@@ -385,7 +395,7 @@ def bench_batched(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["vcycle_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f["workload"], "dofs_times_rhs": f["dofs_times_rhs"], "l2": "inputs larger than L2",
-                       "pass_kernel": args.pass_kernel},
+                       "pass_kernel": args.pass_kernel, "pass_choice": f["pass_choice"]},
             "gpu_launches": f["gpu_launches_per_vcycle"] * args.steps, "clocks": f["clocks"], "setup_s": f["setup_s"],
             "time_to_1e-8": f["time_to_1e-8"]}
     print(json.dumps(line), flush=True)

@@ -1530,6 +1530,18 @@ mg_status build_group(mg_batch* B, const std::vector<int>& mem, mg_handle** out)
     gh->main.B[j] = gh->lv[j].B;
     gh->main.R[j] = gh->lv[j].R;
   }
+  // a group runs the G problems of every pass in one launch: the timed choice
+  // is taken again in that shape (a single problem's timing favours more,
+  // smaller blocks), and the members report the group's choice
+  const int mode = h0->prob.pass_kernel;
+  if (mode == 0 || mode == 4) {
+    if ((st = tune_passes(gh, mode, gh->nrhs)) != MG_OK) return fail_out(st);
+    for (int i = 0; i < G; ++i)
+      for (int j = 1; j <= gh->J; ++j) {
+        B->sub[mem[i]]->lv[j].pass_cta = gh->lv[j].pass_cta;
+        B->sub[mem[i]]->lv[j].rhs_group = gh->lv[j].rhs_group;
+      }
+  }
   *out = gh;
   return MG_OK;
 }
