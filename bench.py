@@ -375,8 +375,10 @@ def batched_figures(args, steps, warmup, solve=True):
         if n in seen:
             continue
         seen.add(n)
-        choice[f"{n}^2"] = {str(j): "%s x%d" % ((lambda kg: (names[kg[0]], kg[1]))(B.level_choice(p_, j)))
-                            for j in range(1, pr["n_levels"])}
+        choice[f"{n}^2"] = {}
+        for j in range(1, pr["n_levels"]):
+            k, g, t = B.level_choice(p_, j)
+            choice[f"{n}^2"][str(j)] = f"{names[k]}, {g} rhs per inverse load" + (f", {t} threads per row" if k == 2 else "")
     desc = (f"batched: {len(probs)} 2-D problems ({args.batch_per_size} each of "
             + ", ".join(f"{n}^2" for n in sizes) + " cells), RT_1, mu=0.01, lognormal c with sigma in [1,3], "
             "4 right-hand sides each, one CUDA graph per batched V-cycle, FP32 smoother")
@@ -460,7 +462,8 @@ def main():
     G = make("fp32")
     setup_s = time.perf_counter() - t_setup
     names = {1: "warp", 2: "block", 3: "persistent blocks"}
-    pass_kernels = {j: names[G.pass_kernel(j)] for j in range(1, w["n_levels"])}
+    pass_kernels = {j: names[G.pass_kernel(j)] + (f" ({G.row_threads(j)} threads per row)" if G.pass_kernel(j) == 2
+                                                   else "") for j in range(1, w["n_levels"])}
     nu, npr = G.sizes()
     N = nu + npr
     # per level j >= 1: (dofs, patches, n_v, nonzeros of a patch's rows) for the V-cycle model

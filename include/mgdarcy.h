@@ -100,7 +100,10 @@ typedef struct {
                            right-hand sides share the inverses, else warp);
                            6, 7, 8: as 1, 2, 3 with every right-hand side on
                            its own (no sharing of the inverse loads; the timed
-                           choice tries this grouping too, mg_level_rhs_group).
+                           choice tries this grouping too, mg_level_rhs_group);
+                           9, 10: block kernel with 2 or 8 threads per patch
+                           row for single right-hand sides (4 otherwise; the
+                           timed choice tries all three, mg_level_row_threads).
                            Degree 2 (patches of 96 dofs) has no warp kernel:
                            1 runs as 2, the rule takes 2, the timed choice
                            picks between 2 and 3.                              */
@@ -274,9 +277,10 @@ void mg_destroy_batch(mg_batch* b);
 mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offset, int64_t* total);
 
 /* Colour-pass choice of problem p on `level` (1 <= level <= J): the kernel as
- * in mg_level_pass_kernel and the right-hand-side grouping as in
- * mg_level_rhs_group (either output may be null).  Host only. */
-mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group);
+ * in mg_level_pass_kernel, the right-hand-side grouping as in
+ * mg_level_rhs_group and the threads per patch row as in mg_level_row_threads
+ * (any output may be null).  Host only. */
+mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group, int* row_threads);
 
 /* z = B_J r for every problem and right-hand side (Sec. 3.2): one CUDA graph
  * whose branches are the problems' V-cycles, the right-hand sides of a problem
@@ -426,6 +430,12 @@ mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel);
  * 4) tries both with every kernel and keeps the fastest pair; the other modes
  * keep 4.  Host only. */
 mg_status mg_level_rhs_group(const mg_handle* h, int level, int* group);
+
+/* Threads per patch row of the block-per-patch colour pass of `level` for
+ * single right-hand sides: 4, 2 (more blocks resident at once) or 8 (a
+ * shorter chain of work per patch); the timed choice (mg_problem.pass_kernel
+ * 0 or 4) tries all three, the other modes keep 4.  Host only. */
+mg_status mg_level_row_threads(const mg_handle* h, int level, int* threads);
 
 /* Number of kernels the library launched on this handle so far. */
 int64_t mg_kernel_launches(const mg_handle* h);

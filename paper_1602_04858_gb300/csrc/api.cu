@@ -160,6 +160,7 @@ void level_geometry(HostLevel& L, int d, int k, int n, double mu) {
   std::memset(&L, 0, sizeof(L));
   L.wait_ns = DEFAULT_WAIT_NS;
   L.rhs_group = 4;
+  L.cta_tpr = 4;
   L.d = d;
   L.k = k;
   L.n = n;
@@ -330,6 +331,7 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   for (int j = 1; j <= h->J; ++j) {
     HostLevel& L = h->lv[j];
     const int first = h->ops->warp_pass ? 0 : 1;   // RT_2: block kernels only
+    L.cta_tpr = 4;
     if (mode != 4 && mode != 0) {
       if (mode == 5) {
         int nsm = 0;
@@ -340,9 +342,12 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
         L.pass_cta = (nrhs >= 4 || mx * nv * nv <= 10000 * (int64_t)(nsm > 0 ? nsm : 1)) ? 1 : 0;
       } else if (mode <= 3) {
         L.pass_cta = mode - 1;
-      } else {   // 6, 7, 8: forced kernel, every right-hand side on its own
+      } else if (mode <= 8) {   // 6, 7, 8: forced kernel, every right-hand side on its own
         L.pass_cta = mode - 6;
         L.rhs_group = 1;
+      } else {   // 9, 10: block kernel with 2 or 8 threads per patch row
+        L.pass_cta = 1;
+        L.cta_tpr = mode == 9 ? 2 : 8;
       }
       L.pass_cta = std::max(L.pass_cta, first);
       continue;
@@ -353,32 +358,43 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       auto it = cache.find(key);
       if (it != cache.end()) {
         L.pass_cta = it->second % 3;
-        L.rhs_group = it->second >= 3 ? 1 : 4;
+        L.rhs_group = (it->second / 3) % 2 ? 1 : 4;
+        L.cta_tpr = (it->second / 6) == 1 ? 2 : ((it->second / 6) == 2 ? 8 : 4);
         continue;
       }
     }
     // kernels x right-hand-side grouping (with four or more right-hand sides:
-    // four sharing each S_v load, or each on its own with four times the blocks)
+    // four sharing each S_v load, or each on its own with four times the
+    // blocks) x threads per patch row of the block kernel for single
+    // right-hand sides (4, 2: more blocks at once, 8: a shorter chain per patch)
     const int ngroup = nrhs >= 4 ? 2 : 1;
     float best = 0.f;
-    int best_var = first, best_grp = 4;
+    bool have = false;
+    int best_var = first, best_grp = 4, best_tpr = 4;
     for (int gi = 0; gi < ngroup; ++gi) {
       L.rhs_group = gi == 0 ? 4 : 1;
-      for (int var = first; var < 3; ++var) {
-        L.pass_cta = var;
-        float ms = 0.f;
-        TRY(time_smoothing(h, j, nrhs, 2, 3, &ms, nullptr));
-        if ((gi == 0 && var == first) || ms < best) {
-          best = ms;
-          best_var = var;
-          best_grp = L.rhs_group;
+      const bool single = nrhs < 4 || L.rhs_group == 1;
+      for (int var = first; var < 3; ++var)
+        for (int tpr : {4, 2, 8}) {
+          if (tpr != 4 && !(var == 1 && single)) continue;
+          L.pass_cta = var;
+          L.cta_tpr = tpr;
+          float ms = 0.f;
+          TRY(time_smoothing(h, j, nrhs, 2, 3, &ms, nullptr));
+          if (!have || ms < best) {
+            have = true;
+            best = ms;
+            best_var = var;
+            best_grp = L.rhs_group;
+            best_tpr = tpr;
+          }
         }
-      }
     }
     L.pass_cta = best_var;
     L.rhs_group = best_grp;
+    L.cta_tpr = best_tpr;
     std::lock_guard<std::mutex> g(mu);
-    cache[key] = best_var + 3 * (best_grp == 1 ? 1 : 0);
+    cache[key] = best_var + 3 * (best_grp == 1 ? 1 : 0) + 6 * (best_tpr == 2 ? 1 : (best_tpr == 8 ? 2 : 0));
   }
   h->launches = l0;
   CU(cudaGetLastError());
@@ -554,7 +570,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
   if (p->m_fine < 1) return fail(MG_ERR_INVALID_ARG, "m_fine must be >= 1");
   if (p->coarse_avg < 0 || p->coarse_avg > 1) return fail(MG_ERR_INVALID_ARG, "bad coarse_avg");
   if (p->dense_level < -1 || p->dense_level >= p->n_levels) return fail(MG_ERR_INVALID_ARG, "bad dense_level");
-  if (p->pass_kernel < 0 || p->pass_kernel > 8) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
+  if (p->pass_kernel < 0 || p->pass_kernel > 10) return fail(MG_ERR_INVALID_ARG, "bad pass_kernel");
   if (!(p->additive >= 0.0 && p->additive <= 1.0)) return fail(MG_ERR_INVALID_ARG, "additive must be in [0, 1]");
   if (p->escalate_window > 100000) return fail(MG_ERR_INVALID_ARG, "escalate_window too large");
   if (p->boundary_patches < 0 || p->boundary_patches > 1) return fail(MG_ERR_INVALID_ARG, "bad boundary_patches");
@@ -915,6 +931,12 @@ mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
 mg_status mg_level_rhs_group(const mg_handle* h, int level, int* group) {
   if (!h || !group || level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
   *group = h->lv[level].rhs_group;
+  return MG_OK;
+}
+
+mg_status mg_level_row_threads(const mg_handle* h, int level, int* threads) {
+  if (!h || !threads || level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  *threads = h->lv[level].cta_tpr;
   return MG_OK;
 }
 
@@ -1423,6 +1445,7 @@ bool same_shape(const mg_handle* a, const mg_handle* b) {
     return false;
   for (int j = 0; j <= a->J; ++j)
     if (a->lv[j].pass_cta != b->lv[j].pass_cta || a->lv[j].rhs_group != b->lv[j].rhs_group ||
+        a->lv[j].cta_tpr != b->lv[j].cta_tpr ||
         a->lv[j].sprec != b->lv[j].sprec)
       return false;
   return true;
@@ -1540,6 +1563,7 @@ mg_status build_group(mg_batch* B, const std::vector<int>& mem, mg_handle** out)
       for (int j = 1; j <= gh->J; ++j) {
         B->sub[mem[i]]->lv[j].pass_cta = gh->lv[j].pass_cta;
         B->sub[mem[i]]->lv[j].rhs_group = gh->lv[j].rhs_group;
+        B->sub[mem[i]]->lv[j].cta_tpr = gh->lv[j].cta_tpr;
       }
   }
   *out = gh;
@@ -1775,12 +1799,13 @@ mg_status mg_batch_layout(const mg_batch* b, int p, int64_t* ndof, int64_t* offs
 
 int64_t mg_batch_kernel_launches(const mg_batch* b) { return b ? b->launches : 0; }
 
-mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group) {
+mg_status mg_batch_level_choice(const mg_batch* b, int p, int level, int* kernel, int* rhs_group, int* row_threads) {
   if (!b || p < 0 || p >= (int)b->sub.size()) return fail(MG_ERR_INVALID_ARG, "bad problem index");
   const mg_handle* h = b->sub[p];
   if (level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
   if (kernel) *kernel = h->lv[level].pass_cta + 1;
   if (rhs_group) *rhs_group = h->lv[level].rhs_group;
+  if (row_threads) *row_threads = h->lv[level].cta_tpr;
   return MG_OK;
 }
 

@@ -326,20 +326,25 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
 // buffers per warp do not fit; its levels run the block kernels).
 constexpr bool WARP_PASS = K <= 1;
 
-// Byte offset of the block-per-patch tables inside a level's table blob.
-template <typename T, typename TS>
+// Byte offsets of the block-per-patch tables inside a level's table blob:
+// four threads per row, then two, then eight.
+constexpr size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+template <typename T, typename TS, int TPR = 4>
 constexpr size_t cta_tables_offset() {
-  return WARP_PASS ? (PassShape<D, K, T, TS, 1>::TAB_BYTES + 255) / 256 * 256 : 0;
+  constexpr size_t o4 = WARP_PASS ? al256(PassShape<D, K, T, TS, 1>::TAB_BYTES) : 0;
+  constexpr size_t o2 = o4 + al256(PassShapeC<D, K, T, TS, 1, 4>::TAB_BYTES);
+  constexpr size_t o8 = o2 + al256(PassShapeC<D, K, T, TS, 1, 2>::TAB_BYTES);
+  return TPR == 4 ? o4 : (TPR == 2 ? o2 : o8);
 }
 
 // One block per patch: grid = patches of the colour x right-hand-side groups.
-template <typename T, typename TS, int NR>
+template <typename T, typename TS, int NR, int TPR = 4>
 void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, const void* b, int* err, int groups,
                         cudaStream_t s) {
-  using C = PassShapeC<D, K, T, TS, NR>;
+  using C = PassShapeC<D, K, T, TS, NR, TPR>;
   static std::atomic<unsigned long long> attr{0};
   once_per_device(attr, [] {
-    cudaFuncSetAttribute(k_colour_pass_cta<D, K, T, TS, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_colour_pass_cta<D, K, T, TS, NR, false, TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          C::SMEM);
   });
   cudaLaunchConfig_t cfg = {};
@@ -352,8 +357,8 @@ void colour_pass_cta_nr(const HostLevel& h, int colour, const void* S, void* x, 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS>();
-  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, false>, mk<T>(h), colour_geom(D, h.n, colour),
+  const unsigned char* tabs = (const unsigned char*)h.R0 + cta_tables_offset<T, TS, TPR>();
+  cudaLaunchKernelEx(&cfg, k_colour_pass_cta<D, K, T, TS, NR, false, TPR>, mk<T>(h), colour_geom(D, h.n, colour),
                      h.count[colour], (const TS*)S, tabs, (T*)x, (const T*)b, h.s_evict_first, err, h.wait_ns, h.ndof,
                      pstride(h, colour), (T*)nullptr, T(0));
 }
@@ -457,7 +462,13 @@ void colour_pass_t(const HostLevel& h, int colour, const void* S, void* x, const
   }
   if (h.pass_cta) {
     if (g4 > 0) colour_pass_cta_nr<T, TS, 4>(h, colour, S, x, b, err, g4, s);
-    if (rest > 0) colour_pass_cta_nr<T, TS, 1>(h, colour, S, (T*)x + off, (const T*)b + off, err, rest, s);
+    if (rest > 0) {   // single right-hand sides: 4, 2 or 8 threads per patch row
+      T* xr = (T*)x + off;
+      const T* br = (const T*)b + off;
+      if (h.cta_tpr == 2) colour_pass_cta_nr<T, TS, 1, 2>(h, colour, S, xr, br, err, rest, s);
+      else if (h.cta_tpr == 8) colour_pass_cta_nr<T, TS, 1, 8>(h, colour, S, xr, br, err, rest, s);
+      else colour_pass_cta_nr<T, TS, 1, 4>(h, colour, S, xr, br, err, rest, s);
+    }
     return;
   }
   if constexpr (WARP_PASS) {
@@ -481,7 +492,7 @@ void colour_pass(const HostLevel& h, int colour, int prec, const void* S, void* 
 // pass (gather descriptors, block plans).
 template <typename T, typename TS>
 size_t tables_bytes() {
-  return cta_tables_offset<T, TS>() + (PassShapeC<D, K, T, TS, 1>::TAB_BYTES + 15) / 16 * 16;
+  return cta_tables_offset<T, TS, 8>() + (PassShapeC<D, K, T, TS, 1, 8>::TAB_BYTES + 15) / 16 * 16;
 }
 int64_t template_elems(int sprec) {
   size_t b;
@@ -493,16 +504,20 @@ int64_t template_elems(int sprec) {
 
 template <typename T, typename TS>
 int build_template_t(const HostLevel& h, void* tabs, cudaStream_t s, std::string* why) {
-  std::vector<unsigned char> blob, blob_c;
+  std::vector<unsigned char> blob, blob_4, blob_2, blob_8;
   std::string msg;
   bool ok = true;
   if constexpr (WARP_PASS) ok = build_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob, msg);
-  if (!ok || !build_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), blob_c, msg)) {
+  if (!ok || !build_cta_tables<D, K, T, TS, 4>(mk<T>(h), tab<T>(), blob_4, msg) ||
+      !build_cta_tables<D, K, T, TS, 2>(mk<T>(h), tab<T>(), blob_2, msg) ||
+      !build_cta_tables<D, K, T, TS, 8>(mk<T>(h), tab<T>(), blob_8, msg)) {
     if (why) *why = "colour-pass tables of the " + std::to_string(h.n) + "^" + std::to_string(D) + " level: " + msg;
     return 1;
   }
   blob.resize(tables_bytes<T, TS>(), 0);
-  std::memcpy(blob.data() + cta_tables_offset<T, TS>(), blob_c.data(), blob_c.size());
+  std::memcpy(blob.data() + cta_tables_offset<T, TS, 4>(), blob_4.data(), blob_4.size());
+  std::memcpy(blob.data() + cta_tables_offset<T, TS, 2>(), blob_2.data(), blob_2.size());
+  std::memcpy(blob.data() + cta_tables_offset<T, TS, 8>(), blob_8.data(), blob_8.size());
   if (cudaMemcpyAsync(tabs, blob.data(), blob.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     if (why) *why = "upload of the colour-pass tables failed";
@@ -631,7 +646,9 @@ int plan_selftest_t(int n, double mu, std::string& why) {
     const int r = check_pass_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
     if (r != 0) return r;
   }
-  const int r = check_cta_tables<D, K, T, TS>(mk<T>(h), tab<T>(), why);
+  int r = check_cta_tables<D, K, T, TS, 4>(mk<T>(h), tab<T>(), why);
+  if (r == 0) r = check_cta_tables<D, K, T, TS, 2>(mk<T>(h), tab<T>(), why);
+  if (r == 0) r = check_cta_tables<D, K, T, TS, 8>(mk<T>(h), tab<T>(), why);
   if (r != 0) return r;
   return check_row_plans(h, why);
 }

@@ -36,12 +36,15 @@ template <> struct PlanShapeC<2, 2> { static constexpr int ZW = 18, ZMW = 2; }; 
 
 constexpr int ELEM_INTS = 12;   // gather descriptor: three int4
 
-template <int D, int K, typename T, typename TS, int NR = 1>
+// TPR_: threads per residual row (4; 2 and 8 are the alternatives the timed
+// kernel choice tries for single right-hand sides: fewer threads fit more
+// blocks at once, more threads shorten the chain of one patch update).
+template <int D, int K, typename T, typename TS, int NR = 1, int TPR_ = 4>
 struct PassShapeC {
   using PS = PatchShape<D, K>;
   using W = PassShape<D, K, T, TS, 1>;   // window geometry and segment tables
   static constexpr int NV = PS::NV, WIN = W::WIN, NC = W::NC;
-  static constexpr int TPR = 4;                              // threads per residual row
+  static constexpr int TPR = TPR_;                           // threads per residual row
   static constexpr int NT = ((NV * TPR + 31) / 32) * 32;     // threads per block
   using SL = SLayout<NV, TS>;
   static constexpr int RG = SL::RG, NVP = SL::NVP;
@@ -50,8 +53,8 @@ struct PassShapeC {
   static constexpr int SPL = pow2_floor(NT / LPP);           // column parts per row group
   static constexpr int JCH = (NV + SPL - 1) / SPL;           // columns per thread
   static constexpr bool BF = std::is_same<TS, __nv_bfloat16>::value;
-  using PL = PlanShapeC<D, K>;
-  static constexpr int ZW = PL::ZW, ZMW = PL::ZMW;
+  using PL = PlanShapeC<D, K>;   // slots for four threads per row
+  static constexpr int ZW = (4 * PL::ZW + TPR - 1) / TPR, ZMW = (4 * PL::ZMW + TPR - 1) / TPR;
   static constexpr int NE = WIN + NV + NC;                   // gathered entries
   static constexpr int EPT = (NE + NT - 1) / NT;             // per thread
   // shared memory (bytes): S_v (+ BF16 row scales), then T data, then ints
@@ -82,6 +85,7 @@ struct PassShapeC {
   static_assert(SMEM <= 227 * 1024 && P_SMEM <= 227 * 1024, "shared memory of one block");
   static_assert(S_BYTES % 16 == 0 && SC_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(RG <= 32, "row group fits the shuffle");
+  static_assert(TPR == 2 || TPR == 4 || TPR == 8, "threads per row: 2, 4 or 8");
 };
 
 // --- host construction -------------------------------------------------------
@@ -117,10 +121,10 @@ void make_elements(const Lvl<D, K, T>& L, int* out) {
 }
 
 // Builds the tables of the block-per-patch pass of one level into blob.
-template <int D, int K, typename T, typename TS>
+template <int D, int K, typename T, typename TS, int TPR = 4>
 bool build_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<unsigned char>& blob,
                       std::string& why) {
-  using C = PassShapeC<D, K, T, TS, 1>;
+  using C = PassShapeC<D, K, T, TS, 1, TPR>;
   constexpr int NT = C::NT, ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>();
   blob.assign(C::TAB_BYTES, 0);
   make_elements<D, K, T, TS>(L, reinterpret_cast<int*>(blob.data() + C::TB_ELEM));
@@ -137,7 +141,7 @@ bool build_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<un
               std::to_string(bm) + " entries) does not fit the block plan";
         return false;
       }
-      // entry i of the row goes to thread 4 l + i % 4, slot i / 4
+      // entry i of the row goes to thread TPR l + i % TPR, slot i / TPR
       for (int i = 0; i < a; ++i) {
         const int th = C::TPR * l + i % C::TPR, s = i / C::TPR;
         unsigned char* e = blob.data() + C::TB_PLAIN + ((size_t)(t * ZW + s) * NT + th) * PB;
@@ -169,12 +173,12 @@ bool build_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<un
 // present type evaluated on a random window reproduces the row visitor, and
 // the gather descriptors address the window column, patch row or cell they
 // are meant to, with zero outside the domain.  0, or 1 with a reason.
-template <int D, int K, typename T, typename TS>
+template <int D, int K, typename T, typename TS, int TPR = 4>
 int check_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& why) {
-  using C = PassShapeC<D, K, T, TS, 1>;
+  using C = PassShapeC<D, K, T, TS, 1, TPR>;
   constexpr int NT = C::NT, ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>();
   std::vector<unsigned char> blob;
-  if (!build_cta_tables<D, K, T, TS>(L, tb, blob, why)) return 1;
+  if (!build_cta_tables<D, K, T, TS, TPR>(L, tb, blob, why)) return 1;
   uint64_t rng = 0x2545F4914F6CDD1Dull;
   auto urand = [&]() {
     rng ^= rng << 13;
@@ -202,7 +206,7 @@ int check_cta_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& wh
     if (!type_present<D>(t, L.n)) continue;
     int v[D];
     type_vertex<D>(t, L.n, v);
-    // plan: the four parts of each row against the row visitor
+    // plan: the TPR parts of each row against the row visitor
     std::vector<double> win(C::WIN), cw(C::NC);
     for (auto& w : win) w = 2.0 * urand() - 1.0;
     for (auto& c : cw) c = std::exp(6.0 * urand() - 3.0);
@@ -354,12 +358,12 @@ __device__ __forceinline__ void st_rhs(T* p, const T (&v)[NR]) {
 // ADD: additive variant (not the paper's smoother): x is only read, and
 // omega delta is added atomically to `sum` instead of updating x|_v, so that
 // the patches of every colour may run on the same x.
-template <int D, int K, typename T, typename TS, int NR, bool ADD = false>
-__global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
+template <int D, int K, typename T, typename TS, int NR, bool ADD = false, int TPR = 4>
+__global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR, TPR>::NT)
     k_colour_pass_cta(const Lvl<D, K, T> L0, const ColourGeom cg, int64_t count, const TS* __restrict__ S,
                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
                       int* __restrict__ err, uint64_t wait_ns, int64_t vs, const ProbStride ps, T* __restrict__ sum, T omega) {
-  using C = PassShapeC<D, K, T, TS, NR>;
+  using C = PassShapeC<D, K, T, TS, NR, TPR>;
   constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -491,10 +495,9 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
 #pragma unroll
   for (int rr = 0; rr < NR; ++rr) acc[rr] = NA == 2 ? acc2[0][rr] + acc2[NA - 1][rr] : acc2[0][rr];
 #pragma unroll
-  for (int rr = 0; rr < NR; ++rr) {
-    acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 1);
-    acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], 2);
-  }
+  for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+    for (int o = 1; o < TPR; o <<= 1) acc[rr] += __shfl_xor_sync(0xffffffffu, acc[rr], o);
   // the inverses (bounded wait; every thread reaches the block barrier)
   const bool timed_out = !mbar_wait_bounded(bar, 0u, wait_ns);
   if (__syncthreads_or(timed_out)) {

@@ -23,7 +23,7 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_level_pass_kernel", "mg_level_rhs_group", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
+    "mg_level_pass_kernel", "mg_level_rhs_group", "mg_level_row_threads", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
     "mg_setup_batch", "mg_destroy_batch", "mg_batch_layout", "mg_vcycle_batch", "mg_solve_batch",
     "mg_batch_kernel_launches", "mg_batch_level_choice", "mg_load_vector",
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_level_pass_kernel.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_level_rhs_group.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.mg_level_row_threads.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
     lib.mg_setup_batch.argtypes = [ctypes.POINTER(mg_problem), i, i, vp, ctypes.POINTER(vp)]
@@ -93,7 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_vcycle_batch.argtypes = [vp, vp, vp]
     lib.mg_solve_batch.argtypes = [vp, vp, vp, i, d, i, i, ctypes.POINTER(mg_stats)]
     lib.mg_batch_kernel_launches.argtypes = [vp]
-    lib.mg_batch_level_choice.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.mg_batch_level_choice.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     lib.mg_batch_kernel_launches.restype = i64
     lib.mg_load_vector.argtypes = [vp, i, vp, vp, vp]
     f = ctypes.c_float
@@ -325,6 +326,12 @@ class Multigrid:
         _check(load().mg_level_pass_kernel(self.h, level, ctypes.byref(k)))
         return k.value
 
+    def row_threads(self, level):
+        """Threads per patch row of the block kernel on a level (mg_level_row_threads): 4, 2 or 8."""
+        t = ctypes.c_int()
+        _check(load().mg_level_row_threads(self.h, level, ctypes.byref(t)))
+        return t.value
+
     def rhs_group(self, level):
         """Right-hand sides sharing each patch-inverse load on a level (mg_level_rhs_group): 4 or 1."""
         g = ctypes.c_int()
@@ -392,10 +399,11 @@ class Batch:
         return self.layout(0)[2]
 
     def level_choice(self, p, level):
-        """(kernel, right-hand-side grouping) of problem p's colour passes on a level (mg_batch_level_choice)."""
-        k, g = ctypes.c_int(), ctypes.c_int()
-        _check(load().mg_batch_level_choice(self.h, p, level, ctypes.byref(k), ctypes.byref(g)))
-        return k.value, g.value
+        """(kernel, right-hand-side grouping, threads per patch row) of problem p's
+        colour passes on a level (mg_batch_level_choice)."""
+        k, g, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().mg_batch_level_choice(self.h, p, level, ctypes.byref(k), ctypes.byref(g), ctypes.byref(t)))
+        return k.value, g.value, t.value
 
     def vcycle(self, r, z):
         _check(load().mg_vcycle_batch(self.h, _ptr(r), _ptr(z)))

@@ -64,7 +64,7 @@ def _setup(lib, **kw):
     (dict(c=None), 1),
     (dict(dense_level=3), 1),
     (dict(dense_level=-2), 1),
-    (dict(pass_kernel=9), 1),
+    (dict(pass_kernel=11), 1),
     (dict(pass_kernel=-1), 1),
     (dict(dim=3, n_coarse=2, n_levels=10, c=np.ones((2, 2, 2))), 1),   # 4.3e9 dofs: rejected before c is read
     (dict(additive=-0.1), 1),

@@ -170,11 +170,11 @@ def test_timed_choice_covers_rhs_grouping():
     B = mgdarcy.Batch(probs, nrhs=NRHS)
     for p, (n0, L, *_rest) in enumerate(SPECS):
         for j in range(1, L):
-            k, g = B.level_choice(p, j)
-            assert k in (1, 2, 3) and g in (1, 4)
+            k, g, t = B.level_choice(p, j)
+            assert k in (1, 2, 3) and g in (1, 4) and t in (2, 4, 8)
     probs, _ = _problems("fp32", 7)
     B = mgdarcy.Batch(probs, nrhs=NRHS)
-    assert all(B.level_choice(p, j) == (2, 1) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))
+    assert all(B.level_choice(p, j) == (2, 1, 4) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))
     probs, _ = _problems("fp32", 2)
     B = mgdarcy.Batch(probs, nrhs=NRHS)
-    assert all(B.level_choice(p, j) == (2, 4) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))
+    assert all(B.level_choice(p, j) == (2, 4, 4) for p, (n0, L, *_r) in enumerate(SPECS) for j in range(1, L))

@@ -56,9 +56,10 @@ _cache = {}
 
 
 # colour-pass kernels: 1 one warp per patch, 2 one thread block per patch,
-# 3 persistent thread blocks
-KERNELS = [1, 2, 3]
-KERNEL_IDS = ["warp", "block", "persistent"]
+# 3 persistent thread blocks, 9 / 10 the block kernel with 2 / 8 threads per
+# patch row
+KERNELS = [1, 2, 3, 9, 10]
+KERNEL_IDS = ["warp", "block", "persistent", "block_2threads", "block_8threads"]
 
 
 def build(case, precision="fp64", variable=True, m_fine=2, dense_level=-1, pass_kernel=0, additive=0.0):
@@ -194,7 +195,7 @@ def test_smoothing_step_fp32_each_kernel(case, kernel):
         assert err < tol, f"level {j}: {err}"
 
 
-@pytest.mark.parametrize("other", [2, 3], ids=["block", "persistent"])
+@pytest.mark.parametrize("other", [2, 3, 9, 10], ids=["block", "persistent", "block_2threads", "block_8threads"])
 @pytest.mark.parametrize("precision", ["fp32", "fp32_bf16inv"])
 @pytest.mark.parametrize("case", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
 def test_colour_pass_kernels_agree(case, precision, other):

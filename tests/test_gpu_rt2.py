@@ -125,8 +125,8 @@ def test_transfer_and_coarse_parity(case):
     assert rel_inf(host(x), mg.coarse_solve(H, b)) < 1e-11
 
 
-KERNELS = [2, 3]
-KERNEL_IDS = ["block", "persistent"]
+KERNELS = [2, 3, 9, 10]
+KERNEL_IDS = ["block", "persistent", "block_2threads", "block_8threads"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
