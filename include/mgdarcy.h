@@ -130,6 +130,13 @@ typedef struct {
                            interior vertices only, which already cover every
                            free dof.  Not with additive smoothing or batches
                            (MG_ERR_UNSUPPORTED).                               */
+  int nrhs;             /* right-hand sides of mg_vcycle: 0 or 1 one, up to 64
+                           (vectors of N_u + N_p entries one after another; the
+                           colour passes share each patch-inverse load among
+                           groups of four).  mg_solve takes one
+                           (MG_ERR_UNSUPPORTED otherwise; mg_solve_batch solves
+                           several).  mg_setup_batch takes its own nrhs
+                           argument and ignores this field.                    */
 } mg_problem;
 
 typedef struct {
@@ -168,7 +175,8 @@ mg_status mg_apply(mg_handle* h, int level, const double* x, double* y);
 
 /* z = B_J r: one V-cycle of Sec. 3.2 with zero initial guess, in the handle's
  * precision (FP64 in/out; FP32 modes convert at entry and exit).
- * r, z: host or device, length n_u + n_p, must not alias. */
+ * r, z: host or device, mg_problem.nrhs vectors of length n_u + n_p one after
+ * another, must not alias. */
 mg_status mg_vcycle(mg_handle* h, const double* r, double* z);
 
 /* Solves A_J x = b with b = (f, g) by right-preconditioned flexible GMRES in

@@ -483,22 +483,24 @@ mg_status vcycle_graph(mg_handle* h) {
 }
 
 // z = B_J r for FP64 device vectors (r, z may not alias).
+// z = B r for the handle's nrhs vectors (one after another, FP64 device).
 mg_status vcycle_dev(mg_handle* h, const double* r, double* z) {
   HostLevel& L = h->lv.back();
+  const int64_t n = L.ndof * h->nrhs;
   if (h->prec == P64) {
-    CU(cudaMemcpyAsync(L.B, r, L.ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(L.B, r, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   } else {
-    launch_d2f(r, (float*)L.B, L.ndof, h->stream);
+    launch_d2f(r, (float*)L.B, n, h->stream);
     ++h->launches;
   }
   TRY(vcycle_graph(h));
   if (h->prec == P64) {
-    CU(cudaMemcpyAsync(z, L.X, L.ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(z, L.X, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   } else {
-    launch_f2d((const float*)L.X, z, L.ndof, h->stream);
+    launch_f2d((const float*)L.X, z, n, h->stream);
     ++h->launches;
   }
-  h->ops->copy_constrained(L, r, z, 1, h->stream);
+  h->ops->copy_constrained(L, r, z, h->nrhs, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
   return MG_OK;
@@ -858,7 +860,7 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
     }
   }
   for (int t = 0; t < 4; ++t)
-    if ((st = h->alloc(&h->t64[t], h->lv[J].ndof)) != MG_OK) return cleanup(st);
+    if ((st = h->alloc(&h->t64[t], (size_t)h->lv[J].ndof * (t < 2 ? nrhs : 1))) != MG_OK) return cleanup(st);
   if ((st = h->alloc(&h->d_rnp, residual_norm_blocks(h->lv[J].ndof))) != MG_OK) return cleanup(st);
   if ((st = h->alloc(&h->d_rn, 1)) != MG_OK) return cleanup(st);
   int bad = 0;
@@ -873,7 +875,8 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
 extern "C" {
 
 mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
-  return setup_internal(p, cuda_stream, 1, 0.0, out);
+  if (p && (p->nrhs < 0 || p->nrhs > 64)) return fail(MG_ERR_INVALID_ARG, "nrhs must be in [0, 64]");
+  return setup_internal(p, cuda_stream, p && p->nrhs > 1 ? p->nrhs : 1, 0.0, out);
 }
 
 mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p) {
@@ -964,7 +967,7 @@ mg_status mg_apply(mg_handle* h, int level, const double* x, double* y) {
 mg_status mg_vcycle(mg_handle* h, const double* r, double* z) {
   if (!h || !r || !z) return fail(MG_ERR_INVALID_ARG, "null argument");
   if (r == z) return fail(MG_ERR_INVALID_ARG, "r and z must not alias");
-  const int64_t n = h->fine().ndof;
+  const int64_t n = h->fine().ndof * h->nrhs;
   const bool dr = is_device_ptr(r), dz = is_device_ptr(z);
   const double* rs = r;
   double* zs = z;
@@ -1152,6 +1155,7 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
                    int restart, mg_stats* stats) {
   if (!h || !f || !g || !x) return fail(MG_ERR_INVALID_ARG, "null argument");
   if (!(tol > 0.0) || maxit < 0) return fail(MG_ERR_INVALID_ARG, "bad tol or maxit");
+  if (h->nrhs != 1) return fail(MG_ERR_UNSUPPORTED, "mg_solve takes one right-hand side (mg_solve_batch takes several)");
   const HostLevel& L = h->fine();
   const int64_t n = L.ndof, nu = L.n_u, np = L.n_p;
   if (restart <= 0 || restart > maxit) restart = maxit > 0 ? maxit : 1;

@@ -39,7 +39,8 @@ class mg_problem(ctypes.Structure):
                 ("degree", ctypes.c_int), ("mu", ctypes.c_double), ("c", ctypes.c_void_p),
                 ("precision", ctypes.c_int), ("m_fine", ctypes.c_int), ("variable_cycle", ctypes.c_int),
                 ("coarse_avg", ctypes.c_int), ("dense_level", ctypes.c_int), ("pass_kernel", ctypes.c_int),
-                ("additive", ctypes.c_double), ("escalate_window", ctypes.c_int), ("boundary_patches", ctypes.c_int)]
+                ("additive", ctypes.c_double), ("escalate_window", ctypes.c_int), ("boundary_patches", ctypes.c_int),
+                ("nrhs", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -209,19 +210,20 @@ class Multigrid:
 
     def __init__(self, dim, n_coarse, n_levels, degree, mu, c, precision="fp64", m_fine=2,
                  variable_cycle=True, coarse_avg=0, dense_level=-1, pass_kernel=0, additive=0.0,
-                 escalate_window=0, boundary_patches=False, stream=None):
+                 escalate_window=0, boundary_patches=False, nrhs=1, stream=None):
         lib = load()
         self._keep = c if not isinstance(c, np.ndarray) else np.ascontiguousarray(c, dtype=np.float64)
         prob = mg_problem(dim, n_coarse, n_levels, degree, float(mu), _ptr(self._keep),
                           PREC[precision] if isinstance(precision, str) else int(precision), int(m_fine),
                           1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel),
-                          float(additive), int(escalate_window), 1 if boundary_patches else 0)
+                          float(additive), int(escalate_window), 1 if boundary_patches else 0, int(nrhs))
         h = ctypes.c_void_p()
         _check(lib.mg_setup(ctypes.byref(prob), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
         self.h = h
         self.dim, self.degree, self.n_levels = dim, degree, n_levels
         self.n_coarse = n_coarse
         self.precision = precision
+        self.nrhs = int(nrhs)
 
     def close(self):
         if getattr(self, "h", None):

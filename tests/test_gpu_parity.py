@@ -447,3 +447,28 @@ def test_load_vector_parity(case):
     b = torch.zeros(S.ndof, dtype=torch.float64, device=DEV)
     G.load_vector(dev(fc.reshape(d, -1)), dev(gc.reshape(-1)), b)
     assert rel_inf(host(b), bo) < 1e-13
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("kernel", [0, 2, 7], ids=["timed", "block", "block_rhs1"])
+def test_vcycle_with_several_right_hand_sides(precision, tol, kernel):
+    """A single problem set up with nrhs = 5 (a group of four sharing each
+    patch-inverse load and one on its own): every vector of one mg_vcycle call
+    against the oracle's V-cycle of that vector; mg_solve refuses the handle."""
+    case = CASES[1]
+    name, d, k, n0, L, mu, cf = case
+    c = cf(n0 * 2 ** (L - 1))
+    H, _ = build(case)
+    G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, pass_kernel=kernel, nrhs=5)
+    nd = H.levels[-1].S.ndof
+    r = np.random.default_rng(33).standard_normal(5 * nd)
+    z = torch.zeros(5 * nd, dtype=torch.float64, device=DEV)
+    G.vcycle(dev(r), z)
+    zh = host(z)
+    for q in range(5):
+        zo = mg.vcycle(H, r[q * nd:(q + 1) * nd])
+        assert np.linalg.norm(zh[q * nd:(q + 1) * nd] - zo) <= tol * np.linalg.norm(zo), q
+    nu, npr = G.sizes()
+    with pytest.raises(mgdarcy.MGError) as e:
+        G.solve(dev(np.zeros(nu)), dev(np.zeros(npr)), torch.zeros(nd, dtype=torch.float64, device=DEV))
+    assert e.value.status == 7
