@@ -449,14 +449,16 @@ def test_load_vector_parity(case):
     assert rel_inf(host(b), bo) < 1e-13
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("kernel", [0, 2, 7], ids=["timed", "block", "block_rhs1"])
-def test_vcycle_with_several_right_hand_sides(precision, tol, kernel):
+def test_vcycle_with_several_right_hand_sides(precision, kernel):
     """A single problem set up with nrhs = 5 (a group of four sharing each
     patch-inverse load and one on its own): every vector of one mg_vcycle call
-    against the oracle's V-cycle of that vector; mg_solve refuses the handle."""
+    against the oracle's V-cycle of that vector (FP64 1e-10, FP32 the bound
+    FP32_VCYCLE_TOL of the case); mg_solve refuses the handle."""
     case = CASES[1]
     name, d, k, n0, L, mu, cf = case
+    tol = 1e-10 if precision == "fp64" else FP32_VCYCLE_TOL.get(name, 1e-5)
     c = cf(n0 * 2 ** (L - 1))
     H, _ = build(case)
     G = mgdarcy.Multigrid(d, n0, L, k, mu, dev(c), precision=precision, pass_kernel=kernel, nrhs=5)
