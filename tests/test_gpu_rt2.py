@@ -256,3 +256,22 @@ def test_batches_reject_degree_2():
     with pytest.raises(mgdarcy.MGError) as e:
         mgdarcy.Batch([dict(dim=2, n_coarse=2, n_levels=3, degree=2, mu=0.0, c=c)], nrhs=1)
     assert e.value.status == 7   # MG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("kernel", [0, 2, 3], ids=["timed", "block", "persistent"])
+def test_vcycle_with_four_right_hand_sides(kernel):
+    """RT_2 with nrhs = 4 in one handle: the block kernels' four-right-hand-side
+    path (each S_v load shared by the four) against the oracle per vector."""
+    case = CASES[0]
+    name, n0, L, mu, cf = case
+    H, _ = build(case)
+    c = cf(n0 * 2 ** (L - 1))
+    G = mgdarcy.Multigrid(2, n0, L, 2, mu, dev(c), pass_kernel=kernel, nrhs=4)
+    nd = H.levels[-1].S.ndof
+    r = np.random.default_rng(71).standard_normal(4 * nd)
+    z = torch.zeros(4 * nd, dtype=torch.float64, device=DEV)
+    G.vcycle(dev(r), z)
+    zh = host(z)
+    for q in range(4):
+        zo = mg.vcycle(H, r[q * nd:(q + 1) * nd])
+        assert rel_inf(zh[q * nd:(q + 1) * nd], zo) < 1e-10, q
