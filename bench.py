@@ -48,6 +48,12 @@ WORKLOAD = "channels_256"
 
 
 def workload_config():
+    if WORKLOAD == "channels_256_rt2":
+        return {"workload": "2-D 256x256 cells, 7 levels (4x4->256x256), RT_2 x Q_2, Brinkman mu=0.01, "
+                            "20 random-walk channels (c=1) in c=1e6 background, variable V-cycle m(J)=2, "
+                            "symmetric multiplicative vertex-patch Schwarz",
+                "levels": 7, "n_fine": 256, "degree": 2, "mu": 0.01, "cycle": "variable, m(J)=2",
+                "l2": "inputs larger than L2 (finest patch inverses 2.4 GB FP32 / 4.8 GB FP64 streamed per sweep)"}
     return {"workload": "2-D 256x256 cells, 7 levels (4x4->256x256), RT_1 x Q_1, Brinkman mu=0.01, "
                         "20 random-walk channels (c=1) in c=1e6 background, variable V-cycle m(J)=2, "
                         "symmetric multiplicative vertex-patch Schwarz",
@@ -236,10 +242,12 @@ def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the warp-per-patch FP32 colour pass on the finest level of this workload
-# (7,225 patches), from an ncu capture of the kernel as it stands; it has to be
-# taken again whenever that kernel changes.
-FINEST_PASS_DRAM_BYTES = 51.028e6 + 0.023e6
+# the FP32 colour pass on the finest level of a workload (7,225 patches), by
+# workload and kernel, from an ncu capture of the kernel as it stands; each has
+# to be taken again whenever its kernel changes.
+FINEST_PASS_DRAM_BYTES = {("channels_256", "warp"): 51.028e6 + 0.023e6,
+                          # RT_2 on the same mesh: the persistent block kernel
+                          ("channels_256_rt2", "persistent blocks"): 277.017e6 + 3.560e6}
 
 
 def vcycle_model(levels, d, prec, l2_bytes, m_fine=2, variable=True):
@@ -411,7 +419,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="channels", choices=["channels", "batched"])
+    ap.add_argument("--workload", default="channels", choices=["channels", "batched", "rt2"],
+                    help="channels: the 256^2 RT_1 benchmark; rt2: the same with RT_2 (no CPU baseline: the oracle's "
+                         "RT_2 hierarchy needs about 6 GB per replica); batched: 64 problems x 4 right-hand sides")
     ap.add_argument("--batch-per-size", type=int, default=16)
     ap.add_argument("--batch-sizes", default="64,128,256,512", help="batched: the mesh sizes taken (one group each)")
     ap.add_argument("--pass-kernel", type=int, default=0,
@@ -431,6 +441,10 @@ def main():
     if args.workload == "batched":
         bench_batched(args)
         return
+    if args.workload == "rt2":
+        global WORKLOAD
+        WORKLOAD = "channels_256_rt2"
+        args.no_cpu_baseline = True
 
     import torch
     from paper_1602_04858_gb300 import inputs, mgdarcy
@@ -649,8 +663,10 @@ def main():
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                              "frac": achieved / hbm,
-                             "traffic": FINEST_PASS_DRAM_BYTES if pass_kernels[J] == "warp" else None,
-                             "kernel": "k_colour_pass<2,1,float,float> (finest level)",
+                             "traffic": FINEST_PASS_DRAM_BYTES.get((WORKLOAD, pass_kernels[J])),
+                             "kernel": {"warp": "k_colour_pass", "block": "k_colour_pass_cta",
+                                        "persistent blocks": "k_colour_pass_ctap"}[pass_kernels[J].split(" (")[0]]
+                                       + "<2,%d,float,float> (finest level)" % w["degree"],
                              "peak_kind": peak_kind, "avg_launch_ms": avg_launch_ms,
                              "bytes_per_launch": per_launch_bytes, "isolated_launch_ms": isolated_launch_ms,
                              "timing": "CUDA events around back-to-back symmetric steps (17 passes) on the "

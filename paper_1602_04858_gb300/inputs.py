@@ -127,6 +127,7 @@ def workload(name: str) -> dict:
     ``channels_256``: 256x256 cells (levels 4x4 -> 256x256), RT_1, mu = 0.01,
         20 random-walk channels 2 cells wide, c = 1 in channels and 1e6
         outside (contrast 1e6), seed 2.
+    ``channels_256_rt2``: the same mesh and field with RT_2 (1.77 M dofs).
     ``lognormal_3d_64``: 64^3 cells (levels 2^3 -> 64^3), RT_0, mu = 0
         (Darcy), c = exp(G), G ~ GRF(sigma=3, ell=8), seed 3.
     """
@@ -135,6 +136,9 @@ def workload(name: str) -> dict:
                     c=lognormal_c(16, 2, 1.0, 4.0, 1))
     if name == "channels_256":
         return dict(d=2, n_coarse=4, n_levels=7, degree=1, mu=0.01,
+                    c=channel_c(256, 20, 2))
+    if name == "channels_256_rt2":
+        return dict(d=2, n_coarse=4, n_levels=7, degree=2, mu=0.01,
                     c=channel_c(256, 20, 2))
     if name == "lognormal_3d_64":
         return dict(d=3, n_coarse=2, n_levels=6, degree=0, mu=0.0,
