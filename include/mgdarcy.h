@@ -214,6 +214,16 @@ mg_status mg_sync(mg_handle* h);
  * rebuilt on its next use. */
 mg_status mg_set_wait_limit(mg_handle* h, double seconds);
 
+/* Caps the grid of the persistent colour-pass kernels (one warp per patch,
+ * persistent blocks) at `blocks` blocks (0: as many as are resident, the
+ * default), on the handle and its FP64 escalation hierarchy: leaves SMs to
+ * concurrent work.  The kernels walk every patch of a colour whatever the
+ * grid, and each patch's arithmetic does not depend on which block takes it,
+ * so results are bit-identical for any cap (the test of one block walking a
+ * whole colour relies on it).  Re-captures the V-cycle graph on its next use;
+ * synchronises the stream. */
+mg_status mg_set_block_limit(mg_handle* h, int blocks);
+
 /* Host buffer of `capacity` doubles that later mg_solve calls fill with the
  * relative residual ||b - A x|| / ||b|| after each iteration (entry 0: the
  * initial guess; entries past the last iteration are left as they were).

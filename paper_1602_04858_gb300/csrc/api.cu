@@ -1351,6 +1351,21 @@ mg_status mg_set_wait_limit(mg_handle* h, double seconds) {
   return MG_OK;
 }
 
+mg_status mg_set_block_limit(mg_handle* h, int blocks) {
+  if (!h || blocks < 0) return fail(MG_ERR_INVALID_ARG, "blocks must be >= 0");
+  for (mg_handle* q : {h, h->shadow64}) {
+    if (!q) continue;
+    for (auto& L : q->lv) L.max_blocks = blocks;
+    // the captured V-cycle holds the old grid sizes
+    if (q->graph_exec) {
+      CU(cudaStreamSynchronize(q->stream));
+      cudaGraphExecDestroy(q->graph_exec);
+      q->graph_exec = nullptr;
+    }
+  }
+  return MG_OK;
+}
+
 mg_status mg_set_residual_history(mg_handle* h, double* host, int capacity) {
   if (!h || capacity < 0 || (capacity > 0 && !host)) return fail(MG_ERR_INVALID_ARG, "bad history buffer");
   h->hist = capacity > 0 ? host : nullptr;

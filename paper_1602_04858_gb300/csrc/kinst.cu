@@ -307,6 +307,7 @@ void colour_pass_nr(const HostLevel& h, int colour, const void* S, void* x, cons
   const int64_t groups_total = (h.count[colour] + P::GPW - 1) / P::GPW;
   int64_t nb = (groups_total + P::WARPS - 1) / P::WARPS;
   if (nb > cap) nb = cap;
+  if (h.max_blocks > 0 && nb > h.max_blocks) nb = h.max_blocks;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nb, groups);
   cfg.blockDim = dim3(32 * P::WARPS);
@@ -430,6 +431,7 @@ void colour_pass_ctap_nr(const HostLevel& h, int colour, const void* S, void* x,
   // the blocks of all right-hand-side groups share the device
   int64_t nb = (cap + groups - 1) / groups;
   if (nb > h.count[colour]) nb = h.count[colour];
+  if (h.max_blocks > 0 && nb > h.max_blocks) nb = h.max_blocks;
   if (nb < 1) nb = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)nb, groups);

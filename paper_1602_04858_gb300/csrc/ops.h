@@ -77,6 +77,8 @@ struct HostLevel {
                          // expiry a kernel sets the error word to 2 and returns
   int pass_cta;          // colour passes of this level: 0 one warp per patch, 1 one block per patch,
                          // 2 persistent blocks, one patch at a time
+  int max_blocks;        // cap on the grid of the persistent colour-pass kernels (0: as many as
+                         // are resident)
   int cta_tpr;           // threads per patch row of the block-per-patch pass for single right-hand
                          // sides: 4, 2 or 8
   int rhs_group;         // right-hand sides sharing each S_v load in the colour passes: 4 (groups

@@ -29,7 +29,7 @@ API = [
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
     "mg_cnn_set_normalisation", "mg_cnn_features", "mg_cnn_targets", "mg_cnn_forward", "mg_cnn_gradients",
     "mg_cnn_train_step", "mg_cnn_guess", "mg_pass_tables_check",
-    "mg_sync", "mg_set_wait_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
+    "mg_sync", "mg_set_wait_limit", "mg_set_block_limit", "mg_set_residual_history", "mg_inject_alloc_failure", "mg_sync_batch",
     "mg_batch_set_wait_limit", "mg_patch_nnz", "mg_measure_fma_peak", "mg_measure_sync_cost", "mg_time_passes", "mg_boundary_patch_info",
 ]
 
@@ -116,6 +116,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_pass_tables_check.argtypes = [i, i, i, i, d, ctypes.c_char_p, i]
     lib.mg_sync.argtypes = [vp]
     lib.mg_set_wait_limit.argtypes = [vp, d]
+    lib.mg_set_block_limit.argtypes = [vp, i]
     lib.mg_set_residual_history.argtypes = [vp, vp, i]
     lib.mg_inject_alloc_failure.argtypes = [i64]
     lib.mg_inject_alloc_failure.restype = None
@@ -274,6 +275,10 @@ class Multigrid:
         if check:
             _check(status)
         return status
+
+    def set_block_limit(self, blocks):
+        """mg_set_block_limit: cap the grid of the persistent colour-pass kernels (0: no cap)."""
+        _check(load().mg_set_block_limit(self.h, int(blocks)))
 
     def set_wait_limit(self, seconds):
         _check(load().mg_set_wait_limit(self.h, float(seconds)))
