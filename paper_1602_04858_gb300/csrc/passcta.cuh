@@ -64,7 +64,7 @@ struct PassShapeC {
   // T data, right-hand sides fastest (entry w of right-hand side rr at w NR + rr):
   // window, patch rows of b, residual, cells, BF16 row scales
   static constexpr int T_WIN = 0, T_B = NR * WIN, T_R = T_B + NR * NV, T_C = T_R + NR * NV, T_SC = T_C + NC;
-  static constexpr int T_N = T_SC + NV;
+  static constexpr int T_N = T_SC + (BF ? NV : 0);
   static constexpr int OFF_I = ((OFF_T + T_N * (int)sizeof(T) + 15) / 16) * 16;
   static constexpr int OFF_BAR = ((OFF_I + 2 * NV * 4 + 15) / 16) * 16;
   static constexpr int SMEM = OFF_BAR + 16;
