@@ -592,7 +592,9 @@ def main():
         Gh = make(prec, variable)
         key = prec if variable else prec + "_V(2,2)"
         ksteps = max(3, args.steps // 2)
+        torch.cuda.nvtx.range_push("timed_vcycles_" + key)   # lets profilers select this mode's V-cycles
         ms_p, _ = time_vcycles(Gh, ksteps, 2)
+        torch.cuda.nvtx.range_pop()
         extra[key] = N * ksteps / (ms_p / 1e3)
         vc_ms[key] = ms_p / ksteps
         x = torch.zeros_like(r)
