@@ -136,16 +136,22 @@ def train(torch, net, feats, targs, epochs=30, batch=16, lr=2e-3, seed=0, log=No
     return hist
 
 
-def evaluate(torch, net, seeds, n, tol=1e-8, smooth_steps=1):
-    """Iterations and solve time from the zero and from the (smoothed) learned guess."""
+def evaluate(torch, net, seeds, n, tol=1e-8, smooth_steps=1, fp64=False):
+    """Iterations and solve time from the zero and from the (smoothed) learned
+    guess (FP32 V-cycle in FP64 FGMRES), and with fp64 the plain FP64 solve
+    from zero beside them."""
     rows = []
     for s in seeds:
         st0, _, _, _, _ = solve_problem(torch, s, n, tol=tol)
         st1, _, _, _, _ = solve_problem(torch, s, n, x0_fn=lambda c, f, x: net.guess(c, f, x), tol=tol,
                                         smooth_steps=smooth_steps)
-        rows.append(dict(seed=s, zero_its=st0.iterations, zero_ms=st0.solve_ms, zero_conv=st0.converged,
-                         learned_its=st1.iterations, learned_ms=st1.solve_ms, learned_conv=st1.converged,
-                         learned_initial_rel_residual=st1.initial_rel_residual))
+        row = dict(seed=s, zero_its=st0.iterations, zero_ms=st0.solve_ms, zero_conv=st0.converged,
+                   learned_its=st1.iterations, learned_ms=st1.solve_ms, learned_conv=st1.converged,
+                   learned_initial_rel_residual=st1.initial_rel_residual)
+        if fp64:
+            st2, _, _, _, _ = solve_problem(torch, s, n, tol=tol, precision="fp64")
+            row.update(fp64_its=st2.iterations, fp64_ms=st2.solve_ms, fp64_conv=st2.converged)
+        rows.append(row)
     return rows
 
 
@@ -158,8 +164,11 @@ def summarise(rows):
                 zero_its_median=float(np.median(z)), learned_its_median=float(np.median(l)),
                 zero_its_max=int(z.max()), learned_its_max=int(l.max()),
                 zero_ms_mean=float(zt.mean()), learned_ms_mean=float(lt.mean()),
-                all_converged=bool(all(r["zero_conv"] and r["learned_conv"] for r in rows)),
-                learned_initial_rel_residual_mean=float(np.mean([r["learned_initial_rel_residual"] for r in rows])))
+                all_converged=bool(all(r["zero_conv"] and r["learned_conv"] and r.get("fp64_conv", True)
+                                       for r in rows)),
+                learned_initial_rel_residual_mean=float(np.mean([r["learned_initial_rel_residual"] for r in rows])),
+                fp64_its_mean=float(np.mean([r["fp64_its"] for r in rows])) if "fp64_its" in rows[0] else None,
+                fp64_ms_mean=float(np.mean([r["fp64_ms"] for r in rows])) if "fp64_ms" in rows[0] else None)
 
 
 def main():
@@ -181,7 +190,7 @@ def main():
     t0 = time.perf_counter()
     hist = train(torch, net, feats, targs, epochs=args.epochs, log=lambda m: print(m, flush=True))
     train_s = time.perf_counter() - t0
-    rows = evaluate(torch, net, list(range(100000, 100000 + args.test)), args.n)
+    rows = evaluate(torch, net, list(range(100000, 100000 + args.test)), args.n, fp64=True)
     summary = summarise(rows)
     summary.update(n=args.n, train_samples=args.train, data_generation_s=gen_s, training_s=train_s,
                    final_loss=hist[-1])
