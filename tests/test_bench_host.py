@@ -49,3 +49,21 @@ def test_batched_workload_recipe():
     # lognormal fields with sigma in [1, 3]: positive, finite, not constant
     for p in probs:
         assert np.all(p["c"] > 0) and np.all(np.isfinite(p["c"])) and p["c"].std() > 0
+
+
+def test_workload_configs_name_their_degree():
+    """The default and the RT_2 workload describe themselves; the traffic
+    figures are keyed by workload and the finest level's kernel."""
+    assert bench.workload_config()["degree"] == 1
+    old = bench.WORKLOAD
+    try:
+        bench.WORKLOAD = "channels_256_rt2"
+        assert bench.workload_config()["degree"] == 2
+    finally:
+        bench.WORKLOAD = old
+    assert set(bench.FINEST_PASS_DRAM_BYTES) == {("channels_256", "warp"), ("channels_256_rt2", "persistent blocks")}
+    # each traffic figure lies within 10 % above its algorithmic bytes (7,225 patches of 40 or 96 dofs)
+    for (wl, _), t in bench.FINEST_PASS_DRAM_BYTES.items():
+        nv = 40 if wl == "channels_256" else 96
+        alg = bench.colour_pass_bytes(7225, nv, 4, 4)
+        assert alg <= t <= 1.1 * alg
