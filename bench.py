@@ -568,6 +568,21 @@ def main():
     per_launch_bytes = step_bytes / len(order)
     isolated_launch_ms = sum(a.elapsed_time(b) for a, b in iso) / len(iso)
 
+    # --- where the V-cycle's time goes: per level, the pass time (graph of two
+    # symmetric steps, mg_time_passes) x the passes a V-cycle runs there
+    # (pre- and post-smoothing of m(j) steps, 2C - 1 passes for the first step
+    # and 2C - 2 for each further one, C = 3^d colours; levels folded into the
+    # dense sub-cycle run none)
+    Ls = G.dense_level()
+    level_breakdown = {}
+    for j in range(Ls + 1, J + 1):
+        m = 2 * 2 ** (J - j)
+        C = 3 ** w["d"]
+        passes = 2 * ((2 * C - 1) + (2 * C - 2) * (m - 1))
+        us = G.time_passes(j)
+        level_breakdown[str(j)] = {"n": w["n_coarse"] << j, "kernel": pass_kernels[j], "us_per_pass": us,
+                                   "passes_per_vcycle": passes, "ms_per_vcycle": us * passes / 1e3}
+
     # --- companions: FP64 and BF16-inverse V-cycles, time to 1e-8 ----------------
     extra = {}
     vc_ms = {"fp32": ms_max / args.steps}
@@ -680,6 +695,7 @@ def main():
                                              "/ CUDA-event time of a V-cycle; frac against the measured HBM copy "
                                              "bandwidth (peak above); FP64 also against the measured FP64 FMA peak",
                                     "l2_bytes": l2_bytes, "modes": rv},
+                "level_breakdown": {"dense_fold_level": Ls, "levels": level_breakdown},
                 "alu_peaks": peaks_alu or None,
                 "sync_costs": sync_costs,
                 "setup_s": setup_s,

@@ -441,6 +441,11 @@ mg_status mg_measure_sync_cost(int kind, int blocks, double* us_per_step, void* 
  * or 3 (persistent blocks).  Host only. */
 mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel);
 
+/* Level Ls whose sub-cycle (levels 0..Ls) setup folded into a dense matrix
+ * (mg_problem.dense_level): 0 when nothing is folded.  The colour passes of
+ * levels 1..Ls then do not run in the V-cycle.  Host only. */
+mg_status mg_dense_level(const mg_handle* h, int* level);
+
 /* Right-hand sides sharing each patch-inverse load in the colour passes of
  * `level` (1 <= level <= J): 4 (groups of four where the handle holds four or
  * more right-hand sides) or 1 (each on its own, four times the blocks).  With

@@ -931,6 +931,12 @@ mg_status mg_level_pass_kernel(const mg_handle* h, int level, int* kernel) {
   return MG_OK;
 }
 
+mg_status mg_dense_level(const mg_handle* h, int* level) {
+  if (!h || !level) return fail(MG_ERR_INVALID_ARG, "null argument");
+  *level = h->Ls > 0 ? h->Ls : 0;
+  return MG_OK;
+}
+
 mg_status mg_level_rhs_group(const mg_handle* h, int level, int* group) {
   if (!h || !group || level < 1 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
   *group = h->lv[level].rhs_group;

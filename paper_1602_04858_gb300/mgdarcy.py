@@ -23,7 +23,7 @@ PREC = {"fp64": 0, "fp32": 1, "fp32_bf16inv": 2}
 API = [
     "mg_setup", "mg_destroy", "mg_sizes", "mg_apply", "mg_vcycle", "mg_solve", "mg_smooth", "mg_colour_pass",
     "mg_level_load", "mg_level_store", "mg_restrict", "mg_prolong_add", "mg_coarse_solve", "mg_patch_info",
-    "mg_level_pass_kernel", "mg_level_rhs_group", "mg_level_row_threads", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
+    "mg_level_pass_kernel", "mg_dense_level", "mg_level_rhs_group", "mg_level_row_threads", "mg_kernel_launches", "mg_status_string", "mg_last_error", "mg_residual_norm", "mg_residual_norm_noalloc",
     "mg_setup_batch", "mg_destroy_batch", "mg_batch_layout", "mg_vcycle_batch", "mg_solve_batch",
     "mg_batch_kernel_launches", "mg_batch_level_choice", "mg_load_vector",
     "mg_cnn_create", "mg_cnn_destroy", "mg_cnn_param_count", "mg_cnn_get_params", "mg_cnn_set_params",
@@ -85,6 +85,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.mg_patch_info.argtypes = [vp, i, i, ctypes.POINTER(i64), ctypes.POINTER(i)]
     lib.mg_level_pass_kernel.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_level_rhs_group.argtypes = [vp, i, ctypes.POINTER(i)]
+    lib.mg_dense_level.argtypes = [vp, ctypes.POINTER(i)]
     lib.mg_level_row_threads.argtypes = [vp, i, ctypes.POINTER(i)]
     lib.mg_residual_norm.argtypes = [vp, i, vp, vp, vp, vp]
     lib.mg_residual_norm_noalloc.argtypes = [i, i, i, d, vp, vp, vp, vp, vp]
@@ -332,6 +333,12 @@ class Multigrid:
         k = ctypes.c_int()
         _check(load().mg_level_pass_kernel(self.h, level, ctypes.byref(k)))
         return k.value
+
+    def dense_level(self):
+        """Level whose sub-cycle setup folded into a dense matrix (mg_dense_level); 0: none."""
+        v = ctypes.c_int()
+        _check(load().mg_dense_level(self.h, ctypes.byref(v)))
+        return v.value
 
     def row_threads(self, level):
         """Threads per patch row of the block kernel on a level (mg_level_row_threads): 4, 2 or 8."""
