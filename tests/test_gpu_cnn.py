@@ -144,7 +144,7 @@ def test_learned_guess_at_full_size():
     method, 30 epochs, 200 held-out problems solved to 1e-8 from the zero and
     from the learned guess.  What the network gains is measured, not assumed:
     every learned solve must reach the tolerance (the zero-guess solve is the
-    judge), and the learned guess may cost at most half an iteration on
+    yardstick), and the learned guess may cost at most half an iteration on
     average.  On GB300 the two averages agree to 0.1 iteration (14.07 from the
     learned guess, 14.03 from zero): a 4-layer 3x3 network sees 9 x 9 cells,
     while the response to f at mu/h^2 = 164 is global, so the gain on this
