@@ -48,6 +48,12 @@ WORKLOAD = "channels_256"
 
 
 def workload_config():
+    if WORKLOAD == "lognormal_3d_64":
+        return {"workload": "3-D 64^3 cells, 6 levels (2^3->64^3), RT_0 x Q_0, Darcy mu=0, c = exp(G), "
+                            "G ~ GRF(sigma=3, 8 cells), variable V-cycle m(J)=2, symmetric multiplicative "
+                            "vertex-patch Schwarz",
+                "levels": 6, "n_fine": 64, "degree": 0, "mu": 0.0, "cycle": "variable, m(J)=2",
+                "l2": "inputs larger than L2 (finest patch inverses 400 MB FP32 / 800 MB FP64 streamed per sweep)"}
     if WORKLOAD == "channels_256_rt2":
         return {"workload": "2-D 256x256 cells, 7 levels (4x4->256x256), RT_2 x Q_2, Brinkman mu=0.01, "
                             "20 random-walk channels (c=1) in c=1e6 background, variable V-cycle m(J)=2, "
@@ -419,9 +425,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="channels", choices=["channels", "batched", "rt2"],
+    ap.add_argument("--workload", default="channels", choices=["channels", "batched", "rt2", "3d"],
                     help="channels: the 256^2 RT_1 benchmark; rt2: the same with RT_2 (no CPU baseline: the oracle's "
-                         "RT_2 hierarchy needs about 6 GB per replica); batched: 64 problems x 4 right-hand sides")
+                         "RT_2 hierarchy needs about 6 GB per replica); 3d: 64^3 RT_0 Darcy on a lognormal field "
+                         "(no CPU baseline); batched: 64 problems x 4 right-hand sides")
     ap.add_argument("--batch-per-size", type=int, default=16)
     ap.add_argument("--batch-sizes", default="64,128,256,512", help="batched: the mesh sizes taken (one group each)")
     ap.add_argument("--pass-kernel", type=int, default=0,
@@ -441,9 +448,9 @@ def main():
     if args.workload == "batched":
         bench_batched(args)
         return
-    if args.workload == "rt2":
+    if args.workload in ("rt2", "3d"):
         global WORKLOAD
-        WORKLOAD = "channels_256_rt2"
+        WORKLOAD = "channels_256_rt2" if args.workload == "rt2" else "lognormal_3d_64"
         args.no_cpu_baseline = True
 
     import torch
@@ -530,14 +537,15 @@ def main():
     value, ms_max = aggregate_throughput(N, args.steps, ms, dist, dev)
 
     # --- dominant kernel: finest-level colour pass ---------------------------------
-    # In the V-cycle the 17 passes of a symmetric smoothing step run back to
+    # In the V-cycle the 2C - 1 passes of a symmetric smoothing step run back to
     # back (programmatic dependent launch overlaps each pass's prologue with
     # the previous pass), so the average launch duration is taken over whole
-    # steps: CUDA events on the launching stream around each step of 17 passes.
+    # steps: CUDA events on the launching stream around each step of 2C - 1 passes.
     # Events around every single pass break that overlap; that (pessimistic)
     # figure is reported beside it as isolated_launch_ms.
     J = w["n_levels"] - 1
-    order = list(range(9)) + list(range(7, -1, -1))
+    C = 3 ** w["d"]
+    order = list(range(C)) + list(range(C - 2, -1, -1))
     step_bytes = sum(colour_pass_bytes(*G.patch_info(J, col), 4, 4) for col in order)
     G.level_load(J, torch.zeros_like(r), r)
     reps = max(4, args.steps // 2)
@@ -683,10 +691,10 @@ def main():
                              "traffic": FINEST_PASS_DRAM_BYTES.get((WORKLOAD, pass_kernels[J])),
                              "kernel": {"warp": "k_colour_pass", "block": "k_colour_pass_cta",
                                         "persistent blocks": "k_colour_pass_ctap"}[pass_kernels[J].split(" (")[0]]
-                                       + "<2,%d,float,float> (finest level)" % w["degree"],
+                                       + "<%d,%d,float,float> (finest level)" % (w["d"], w["degree"]),
                              "peak_kind": peak_kind, "avg_launch_ms": avg_launch_ms,
                              "bytes_per_launch": per_launch_bytes, "isolated_launch_ms": isolated_launch_ms,
-                             "timing": "CUDA events around back-to-back symmetric steps (17 passes) on the "
+                             "timing": f"CUDA events around back-to-back symmetric steps ({len(order)} passes) on the "
                                        "launching stream, as the passes run inside the V-cycle"},
                 "clocks": clocks,
                 "roofline_vcycle": {"model": "algorithmic bytes of one V-cycle: per level the patch inverses once "
