@@ -509,7 +509,9 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 //     on earlier passes, so the first copies precede the wait for the
 //     preceding kernel (programmatic dependent launch);
 //  2. the lanes gather the window of x, the patch rows of b and the 2^D cell
-//     coefficients by contiguous segments (cp.async, zero outside the domain);
+//     coefficients by per-lane element descriptors (cp.async, zero outside
+//     the domain) into one of two stage buffers; the loop alternates the
+//     buffers in two unrolled copies, so stage addresses are constants;
 //  3. local residual (b - A x)|_v from the lane plan of the patch's type: each
 //     lane accumulates its pieces, the row map adds the pieces of a row;
 //  4. delta = S_v r, the columns of S_v split over the lanes (FP32: packed
@@ -556,7 +558,10 @@ __device__ __forceinline__ void cp_async_t(T* dst, const T* src, bool ok) {
   else cp_async4(dst, src, ok ? 4u : 0u);
 }
 
-// Plan entries of one lane for one patch type, held in registers.
+// Plan entries of one lane for one patch type, held in registers.  After
+// rebase() the window columns and cells are byte offsets into shared memory
+// (from the window and cell bases of the lane's patch in stage buffer 0), so
+// that a load in stage buffer BI is one shared load at register + constant.
 template <class P, typename T>
 struct PlanRegs {
   static constexpr int ZP = P::PSum::ZP, ZM = P::PSum::ZM;
@@ -571,19 +576,35 @@ struct PlanRegs {
 #pragma unroll
     for (int s = 0; s < ZM; ++s) MassLd<T>::get(pm + (size_t)s * LW * MASS_BYTES, mc[s], mw[s], mcell[s]);
   }
+  __device__ __forceinline__ void rebase(int wofs, int cofs) {
+#pragma unroll
+    for (int s = 0; s < ZP; ++s) pw[s] = wofs + pw[s] * (int)sizeof(T);
+#pragma unroll
+    for (int s = 0; s < ZM; ++s) {
+      mw[s] = wofs + mw[s] * (int)sizeof(T);
+      mcell[s] = cofs + mcell[s] * (int)sizeof(T);
+    }
+  }
 };
+
+template <typename T>
+__device__ __forceinline__ T lds_at(const unsigned char* sm, int byte_off) {
+  return *reinterpret_cast<const T*>(sm + byte_off);
+}
 
 // Lane pieces of the local residual: piece PI accumulates its plain slots
 // (coefficient x window column) and mass slots (coefficient x cell
-// coefficient x window column) into one partial sum.
+// coefficient x window column) into one partial sum.  BOFF is the byte offset
+// of the stage buffer holding the patch's window and cells.
 // With one right-hand side the slots of a piece feed NA independent partial
 // sums (slot s into sum s mod NA), added at the end: the chain of dependent
 // FMAs, not the FMA count, sets the latency of a warp's residual.
-template <int PI, class P, typename T, int NR>
-__device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* win, const T* cw, T* part, int lp) {
+template <int PI, int BOFF, class P, typename T, int NR>
+__device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const unsigned char* sm, T* part, int lp) {
   using PL = typename P::PL;
   using PSum = typename P::PSum;
   constexpr int NA = NR == 1 ? 4 : 1;
+  constexpr int RB = P::WIN * (int)sizeof(T);   // bytes between right-hand sides' windows
   T acc[NA][NR];
 #pragma unroll
   for (int a = 0; a < NA; ++a)
@@ -592,12 +613,12 @@ __device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* wi
 #pragma unroll
   for (int s = PSum::zoff(PI); s < PSum::zoff(PI) + PL::z(PI); ++s)
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) acc[s % NA][rr] += R.pc[s] * win[rr * P::WIN + R.pw[s]];
+    for (int rr = 0; rr < NR; ++rr) acc[s % NA][rr] += R.pc[s] * lds_at<T>(sm, R.pw[s] + (BOFF + rr * RB));
 #pragma unroll
   for (int s = PSum::zmoff(PI); s < PSum::zmoff(PI) + PL::zm(PI); ++s) {
-    const T cc = R.mc[s] * cw[R.mcell[s]];
+    const T cc = R.mc[s] * lds_at<T>(sm, R.mcell[s] + BOFF);
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) acc[(s + 1) % NA][rr] += cc * win[rr * P::WIN + R.mw[s]];
+    for (int rr = 0; rr < NR; ++rr) acc[(s + 1) % NA][rr] += cc * lds_at<T>(sm, R.mw[s] + (BOFF + rr * RB));
   }
 #pragma unroll
   for (int rr = 0; rr < NR; ++rr) {
@@ -605,7 +626,7 @@ __device__ __forceinline__ void plan_pieces(const PlanRegs<P, T>& R, const T* wi
     if constexpr (NA == 4) t = (acc[0][rr] + acc[1][rr]) + (acc[2][rr] + acc[3][rr]);
     part[rr * P::PARTS + PI * P::LW + lp] = t;
   }
-  if constexpr (PI + 1 < PL::NP) plan_pieces<PI + 1, P, T, NR>(R, win, cw, part, lp);
+  if constexpr (PI + 1 < PL::NP) plan_pieces<PI + 1, BOFF, P, T, NR>(R, sm, part, lp);
 }
 
 template <int D, int K, typename T, typename TS, int NR>
@@ -617,7 +638,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   using PL = typename P::PL;
   using PSum = typename P::PSum;
   constexpr int NV = P::NV, RG = P::RG, NVP = P::NVP, LPP = P::LPP, GPW = P::GPW, LW = P::LW;
-  constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>(), NSI = P::NSI;
+  constexpr int WIN = P::WIN, PARTS = P::PARTS, SSPL = P::SSPL, PB = plain_bytes<T>();
   x += (int64_t)blockIdx.y * NR * vs;
   b += (int64_t)blockIdx.y * NR * vs;
   // the problem of this block's right-hand sides: its coefficients and inverses
@@ -631,7 +652,6 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   unsigned char* wbase = smem + (size_t)warp * P::WARP_BYTES;
   constexpr int NSB = P::NSB;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * P::WARP_BYTES) + warp * NSB;
-  const int4* segs = reinterpret_cast<const int4*>(tabs + P::TB_SEG);
   const unsigned char* plan_p = tabs + P::TB_PLAIN + (size_t)lp * PB;
   const unsigned char* plan_m = tabs + P::TB_MASS + (size_t)lp * MASS_BYTES;
   const uint32_t* rowp = reinterpret_cast<const uint32_t*>(tabs + P::TB_ROWP);
@@ -639,10 +659,15 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   const int64_t W = (int64_t)gridDim.x * P::WARPS;
   const uint64_t pol = evict_first ? l2_policy_evict_first() : l2_policy_evict_last();
 
+  // per-patch T data of this lane's patch in stage buffer bi (0 or 1)
   auto st_T = [&](int bi) {
     return reinterpret_cast<T*>(wbase + NSB * P::STAGE_S + (size_t)bi * P::STAGE_T) + g * P::T_PER_PATCH;
   };
   auto npat = [&](int64_t pg) { return (int)((count - pg * GPW) < GPW ? (count - pg * GPW) : GPW); };
+  // byte offsets (from smem) of the window and the cells of buffer 0
+  const int wofs0 = (int)(reinterpret_cast<unsigned char*>(st_T(0) + P::OFF_W) - smem);
+  const int cofs0 = (int)(reinterpret_cast<unsigned char*>(st_T(0) + P::OFF_C) - smem);
+  constexpr int TSTEP = (int)P::STAGE_T;   // bytes from buffer 0 to buffer 1
 
   // (1) bulk copies of the inverses of patch group pg into buffer sb (lane 0)
   auto issue_S = [&](int64_t pg, int sb) {
@@ -706,23 +731,30 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     for (int q = 1; q < D + 2; ++q) r = (c == q) ? Pv[q] : r;
     return r;
   };
-  // (2) asynchronous gather of the window, the patch rows of b and the cells:
-  //     one entry per element, consecutive lanes to consecutive shared-memory
-  //     words; window entries outside the domain (vmask bit clear) are zero
-  auto issue_gather = [&](int bi, const int (&v)[D], bool act, uint32_t vmask, int (&Pv)[D + 2]) {
-    T* tw = st_T(bi);
+  // (2) asynchronous gather of the window, the patch rows of b and the cells
+  //     into stage buffer BI: lane lp takes elements lp + LW i.  The elements
+  //     are the window columns (each at its own position), then the patch rows
+  //     of b, then the cells, so the kind of slot i is a compile-time constant
+  //     except in the slots where the kinds change; window entries outside the
+  //     domain (vmask bit clear) are zero
+  auto issue_gather = [&](auto BIc, const int (&v)[D], bool act, uint32_t vmask, int (&Pv)[D + 2]) {
+    constexpr int BI = decltype(BIc)::value;
+    T* tw = st_T(BI);
     offsets(v, Pv);
     if (act) {
 #pragma unroll
       for (int i = 0; i < P::EPL; ++i) {
-        const int pk = el[i].y, kind = elem_kind(pk);
+        const bool win_slot = (i + 1) * LW <= WIN;
+        const bool b_slot = i * LW >= WIN && (i + 1) * LW <= WIN + NV;
+        const int pk = el[i].y;
+        const int kind = win_slot ? 0 : (b_slot ? 1 : elem_kind(pk));
         if (kind == 3) continue;
         const int gi = el[i].x + pick(Pv, elem_comp(pk));
-        const int dst = elem_dst(pk);
+        const int dst = win_slot ? i * LW + lp : elem_dst(pk);
         if (kind == 2) {
           cp_async_t(tw + P::OFF_C + dst, L.c + gi, true);
         } else {
-          const bool ok = (vmask >> i) & 1u;
+          const bool ok = kind == 1 || ((vmask >> i) & 1u);   // patch rows lie in the domain
           const T* base = (kind == 0) ? x : b;
           T* dd = tw + ((kind == 0) ? P::OFF_W : P::OFF_B) + dst;
           const int rs = (kind == 0) ? WIN : NV;
@@ -743,6 +775,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   int rtype = patch_type<D>(vc, L.n);
   uint32_t vmc = __ldg(valp + rtype * LW + lp);
   R.load(plan_p + (size_t)rtype * PSum::ZP * LW * PB, plan_m + (size_t)rtype * PSum::ZM * LW * MASS_BYTES);
+  R.rebase(wofs0, cofs0);
   // row maps of this lane's patch rows for the patch type rtype, reloaded with
   // the plan when the type changes (most patches are interior)
   uint32_t rps[P::NROWIT];
@@ -767,11 +800,15 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   __syncwarp();
   int Pc[D + 2], Pn[D + 2];   // offsets of the current and the next group's patch
   offsets(vc, Pc);
-  if (pg < ngroups) issue_gather(0, vc, actc, vmc, Pc);
+  if (pg < ngroups) issue_gather(std::integral_constant<int, 0>{}, vc, actc, vmc, Pc);
   int mtype = rtype;   // type of the in-domain mask held in vmc
-  for (int k = 0; pg < ngroups; ++k, pg += W) {
-    const int bi = k & 1;
-    const int sb = (NSB == 1) ? 0 : (k % NSB);
+  int k = 0;           // groups done by this warp
+  // One patch group in stage buffer BI (k even: 0, odd: 1; the loop below runs
+  // the two alternately, so every stage address is register + constant).
+  // Returns false when the warp has no further group or a wait timed out.
+  auto step = [&](auto BIc) -> bool {
+    constexpr int BI = decltype(BIc)::value;
+    constexpr int sb = (NSB == 1) ? 0 : BI;   // inverse buffer: k mod NSB
     const int64_t pn = pg + W;
     int vn[D];
     const bool actn = vertex(pn, vn);
@@ -781,7 +818,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
         vmc = __ldg(valp + tn * LW + lp);
         mtype = tn;
       }
-      issue_gather(bi ^ 1, vn, actn, vmc, Pn);
+      issue_gather(std::integral_constant<int, BI ^ 1>{}, vn, actn, vmc, Pn);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
@@ -789,16 +826,17 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     const int type = patch_type<D>(vc, L.n);
     if (type != rtype) {
       R.load(plan_p + (size_t)type * PSum::ZP * LW * PB, plan_m + (size_t)type * PSum::ZM * LW * MASS_BYTES);
+      R.rebase(wofs0, cofs0);
       load_rowmap(type, rps);
       rtype = type;
     }
     __syncwarp();
-    T* pb = st_T(bi);
+    T* pb = st_T(BI);
     const T* win = pb + P::OFF_W;
     T* part = pb + P::OFF_P;
     // (3a) lane pieces of the local residual
     if (actc) {
-      plan_pieces<0, P, T, NR>(R, win, pb + P::OFF_C, part, lp);
+      plan_pieces<0, BI * TSTEP, P, T, NR>(R, smem, part, lp);
       if (lp == 0) {
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) part[rr * PARTS + P::ZSLOT] = T(0);
@@ -813,7 +851,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
       // may still be in flight: let them land (bounded) before the warp leaves
       mbar_wait_bounded(bars + sb, (uint32_t)((k / NSB) & 1), 100000000ull);
       if (NSB > 1 && pn < ngroups) mbar_wait_bounded(bars + (sb ^ 1), (uint32_t)(((k + 1) / NSB) & 1), 100000000ull);
-      break;
+      return false;
     }
     const unsigned char* sbase = wbase + (size_t)sb * P::STAGE_S;
     const float* sc = reinterpret_cast<const float*>(sbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
@@ -943,7 +981,15 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
 #pragma unroll
     for (int c = 0; c < D + 2; ++c) Pc[c] = Pn[c];
     actc = actn;
-  }
+    ++k;
+    pg += W;
+    return pg < ngroups;
+  };
+  if (pg < ngroups)
+    for (;;) {
+      if (!step(std::integral_constant<int, 0>{})) break;
+      if (!step(std::integral_constant<int, 1>{})) break;
+    }
 }
 
 // ---------------------------------------------------------------------------

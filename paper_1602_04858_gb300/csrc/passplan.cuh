@@ -709,6 +709,17 @@ bool build_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<u
                                   reinterpret_cast<int2*>(blob.data() + P::TB_ELW),
                                   reinterpret_cast<int2*>(blob.data() + P::TB_ROWD),
                                   reinterpret_cast<uint32_t*>(blob.data() + P::TB_VAL));
+  {   // the kernel derives an element's kind (and a window column) from its position
+    const int2* elw = reinterpret_cast<const int2*>(blob.data() + P::TB_ELW);
+    for (int q = 0; q < P::EPL * P::LW; ++q) {
+      const int pk = elw[q].y;   // element q = lane + LW i sits at [i][lane]
+      const int qkind = q < P::WIN ? 0 : (q < P::WIN + P::NV ? 1 : (q < P::NE ? 2 : 3));
+      if (elem_kind(pk) != qkind || (qkind == 0 && elem_dst(pk) != q)) {
+        why = "warp pass element " + std::to_string(q) + " out of its layout position";
+        return false;
+      }
+    }
+  }
   uint32_t* rowp = reinterpret_cast<uint32_t*>(blob.data() + P::TB_ROWP);
   for (int t = 0; t < P::NTYPE; ++t) {
     if (!type_present<D>(t, L.n)) continue;
@@ -945,6 +956,11 @@ int check_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::string& w
         for (int lp = 0; lp < LW; ++lp) {
           const int2 e2 = elw[i * LW + lp];
           const int kind = elem_kind(e2.y), comp = elem_comp(e2.y), dst = elem_dst(e2.y);
+          // the kernel takes the kind of element q = lp + LW i from q (window
+          // columns, then patch rows of b, then cells) and the window column from q
+          const int q = lp + LW * i;
+          const int qkind = q < P::WIN ? 0 : (q < P::WIN + P::NV ? 1 : (q < P::NE ? 2 : 3));
+          if (kind != qkind || (kind == 0 && dst != q)) { why = "warp element out of its layout position"; return 1; }
           if (kind == 3) continue;
           const int64_t g = (int64_t)e2.x + vertex_offset<D, K>(L.N, L.n, comp, v);
           const bool valid = (val[t * LW + lp] >> i) & 1u;

@@ -67,3 +67,17 @@ def test_workload_configs_name_their_degree():
         nv = 40 if wl == "channels_256" else 96
         alg = bench.colour_pass_bytes(7225, nv, 4, 4)
         assert alg <= t <= 1.1 * alg
+
+
+def test_traffic_figures_are_the_committed_captures():
+    """Each traffic figure bench.py reports is the DRAM read + write of one
+    launch in the committed ncu summary of that workload's finest pass."""
+    import re
+    prof = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles")
+    files = {"channels_256": "colour_pass_channels256_fp32.md",
+             "channels_256_rt2": "colour_pass_channels256_rt2_fp32.md"}
+    for (wl, _), t in bench.FINEST_PASS_DRAM_BYTES.items():
+        with open(os.path.join(prof, files[wl])) as f:
+            m = re.search(r"DRAM traffic: ([0-9.]+) MB per launch", f.read())
+        assert m, files[wl]
+        assert abs(t / 1e6 - float(m.group(1))) < 0.006
