@@ -248,12 +248,12 @@ def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the FP32 colour pass on the finest level of a workload (7,225 patches), by
-# workload and kernel, from an ncu capture of the kernel as it stands; each has
-# to be taken again whenever its kernel changes.
-FINEST_PASS_DRAM_BYTES = {("channels_256", "warp"): 51.028e6 + 0.023e6,
-                          # RT_2 on the same mesh: the persistent block kernel
-                          ("channels_256_rt2", "persistent blocks"): 277.017e6 + 3.560e6}
+# the FP32 colour pass on the finest level of a workload, by workload and
+# kernel, from an ncu capture of the kernel as it stands; each has to be taken
+# again whenever its kernel changes (a workload without an entry reports null).
+FINEST_PASS_DRAM_BYTES = {("channels_256", "warp"): 51.037696e6 + 0.000512e6,
+                          # 64^3 RT_0: 9,261 patches of 20 dofs per colour
+                          ("lognormal_3d_64", "warp"): 20.326656e6 + 0.002304e6}
 
 
 def vcycle_model(levels, d, prec, l2_bytes, m_fine=2, variable=True):

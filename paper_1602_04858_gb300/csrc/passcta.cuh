@@ -88,6 +88,21 @@ struct PassShapeC {
   static_assert(TPR == 2 || TPR == 4 || TPR == 8, "threads per row: 2, 4 or 8");
 };
 
+// A thread's plan columns and cells as byte offsets from the block's shared
+// memory (T data from byte TOFF), so that each plan load is one shared load at
+// register + constant.
+template <typename T, int NR, int TOFF, class C, int ZW, int ZMW>
+__device__ __forceinline__ void plan_bytes(int (&pw)[ZW], int (&mw)[ZMW], int (&mcell)[ZMW]) {
+  constexpr int B = (int)sizeof(T);
+#pragma unroll
+  for (int s = 0; s < ZW; ++s) pw[s] = TOFF + (C::T_WIN + pw[s] * NR) * B;
+#pragma unroll
+  for (int s = 0; s < ZMW; ++s) {
+    mw[s] = TOFF + (C::T_WIN + mw[s] * NR) * B;
+    mcell[s] = TOFF + (C::T_C + mcell[s]) * B;
+  }
+}
+
 // --- host construction -------------------------------------------------------
 
 // Gather descriptors, one per entry (expanded from the segment descriptors):
@@ -406,6 +421,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR, TPR>::NT)
     for (int s = 0; s < ZW; ++s) PlainLd<T>::get(pp + (size_t)s * NT * PB, pc[s], pw[s]);
 #pragma unroll
     for (int s = 0; s < ZMW; ++s) MassLd<T>::get(pm + (size_t)s * NT * MASS_BYTES, mc[s], mw[s], mcell[s]);
+    plan_bytes<T, NR, C::OFF_T, C>(pw, mw, mcell);
   }
   int kind[EPT], dst[EPT], aux[EPT];
   int64_t src[EPT];
@@ -475,19 +491,18 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR, TPR>::NT)
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) acc2[a][rr] = T(0);
   if (row < NV) {
-    const T* win = st + C::T_WIN;
 #pragma unroll
     for (int s = 0; s < ZW; ++s) {
       T wv[NR];
-      ld_rhs<T, NR>(win + pw[s] * NR, wv);
+      ld_rhs<T, NR>(reinterpret_cast<const T*>(sm + pw[s]), wv);
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) acc2[s % NA][rr] += pc[s] * wv[rr];
     }
 #pragma unroll
     for (int s = 0; s < ZMW; ++s) {
-      const T cc = mc[s] * st[C::T_C + mcell[s]];
+      const T cc = mc[s] * *reinterpret_cast<const T*>(sm + mcell[s]);
       T wv[NR];
-      ld_rhs<T, NR>(win + mw[s] * NR, wv);
+      ld_rhs<T, NR>(reinterpret_cast<const T*>(sm + mw[s]), wv);
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) acc2[(s + 1) % NA][rr] += cc * wv[rr];
     }
@@ -669,6 +684,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
     for (int s = 0; s < ZW; ++s) PlainLd<T>::get(pp + (size_t)s * NT * PB, pc[s], pw[s]);
 #pragma unroll
     for (int s = 0; s < ZMW; ++s) MassLd<T>::get(pm + (size_t)s * NT * MASS_BYTES, mc[s], mw[s], mcell[s]);
+    plan_bytes<T, NR, C::P_OFF_T, C>(pw, mw, mcell);
   };
   load_plan(rtype);
   // gather descriptors of this thread's entries (the same for every patch)
@@ -760,19 +776,18 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR>::NT)
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) acc[rr] = T(0);
     if (row < NV) {
-      const T* win = st + C::T_WIN;
 #pragma unroll
       for (int s = 0; s < ZW; ++s) {
         T wv[NR];
-        ld_rhs<T, NR>(win + pw[s] * NR, wv);
+        ld_rhs<T, NR>(reinterpret_cast<const T*>(sm + pw[s]), wv);
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) acc[rr] += pc[s] * wv[rr];
       }
 #pragma unroll
       for (int s = 0; s < ZMW; ++s) {
-        const T cc = mc[s] * st[C::T_C + mcell[s]];
+        const T cc = mc[s] * *reinterpret_cast<const T*>(sm + mcell[s]);
         T wv[NR];
-        ld_rhs<T, NR>(win + mw[s] * NR, wv);
+        ld_rhs<T, NR>(reinterpret_cast<const T*>(sm + mw[s]), wv);
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) acc[rr] += cc * wv[rr];
       }
