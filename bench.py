@@ -253,7 +253,9 @@ def aggregate_throughput(dofs, steps, local_ms, dist=None, device="cpu"):
 # again whenever its kernel changes (a workload without an entry reports null).
 FINEST_PASS_DRAM_BYTES = {("channels_256", "warp"): 51.037696e6 + 0.000512e6,
                           # 64^3 RT_0: 9,261 patches of 20 dofs per colour
-                          ("lognormal_3d_64", "warp"): 20.326656e6 + 0.002304e6}
+                          ("lognormal_3d_64", "warp"): 20.326656e6 + 0.002304e6,
+                          # RT_2 on the 256^2 mesh: the persistent block kernel
+                          ("channels_256_rt2", "persistent blocks"): 277.022976e6 + 3.764992e6}
 
 
 def vcycle_model(levels, d, prec, l2_bytes, m_fine=2, variable=True):
