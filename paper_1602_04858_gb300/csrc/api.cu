@@ -482,6 +482,74 @@ mg_status vcycle_graph(mg_handle* h) {
   return MG_OK;
 }
 
+// Time of one whole V-cycle on the handle's level vectors: the graph is
+// captured afresh, replayed once untimed and `reps` times between events, and
+// dropped afterwards (the level vectors' contents are overwritten).
+mg_status time_vcycle(mg_handle* h, int reps, float* ms) {
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  const int64_t l0 = h->launches;
+  TRY(vcycle_graph(h));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaError_t e = cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(h->graph_exec, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(h->graph_exec);
+  h->graph_exec = nullptr;
+  h->launches = l0;
+  if (e != cudaSuccess) return fail(MG_ERR_CUDA, std::string("timed V-cycle: ") + cudaGetErrorString(e));
+  *ms = t / (reps > 0 ? reps : 1);
+  return MG_OK;
+}
+
+// Whole-cycle check of the timed per-level kernel choice (pass_kernel 0 and
+// 4).  Each level's candidates are timed on their own, which misses how its
+// passes overlap the launches around them inside the V-cycle graph, so near
+// ties can go the wrong way.  Every level above the dense fold whose timed
+// choice differs from the fixed rule's (pass_kernel 5) is tried on the rule's
+// choice as well, finest level first, and the choice with the faster whole
+// V-cycle is kept.
+mg_status refine_in_cycle(mg_handle* h, int nrhs) {
+  struct Pick { int var, grp, tpr; };
+  std::vector<Pick> timed(h->J + 1), rule(h->J + 1);
+  for (int j = 1; j <= h->J; ++j) timed[j] = {h->lv[j].pass_cta, h->lv[j].rhs_group, h->lv[j].cta_tpr};
+  TRY(tune_passes(h, 5, nrhs));
+  for (int j = 1; j <= h->J; ++j) rule[j] = {h->lv[j].pass_cta, 4, 4};
+  auto set = [&](int j, const Pick& q) {
+    h->lv[j].pass_cta = q.var;
+    h->lv[j].rhs_group = q.grp;
+    h->lv[j].cta_tpr = q.tpr;
+  };
+  for (int j = 1; j <= h->J; ++j) set(j, timed[j]);
+  float best = 0.f;
+  bool timed_once = false;
+  for (int j = h->J; j > h->Ls && j >= 1; --j) {
+    const Pick& a = timed[j];
+    const Pick& r = rule[j];
+    const bool single = nrhs < 4;
+    if (a.var == r.var && (single || a.grp == r.grp) && (a.var != 1 || a.tpr == r.tpr)) continue;
+    if (!timed_once) {
+      TRY(time_vcycle(h, 10, &best));
+      timed_once = true;
+    }
+    set(j, r);
+    float t = 0.f;
+    TRY(time_vcycle(h, 10, &t));
+    if (t < best) best = t;
+    else set(j, a);
+  }
+  return MG_OK;
+}
+
 // z = B_J r for FP64 device vectors (r, z may not alias).
 // z = B r for the handle's nrhs vectors (one after another, FP64 device).
 mg_status vcycle_dev(mg_handle* h, const double* r, double* z) {
@@ -558,7 +626,7 @@ int mg_pass_tables_check(int dim, int degree, int precision, int n, double mu, c
 // Builds one hierarchy whose level vectors hold nrhs right-hand sides; an
 // automatic dense fold (dense_level = -1) may use at most dense_budget bytes.
 static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs, double dense_budget,
-                                mg_handle** out) {
+                                mg_handle** out, bool whole_cycle_check = false) {
   if (!p || !out) return fail(MG_ERR_INVALID_ARG, "null argument");
   if (nrhs < 1) return fail(MG_ERR_INVALID_ARG, "nrhs must be >= 1");
   *out = nullptr;
@@ -868,6 +936,8 @@ static mg_status setup_internal(const mg_problem* p, void* cuda_stream, int nrhs
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return cleanup(fail(MG_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(cudaGetLastError())));
   if (bad) return cleanup(fail(MG_ERR_BREAKDOWN, "zero pivot in a patch or coarse factorisation"));
+  if (whole_cycle_check && (p->pass_kernel == 0 || p->pass_kernel == 4) && (st = refine_in_cycle(h, nrhs)) != MG_OK)
+    return cleanup(st);
   *out = h;
   return MG_OK;
 }
@@ -876,7 +946,7 @@ extern "C" {
 
 mg_status mg_setup(const mg_problem* p, void* cuda_stream, mg_handle** out) {
   if (p && (p->nrhs < 0 || p->nrhs > 64)) return fail(MG_ERR_INVALID_ARG, "nrhs must be in [0, 64]");
-  return setup_internal(p, cuda_stream, p && p->nrhs > 1 ? p->nrhs : 1, 0.0, out);
+  return setup_internal(p, cuda_stream, p && p->nrhs > 1 ? p->nrhs : 1, 0.0, out, true);
 }
 
 mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p) {

@@ -558,6 +558,16 @@ __device__ __forceinline__ void cp_async_t(T* dst, const T* src, bool ok) {
   else cp_async4(dst, src, ok ? 4u : 0u);
 }
 
+// f(integral_constant<int, I>) for I = 0 .. N-1, each with I a constant expression.
+template <class F, int... I>
+__device__ __forceinline__ void static_for_seq(F&& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  static_for_seq(f, std::make_integer_sequence<int, N>{});
+}
+
 // Plan entries of one lane for one patch type, held in registers.  After
 // rebase() the window columns and cells are byte offsets into shared memory
 // (from the window and cell bases of the lane's patch in stage buffer 0), so
@@ -731,6 +741,21 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     for (int q = 1; q < D + 2; ++q) r = (c == q) ? Pv[q] : r;
     return r;
   };
+  // component offset of this lane's entry in the slot starting at entry F
+  // (gather elements, or patch rows if ROW): chosen by the lane alone where the
+  // slot holds one offset class or two with a single change, else decoded from
+  // the descriptor's component
+  auto slot_offset = [&](auto ROWc, auto Fc, const int (&Pv)[D + 2], int packed) -> int {
+    constexpr bool ROW = decltype(ROWc)::value;
+    constexpr int F = decltype(Fc)::value;
+    if constexpr (P::template slot_static<ROW>(F)) {
+      constexpr int a = P::template cls<ROW>(F), s = P::template slot_split<ROW>(F);
+      if constexpr (s >= LW) return Pv[a];
+      else return lp < s ? Pv[a] : Pv[P::template slot_second<ROW>(F)];
+    } else {
+      return pick(Pv, ROW ? row_comp(packed) : elem_comp(packed));
+    }
+  };
   // (2) asynchronous gather of the window, the patch rows of b and the cells
   //     into stage buffer BI: lane lp takes elements lp + LW i.  The elements
   //     are the window columns (each at its own position), then the patch rows
@@ -742,15 +767,15 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     T* tw = st_T(BI);
     offsets(v, Pv);
     if (act) {
-#pragma unroll
-      for (int i = 0; i < P::EPL; ++i) {
-        const bool win_slot = (i + 1) * LW <= WIN;
-        const bool b_slot = i * LW >= WIN && (i + 1) * LW <= WIN + NV;
+      static_for<P::EPL>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value, f = i * LW;
+        constexpr bool win_slot = f + LW <= WIN;
+        constexpr bool b_slot = f >= WIN && f + LW <= WIN + NV;
         const int pk = el[i].y;
         const int kind = win_slot ? 0 : (b_slot ? 1 : elem_kind(pk));
-        if (kind == 3) continue;
-        const int gi = el[i].x + pick(Pv, elem_comp(pk));
-        const int dst = win_slot ? i * LW + lp : elem_dst(pk);
+        if (kind == 3) return;
+        const int gi = el[i].x + slot_offset(std::false_type{}, std::integral_constant<int, f>{}, Pv, pk);
+        const int dst = win_slot ? f + lp : elem_dst(pk);
         if (kind == 2) {
           cp_async_t(tw + P::OFF_C + dst, L.c + gi, true);
         } else {
@@ -761,7 +786,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
 #pragma unroll
           for (int rr = 0; rr < NR; ++rr) cp_async_t(dd + rr * rs, ok ? base + (gi + rr * vs) : base, ok);
         }
-      }
+      });
     }
     cp_async_commit();
   };
@@ -802,6 +827,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   offsets(vc, Pc);
   if (pg < ngroups) issue_gather(std::integral_constant<int, 0>{}, vc, actc, vmc, Pc);
   int mtype = rtype;   // type of the in-domain mask held in vmc
+  int tcur = rtype;    // type of the current group's patch
   int k = 0;           // groups done by this warp
   // One patch group in stage buffer BI (k even: 0, odd: 1; the loop below runs
   // the two alternately, so every stage address is register + constant).
@@ -812,8 +838,9 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     const int64_t pn = pg + W;
     int vn[D];
     const bool actn = vertex(pn, vn);
+    int tn = tcur;        // type of the next group's patch
     if (pn < ngroups) {   // gather the next group while this one is computed
-      const int tn = patch_type<D>(vn, L.n);
+      tn = patch_type<D>(vn, L.n);
       if (tn != mtype) {
         vmc = __ldg(valp + tn * LW + lp);
         mtype = tn;
@@ -823,7 +850,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     } else {
       cp_async_wait<0>();
     }
-    const int type = patch_type<D>(vc, L.n);
+    const int type = tcur;
     if (type != rtype) {
       R.load(plan_p + (size_t)type * PSum::ZP * LW * PB, plan_m + (size_t)type * PSum::ZM * LW * MASS_BYTES);
       R.rebase(wofs0, cofs0);
@@ -960,11 +987,12 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
     if (lane == 0 && pg + NSB * W < ngroups) issue_S(pg + NSB * W, sb);
     // (5) x|_v = window copy of x|_v + delta, one patch row per lane and step
     if (actc) {
-#pragma unroll
-      for (int it = 0; it < P::NROWIT; ++it) {
+      static_for<P::NROWIT>([&](auto Ic) {
+        constexpr int it = decltype(Ic)::value;
         const int rp = rd[it].y;
-        if (!row_valid(rp)) continue;
-        const int l = lp + LW * it, gi = rd[it].x + pick(Pc, row_comp(rp)), wc = row_wcol(rp);
+        if ((it + 1) * LW > NV && !row_valid(rp)) return;   // rows past the patch
+        const int l = lp + LW * it, wc = row_wcol(rp);
+        const int gi = rd[it].x + slot_offset(std::true_type{}, std::integral_constant<int, it * LW>{}, Pc, rp);
 #pragma unroll
         for (int rr = 0; rr < NR; ++rr) {
           T a = part[rr * PARTS + l];
@@ -973,7 +1001,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
           if constexpr (P::BF) a *= pb[P::OFF_SC + l];
           x[gi + rr * vs] = win[rr * WIN + wc] + a;
         }
-      }
+      });
     }
     __syncwarp();
 #pragma unroll
@@ -981,6 +1009,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
 #pragma unroll
     for (int c = 0; c < D + 2; ++c) Pc[c] = Pn[c];
     actc = actn;
+    tcur = tn;
     ++k;
     pg += W;
     return pg < ngroups;

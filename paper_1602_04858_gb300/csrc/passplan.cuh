@@ -240,6 +240,41 @@ struct PassShape {
   // patch, element e taken by lane e mod LW (EPL per lane)
   static constexpr int NE = WIN + NV + NC;
   static constexpr int EPL = (NE + LW - 1) / LW;
+  // Offset class of gathered element q: the index of the patch's component
+  // offset its array index adds (window columns and patch rows by component,
+  // the pressure with the last velocity component, whose array offset it
+  // shares; cells D + 1); -1 past the last element.  The host builder checks
+  // every element against it.
+  static constexpr int cls_of(int c) { return c < D - 1 ? c : D - 1; }
+  static constexpr int elem_class(int q) {
+    return q < 0 ? -1
+         : q < WIN ? cls_of(q / WU)
+         : q < WIN + NV ? cls_of((q - WIN) / PS::NU1)
+         : q < NE ? D + 1 : -1;
+  }
+  static constexpr int row_class(int l) { return l < NV ? cls_of(l / PS::NU1) : -1; }
+  // A slot (entries f, f + 1, ..., f + LW - 1 over the lanes) whose entries have
+  // one class, or two with a single change at lane split(): its offset is
+  // chosen without decoding the component.  cls(q) is elem_class or row_class.
+  template <bool ROW> static constexpr int cls(int q) { return ROW ? row_class(q) : elem_class(q); }
+  template <bool ROW> static constexpr int slot_split(int f) {
+    for (int l = 1; l < LW; ++l) {
+      const int c = cls<ROW>(f + l);
+      if (c >= 0 && c != cls<ROW>(f)) return l;
+    }
+    return LW;
+  }
+  template <bool ROW> static constexpr int slot_second(int f) {
+    return slot_split<ROW>(f) < LW ? cls<ROW>(f + slot_split<ROW>(f)) : cls<ROW>(f);
+  }
+  template <bool ROW> static constexpr bool slot_static(int f) {
+    if (cls<ROW>(f) < 0) return false;
+    for (int l = slot_split<ROW>(f); l < LW; ++l) {
+      const int c = cls<ROW>(f + l);
+      if (c >= 0 && c != slot_second<ROW>(f)) return false;
+    }
+    return true;
+  }
   static constexpr size_t WARP_BYTES = NSB * STAGE_S + 2 * STAGE_T;
   static constexpr size_t SMEM = (size_t)WARPS * WARP_BYTES + (size_t)WARPS * NSB * sizeof(uint64_t) + 16;
   // per-level tables
@@ -718,7 +753,19 @@ bool build_pass_tables(const Lvl<D, K, T>& L, const Tab<K, T>& tb, std::vector<u
         why = "warp pass element " + std::to_string(q) + " out of its layout position";
         return false;
       }
+      const int c = elem_comp(pk), ecls = c <= D ? P::cls_of(c) : D + 1;
+      if (qkind != 3 && ecls != P::elem_class(q)) {
+        why = "warp pass element " + std::to_string(q) + " of another offset class than its position";
+        return false;
+      }
     }
+    // and a patch row's offset class from the row
+    const int2* rowd = reinterpret_cast<const int2*>(blob.data() + P::TB_ROWD);
+    for (int l = 0; l < P::NV; ++l)
+      if (P::cls_of(row_comp(rowd[l].y)) != P::row_class(l)) {
+        why = "patch row " + std::to_string(l) + " of another offset class than its position";
+        return false;
+      }
   }
   uint32_t* rowp = reinterpret_cast<uint32_t*>(blob.data() + P::TB_ROWP);
   for (int t = 0; t < P::NTYPE; ++t) {
