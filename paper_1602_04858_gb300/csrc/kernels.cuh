@@ -516,7 +516,7 @@ __device__ __forceinline__ void load_rg_smem<__nv_bfloat16, float>(const __nv_bf
 //     lane accumulates its pieces, the row map adds the pieces of a row;
 //  4. delta = S_v r, the columns of S_v split over the lanes (FP32: packed
 //     pair FMAs), partial sums reduced in shared memory;
-//  5. x|_v = (window copy of x|_v) + delta, stored by patch-row segments.
+//  5. x|_v = (window copy of x|_v) + delta, one patch row per lane.
 // ---------------------------------------------------------------------------
 template <typename T> struct PlainLd;
 template <> struct PlainLd<float> {
@@ -661,6 +661,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
   const int g = lane / LW, lp = lane - g * LW;
   unsigned char* wbase = smem + (size_t)warp * P::WARP_BYTES;
   constexpr int NSB = P::NSB;
+  static_assert(NSB == 1 || NSB == 2, "the loop's two copies take inverse buffer k mod NSB from their parity");
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)P::WARPS * P::WARP_BYTES) + warp * NSB;
   const unsigned char* plan_p = tabs + P::TB_PLAIN + (size_t)lp * PB;
   const unsigned char* plan_m = tabs + P::TB_MASS + (size_t)lp * MASS_BYTES;
