@@ -234,10 +234,13 @@ mg_status mg_set_block_limit(mg_handle* h, int blocks);
 mg_status mg_set_residual_history(mg_handle* h, double* host, int capacity);
 
 /* Failure injection for tests of the error paths (not a solver feature): the
- * library's next `after` device allocations succeed and the one after them is
- * refused with MG_ERR_OOM, as if the device had run out of memory; the call
- * that made it fails cleanly and frees what it had allocated.  One refusal per
- * call of this function; after < 0 cancels.  No CUDA call is made. */
+ * next `after` device allocations of the solver (mg_setup, mg_solve and the
+ * batch entry points; not the learned guess's mg_cnn_*) succeed and the one
+ * after them is refused with MG_ERR_OOM, as if the device had run out of
+ * memory; the call that made it fails cleanly and frees what it had allocated
+ * (a Krylov workspace being enlarged is left empty and allocated again by the
+ * next solve).  One refusal per call of this function; after < 0 cancels.  No
+ * CUDA call is made. */
 void mg_inject_alloc_failure(int64_t after);
 
 /* ||b - A_level x||_2 in FP64 (eq. Brinkman-weak; constrained rows give b - x),

@@ -67,6 +67,18 @@ struct VecSet {
   std::vector<void*> X, B, R;
 };
 
+// The two timing events of a solve, destroyed on every return path.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 }  // namespace
 
 mg_status mgd::set_last_error(mg_status s, const std::string& msg) { return fail(s, msg); }
@@ -1180,6 +1192,10 @@ mg_status gm_workspace(mg_handle* h, int m) {
       ++it;
     }
   }
+  // nothing freed stays reachable: a refused allocation below leaves an
+  // empty workspace, which the next solve allocates again
+  h->V = h->Z = h->d_partial = h->d_coef = nullptr;
+  h->gm_m = 0;
   TRY(h->alloc(&h->V, (size_t)(m + 1) * n));
   TRY(h->alloc(&h->Z, (size_t)m * n));
   TRY(h->alloc(&h->d_partial, (size_t)(m + 2) * multidot_blocks()));
@@ -1236,10 +1252,10 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
   const int64_t n = L.ndof, nu = L.n_u, np = L.n_p;
   if (restart <= 0 || restart > maxit) restart = maxit > 0 ? maxit : 1;
   TRY(gm_workspace(h, restart));
-  cudaEvent_t e0, e1;
-  CU(cudaEventCreate(&e0));
-  CU(cudaEventCreate(&e1));
-  CU(cudaEventRecord(e0, h->stream));
+  EventPair ev;
+  CU(cudaEventCreate(&ev.e0));
+  CU(cudaEventCreate(&ev.e1));
+  CU(cudaEventRecord(ev.e0, h->stream));
   double* b = h->t64[2];
   double* xd = h->t64[3];
   double* w = h->t64[0];
@@ -1384,12 +1400,10 @@ mg_status mg_solve(mg_handle* h, const double* f, const double* g, double* x, in
     ++h->launches;
   }
   CU(cudaMemcpyAsync(x, xd, n * sizeof(double), xdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaEventRecord(e1, h->stream));
+  CU(cudaEventRecord(ev.e1, h->stream));
   CU(cudaStreamSynchronize(h->stream));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   if (stats) {
     stats->iterations = its;
     stats->converged = converged ? 1 : 0;
@@ -1490,6 +1504,7 @@ struct mg_batch {
   }
   template <typename T>
   mg_status alloc(T** p, size_t count) {
+    if (alloc_refused()) return fail(MG_ERR_OOM, "device allocation refused (failure injection)");
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
     if (e != cudaSuccess)
@@ -1876,10 +1891,14 @@ mg_status mg_setup_batch(const mg_problem* problems, int nprob, int nrhs, void* 
     delete B;
     return st;
   }
-  cudaMemcpy(B->seg.bseg, bseg.data(), bseg.size() * sizeof(int), cudaMemcpyHostToDevice);
-  cudaMemcpy(B->seg.bstart, bs.data(), bs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-  cudaMemcpy(B->seg.bend, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
-  cudaMemcpy(B->seg.sfirst, sfirst.data(), sfirst.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (cudaMemcpy(B->seg.bseg, bseg.data(), bseg.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(B->seg.bstart, bs.data(), bs.size() * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(B->seg.bend, be.data(), be.size() * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(B->seg.sfirst, sfirst.data(), sfirst.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    st = fail(MG_ERR_CUDA, std::string("batch segment tables: ") + cudaGetErrorString(cudaGetLastError()));
+    delete B;
+    return st;
+  }
   *out = B;
   return MG_OK;
 }
@@ -1957,6 +1976,10 @@ mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, 
         ++it;
       }
     }
+    // as for a single handle: no freed buffer stays reachable if an
+    // allocation below is refused
+    B->V = B->Z = B->w = B->r = B->bb = B->xx = B->partial = B->coef = nullptr;
+    B->gm_m = 0;
     TRY(B->alloc(&B->V, (size_t)(m + 1) * n));
     TRY(B->alloc(&B->Z, (size_t)m * n));
     TRY(B->alloc(&B->w, n));
@@ -1968,10 +1991,10 @@ mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, 
     B->gm_m = m;
   }
   TRY(batch_graph(B));
-  cudaEvent_t e0, e1;
-  CU(cudaEventCreate(&e0));
-  CU(cudaEventCreate(&e1));
-  CU(cudaEventRecord(e0, B->stream));
+  EventPair ev;
+  CU(cudaEventCreate(&ev.e0));
+  CU(cudaEventCreate(&ev.e1));
+  CU(cudaEventRecord(ev.e0, B->stream));
   CU(cudaMemcpyAsync(B->bb, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
   if (use_x0) CU(cudaMemcpyAsync(B->xx, x, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
   else CU(cudaMemsetAsync(B->xx, 0, n * sizeof(double), B->stream));
@@ -2082,12 +2105,10 @@ mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, 
     ++B->launches;
   }
   CU(cudaMemcpyAsync(x, B->xx, n * sizeof(double), cudaMemcpyDeviceToDevice, B->stream));
-  CU(cudaEventRecord(e1, B->stream));
+  CU(cudaEventRecord(ev.e1, B->stream));
   CU(cudaStreamSynchronize(B->stream));
   float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   TRY(take_batch_flags(B));
   bool all = true;
   for (int s = 0; s < ns; ++s) {
@@ -2099,6 +2120,7 @@ mg_status mg_solve_batch(mg_batch* B, const double* rhs, double* x, int use_x0, 
       stats[s].initial_rel_residual = rel0[s] < 0 ? 0.0 : rel0[s];
       stats[s].removed_flux = 0.0;
       stats[s].solve_ms = ms;
+      stats[s].escalated_at = -1;   // batches do not escalate
     }
   }
   return all ? MG_OK : fail(MG_ERR_NOT_CONVERGED, "some systems of the batch reached maxit");

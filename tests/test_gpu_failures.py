@@ -161,3 +161,25 @@ def test_refused_allocation_in_solve_leaves_handle_usable():
         mgdarcy.inject_alloc_failure(-1)
     st, status = G.solve(f, g, x, tol=1e-8, maxit=50)
     assert status == 0 and st.converged
+
+
+def test_refused_workspace_growth_keeps_no_freed_buffer():
+    """A solve with a larger restart frees the Krylov workspace before it
+    allocates the larger one.  If one of those allocations is refused, the
+    handle must hold no freed buffer: a later solve with the old, smaller
+    restart allocates again and repeats the first solve's result."""
+    G = make()
+    f, g = load(G)
+    x0 = torch.zeros(G.ndof(), dtype=torch.float64, device="cuda")
+    st0, status0 = G.solve(f, g, x0, tol=1e-8, maxit=60, restart=10, check=False)
+    x = torch.zeros_like(x0)
+    mgdarcy.inject_alloc_failure(1)            # the second buffer of the larger workspace
+    try:
+        _, status = G.solve(f, g, x, tol=1e-8, maxit=60, restart=30, check=False)
+        assert status == OOM
+    finally:
+        mgdarcy.inject_alloc_failure(-1)
+    x1 = torch.zeros_like(x0)
+    st1, status1 = G.solve(f, g, x1, tol=1e-8, maxit=60, restart=10, check=False)
+    assert status1 == status0 and st1.iterations == st0.iterations
+    assert torch.max(torch.abs(x1 - x0)).item() <= 1e-12 * torch.max(torch.abs(x0)).item()
