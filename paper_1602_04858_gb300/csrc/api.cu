@@ -364,7 +364,12 @@ mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
       L.pass_cta = std::max(L.pass_cta, first);
       continue;
     }
-    const std::vector<int> key = {h->device, h->d, h->k, L.n, L.sprec, h->prec, nrhs, L.mu == 0.0 ? 1 : 0};
+    // the timed passes depend on the launch shape (problems of a group, right-
+    // hand sides) and on the smoother's options as well as on the level
+    int bpatches = 0;
+    for (int col = 0; col < num_colours(h->d); ++col) bpatches = bpatches || L.bcount[col] > 0;
+    const std::vector<int> key = {h->device, h->d, h->k, L.n, L.sprec, h->prec, nrhs, L.mu == 0.0 ? 1 : 0,
+                                  h->grp_nprob, h->additive > 0.0 ? 1 : 0, bpatches};
     {
       std::lock_guard<std::mutex> g(mu);
       auto it = cache.find(key);

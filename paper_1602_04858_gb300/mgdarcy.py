@@ -165,6 +165,16 @@ def _ptr(a, dtype="float64"):
     return a.data_ptr()
 
 
+def _need(a, count, what):
+    """The C interface takes bare pointers: refuse a buffer shorter than the
+    entries the call reads or writes (None passes, for optional arguments)."""
+    if a is None:
+        return
+    n = a.size if isinstance(a, np.ndarray) else a.numel()
+    if n < count:
+        raise ValueError(f"{what} has {n} entries, the call needs {count}")
+
+
 def _check(status):
     if status != MG_OK:
         raise MGError(status, load().mg_last_error().decode())
@@ -215,6 +225,7 @@ class Multigrid:
                  escalate_window=0, boundary_patches=False, nrhs=1, stream=None):
         lib = load()
         self._keep = c if not isinstance(c, np.ndarray) else np.ascontiguousarray(c, dtype=np.float64)
+        _need(self._keep, (int(n_coarse) << (int(n_levels) - 1)) ** int(dim), "c (one value per finest cell)")
         prob = mg_problem(dim, n_coarse, n_levels, degree, float(mu), _ptr(self._keep),
                           PREC[precision] if isinstance(precision, str) else int(precision), int(m_fine),
                           1 if variable_cycle else 0, int(coarse_avg), int(dense_level), int(pass_kernel),
@@ -226,6 +237,7 @@ class Multigrid:
         self.n_coarse = n_coarse
         self.precision = precision
         self.nrhs = int(nrhs)
+        self._nd = {}
 
     def close(self):
         if getattr(self, "h", None):
@@ -247,16 +259,35 @@ class Multigrid:
         nu, np_ = self.sizes(level)
         return nu + np_
 
+    def _sizes(self, level):
+        """mg_sizes of a level, cached (the argument checks of every call use it)."""
+        if level not in self._nd:
+            self._nd[level] = self.sizes(level)
+        return self._nd[level]
+
+    def _vec(self, level, *named):
+        n = sum(self._sizes(level))
+        for what, a in named:
+            _need(a, n, what)
+
     def apply(self, x, y, level=-1):
+        self._vec(level, ("x", x), ("y", y))
         _check(load().mg_apply(self.h, level, _ptr(x), _ptr(y)))
 
     def vcycle(self, r, z):
+        n = sum(self._sizes(-1)) * max(1, self.nrhs)
+        _need(r, n, "r")
+        _need(z, n, "z")
         _check(load().mg_vcycle(self.h, _ptr(r), _ptr(z)))
 
     def solve(self, f, g, x, use_x0=False, tol=1e-8, maxit=200, restart=0, check=True, history=None):
         """mg_solve; history: None or a float64 NumPy array that receives the
         relative residual after each iteration (mg_set_residual_history)."""
         lib = load()
+        nu, np_ = self._sizes(-1)
+        _need(f, nu, "f")
+        _need(g, np_, "g")
+        _need(x, nu + np_, "x")
         st = mg_stats()
         if history is not None:
             _check(lib.mg_set_residual_history(self.h, _ptr(history), int(history.size)))
@@ -354,6 +385,7 @@ class Multigrid:
 
     def residual_norm(self, x, b, r=None, level=-1):
         """||b - A x||_2 (FP64) of device tensors; also stores r = b - A x if given."""
+        self._vec(level, ("x", x), ("b", b), ("r", r))
         out = ctypes.c_double()
         _check(load().mg_residual_norm(self.h, level, _ptr(x), _ptr(b), _ptr(r), ctypes.addressof(out)))
         return out.value
@@ -379,6 +411,8 @@ class Batch:
         self._keep = []
         for k, p in enumerate(problems):
             c = p["c"]
+            _need(c, (int(p["n_coarse"]) << (int(p["n_levels"]) - 1)) ** int(p["dim"]),
+                  f"problem {k}: c (one value per finest cell)")
             self._keep.append(c)
             prec = p.get("precision", "fp32")
             arr[k] = mg_problem(p["dim"], p["n_coarse"], p["n_levels"], p["degree"], float(p["mu"]), _ptr(c),
@@ -420,9 +454,15 @@ class Batch:
         return k.value, g.value, t.value
 
     def vcycle(self, r, z):
+        n = self.total()
+        _need(r, n, "r")
+        _need(z, n, "z")
         _check(load().mg_vcycle_batch(self.h, _ptr(r), _ptr(z)))
 
     def solve(self, rhs, x, use_x0=False, tol=1e-8, maxit=200, restart=20, check=True):
+        n = self.total()
+        _need(rhs, n, "rhs")
+        _need(x, n, "x")
         st = (mg_stats * (self.nprob * self.nrhs))()
         status = load().mg_solve_batch(self.h, _ptr(rhs), _ptr(x), 1 if use_x0 else 0, float(tol), int(maxit),
                                        int(restart), st)

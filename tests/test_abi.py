@@ -109,3 +109,19 @@ def test_escalate_window_is_validated(lib):
     p = mgdarcy.mg_problem(2, 2, 3, 0, 1.0, c.ctypes.data, 1, 2, 1, 0, 0, 0, 0.0, 1000000)
     h = ctypes.c_void_p()
     assert lib.mg_setup(ctypes.byref(p), None, ctypes.byref(h)) == 1
+
+
+def test_binding_refuses_short_buffers(lib):
+    """The C interface takes bare pointers, so the binding checks each
+    buffer's length against what the call reads or writes before calling:
+    a coefficient array with fewer values than finest cells is refused before
+    any set-up runs (no GPU needed), for a single problem and in a batch."""
+    with pytest.raises(ValueError, match="c "):
+        mgdarcy.Multigrid(2, 2, 3, 0, 1.0, np.ones(63))
+    with pytest.raises(ValueError, match="problem 1"):
+        mgdarcy.Batch([dict(dim=2, n_coarse=2, n_levels=3, degree=0, mu=1.0, c=np.ones(64)),
+                       dict(dim=3, n_coarse=2, n_levels=2, degree=0, mu=0.0, c=np.ones(63))])
+    mgdarcy._need(np.ones(5), 5, "x")
+    mgdarcy._need(None, 5, "r")
+    with pytest.raises(ValueError, match="x has 4 entries"):
+        mgdarcy._need(np.ones(4), 5, "x")
