@@ -19,6 +19,9 @@ heterogeneous porous media", arXiv:1602.04858, that it follows):
                  multiplicative Schwarz smoother (Sec. 3.3, eq.
                  smoother-Multiplicative), the (variable) V-cycle (Sec. 3.2).
 * ``krylov``     right-preconditioned flexible GMRES (Sec. 3.2, Sec. 4.1).
+* ``cnn``        FP64 reference of the learned-initial-guess network (not in
+                 the paper): 3x3 convolutions, ReLU, mean squared error and
+                 their gradients, in plain loops and NumPy.
 
 Parity unpinned: the GMRES iteration counts of the paper's Tables 1-4 (their
 permeability fields are not available), only their trend is checked.
