@@ -161,3 +161,45 @@ def test_3d_64_solve_reaches_1e8(darcy3d_64, prec):
     b = torch.cat([f, g])
     res = G.residual_norm(x, b) / float(torch.linalg.vector_norm(b))
     assert st.converged == 1 and res <= 1.01e-8
+
+
+def _literal_system(w, G):
+    """The benchmark workload with its literal right-hand side f = (1, 0),
+    g = 0 and no-slip walls, and that system's exact discrete solution:
+    f = grad x is balanced by the pressure alone, so u_h = 0 and
+    p_h = Pi_Q x - 1/2 for any coefficient c and any mu (Pi_Q x = x for
+    k >= 1; zero weighted mean, as the solver returns it).  The pressure
+    nodes are the Gauss points of each cell, x fastest."""
+    n, k = w["n_coarse"] << (w["n_levels"] - 1), w["degree"]
+    nu, npr = G.sizes()
+    f = torch.zeros((2, n * n), dtype=torch.float64, device="cuda")
+    f[0] = 1.0
+    b = torch.zeros(nu + npr, dtype=torch.float64, device="cuda")
+    G.load_vector(f, None, b)
+    t, _ = np.polynomial.legendre.leggauss(k + 1)
+    ix = np.arange(n * (k + 1))
+    xc = (ix // (k + 1) + (1.0 + t[ix % (k + 1)]) / 2.0) / n
+    xe = np.zeros(nu + npr)
+    xe[nu:] = np.tile(xc, n * (k + 1)) - 0.5
+    return b, torch.as_tensor(xe, device="cuda"), nu
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_literal_rhs_has_its_closed_form_solution(prec):
+    """At the full benchmark size, where the oracle cannot solve: the exact
+    solution's residual through the library's operator and load vector is
+    rounding (1e-14 relative in the oracle at 32^2-64^2), and the solve to
+    1e-10 lands on it.  From a residual of 1e-10 ||b||, the error bound
+    through the contrast-1e6 Schur complement is about 5e-7 in p; a wrong
+    pressure-gradient term, load vector or pressure normalisation is off by
+    O(0.1)."""
+    w = inputs.workload("channels_256")
+    G = _gpu(w, prec)
+    b, xe, nu = _literal_system(w, G)
+    bn = float(torch.linalg.vector_norm(b))
+    assert G.residual_norm(xe, b) <= 1e-11 * bn
+    x = torch.zeros_like(b)
+    st, _ = G.solve(b[:nu].contiguous(), b[nu:].contiguous(), x, tol=1e-10, maxit=400)
+    assert st.converged
+    assert torch.max(torch.abs(x[:nu])).item() <= 1e-5
+    assert torch.max(torch.abs(x[nu:] - xe[nu:])).item() <= 1e-5
