@@ -94,7 +94,8 @@ typedef struct {
                            three, timed at setup on the level itself (two
                            symmetric smoothing steps as a CUDA graph, see
                            mg_time_passes; cached per level shape, precision,
-                           right-hand sides and device; a level whose timed
+                           right-hand sides, problems of a batch group,
+                           smoother options and device; a level whose timed
                            choice differs from the rule of 5 keeps it only if
                            the whole V-cycle is faster with it, finest level
                            first, mg_setup only), 5: a fixed rule

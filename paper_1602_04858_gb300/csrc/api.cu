@@ -268,24 +268,6 @@ const DKOps* ops_for(int d, int k) {
 
 int m_of(const mg_handle* h, int j) { return h->variable ? h->m_fine << (h->J - j) : h->m_fine; }
 
-// Sets the colour-pass kernel of every level (HostLevel::pass_cta: 0 warp
-// per patch, 1 block per patch, 2 persistent blocks).  All compute the same
-// update up to rounding.  A warp per patch, persistent over the colour, keeps
-// the copies of the patch inverses streaming and suits levels whose passes
-// fill the GPU; a block per patch shortens the latency of one patch update,
-// which is what a pass costs on coarse levels; persistent blocks load their
-// tables once and overlap the next patch's copies with the current one.
-// Modes: 1 warp, 2 block, 3 persistent blocks everywhere; 5 a fixed rule:
-// block per patch on levels whose largest colour holds at most 10,000 inverse
-// entries (n_v^2 per patch) per SM, warp per patch elsewhere (the crossover
-// measured on GB300 for FP32: 2-D RT_1 colours of 441 patches and 3-D RT_0
-// colours of 1,103 favour the block, 2-D RT_1 colours of 1,800 patches the
-// warp), and block per patch on every level when four or more right-hand
-// sides share the inverses; 0 (default) and 4 time each kernel on the level's own vectors (two symmetric smoothing
-// steps captured as a CUDA graph and replayed three times, as the passes run
-// back to back inside the V-cycle graph) and keeps the fastest, the choice
-// cached per level shape and device (timings taken under a profiler that
-// serialises kernels can change it).
 // Time of `steps` smoothing steps of level j on the level's own vectors (their
 // contents are overwritten), captured once as a CUDA graph and replayed `reps`
 // times between CUDA events after one untimed replay, so that the launches run
@@ -336,6 +318,27 @@ mg_status time_smoothing(mg_handle* h, int j, int nrhs, int steps, int reps, flo
   return MG_OK;
 }
 
+// Sets the colour-pass kernel of every level (HostLevel::pass_cta: 0 warp
+// per patch, 1 block per patch, 2 persistent blocks).  All compute the same
+// update up to rounding.  A warp per patch, persistent over the colour, keeps
+// the copies of the patch inverses streaming and suits levels whose passes
+// fill the GPU; a block per patch shortens the latency of one patch update,
+// which is what a pass costs on coarse levels; persistent blocks load their
+// tables once and overlap the next patch's copies with the current one.
+// Modes: 1 warp, 2 block, 3 persistent blocks everywhere; 5 a fixed rule:
+// block per patch on levels whose largest colour holds at most 10,000 inverse
+// entries (n_v^2 per patch) per SM, warp per patch elsewhere (the crossover
+// measured on GB300 for FP32: 2-D RT_1 colours of 441 patches and 3-D RT_0
+// colours of 1,103 favour the block, 2-D RT_1 colours of 1,800 patches the
+// warp), and block per patch on every level when four or more right-hand
+// sides share the inverses; 0 (default) and 4 time each kernel on the level's
+// own vectors (two symmetric smoothing steps captured as a CUDA graph and
+// replayed three times, as the passes run back to back inside the V-cycle
+// graph) and keep the fastest, the choice cached per level shape, launch
+// shape, smoother options and device (timings taken under a profiler that
+// serialises kernels can change it); 6, 7, 8 force warp, block or persistent
+// blocks with every right-hand side on its own; 9, 10 the block kernel with
+// 2 or 8 threads per patch row.
 mg_status tune_passes(mg_handle* h, int mode, int nrhs) {
   static std::mutex mu;
   static std::map<std::vector<int>, int> cache;
