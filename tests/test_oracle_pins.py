@@ -520,26 +520,38 @@ def test_boundary_patch_vcycle_against_dense_construction(d, k):
     assert np.max(np.abs(Bf - Bf.T)) < 1e-12 * np.max(np.abs(Bf))
 
 
-@pytest.mark.parametrize("d,k", [(2, 0), (2, 1)])
-def test_variable_cycle_smoothing_counts_against_dense_construction(d, k):
+# (d, k, levels, smoothing steps per level of the variable cycle with m(J) = 2,
+#  plausible miscounts); the counts written out by hand from Sec. 3.2
+SMOOTHING_COUNT_CASES = [
+    (2, 0, 3, {2: 2, 1: 4}, ({2: 4, 1: 2}, {2: 8, 1: 4}, {2: 2, 1: 8})),
+    (2, 1, 3, {2: 2, 1: 4}, ({2: 4, 1: 2}, {2: 8, 1: 4}, {2: 2, 1: 8})),
+    # four levels: m(j) = 2, 4, 8; a count linear in the depth (2, 4, 6)
+    # agrees with the doubling on three levels and differs only here
+    (2, 0, 4, {3: 2, 2: 4, 1: 8}, ({3: 2, 2: 4, 1: 6}, {3: 2, 2: 8, 1: 4}, {3: 4, 2: 8, 1: 16})),
+]
+
+
+@pytest.mark.parametrize("d,k,L,counts,wrong", SMOOTHING_COUNT_CASES, ids=["rt0-3", "rt1-3", "rt0-4"])
+def test_variable_cycle_smoothing_counts_against_dense_construction(d, k, L, counts, wrong):
     """Sec. 3.2, variable V-cycle: m(j) doubles on each coarser level.  Three
-    levels (2x2 -> 4x4 -> 8x8) with m(J) = 2: two smoothing steps on the finest
-    level and four on the middle one, written out here by hand, against the
-    oracle's vcycle; the standard cycle takes two on both.  A count off by a
-    factor of two on either level fails."""
-    H = _hier(d, k, 2, 3, 0.3, seed=14, sigma_c=1.5)
+    levels (2x2 -> 4x4 -> 8x8) or four (-> 16x16) with m(J) = 2: the smoothing
+    steps of each level written out by hand (2 on the finest, then 4, then 8)
+    against the oracle's vcycle; the standard cycle takes two on every level.
+    The plausible miscounts listed with each case (a factor of two off on one
+    level, a count growing linearly with the depth) give another operator."""
+    H = _hier(d, k, 2, L, 0.3, seed=14, sigma_c=1.5)
     LJ = H.levels[-1]
     b = np.random.default_rng(15).standard_normal(LJ.S.ndof)
     b[LJ.cm] = 0.0
     scale = None
-    for variable, counts in ((True, {2: 2, 1: 4}), (False, {2: 2, 1: 2})):
-        x = _dense_ritz_vcycle(H, counts, b)
+    for variable, cnt in ((True, counts), (False, {j: 2 for j in counts})):
+        x = _dense_ritz_vcycle(H, cnt, b)
         z = mg.vcycle(H, b, m_fine=2, variable=variable)
         scale = np.max(np.abs(x))
         assert np.max(np.abs(z - x)) < 1e-10 * scale
     # the comparison separates the plausible miscounts
-    for wrong in ({2: 4, 1: 2}, {2: 8, 1: 4}, {2: 2, 1: 8}):
-        x = _dense_ritz_vcycle(H, wrong, b)
+    for w in wrong:
+        x = _dense_ritz_vcycle(H, w, b)
         assert np.max(np.abs(mg.vcycle(H, b, m_fine=2, variable=True) - x)) > 1e-6 * scale
 
 
@@ -554,6 +566,33 @@ def test_fgmres_matches_dense_solve():
     x, its, hist = krylov.fgmres(lambda v: A @ v, lambda v: M @ v, b, tol=1e-13, maxit=200, restart=25)
     assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
     assert hist[-1] <= 1e-13
+
+
+def test_fgmres_residual_is_the_krylov_minimum():
+    """GMRES optimality, the property the outer solver of Sec. 3.2 rests on:
+    from x0 = 0 with a fixed right preconditioner M, the residual after k
+    iterations is the minimum of ||b - A M y|| over the Krylov space
+    K_k(A M, b), here from a dense least-squares solve on a QR basis of that
+    space.  A wrong Gram-Schmidt coefficient, Givens rotation or update basis
+    leaves a residual above the minimum."""
+    rng = np.random.default_rng(21)
+    n = 40
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) * 0.4
+    M = np.diag(1.0 / (np.diag(A) + 0.5 * rng.uniform(size=n)))
+    b = rng.standard_normal(n)
+    AM = A @ M
+    for k in range(1, 9):
+        x, its, _ = krylov.fgmres(lambda v: A @ v, lambda v: M @ v, b, tol=1e-300, maxit=k, restart=k)
+        assert its == k
+        K = np.empty((n, k))
+        v = b.copy()
+        for i in range(k):
+            K[:, i] = v
+            v = AM @ v
+        Q, _ = np.linalg.qr(K)
+        y = np.linalg.lstsq(AM @ Q, b, rcond=None)[0]
+        rmin = np.linalg.norm(b - AM @ Q @ y)
+        assert abs(np.linalg.norm(b - A @ x) - rmin) <= 1e-10 * rmin, k
 
 
 @pytest.mark.parametrize("k", [0, 1])
