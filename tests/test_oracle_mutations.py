@@ -25,16 +25,17 @@ def must_fail(pin, *args):
         pin(*args)
 
 
-def mutant(module, name, *edits):
-    """The oracle function module.name with each (old, new) of `edits` made in
-    its source (every `old` found exactly once), compiled in a copy of the
-    module's namespace."""
-    src = textwrap.dedent(inspect.getsource(getattr(module, name)))
+def mutant(owner, name, *edits):
+    """The oracle function owner.name (owner a module or a class) with each
+    (old, new) of `edits` made in its source (every `old` found exactly once),
+    compiled in a copy of the namespace of the module that defines it."""
+    fn = getattr(owner, name)
+    src = textwrap.dedent(inspect.getsource(fn))
     for old, new in edits:
         assert src.count(old) == 1, (name, old)
         src = src.replace(old, new)
-    ns = dict(vars(module))
-    exec(compile(src, f"<planted {module.__name__}.{name}>", "exec"), ns)
+    ns = dict(fn.__globals__)
+    exec(compile(src, f"<planted {owner.__name__}.{name}>", "exec"), ns)
     return ns[name]
 
 
@@ -118,6 +119,14 @@ def test_nitsche_boundary_data_sign(monkeypatch):
     """The boundary-data term -mu <dv/dn, g> of F (eq. BCh) with the wrong sign."""
     plant(monkeypatch, fem, "load_vector", "- mu * nu * D[a]", "+ mu * nu * D[a]")
     must_fail(pins.test_polynomial_reproduction, 2, 1, 4, 1.0)
+
+
+def test_pressure_weights_missing_cell_measure(monkeypatch):
+    """w_i = (1, q_i) without the h^d of the cell: the pressure rows built from
+    them no longer integrate the source."""
+    monkeypatch.setattr(fem.Space, "pressure_weights", mutant(
+        fem.Space, "pressure_weights", ("np.ones(idx.shape[0]) * self.h ** self.d", "np.ones(idx.shape[0])")))
+    must_fail(pins.test_divergence_is_exact_pointwise, 2, 1, 3)
 
 
 # --- right-hand side: eq. (BCh), the divergence source ----------------------------
