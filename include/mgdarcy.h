@@ -174,7 +174,8 @@ void mg_destroy(mg_handle* h);
 mg_status mg_sizes(const mg_handle* h, int level, int64_t* n_u, int64_t* n_p);
 
 /* y = A_level x (FP64), the operator of eq. (Brinkman-weak) on level `level`
- * (-1: finest).  x, y: host or device, length n_u + n_p, must not alias. */
+ * (-1: finest).  x, y: host or device, length n_u + n_p, must not alias
+ * (the same pointer: MG_ERR_INVALID_ARG). */
 mg_status mg_apply(mg_handle* h, int level, const double* x, double* y);
 
 /* z = B_J r: one V-cycle of Sec. 3.2 with zero initial guess, in the handle's
@@ -374,7 +375,8 @@ mg_status mg_cnn_guess(mg_cnn* net, const double* c, const double* f, double* x0
 
 /* x <- x + R_j (b - A_j x): `steps` symmetric multiplicative Schwarz
  * steps (eq. smoother-Multiplicative) on level `level` >= 1, in the handle's
- * precision.  x, b: device, FP64, length n_u + n_p of that level. */
+ * precision.  x, b: device, FP64, length n_u + n_p of that level (a host
+ * pointer: MG_ERR_INVALID_ARG). */
 mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int steps);
 
 /* One colour pass of the smoother (the patches of one colour, Sec. 3.3):
@@ -383,20 +385,24 @@ mg_status mg_smooth(mg_handle* h, int level, double* x, const double* b, int ste
  * handle's internal level vectors (loaded with mg_level_load).  For timing. */
 mg_status mg_colour_pass(mg_handle* h, int level, int colour);
 
-/* Copies FP64 x, b (device, level sizes) into the handle's level vectors in
- * the handle's precision, and back (mg_level_store copies x out). */
+/* Copies FP64 x, b (device, level sizes; either may be NULL in mg_level_load)
+ * into the handle's level vectors in the handle's precision, and back
+ * (mg_level_store copies x out).  A host pointer: MG_ERR_INVALID_ARG. */
 mg_status mg_level_load(mg_handle* h, int level, const double* x, const double* b);
 mg_status mg_level_store(mg_handle* h, int level, double* x);
 
 /* b_{level-1} = P^T r (eq. 3, transpose of the injection of Sec. 3.1) with
- * the constrained rows of r and of the result taken as zero.  FP64, device. */
+ * the constrained rows of r and of the result taken as zero.  FP64, device
+ * (a host pointer: MG_ERR_INVALID_ARG). */
 mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_coarse);
 
-/* x_fine += P x_coarse (the natural injection of Sec. 3.1).  FP64, device. */
+/* x_fine += P x_coarse (the natural injection of Sec. 3.1).  FP64, device
+ * (a host pointer: MG_ERR_INVALID_ARG). */
 mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double* x_fine);
 
 /* x = A_0^{-1} b on the free dofs of level 0 with zero pressure mean,
- * x = 0 on the constrained dofs.  FP64, device. */
+ * x = 0 on the constrained dofs.  FP64, device (a host pointer:
+ * MG_ERR_INVALID_ARG). */
 mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x);
 
 /* Patch counts: number of patches of `colour` on `level` and their size n_v. */

@@ -1041,6 +1041,7 @@ mg_status mg_level_row_threads(const mg_handle* h, int level, int* threads) {
 
 mg_status mg_apply(mg_handle* h, int level, const double* x, double* y) {
   if (!h || !x || !y) return fail(MG_ERR_INVALID_ARG, "null argument");
+  if (x == y) return fail(MG_ERR_INVALID_ARG, "x and y must not alias");
   if (level < 0) level = h->J;
   if (level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
   const int64_t n = h->lv[level].ndof;
@@ -1082,6 +1083,8 @@ mg_status mg_vcycle(mg_handle* h, const double* r, double* z) {
 
 mg_status mg_level_load(mg_handle* h, int level, const double* x, const double* b) {
   if (!h || level < 0 || level > h->J) return fail(MG_ERR_INVALID_ARG, "bad level");
+  if ((x && !is_device_ptr(x)) || (b && !is_device_ptr(b)))
+    return fail(MG_ERR_INVALID_ARG, "x and b must be device pointers");
   HostLevel& L = h->lv[level];
   if (h->prec == P64) {
     if (x) CU(cudaMemcpyAsync(L.X, x, L.ndof * 8, cudaMemcpyDeviceToDevice, h->stream));
@@ -1096,6 +1099,7 @@ mg_status mg_level_load(mg_handle* h, int level, const double* x, const double* 
 
 mg_status mg_level_store(mg_handle* h, int level, double* x) {
   if (!h || level < 0 || level > h->J || !x) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  if (!is_device_ptr(x)) return fail(MG_ERR_INVALID_ARG, "x must be a device pointer");
   HostLevel& L = h->lv[level];
   if (h->prec == P64) CU(cudaMemcpyAsync(x, L.X, L.ndof * 8, cudaMemcpyDeviceToDevice, h->stream));
   else { launch_f2d((const float*)L.X, x, L.ndof, h->stream); ++h->launches; }
@@ -1125,6 +1129,8 @@ mg_status mg_colour_pass(mg_handle* h, int level, int colour) {
 
 mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_coarse) {
   if (!h || level < 1 || level > h->J || !r_fine || !b_coarse) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  if (!is_device_ptr(r_fine) || !is_device_ptr(b_coarse))
+    return fail(MG_ERR_INVALID_ARG, "r_fine and b_coarse must be device pointers");
   h->ops->restrict_(h->lv[level], h->lv[level - 1], 0, r_fine, b_coarse, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
@@ -1133,6 +1139,8 @@ mg_status mg_restrict(mg_handle* h, int level, const double* r_fine, double* b_c
 
 mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double* x_fine) {
   if (!h || level < 1 || level > h->J || !x_coarse || !x_fine) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  if (!is_device_ptr(x_coarse) || !is_device_ptr(x_fine))
+    return fail(MG_ERR_INVALID_ARG, "x_coarse and x_fine must be device pointers");
   h->ops->prolong_add(h->lv[level], h->lv[level - 1], 0, x_coarse, x_fine, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());
@@ -1141,6 +1149,7 @@ mg_status mg_prolong_add(mg_handle* h, int level, const double* x_coarse, double
 
 mg_status mg_coarse_solve(mg_handle* h, const double* b, double* x) {
   if (!h || !b || !x) return fail(MG_ERR_INVALID_ARG, "bad argument");
+  if (!is_device_ptr(b) || !is_device_ptr(x)) return fail(MG_ERR_INVALID_ARG, "b and x must be device pointers");
   launch_coarse_apply(h->d_inv0, h->d_free0, h->nf0, h->lv[0].ndof, 0, b, x, 1, h->stream);
   ++h->launches;
   CU(cudaGetLastError());

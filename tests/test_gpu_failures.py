@@ -183,3 +183,30 @@ def test_refused_workspace_growth_keeps_no_freed_buffer():
     st1, status1 = G.solve(f, g, x1, tol=1e-8, maxit=60, restart=10, check=False)
     assert status1 == status0 and st1.iterations == st0.iterations
     assert torch.max(torch.abs(x1 - x0)).item() <= 1e-12 * torch.max(torch.abs(x0)).item()
+
+
+def test_device_only_steps_refuse_host_pointers():
+    """The single-step entry points take device vectors only: a host array is
+    refused with MG_ERR_INVALID_ARG before any kernel sees it, and so is
+    mg_apply with x and y the same buffer.  The handle works normally
+    afterwards."""
+    G = make(precision="fp64")
+    n1, n0, nJ = G.ndof(1), G.ndof(0), G.ndof()
+    hx, hc = np.zeros(n1), np.zeros(n0)
+    dx = torch.zeros(n1, dtype=torch.float64, device="cuda")
+    dc = torch.zeros(n0, dtype=torch.float64, device="cuda")
+    calls = [lambda: G.restrict(1, hx, dc), lambda: G.restrict(1, dx, hc), lambda: G.prolong_add(1, hc, dx),
+             lambda: G.coarse_solve(hc, dc), lambda: G.smooth(1, hx, dx), lambda: G.level_load(1, hx, None),
+             lambda: G.level_store(1, hx)]
+    y = torch.zeros(nJ, dtype=torch.float64, device="cuda")
+    calls.append(lambda: G.apply(y, y))
+    for call in calls:
+        with pytest.raises(mgdarcy.MGError) as e:
+            call()
+        assert e.value.status == 1
+    torch.cuda.synchronize()
+    x = torch.as_tensor(np.random.default_rng(5).standard_normal(nJ), device="cuda")
+    G.apply(x, y)
+    G.restrict(1, dx, dc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all().item() and torch.count_nonzero(y).item() > 0
