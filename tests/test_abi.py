@@ -125,3 +125,43 @@ def test_binding_refuses_short_buffers(lib):
     mgdarcy._need(None, 5, "r")
     with pytest.raises(ValueError, match="x has 4 entries"):
         mgdarcy._need(np.ones(4), 5, "x")
+
+
+C_CALLER = r"""
+#include "mgdarcy.h"
+#include <stdio.h>
+#include <string.h>
+int main(void) {
+  mg_problem p;
+  mg_handle* h = 0;
+  memset(&p, 0, sizeof p);
+  p.dim = 4;
+  mg_status s = mg_setup(&p, 0, &h);
+  printf("%d|%s|%s\n", (int)s, mg_status_string(s), mg_last_error());
+  mg_destroy(0);
+  mg_destroy_batch(0);
+  return (s == MG_ERR_INVALID_ARG && h == 0) ? 0 : 1;
+}
+"""
+
+
+def test_plain_c_caller(lib, tmp_path):
+    """The boundary is a C interface: the header compiles as strict C99 and a
+    C program links against the library and gets an argument error back as a
+    status, with no C++ runtime of its own and no GPU."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.dirname(HEADER)
+    libdir = os.path.dirname(mgdarcy.LIB_PATH)
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src),
+                    "-L", libdir, "-lmgdarcy", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    status, text, msg = out.stdout.strip().split("|")
+    assert int(status) == 1 and text == "invalid argument" and "dim" in msg
