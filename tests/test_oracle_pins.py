@@ -60,6 +60,21 @@ def test_lagrange_partition_of_unity(nodes):
         assert np.allclose(basis.lagrange_deriv(nodes, a, x), fd, atol=1e-7)
 
 
+# --- dof layout ----------------------------------------------------------------
+
+@pytest.mark.parametrize("d,n,k,n_u,n_p", [
+    (2, 16, 0, 544, 256), (2, 64, 1, 33024, 16384), (2, 128, 0, 33024, 16384), (2, 128, 1, 131584, 65536),
+    (2, 256, 1, 525312, 262144), (2, 512, 1, 2099200, 1048576), (2, 256, 2, 1181184, 589824),
+    (3, 64, 0, 798720, 262144), (3, 128, 0, 6340608, 2097152)])
+def test_dof_counts_by_hand(d, n, k, n_u, n_p):
+    """RT_k x Q_k on n^d cells (Sec. 2.3) with the nodal basis: u_i has
+    n(k+1)+1 nodes along x_i and n(k+1) across, p has n(k+1) per direction, so
+    N_u = d (n(k+1)+1) (n(k+1))^(d-1) and N_p = (n(k+1))^d; the counts of the
+    workload meshes, multiplied out by hand."""
+    S = fem.Space(d, n, k)
+    assert (S.n_u, S.n_p, S.ndof) == (n_u, n_p, n_u + n_p)
+
+
 # --- operator: closed forms, exactness, symmetry ---------------------------
 
 def _golden_energy_vectors(S, name):
