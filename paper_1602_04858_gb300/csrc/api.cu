@@ -169,7 +169,7 @@ bool is_device_ptr(const void* p) {
 }
 
 void level_geometry(HostLevel& L, int d, int k, int n, double mu) {
-  std::memset(&L, 0, sizeof(L));
+  L = HostLevel{};
   L.wait_ns = DEFAULT_WAIT_NS;
   L.rhs_group = 4;
   L.cta_tpr = 4;

@@ -882,14 +882,14 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
       return false;
     }
     const unsigned char* sbase = wbase + (size_t)sb * P::STAGE_S;
-    const float* sc = reinterpret_cast<const float*>(sbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
+    [[maybe_unused]] const float* sc = reinterpret_cast<const float*>(sbase + (size_t)GPW * P::S_BYTES) + (size_t)g * NVP;
     if (actc) {
 #pragma unroll
       for (int it = 0; it < P::NROWIT; ++it) {
         const int l = lp + it * LW;
         if (l < NV) {
           const uint32_t rp = rps[it];
-          T srow = T(1);
+          [[maybe_unused]] T srow = T(1);
           if constexpr (P::BF) {
             srow = (T)sc[l];
             pb[P::OFF_SC + l] = srow;
@@ -915,7 +915,7 @@ __global__ void __launch_bounds__(128) k_colour_pass(const Lvl<D, K, T> L0, cons
         const TS* Sg = reinterpret_cast<const TS*>(sbase + (size_t)g * P::S_BYTES) + q * RG;
         // with one right-hand side, columns jj feed NA independent partial
         // sums (jj mod NA), added at the end (shorter dependent FMA chains)
-        constexpr int NA = NR == 1 ? 2 : 1;
+        [[maybe_unused]] constexpr int NA = NR == 1 ? 2 : 1;
         if constexpr (P::F2) {
           float2 acc[NA][RG / 2][NR];
 #pragma unroll

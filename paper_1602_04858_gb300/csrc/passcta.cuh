@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(PassShapeC<D, K, T, TS, NR, TPR>::NT)
                       const unsigned char* __restrict__ tabs, T* x, const T* __restrict__ b, int evict_first,
                       int* __restrict__ err, uint64_t wait_ns, int64_t vs, const ProbStride ps, T* __restrict__ sum, T omega) {
   using C = PassShapeC<D, K, T, TS, NR, TPR>;
-  constexpr int NT = C::NT, NV = C::NV, WIN = C::WIN, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
+  constexpr int NT = C::NT, NV = C::NV, RG = C::RG, NVP = C::NVP, SPL = C::SPL;
   constexpr int ZW = C::ZW, ZMW = C::ZMW, PB = plain_bytes<T>(), EPT = C::EPT;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* const sm = smem;   // C::SMEM bytes
