@@ -84,3 +84,29 @@ def test_traffic_figures_are_the_committed_captures():
             m = re.search(r"DRAM traffic: ([0-9.]+) MB per launch", f.read())
         assert m, files[wl]
         assert abs(t / 1e6 - float(m.group(1))) < 0.006
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """bench.py --impl reference: one JSON line with the keys of the benchmark
+    contract, the reference arm's own cpu_baseline and e2e objects, and the
+    metric, unit and direction of the GPU arm (here on the 16^2 workload so
+    that the oracle finishes at once; the real run uses the 256^2 one)."""
+    import json
+    import types
+    monkeypatch.setattr(bench, "WORKLOAD", "small_2d")
+    bench.reference_arm(types.SimpleNamespace(gpus=1, steps=2, warmup=1), 0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+    # other ranks print nothing
+    bench.reference_arm(types.SimpleNamespace(gpus=2, steps=1, warmup=0), 1)
+    assert capsys.readouterr().out.strip() == ""
