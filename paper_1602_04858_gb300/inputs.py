@@ -102,7 +102,8 @@ def inclusions_mask(n: int, seed: int, fraction: float = 0.15) -> np.ndarray:
 def foam_mask(n: int, seed: int, level: float = 1.2) -> np.ndarray:
     """Foam-like phase: the islands where a Gaussian random field (sigma = 1,
     correlation length n/40 cells) exceeds `level`; mostly disconnected blobs
-    of irregular shape covering about 12 % of the cells.  2-D bool (y, x)."""
+    of irregular shape covering about 12 % of the cells (8-14 % over seeds).
+    2-D bool (y, x)."""
     return grf(n, 2, 1.0, max(1.0, n / 40.0), seed) > level
 
 
