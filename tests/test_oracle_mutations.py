@@ -232,6 +232,27 @@ def test_post_smoothing_dropped(monkeypatch):
     must_fail(pins.test_vcycle_is_symmetric, 2, 1, 3, False)
 
 
+def test_boundary_patches_keep_pressure_only_corners(monkeypatch):
+    """Boundary-vertex patches (Sec. 3.3) without the rule that drops a patch
+    holding no velocity dof (an RT_0 corner: one pressure, zero under the
+    mean-zero constraint)."""
+    plant(monkeypatch, mg, "boundary_patches_of",
+          "        if not np.any(dofs < S.n_u):\n            continue\n", "")
+    must_fail(pins.test_boundary_patch_sizes_by_hand, 2, 0, 4, {3: 12})
+
+
+def test_boundary_patch_vertex_off_by_one(monkeypatch):
+    """The vertex of a boundary dof's patch one cell off along every direction."""
+    plant(monkeypatch, mg, "boundary_patches_of", "v = hi[cand, e] + choice[e]", "v = hi[cand, e] + choice[e] + 1")
+    must_fail(pins.test_boundary_patch_sizes_by_hand, 2, 1, 4, {8: 4, 18: 12})
+
+
+def test_additive_damping_ignored(monkeypatch):
+    """The additive variant (not the paper's smoother) without its damping omega."""
+    plant(monkeypatch, mg, "additive_step", "return x + omega * d", "return x + d")
+    must_fail(pins.test_additive_step_is_sum_of_ritz_corrections, 2, 1)
+
+
 def test_forward_sweep_only(monkeypatch):
     """The smoothing step without its backward sweep (colours 0..C-1 only):
     the V-cycle is no longer symmetric."""
