@@ -137,8 +137,8 @@ __host__ __device__ __forceinline__ int64_t cell_linear(const Lvl<D, K, T>& L, c
 
 // Visits every (column, coefficient) of the row of velocity dof (i, idx)
 // (free row).  vis(comp, idx, coef) may be called more than once per column.
-// the row visitors (this one and the two below) also run on the host, with
-// host-only callables
+// The row visitors (this one and the two below) also run on the host, with
+// host-only callables.
 #pragma nv_exec_check_disable
 template <int D, int K, typename T, class Vis>
 __host__ __device__ __forceinline__ void visit_u_row(const Lvl<D, K, T>& L, const Tab<K, T>& tb, int i,

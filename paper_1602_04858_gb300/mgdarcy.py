@@ -316,24 +316,32 @@ class Multigrid:
         _check(load().mg_set_wait_limit(self.h, float(seconds)))
 
     def smooth(self, level, x, b, steps=1):
+        self._vec(level, ("x", x), ("b", b))
         _check(load().mg_smooth(self.h, level, _ptr(x), _ptr(b), steps))
 
     def level_load(self, level, x, b):
+        self._vec(level, ("x", x), ("b", b))
         _check(load().mg_level_load(self.h, level, _ptr(x), _ptr(b)))
 
     def level_store(self, level, x):
+        self._vec(level, ("x", x))
         _check(load().mg_level_store(self.h, level, _ptr(x)))
 
     def colour_pass(self, level, colour):
         _check(load().mg_colour_pass(self.h, level, colour))
 
     def restrict(self, level, r_fine, b_coarse):
+        self._vec(level, ("r_fine", r_fine))
+        self._vec(level - 1, ("b_coarse", b_coarse))
         _check(load().mg_restrict(self.h, level, _ptr(r_fine), _ptr(b_coarse)))
 
     def prolong_add(self, level, x_coarse, x_fine):
+        self._vec(level - 1, ("x_coarse", x_coarse))
+        self._vec(level, ("x_fine", x_fine))
         _check(load().mg_prolong_add(self.h, level, _ptr(x_coarse), _ptr(x_fine)))
 
     def coarse_solve(self, b, x):
+        self._vec(0, ("b", b), ("x", x))
         _check(load().mg_coarse_solve(self.h, _ptr(b), _ptr(x)))
 
     def patch_info(self, level, colour):
@@ -392,6 +400,10 @@ class Multigrid:
 
     def load_vector(self, f, g, b, level=-1):
         """b = load vector of cellwise-constant f (dim x cells) and g (cells or None); device tensors."""
+        cells = (int(self.n_coarse) << (level if level >= 0 else self.n_levels - 1)) ** int(self.dim)
+        _need(f, self.dim * cells, "f")
+        _need(g, cells, "g")
+        self._vec(level, ("b", b))
         _check(load().mg_load_vector(self.h, level, _ptr(f), _ptr(g), _ptr(b)))
 
     def launches(self):

@@ -165,3 +165,41 @@ def test_plain_c_caller(lib, tmp_path):
     assert out.returncode == 0, out.stdout + out.stderr
     status, text, msg = out.stdout.strip().split("|")
     assert int(status) == 1 and text == "invalid argument" and "dim" in msg
+
+
+def test_binding_checks_every_buffer_length(lib):
+    """Every call of the binding that passes vectors checks their lengths
+    against the level sizes before calling the library: a buffer one entry
+    short raises ValueError, and the right lengths reach the C function (which
+    here refuses the null handle with its own status).  Host only: the handle
+    is a stand-in with the sizes of a 2x2 -> 8x8 RT_0 hierarchy."""
+    G = object.__new__(mgdarcy.Multigrid)
+    G.h = None
+    G.dim, G.degree, G.n_levels, G.n_coarse, G.nrhs = 2, 0, 3, 2, 1
+    G._nd = {0: (12, 4), 1: (40, 16), 2: (144, 64), -1: (144, 64)}
+    ok = {j: np.zeros(sum(v)) for j, v in G._nd.items()}
+    short = {j: np.zeros(sum(v) - 1) for j, v in G._nd.items()}
+    f_ok, f_short = np.zeros(2 * 64), np.zeros(2 * 64 - 1)
+    calls = {
+        "apply": (lambda v: G.apply(v[-1], ok[-1])),
+        "vcycle": (lambda v: G.vcycle(ok[-1], v[-1])),
+        "solve": (lambda v: G.solve(np.zeros(144), np.zeros(64), v[-1])),
+        "smooth": (lambda v: G.smooth(1, v[1], ok[1])),
+        "level_load": (lambda v: G.level_load(1, ok[1], v[1])),
+        "level_store": (lambda v: G.level_store(2, v[2])),
+        "restrict": (lambda v: G.restrict(2, ok[2], v[1])),
+        "prolong_add": (lambda v: G.prolong_add(2, v[1], ok[2])),
+        "coarse_solve": (lambda v: G.coarse_solve(v[0], ok[0])),
+        "residual_norm": (lambda v: G.residual_norm(ok[-1], v[-1])),
+        "load_vector": (lambda v: G.load_vector(f_ok, None, v[-1])),
+    }
+    for name, call in calls.items():
+        with pytest.raises(ValueError):
+            call(short)
+        with pytest.raises(mgdarcy.MGError) as e:    # the lengths pass; the library refuses the null handle
+            call(ok)
+        assert e.value.status == 1, name
+    with pytest.raises(ValueError):
+        G.load_vector(f_short, None, ok[-1])
+    with pytest.raises(ValueError):
+        G.solve(np.zeros(143), np.zeros(64), ok[-1])
