@@ -1,9 +1,11 @@
 """Failure detection through the C interface, in forms that fault, trap or hang
 no GPU: device-side waits made to run out by a zero wait limit (the kernels
 record the timeout, let their own copies land and return early), GMRES
-stopped at maxit, a device allocation refused by the library's
-failure-injection hook, and a zero right-hand side.  After each failure the
-handle (or a new one) must work normally again.
+stopped at maxit, device allocations refused by the library's
+failure-injection hook (in set-up, in a solve's workspace and in its
+enlargement), host pointers and aliased buffers refused before any kernel
+runs, and a zero right-hand side.  After each failure the handle (or a new
+one) must work normally again.
 """
 import numpy as np
 import pytest
