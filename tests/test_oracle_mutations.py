@@ -121,6 +121,21 @@ def test_nitsche_boundary_data_sign(monkeypatch):
     must_fail(pins.test_polynomial_reproduction, 2, 1, 4, 1.0)
 
 
+def test_normal_velocity_constrained_on_one_side_only(monkeypatch):
+    """The strongly imposed normal velocity (reading of eq. BCh) set on the
+    x_i = 0 faces only, the x_i = 1 faces left free."""
+    monkeypatch.setattr(fem.Space, "constrained", mutant(
+        fem.Space, "constrained", ("on = (idx[:, i] == 0) | (idx[:, i] == self.N)", "on = idx[:, i] == 0")))
+    must_fail(pins.test_literal_channel_rhs_closed_form, 1)
+
+
+def test_evaluated_divergence_missing_the_mesh_size(monkeypatch):
+    """Point evaluation of div u without the 1/h of the reference derivative."""
+    plant(monkeypatch, fem, "evaluate", "div[q] += coef[a] * grads[a, 0, kd] / h",
+          "div[q] += coef[a] * grads[a, 0, kd]")
+    must_fail(pins.test_load_vector_divergence_source, 2, 1, 3)
+
+
 def test_pressure_weights_missing_cell_measure(monkeypatch):
     """w_i = (1, q_i) without the h^d of the cell: the pressure rows built from
     them no longer integrate the source."""
