@@ -285,6 +285,14 @@ def test_forward_sweep_only(monkeypatch):
     must_fail(pins.test_vcycle_is_symmetric, 2, 1, 3, False)
 
 
+def test_coarse_solve_bordered_with_ones(monkeypatch):
+    """The coarsest solve (B_0 = A_0^{-1} on the mean-zero space, Sec. 3.2)
+    bordered with ones over every free dof instead of the pressure weights."""
+    monkeypatch.setattr(mg.Hierarchy, "__init__", mutant(
+        mg.Hierarchy, "__init__", ("Bm[:nf, nf] = wf", "Bm[:nf, nf] = 1.0"), ("Bm[nf, :nf] = wf", "Bm[nf, :nf] = 1.0")))
+    must_fail(pins.test_two_grid_against_dense_ritz_construction, 2, 1)
+
+
 def test_residual_not_updated_before_restriction(monkeypatch):
     """The coarse level given the restricted right-hand side b instead of the
     residual b - A x after pre-smoothing (the garbled coarse-correction line
