@@ -23,13 +23,17 @@
  * preconditioner.
  *
  * Memory: pointers documented "host or device" may point to either (the
- * library asks the CUDA runtime which); device pointers must be on the
- * device that was current at mg_setup.  The caller owns every buffer it
- * passes; the handle owns its workspace.  Calls are asynchronous on the
- * stream given to mg_setup unless stated otherwise; calls that return
+ * library asks the CUDA runtime which); pointers documented "device" are
+ * checked the same way and a host pointer is refused with MG_ERR_INVALID_ARG.
+ * Device pointers must be on the device that was current at mg_setup.  Lengths
+ * cannot be checked through bare pointers: every buffer must hold the entries
+ * documented for it (the Python binding checks them).  The caller owns every
+ * buffer it passes; the handle owns its workspace.  Calls are asynchronous on
+ * the stream given to mg_setup unless stated otherwise; calls that return
  * statistics, or that receive host pointers, synchronise that stream.
  * Errors are returned as mg_status (never thrown, never trapped);
- * mg_last_error() gives a message.  A handle is not thread-safe.
+ * mg_last_error() gives the calling thread's last message.  A handle is not
+ * thread-safe.
  */
 #ifndef MGDARCY_H
 #define MGDARCY_H
