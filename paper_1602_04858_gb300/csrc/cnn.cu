@@ -541,6 +541,18 @@ struct mg_cnn {
 
 namespace {
 
+// Whether the CUDA runtime reports p as device (or managed) memory.
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mg_status not_on_device() { return set_last_error(MG_ERR_INVALID_ARG, "device pointers required"); }
+
 mg_status cnn_cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return MG_OK;
   return set_last_error(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
@@ -747,6 +759,7 @@ mg_status mg_cnn_set_normalisation(mg_cnn* N, const float* host12) {
 
 mg_status mg_cnn_forward(mg_cnn* N, const float* in, int batch, float* out) {
   if (!N || !in || !out || batch < 1 || batch > N->max_batch) return set_last_error(MG_ERR_INVALID_ARG, "bad arguments");
+  if (!on_device(in) || !on_device(out)) return not_on_device();
   forward(N, in, batch);
   return cnn_cuda(cudaMemcpyAsync(out, N->outf, (size_t)batch * 3 * N->n * N->n * sizeof(float),
                                   cudaMemcpyDeviceToDevice, N->stream), "forward");
@@ -755,6 +768,7 @@ mg_status mg_cnn_forward(mg_cnn* N, const float* in, int batch, float* out) {
 mg_status mg_cnn_gradients(mg_cnn* N, const float* in, const float* target, int batch, float* loss, float* grads_host) {
   if (!N || !in || !target || batch < 1 || batch > N->max_batch)
     return set_last_error(MG_ERR_INVALID_ARG, "bad arguments");
+  if (!on_device(in) || !on_device(target)) return not_on_device();
   forward(N, in, batch);
   mg_status st = backward(N, in, target, batch, loss);
   if (st != MG_OK || !grads_host) return st;
@@ -764,6 +778,7 @@ mg_status mg_cnn_gradients(mg_cnn* N, const float* in, const float* target, int 
 mg_status mg_cnn_train_step(mg_cnn* N, const float* in, const float* target, int batch, float lr, float* loss) {
   if (!N || !in || !target || batch < 1 || batch > N->max_batch || !(lr > 0.f))
     return set_last_error(MG_ERR_INVALID_ARG, "bad arguments");
+  if (!on_device(in) || !on_device(target)) return not_on_device();
   forward(N, in, batch);
   mg_status st = backward(N, in, target, batch, loss);
   if (st != MG_OK) return st;
@@ -778,6 +793,7 @@ mg_status mg_cnn_train_step(mg_cnn* N, const float* in, const float* target, int
 
 mg_status mg_cnn_features(mg_cnn* N, const double* c, const double* f, float* in) {
   if (!N || !c || !f || !in) return set_last_error(MG_ERR_INVALID_ARG, "null argument");
+  if (!on_device(c) || !on_device(f) || !on_device(in)) return not_on_device();
   const int64_t cells = (int64_t)N->n * N->n;
   k_features<<<cdiv(cells, 256), 256, 0, N->stream>>>(c, f, cells, N->norm, in);
   return cnn_cuda(cudaGetLastError(), "features");
@@ -785,6 +801,7 @@ mg_status mg_cnn_features(mg_cnn* N, const double* c, const double* f, float* in
 
 mg_status mg_cnn_targets(mg_cnn* N, const double* x, float* target) {
   if (!N || !x || !target) return set_last_error(MG_ERR_INVALID_ARG, "null argument");
+  if (!on_device(x) || !on_device(target)) return not_on_device();
   const int64_t cells = (int64_t)N->n * N->n;
   k_dofs_to_fields<<<cdiv(cells, 256), 256, 0, N->stream>>>(x, N->norm, N->n, target);
   return cnn_cuda(cudaGetLastError(), "targets");
@@ -792,6 +809,7 @@ mg_status mg_cnn_targets(mg_cnn* N, const double* x, float* target) {
 
 mg_status mg_cnn_guess(mg_cnn* N, const double* c, const double* f, double* x0) {
   if (!N || !c || !f || !x0) return set_last_error(MG_ERR_INVALID_ARG, "null argument");
+  if (!on_device(c) || !on_device(f) || !on_device(x0)) return not_on_device();
   const int64_t cells = (int64_t)N->n * N->n;
   k_features<<<cdiv(cells, 256), 256, 0, N->stream>>>(c, f, cells, N->norm, N->feat);
   forward(N, N->feat, 1);
